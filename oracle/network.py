@@ -1,0 +1,66 @@
+"""Chemistry network side of the step in FP64: Box-Cox, Z-score, MLP, de-normalisation.
+
+  * Inputs (Sec. 2): (T, p, Y_1..Y_n). Species enter through the Box-Cox transform
+    BC(y) = (y^lambda - 1) / lambda (Box & Cox 1964; the paper is silent on it, lambda is a
+    network parameter, 0.1 here), negative y read as 0. All inputs are then Z-scored
+    (Sec. 3.3.1): x = (v - mean) / std.
+  * Hidden layers: h_l = GELU(h_{l-1} W_l^T + b_l) with the tanh form of Sec. 3.3.2,
+    GELU(x) = 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))); the output layer is linear
+    (the paper names GELU as the activation; a linear read-out is this project's reading).
+  * Outputs are de-normalised changes of the Box-Cox coordinates over dt:
+    du_k = std_k O_k + mean_k, u_k = BC(Y_k) + du_k, Y'_k = max(lambda u_k + 1, 0)^(1/lambda),
+    then Y' is divided by its sum.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def boxcox(y, lam):
+    y = np.maximum(np.asarray(y, dtype=np.float64), 0.0)
+    return (y**lam - 1.0) / lam
+
+
+def boxcox_inverse(u, lam):
+    return np.maximum(lam * np.asarray(u, dtype=np.float64) + 1.0, 0.0) ** (1.0 / lam)
+
+
+def gelu_tanh(x):
+    x = np.asarray(x, dtype=np.float64)
+    return 0.5 * x * (1.0 + np.tanh(np.sqrt(2.0 / np.pi) * (x + 0.044715 * x**3)))
+
+
+def gelu_tanh_grad(x):
+    """d GELU / dx of the tanh form."""
+    x = np.asarray(x, dtype=np.float64)
+    c = np.sqrt(2.0 / np.pi)
+    t = np.tanh(c * (x + 0.044715 * x**3))
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t**2) * c * (1.0 + 3.0 * 0.044715 * x**2)
+
+
+def normalise_inputs(net, T, p, Y):
+    """Network input rows x [N, n+2] from the cell states."""
+    v = np.concatenate([np.asarray(T, dtype=np.float64)[None, :],
+                        np.asarray(p, dtype=np.float64)[None, :],
+                        boxcox(Y, net.lam)], axis=0)
+    return ((v - net.in_mean[:, None]) / net.in_std[:, None]).T
+
+
+def mlp_forward(net, x, return_pre=False):
+    """Plain layer-by-layer forward pass; x [N, K0] -> O [N, n]."""
+    h = np.asarray(x, dtype=np.float64)
+    pre = []
+    L = net.n_layers
+    for l in range(L):
+        z = h @ net.W[l].T + net.b[l][None, :]
+        pre.append(z)
+        h = gelu_tanh(z) if l < L - 1 else z
+    return (h, pre) if return_pre else h
+
+
+def denormalise(net, Y, O):
+    """New mass fractions Y' [n, N] from the old Y [n, N] and network outputs O [N, n]."""
+    du = O.T * net.out_std[:, None] + net.out_mean[:, None]
+    u = boxcox(Y, net.lam) + du
+    Yn = boxcox_inverse(u, net.lam)
+    return Yn / np.sum(Yn, axis=0, keepdims=True)
