@@ -1,0 +1,398 @@
+#!/usr/bin/env python3
+"""Reaction-step throughput (cells/s) of the GB300 library on a seeded synthetic field.
+
+One step = one df_chem_step over the whole field (a0 compaction, a1-a5 EoS and inputs,
+a6-a7 network, a8-a10 de-normalisation, Newton T recovery, write-back). Default workload:
+the 2^20-cell 1D supercritical mixing layer with the 30-species mechanism and the
+32-1600-800-400-30 network, every cell reacting, network in BF16 on tcgen05.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32|fp8]
+                  [--impl ours|reference]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun) every rank advances its own field of
+the same size (weak scaling, no collective on the data path); value = all cells / max time.
+--impl reference times the FP64 CPU oracle (the only reference this method has) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reaction-step cells/s (BF16/FP8 vs FP32) at stated dY/T error vs FP64 oracle"
+UNIT = "cells/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp8"])
+    ap.add_argument("--workload", default="layer1d-30sp-1m")
+    ap.add_argument("--cells", type=int, default=0, help="override the workload's cell count")
+    ap.add_argument("--fp32-steps", type=int, default=3, help="timed steps of the FP32 comparison")
+    ap.add_argument("--cpu-sample", type=int, default=16384, help="cells of the CPU oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v, local):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{local}")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def layer_flops(widths, rows):
+    return [2.0 * widths[l] * widths[l + 1] * rows for l in range(len(widths) - 1)]
+
+
+def eos_fp64_flops(n, iters_per_cell):
+    """Algorithmic FP64 flops per cell of the two EoS kernels (counted from the equations:
+    per composition 2n(n-1) for the three pair forms, ~20n for the species sums; ~140 per
+    evaluation of Z, h, cp at one temperature)."""
+    pre = 2 * n * (n - 1) + 20 * n + 140
+    post = 2 * n * (n - 1) + 27 * n + 140 * iters_per_cell
+    return pre, post
+
+
+def cpu_oracle_leg(mech, net, T, p, Y, sel, T_react, gpu_after=None):
+    """Times the FP64 oracle step on the sampled cells; if the GPU's results for the same
+    cells are given, also states the GPU's error against it."""
+    from oracle import step as ostep
+    t0 = time.perf_counter()
+    To, Yo, so = ostep.chem_step(mech, net, T[sel], p[sel], Y[:, sel], net.dt, T_react=T_react)
+    dt = time.perf_counter() - t0
+    out = {"value": sel.shape[0] / dt, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
+           "kind": "oracle", "sample": f"{sel.shape[0]} evenly strided cells of the field, one "
+           "FP64 numpy step (EoS, MLP, Newton), BLAS threads = numpy default",
+           "seconds": dt}
+    err = None
+    if gpu_after is not None:
+        Tg, Yg = gpu_after
+        err = {"max_abs_dY": float(np.abs(Yg - Yo).max()),
+               "mean_abs_dY": float(np.abs(Yg - Yo).mean()),
+               "max_abs_dT_K": float(np.abs(Tg - To).max()),
+               "mean_abs_dT_K": float(np.abs(Tg - To).mean()),
+               "cells": int(sel.shape[0])}
+    return out, err
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import synth
+    from oracle import step as ostep
+    w = synth.configs.WORKLOADS[args.workload]
+    N = args.cells or w.n_cells
+    mech, net, T, p, Y = synth.configs.build(args.workload, n_cells=N)
+    S = min(4096, N)
+    sel = np.linspace(0, N - 1, S).astype(np.int64)
+    Ts, ps, Ys = T[sel], p[sel], Y[:, sel]
+    for _ in range(args.warmup):
+        ostep.chem_step(mech, net, Ts, ps, Ys, net.dt, T_react=w.T_react)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Ts, Ys, _ = ostep.chem_step(mech, net, Ts, ps, Ys, net.dt, T_react=w.T_react)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    v = S / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "n_cells": N,
+                                            "sample_cells_per_step": S},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle",
+                             "cores": len(os.sched_getaffinity(0)),
+                             "sample": f"{S} evenly strided cells of the field per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2508_18969_gb300 as df
+    import synth
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.configs.WORKLOADS[args.workload]
+    N = args.cells or w.n_cells
+    mech, net, T, p, Y = synth.configs.build(args.workload, n_cells=N, field_seed=w.seed + rank)
+    prec = {"bf16": df.DF_BF16, "fp32": df.DF_FP32, "fp8": df.DF_FP8_E4M3}[args.precision]
+    st = df.State(mech, net, precision=prec, T_react=w.T_react, device=local,
+                  batch_cells=min(N, 1 << 20))
+    Td = torch.tensor(T, device=dev)
+    pd = torch.tensor(p, device=dev)
+    Yd = torch.tensor(Y, device=dev).contiguous()
+    status = torch.empty(N, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # first step from the pristine field: its sampled cells are the ones the CPU oracle
+    # leg recomputes (error statement)
+    st.chem_step(Td, pd, Yd, status=status)
+    rc, n_act, n_flag, iters = st.step_summary()
+    sel = np.linspace(0, N - 1, min(args.cpu_sample, N)).astype(np.int64)
+    gpu_first = (Td.cpu().numpy()[sel], Yd.cpu().numpy()[:, sel])
+
+    for _ in range(args.warmup):
+        st.chem_step(Td, pd, Yd, status=status)
+    torch.cuda.synchronize()
+    st.profile_read()          # drop anything recorded so far
+    st.profile_enable(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            st.chem_step(Td, pd, Yd, status=status)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    st.profile_enable(False)
+    prof = st.profile_read()
+    rc, n_act, n_flag, iters = st.step_summary()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(world, ms, local)
+    value = world * N / (ms_max * 1e-3)
+
+    # end to end: host (pinned) fields in, device step, host fields out, every step
+    e2e = None
+    if not args.no_e2e:
+        Th = torch.tensor(T).pin_memory()
+        ph = torch.tensor(p).pin_memory()
+        Yh = torch.tensor(Y).pin_memory()
+        To = torch.empty_like(Th).pin_memory()
+        Yo = torch.empty_like(Yh).pin_memory()
+        K2 = max(3, args.steps // 2)
+
+        def e2e_step():
+            Td.copy_(Th, non_blocking=True)
+            pd.copy_(ph, non_blocking=True)
+            Yd.copy_(Yh, non_blocking=True)
+            st.chem_step(Td, pd, Yd, status=status)
+            To.copy_(Td, non_blocking=True)
+            Yo.copy_(Yd, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(K2):
+            e2e_step()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(world, a0.elapsed_time(a1) / K2, local)
+        e2e = {"value": world * N / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(8 * N * (2 + mech.n)),
+               "d2h_bytes_per_step": int(8 * N * (1 + mech.n)), "ms_per_step": ems}
+
+    # plain FP32 step (SIMT network) for the ratio the method is judged by
+    fp32 = None
+    if prec != df.DF_FP32 and args.fp32_steps > 0:
+        s32 = df.State(mech, net, precision=df.DF_FP32, T_react=w.T_react, device=local,
+                       batch_cells=min(N, 1 << 20))
+        s32.chem_step(Td, pd, Yd, status=status)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        s32.profile_enable(True)
+        f0.record(stream)
+        for _ in range(args.fp32_steps):
+            s32.chem_step(Td, pd, Yd, status=status)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        p32 = s32.profile_read()
+        fms = max_over_ranks(world, f0.elapsed_time(f1) / args.fp32_steps, local)
+        fp32 = {"value": world * N / (fms * 1e-3), "ms_per_step": fms,
+                "kernels_ms_per_step": {k: v[1] / args.fp32_steps for k, v in p32.items()}}
+        s32.close()
+
+    if rank != 0:
+        return 0
+
+    # roofline of the dominant kernel family (CUDA-event times recorded on the launch stream)
+    pk, pk_src = peaks()
+    rows = n_act  # reacting cells per step (one batch at this size)
+    fl = layer_flops(w.widths, rows)
+    iters_per_cell = iters / max(n_act, 1)
+    pre_f, post_f = eos_fp64_flops(mech.n, iters_per_cell)
+    fams = {k: (v[0], v[1]) for k, v in prof.items()}
+    dom = max(fams, key=lambda k: fams[k][1])
+    launches, tot = fams[dom]
+    avg_s = tot / launches * 1e-3
+    if dom.startswith("layer") and prec != df.DF_FP32:
+        l = int(dom[5:])
+        peak = pk["bf16_tflops_sustained"] * (2.0 if prec == df.DF_FP8_E4M3 else 1.0)
+        ach = fl[l] / avg_s / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "kernel": f"tc_gemm {dom}",
+                "peak_source": f"bf16_tflops_sustained ({pk_src})" + (" x2 nominal fp8/bf16" if prec == df.DF_FP8_E4M3 else "")}
+    elif dom.startswith("layer"):
+        l = int(dom[5:])
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = fl[l] / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": f"sgemm {dom}",
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"}
+    elif dom in ("eos_pre", "eos_post"):
+        per = pre_f if dom == "eos_pre" else post_f
+        peak = 1.25
+        ach = per * rows / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": dom,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300 table), algorithmic FP64 flops"}
+    else:
+        ach = (12.0 * N) / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "kernel": dom,
+                "peak_source": f"hbm_gbs ({pk_src})"}
+
+    cpu = None
+    errs = None
+    if not args.no_cpu_baseline:
+        cpu, errs = cpu_oracle_leg(mech, net, T, p, Y, sel, w.T_react, gpu_first)
+
+    kpl = 3 + 1 + len(w.widths) - 1 + 1   # compaction (3) + eos_pre + layers + eos_post
+    nb = (N + (1 << 20) - 1) // (1 << 20)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"bf16": "bf16+f64", "fp32": "f32+f64", "fp8": "fp8e4m3+f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_cells": N, "n_species": mech.n,
+                   "network": "-".join(str(x) for x in w.widths), "precision": args.precision,
+                   "reacting_cells": int(n_act), "T_react_K": w.T_react,
+                   "l2": "inputs larger than L2 (fields 8*(2+n)*N bytes, activations GBs)"},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": int(kpl * nb * args.steps),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "kernels_ms_per_step": {k: v[1] / args.steps for k, v in fams.items()},
+        "newton_iterations_per_cell": iters_per_cell,
+        "flagged_cells": int(n_flag),
+        "fp32_step": fp32,
+        "speedup_vs_fp32": (value / fp32["value"]) if fp32 else None,
+        "error_vs_fp64_oracle": errs,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,183 @@
+/*
+ * df.h -- C ABI of the GB300 reaction-step library (libdfgb.so).
+ *
+ * The library advances the chemistry of every cell of a real-fluid flame by one time step,
+ * the pointwise data-parallel step of the DeepFlame method (Sec. 2, "Deep learning
+ * approaches": a network maps the thermochemical state (T, p, Y_i) of a cell to its chemical
+ * change; real-fluid properties follow the Peng-Robinson EoS). One step of one cell:
+ *   a0  the cell reacts if T > T_react; reacting cells are listed in ascending index order;
+ *   a1  W_mix = 1 / sum_k Y_k / W_k,  X_k = Y_k W_mix / W_k;
+ *   a2  Peng-Robinson a_m(T), b_m with van der Waals mixing and k_ij;
+ *   a3  compressibility Z: real root of the PR cubic above B of least departure Gibbs energy;
+ *   a4  conserved mass-specific enthalpy h0 = h_ig(T, Y) + h_dep / W_mix;
+ *   a5  network input (T, p, BC(Y_k)) Z-scored (Sec. 3.3.1), BC = Box-Cox;
+ *   a6  hidden layers h = GELU(h W^T + b), tanh-form GELU (Sec. 3.3.2);
+ *   a7  linear output layer;
+ *   a8  Y'_k = inverse Box-Cox of BC(Y_k) + (std_k O_k + mean_k), renormalised;
+ *   a9  T' from h(T', p, Y') = h0 by safeguarded Newton;
+ *   a10 T, Y of reacting cells overwritten with T', Y'.
+ *
+ * Conventions shared by every entry point:
+ *   - Field arrays are DEVICE pointers owned by the caller, FP64, one value per cell:
+ *     T[i], p[i]; mass fractions are species-major, Y[k * ldY + i] (ldY >= n_cells).
+ *   - Work is enqueued on the CUDA stream `stream` (a cudaStream_t, NULL = legacy default
+ *     stream) and returns without synchronising, unless the entry point says otherwise.
+ *   - Every entry point returns a df_status; on error nothing has been enqueued unless
+ *     the code is DF_ERR_CUDA, and df_get_last_error() describes the cause.
+ *   - A df_state is used by one host thread at a time.
+ */
+#ifndef DF_H
+#define DF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct df_state df_state;
+typedef int32_t df_status;
+
+#define DF_OK 0
+#define DF_ERR_INVALID_ARG 1      /* bad pointer, size, stride or option */
+#define DF_ERR_CUDA 2             /* a CUDA call failed; see df_get_last_error */
+#define DF_ERR_NOT_CONVERGED 3    /* reported by df_get_step_summary only */
+#define DF_ERR_NONFINITE_INPUT 4  /* reported by df_get_step_summary only */
+#define DF_ERR_DT_MISMATCH 5      /* dt differs from the network's time step */
+#define DF_ERR_UNSUPPORTED 6      /* valid but not implemented (e.g. 1/lambda not integral) */
+#define DF_ERR_OOM 7              /* device allocation failed */
+#define DF_ERR_TIMEOUT 8          /* a kernel wait hit its limit and the kernel gave up */
+
+/* Per-cell status bits written by df_chem_step (0 = advanced normally). A flagged cell
+ * keeps its old T and Y. */
+#define DF_CELL_NOT_CONVERGED 1   /* Newton on h(T) did not meet the tolerance */
+#define DF_CELL_NO_ROOT 2         /* the PR cubic has no real root above B */
+#define DF_CELL_NONFINITE 4       /* non-finite T, p or Y, p <= 0, or non-finite result */
+
+/* Arithmetic of the network layers (a5-a7). The equation of state, Box-Cox, renormalisation
+ * and Newton steps are FP64 in every mode (Sec. 3.3.1 keeps all non-network work double). */
+typedef enum {
+  DF_FP32 = 0,      /* SIMT FP32 GEMMs, accurate tanh: the plain FP32 step */
+  DF_BF16 = 1,      /* tcgen05 BF16 GEMMs, FP32 accumulation, BF16 activations */
+  DF_FP8_E4M3 = 2   /* tcgen05 FP8 e4m3 GEMMs, per-output-channel weight scales */
+} df_precision;
+
+/* Mechanism constants (host pointers, deep-copied by df_state_create). */
+typedef struct {
+  int32_t n_species;          /* n, 1..32 */
+  const double* W;            /* [n] molar masses, kg/mol */
+  const double* Tc;           /* [n] critical temperatures, K */
+  const double* pc;           /* [n] critical pressures, Pa */
+  const double* omega;        /* [n] acentric factors */
+  const double* kij;          /* [n*n] binary interaction parameters, row-major, symmetric */
+  const double* nasa;         /* [n*7] NASA-7 coefficients a1..a7 per species, row-major */
+} df_mech_desc;
+
+/* Chemistry network (host pointers, deep-copied by df_state_create). */
+typedef struct {
+  int32_t n_layers;           /* linear layers L, 1..8 */
+  const int32_t* widths;      /* [L+1]; widths[0] = n + 2 (T, p, Y), widths[L] = n */
+  const float* const* W;      /* [L] layer l is widths[l+1] x widths[l], row-major (out, in) */
+  const float* const* b;      /* [L] layer l is widths[l+1] */
+  double lambda;              /* Box-Cox exponent; 1/lambda must be an integer in 1..64 */
+  const double* in_mean;      /* [n+2] Z-score of the inputs (T, p, BC(Y_1..n)) */
+  const double* in_std;       /* [n+2] */
+  const double* out_mean;     /* [n] de-normalisation of the outputs */
+  const double* out_std;      /* [n] */
+  double dt;                  /* time step the network advances, s */
+} df_mlp_desc;
+
+typedef struct {
+  int32_t precision;          /* df_precision */
+  double T_react;             /* cells with T > T_react react (K); 0 lets every cell through */
+  double newton_tol;          /* stop when |dT| <= newton_tol * T; <= 0 selects 1e-10 */
+  int32_t newton_max_iter;    /* <= 0 selects 30 */
+  int32_t device;             /* CUDA device ordinal the state lives on */
+  int64_t batch_cells;        /* reacting cells per internal batch; <= 0 selects 2^20 */
+} df_options;
+
+/* Creates a state on opt->device: copies the mechanism and network, derives the per-species
+ * EoS constants and the low-precision weight copies, allocates scratch for one batch.
+ * On success *out is the new state; on error *out is NULL. Thread-safe. */
+df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
+                          const df_options* opt, df_state** out);
+
+/* Frees the state and its device memory (synchronises the device first). NULL is a no-op. */
+void df_state_destroy(df_state* s);
+
+/* Real-fluid properties (a1-a4 without the network): rho [kg/m^3], h [J/kg], cp [J/(kg K)]
+ * and Z of every cell. Any output pointer may be NULL and is then not written. */
+df_status df_real_fluid_props(df_state* s, int64_t n_cells, const double* T, const double* p,
+                              const double* Y, int64_t ldY, double* rho, double* h, double* cp,
+                              double* Z, void* stream);
+
+/* One reaction step (a0-a10) of n_cells cells, in place on T and Y; p is read only.
+ * dt must equal the network's dt to 1e-12 relative, else DF_ERR_DT_MISMATCH.
+ * cell_status (device, [n_cells], may be NULL) receives the DF_CELL_* bits (0 for cells that
+ * do not react). n_active_out (device, may be NULL) receives the number of reacting cells.
+ * Asynchronous: problems inside kernels are reported by df_get_step_summary. */
+df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const double* p,
+                       double* Y, int64_t ldY, int32_t* cell_status, int64_t* n_active_out,
+                       void* stream);
+
+/* Statistics of the last df_chem_step on a state. */
+typedef struct {
+  int64_t n_active;           /* reacting cells */
+  int64_t n_flagged;          /* reacting cells that received a DF_CELL_* flag */
+  int64_t newton_iterations;  /* T-from-h Newton iterations summed over reacting cells */
+} df_step_stats;
+
+/* Synchronises `stream`, fills *stats (may be NULL) for the last df_chem_step, and returns
+ * DF_OK, DF_ERR_NOT_CONVERGED if any reacting cell was flagged, or DF_ERR_TIMEOUT if a
+ * kernel wait gave up since the previous call. */
+df_status df_get_step_summary(df_state* s, void* stream, df_step_stats* stats);
+
+/* ---- stage entry points: the steps of df_chem_step one at a time (same kernels) ---- */
+
+/* a0: idx (device, [n_cells] int32) receives the ascending indices of cells with
+ * T > T_react, count (device, one int64) their number. */
+df_status df_active_compact(df_state* s, int64_t n_cells, const double* T, int32_t* idx,
+                            int64_t* count, void* stream);
+
+/* a1-a5 for n_cells cells: h0 (device [n_cells], may be NULL) the conserved enthalpy,
+ * Z (device, may be NULL), x (device [n_cells * (n+2)] row-major FP32, may be NULL) the
+ * normalised network input, status (device int32, may be NULL). */
+df_status df_eos_pre(df_state* s, int64_t n_cells, const double* T, const double* p,
+                     const double* Y, int64_t ldY, double* h0, double* Z, float* x,
+                     int32_t* status, void* stream);
+
+/* a6-a7: network output O (device [n_rows * n] row-major FP32) from input x (device
+ * [n_rows * (n+2)] row-major FP32), computed in the state's precision. */
+df_status df_mlp_forward(df_state* s, int64_t n_rows, const float* x, float* O, void* stream);
+
+/* a8-a10 given the network output O [n_cells * n] and h0 [n_cells]: writes Y' into Y and
+ * T' into T (device, in place), status (device int32, may be NULL). */
+df_status df_eos_post(df_state* s, int64_t n_cells, const float* O, const double* h0,
+                      double* T, const double* p, double* Y, int64_t ldY, int32_t* status,
+                      void* stream);
+
+/* ---- kernel timing ---- */
+
+/* When enabled, df_chem_step records a pair of CUDA events on its stream around each of its
+ * kernel launches, grouped into families ("compact", "eos_pre", "layer0".."layer7",
+ * "eos_post"). Costs two event records per launch; off by default. */
+df_status df_profile_enable(df_state* s, int32_t enable);
+
+/* Synchronises the device and reports, for up to max_entries families in first-launch order,
+ * names (max_entries x 32 chars, NUL-terminated), launches and total device time in ms
+ * since the last read or enable; then resets the counters. *n_entries receives the count. */
+df_status df_profile_read(df_state* s, int32_t max_entries, char* names, int64_t* launches,
+                          double* total_ms, int32_t* n_entries);
+
+/* Description of the most recent error on this state (or of the last failed create when
+ * s is NULL). Valid until the next call on the same state. */
+const char* df_get_last_error(df_state* s);
+
+/* Library version string. */
+const char* df_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DF_H */

@@ -64,3 +64,26 @@ def denormalise(net, Y, O):
     u = boxcox(Y, net.lam) + du
     Yn = boxcox_inverse(u, net.lam)
     return Yn / np.sum(Yn, axis=0, keepdims=True)
+
+
+def round_to_bf16(a):
+    """Round to the nearest bfloat16 (ties to even), via binary32: the value a kernel gets
+    when it converts an FP32 number to BF16. Returned as float64."""
+    f = np.asarray(a, dtype=np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    r = ((u + np.uint64(0x7FFF) + lsb) & np.uint64(0xFFFF0000)).astype(np.uint32)
+    out = r.view(np.float32).astype(np.float64)
+    return np.where(np.isnan(f), np.nan, out)
+
+
+def mlp_forward_rounded(net, x, rnd):
+    """MLP forward with the input, the weights and every hidden activation passed through
+    the rounding function rnd (e.g. round_to_bf16); sums and GELU stay FP64. This is the
+    network as a reduced-precision path stores it, for checking such a path element-wise."""
+    h = rnd(np.asarray(x, dtype=np.float64))
+    L = net.n_layers
+    for l in range(L):
+        z = h @ rnd(net.W[l]).T + net.b[l][None, :]
+        h = rnd(gelu_tanh(z)) if l < L - 1 else z
+    return h

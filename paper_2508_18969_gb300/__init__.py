@@ -1,0 +1,10 @@
+"""GB300-native reaction step of the DeepFlame method (arxiv 2508.18969).
+
+The per-cell chemistry step -- real-fluid Peng-Robinson state, Box-Cox/Z-score inputs,
+chemistry MLP on tcgen05 tensor cores, Newton recovery of T from conserved enthalpy --
+runs in hand-written sm_103a CUDA kernels behind the C ABI of include/df.h (libdfgb.so).
+This package is the thin Python binding of that ABI.
+"""
+from ._lib import (DF_BF16, DF_FP8_E4M3, DF_FP32, DF_CELL_NO_ROOT, DF_CELL_NONFINITE,  # noqa: F401
+                   DF_CELL_NOT_CONVERGED, LIB_PATH)
+from .api import DFError, State, version  # noqa: F401

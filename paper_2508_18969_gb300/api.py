@@ -1,0 +1,164 @@
+"""Python binding of the reaction-step library: same names as the C ABI, torch tensors in.
+
+Every call marshals pointers and sizes and calls libdfgb.so; no arithmetic of the step
+happens here. Tensors must live on the state's CUDA device; fields are float64, the mass
+fractions species-major [n, N] (row stride = ldY).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+class DFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{L.STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class State:
+    """Owns a df_state: mechanism constants, network weights and scratch on one GPU.
+
+    mech: object with n, W, Tc, pc, omega, kij [n, n], nasa [n, 7] (numpy float64);
+    net: object with widths, W (list of [out, in]), b, lam, in_mean, in_std, out_mean,
+    out_std, dt.
+    """
+
+    def __init__(self, mech, net, precision: int = L.DF_FP32, T_react: float = 600.0,
+                 newton_tol: float = 0.0, newton_max_iter: int = 0, device: int = 0,
+                 batch_cells: int = 0):
+        self._lib = L.load()
+        self._keep = []
+        d = lambda a: self._arr(np.ascontiguousarray(a, dtype=np.float64), C.c_double)
+        md = L.MechDesc(int(mech.n), d(mech.W), d(mech.Tc), d(mech.pc), d(mech.omega),
+                        d(np.asarray(mech.kij).reshape(-1)), d(np.asarray(mech.nasa).reshape(-1)))
+        nl = len(net.W)
+        widths = (C.c_int32 * (nl + 1))(*[int(w) for w in net.widths])
+        Wp = (C.POINTER(C.c_float) * nl)()
+        bp = (C.POINTER(C.c_float) * nl)()
+        for l in range(nl):
+            Wp[l] = self._arr(np.ascontiguousarray(net.W[l], dtype=np.float32).reshape(-1), C.c_float)
+            bp[l] = self._arr(np.ascontiguousarray(net.b[l], dtype=np.float32), C.c_float)
+        self._keep += [widths, Wp, bp]
+        nd = L.MlpDesc(nl, widths, Wp, bp, float(net.lam), d(net.in_mean), d(net.in_std),
+                       d(net.out_mean), d(net.out_std), float(net.dt))
+        opt = L.Options(int(precision), float(T_react), float(newton_tol), int(newton_max_iter),
+                        int(device), int(batch_cells))
+        h = C.c_void_p()
+        rc = self._lib.df_state_create(C.byref(md), C.byref(nd), C.byref(opt), C.byref(h))
+        self._keep = []
+        if rc != L.DF_OK:
+            raise DFError(rc, self._lib.df_get_last_error(None).decode())
+        self.h = h
+        self.n = int(mech.n)
+        self.K0 = self.n + 2
+        self.dt = float(net.dt)
+        self.device = torch.device("cuda", device)
+
+    def _arr(self, a, ctype):
+        self._keep.append(a)
+        return a.ctypes.data_as(C.POINTER(ctype))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.df_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != L.DF_OK:
+            raise DFError(rc, self._lib.df_get_last_error(self.h).decode())
+
+    # ---- full step ----
+    def chem_step(self, T, p, Y, dt=None, status=None, n_active=None, stream=None):
+        N = T.shape[0]
+        self._check(self._lib.df_chem_step(self.h, N, self.dt if dt is None else float(dt),
+                                           _ptr(T), _ptr(p), _ptr(Y), Y.stride(0), _ptr(status),
+                                           _ptr(n_active), _stream(stream)))
+
+    def step_summary(self, stream=None):
+        """(status code, reacting cells, flagged cells, Newton iterations) of the last step."""
+        s = L.StepStats()
+        rc = self._lib.df_get_step_summary(self.h, _stream(stream), C.byref(s))
+        return rc, s.n_active, s.n_flagged, s.newton_iterations
+
+    def real_fluid_props(self, T, p, Y, stream=None):
+        N = T.shape[0]
+        out = [torch.empty(N, dtype=torch.float64, device=T.device) for _ in range(4)]
+        self._check(self._lib.df_real_fluid_props(self.h, N, _ptr(T), _ptr(p), _ptr(Y), Y.stride(0),
+                                                  *[_ptr(o) for o in out], _stream(stream)))
+        return tuple(out)
+
+    # ---- kernel timing ----
+    def profile_enable(self, on: bool = True):
+        self._check(self._lib.df_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        """{family: (launches, total_ms)} since the last read; synchronises the device."""
+        cap = 32
+        names = C.create_string_buffer(32 * cap)
+        la = (C.c_int64 * cap)()
+        ms = (C.c_double * cap)()
+        n = C.c_int32()
+        self._check(self._lib.df_profile_read(self.h, cap, names, la, ms, C.byref(n)))
+        raw = names.raw
+        out = {}
+        for i in range(n.value):
+            nm = raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+            out[nm] = (int(la[i]), float(ms[i]))
+        return out
+
+    # ---- stages ----
+    def active_compact(self, T, stream=None):
+        N = T.shape[0]
+        idx = torch.empty(max(N, 1), dtype=torch.int32, device=T.device)
+        cnt = torch.zeros(1, dtype=torch.int64, device=T.device)
+        self._check(self._lib.df_active_compact(self.h, N, _ptr(T), _ptr(idx), _ptr(cnt),
+                                                _stream(stream)))
+        return idx, cnt
+
+    def eos_pre(self, T, p, Y, stream=None):
+        N = T.shape[0]
+        h0 = torch.empty(N, dtype=torch.float64, device=T.device)
+        Z = torch.empty(N, dtype=torch.float64, device=T.device)
+        x = torch.empty(N, self.K0, dtype=torch.float32, device=T.device)
+        st = torch.empty(N, dtype=torch.int32, device=T.device)
+        self._check(self._lib.df_eos_pre(self.h, N, _ptr(T), _ptr(p), _ptr(Y), Y.stride(0),
+                                         _ptr(h0), _ptr(Z), _ptr(x), _ptr(st), _stream(stream)))
+        return h0, Z, x, st
+
+    def mlp_forward(self, x, stream=None):
+        x = x.contiguous()
+        O = torch.empty(x.shape[0], self.n, dtype=torch.float32, device=x.device)
+        self._check(self._lib.df_mlp_forward(self.h, x.shape[0], _ptr(x), _ptr(O), _stream(stream)))
+        return O
+
+    def eos_post(self, O, h0, T, p, Y, stream=None):
+        N = T.shape[0]
+        st = torch.empty(N, dtype=torch.int32, device=T.device)
+        self._check(self._lib.df_eos_post(self.h, N, _ptr(O.contiguous()), _ptr(h0), _ptr(T),
+                                          _ptr(p), _ptr(Y), Y.stride(0), _ptr(st), _stream(stream)))
+        return st
+
+
+def version() -> str:
+    return L.load().df_version().decode()

@@ -1,0 +1,115 @@
+// a0: stable compaction of the reacting cells (T > T_react) into an ascending index list.
+// Three launches, no inter-block waiting: per-chunk counts (warp ballot + popc), one-block
+// exclusive scan of the chunk counts, then a scatter that ranks each reacting cell inside
+// its chunk with ballot/popc prefix sums. Cells are visited in the same order by the
+// count and the scatter pass, so the list is in ascending cell order.
+#include "dfgb_internal.cuh"
+
+namespace dfgb {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;                         // cells per thread per chunk
+constexpr int kChunk = kThreads * kItems;          // 4096 cells per block
+constexpr int kWarps = kThreads / 32;
+constexpr int kCellNonfinite = 4;
+
+__device__ __forceinline__ bool reacts(double t, double thr) { return t > thr; }
+
+__global__ void __launch_bounds__(kThreads) count_kernel(int64_t n, double thr,
+    const double* __restrict__ T, int32_t* __restrict__ status, int64_t* __restrict__ counts) {
+  __shared__ int warp_tot[kWarps];
+  const int64_t base = (int64_t)blockIdx.x * kChunk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int mine = 0;
+#pragma unroll 4
+  for (int j = 0; j < kItems; ++j) {
+    const int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
+    bool a = false;
+    if (i < n) {
+      const double t = T[i];
+      a = reacts(t, thr);
+      if (status) status[i] = isfinite(t) ? 0 : kCellNonfinite;
+    }
+    mine += __popc(__ballot_sync(0xffffffffu, a)) * (lane == 0);
+  }
+  if (lane == 0) warp_tot[warp] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t s = 0;
+    for (int w = 0; w < kWarps; ++w) s += warp_tot[w];
+    counts[blockIdx.x] = s;
+  }
+}
+
+// Exclusive scan of nb chunk counts by one block; offsets[b] and the total into *count.
+__global__ void __launch_bounds__(1024) scan_kernel(int64_t nb, const int64_t* __restrict__ counts,
+                                                    int64_t* __restrict__ offsets,
+                                                    int64_t* __restrict__ count) {
+  __shared__ int64_t part[1024];
+  const int t = threadIdx.x;
+  const int64_t per = (nb + 1023) / 1024;
+  const int64_t b0 = t * per, b1 = (b0 + per < nb) ? b0 + per : nb;
+  int64_t s = 0;
+  for (int64_t b = b0; b < b1; ++b) s += counts[b];
+  part[t] = s;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {  // Hillis-Steele inclusive scan of the 1024 partials
+    int64_t v = (t >= d) ? part[t - d] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int64_t run = (t > 0) ? part[t - 1] : 0;
+  for (int64_t b = b0; b < b1; ++b) {
+    offsets[b] = run;
+    run += counts[b];
+  }
+  if (t == 1023) *count = part[1023];
+}
+
+__global__ void __launch_bounds__(kThreads) scatter_kernel(int64_t n, double thr,
+    const double* __restrict__ T, const int64_t* __restrict__ offsets, int32_t* __restrict__ idx) {
+  __shared__ int warp_tot[kWarps];
+  const int64_t base = (int64_t)blockIdx.x * kChunk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t run = offsets[blockIdx.x];
+  for (int j = 0; j < kItems; ++j) {
+    const int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
+    const bool a = (i < n) && reacts(T[i], thr);
+    const unsigned m = __ballot_sync(0xffffffffu, a);
+    if (lane == 0) warp_tot[warp] = __popc(m);
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const int c = warp_tot[w];
+      before += (w < warp) ? c : 0;
+      total += c;
+    }
+    if (a) idx[run + before + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
+    run += total;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int64_t compact_scratch_words(int64_t n) {
+  const int64_t nb = (n + kChunk - 1) / kChunk;
+  return 2 * (nb > 0 ? nb : 1);
+}
+
+cudaError_t launch_compact(int64_t n, double T_react, const double* T, int32_t* idx,
+                           int64_t* count, int32_t* status, int64_t* scratch, cudaStream_t st) {
+  if (n <= 0) return cudaMemsetAsync(count, 0, sizeof(int64_t), st);
+  const int64_t nb = (n + kChunk - 1) / kChunk;
+  int64_t* counts = scratch;
+  int64_t* offsets = scratch + nb;
+  count_kernel<<<(unsigned)nb, kThreads, 0, st>>>(n, T_react, T, status, counts);
+  scan_kernel<<<1, 1024, 0, st>>>(nb, counts, offsets, count);
+  scatter_kernel<<<(unsigned)nb, kThreads, 0, st>>>(n, T_react, T, offsets, idx);
+  return cudaGetLastError();
+}
+
+}  // namespace dfgb

@@ -1,0 +1,115 @@
+// Internal declarations of libdfgb: device-side parameter blocks and host launchers.
+// Not part of the public ABI (include/df.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda.h>
+#include <stdint.h>
+
+namespace dfgb {
+
+constexpr double kR = 8.31446261815324;   // J/(mol K)
+constexpr int kMaxSpecies = 32;           // register-resident species arrays
+constexpr int kSpcStride = 10;            // doubles per species in EosParams::spc
+
+// Error bits a kernel ORs into the state's device error word.
+constexpr int kErrTimeout = 1;            // a bounded wait gave up
+
+// Which rows of a batch a kernel handles. Row r of the batch is reacting-list position
+// row0 + r, i.e. cell idx[row0 + r] (cell row0 + r when idx is NULL). The number of valid
+// rows is min(nmax, *count - row0) when count is given, else nmax.
+struct RowMap {
+  const int32_t* idx;
+  const int64_t* count;
+  int64_t row0;
+  int64_t nmax;
+};
+
+__host__ __device__ inline int64_t clamp_rows(int64_t c, int64_t row0, int64_t nmax) {
+  int64_t v = c - row0;
+  return v < 0 ? 0 : (v > nmax ? nmax : v);
+}
+
+#ifdef __CUDACC__
+__device__ inline int64_t valid_rows(const RowMap& m) {
+  return m.count ? clamp_rows(*m.count, m.row0, m.nmax) : m.nmax;
+}
+__device__ inline int64_t row_cell(const RowMap& m, int64_t r) {
+  return m.idx ? (int64_t)m.idx[m.row0 + r] : m.row0 + r;
+}
+#endif
+
+// Constants of the equation-of-state steps, in device memory.
+//   spc[k * kSpcStride + j]: j = 0 1/W_k, 1 s_k, 2 r_k, 3 b_k, 4..9 enthalpy coefficients
+//   hc_0..hc_5 with h_k(T) = hc_0 + hc_1 T + hc_2 T^2 + ... + hc_5 T^5 (J/mol), where
+//   sqrt(a_k(T)) = s_k - r_k sqrt(T) (Peng-Robinson alpha function expanded in sqrt(T)).
+//   Kmat[i * n + j] = 1 - k_ij.
+//   norm: in_mean[K0], in_inv_std[K0], out_mean[n], out_std[n].
+struct EosParams {
+  int n;                 // species
+  int K0;                // n + 2 network inputs
+  int inv_lambda;        // Box-Cox 1/lambda (integer)
+  double lambda;
+  double T_react;
+  double newton_tol;
+  int newton_max_iter;
+  const double* spc;
+  const double* Kmat;
+  const double* norm;
+  int* err;              // device error word
+  int64_t* flagged;      // device count of cells flagged by eos_post (may be NULL)
+  int64_t* newton_iters; // device sum of Newton iterations (may be NULL)
+};
+
+enum XKind { kXF32 = 0, kXBF16 = 1, kXFP8 = 2 };
+
+// ---- launchers (eos.cu) ----
+// status (row-indexed, may be NULL) receives the per-row flags.
+cudaError_t launch_eos_pre(const EosParams& P, const RowMap& rows, const double* T,
+                           const double* p, const double* Y, int64_t ldY, double* h0,
+                           double* Z, void* x, int xkind, int64_t ldx, float x_scale,
+                           int32_t* status, cudaStream_t st);
+// pre_status (row-indexed, may be NULL) carries eos_pre's flags; cell_status (cell-indexed,
+// may be NULL) receives the final flags.
+cudaError_t launch_eos_post(const EosParams& P, const RowMap& rows, const float* O, int64_t ldo,
+                            const double* h0, double* T, const double* p, double* Y,
+                            int64_t ldY, const int32_t* pre_status, int32_t* cell_status,
+                            cudaStream_t st);
+cudaError_t launch_props(const EosParams& P, int64_t n, const double* T, const double* p,
+                         const double* Y, int64_t ldY, double* rho, double* h, double* cp,
+                         double* Z, cudaStream_t st);
+
+// ---- launchers (compact.cu) ----
+// Stable list of cells with T > T_react. Needs scratch of compact_scratch_words(n) int64.
+int64_t compact_scratch_words(int64_t n);
+cudaError_t launch_compact(int64_t n, double T_react, const double* T, int32_t* idx,
+                           int64_t* count, int32_t* status, int64_t* scratch, cudaStream_t st);
+
+// ---- launchers (mlp_simt.cu) ----
+// C[r, c] = act(sum_k A[r, k] W[c, k] + bias[c]) for valid rows r < rows(map), c < N.
+// A is [rows x lda] FP32, W is [N x ldw] FP32 with K a multiple of 8 (zero padded).
+cudaError_t launch_sgemm_bias_act(const RowMap& rows, int N, int K, const float* A, int64_t lda,
+                                  const float* W, int64_t ldw, const float* bias, float* C,
+                                  int64_t ldc, bool gelu, int num_sms, cudaStream_t st);
+
+// ---- tcgen05 GEMM (mlp_tc.cu) ----
+struct TcLayer {
+  CUtensorMap tmA;       // activations in, box {64 (K), 128 (M)}
+  CUtensorMap tmB;       // weights [N x K], box {64, BN}
+  int N, K, BN;
+  const float* bias;     // [N]
+  const float* col_scale;// [N] per-output-channel dequant scale (FP8) or NULL
+  void* out;             // [rows x ldo] BF16 / FP8 activations, or FP32 for the last layer
+  int64_t ldo;
+  int out_kind;          // XKind; kXF32 for the last layer
+  bool gelu;
+  float out_scale;       // multiply before quantising the output (FP8 activations)
+  int elem_bytes;        // 2 (BF16) or 1 (FP8)
+};
+bool tc_encode_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
+                  uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,
+                  uint32_t box_outer, char* err, size_t errlen);
+cudaError_t launch_tc_gemm(const TcLayer& L, const RowMap& rows, int num_sms, int* err,
+                           cudaStream_t st);
+
+}  // namespace dfgb

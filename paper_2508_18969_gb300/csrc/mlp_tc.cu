@@ -1,0 +1,481 @@
+// a6-a7 on the 5th-generation tensor cores: one network layer as a persistent GEMM,
+//   out[r, c] = act(scale[c] * sum_k A[r, k] W[c, k] + bias[c]),
+// with A (activations, K-major) and W (weights [N x K], K-major) streamed into shared memory
+// by TMA (128-byte swizzle), multiplied by tcgen05.mma (kind::f16 for BF16, kind::f8f6f4 for
+// FP8 e4m3) into FP32 accumulators in tensor memory, and read back by tcgen05.ld for a fused
+// epilogue (per-channel scale, bias, tanh-GELU of Sec. 3.3.2, quantisation of the next
+// layer's input). The paper's double buffering of batch k against batch k+1 (Sec. 3.3.3)
+// becomes a multi-stage TMA ring and two TMEM accumulators, so the epilogue of one tile
+// overlaps the MMAs of the next.
+//
+// Warp roles (192 threads, one CTA per SM):
+//   warp 0      TMA producer (one lane)
+//   warp 1      TMEM allocator and MMA issuer (one lane)
+//   warps 2..5  epilogue; warp w reads TMEM lanes 32*(w%4) .. 32*(w%4)+31
+// Every mbarrier wait is bounded by a clock budget; on expiry the CTA sets the error word,
+// drains its own copies and MMAs, frees its TMEM and returns.
+#include "dfgb_internal.cuh"
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <string.h>
+#include <stdio.h>
+
+namespace dfgb {
+namespace {
+
+constexpr int BM = 128;
+constexpr int kRowBytes = 128;                 // K bytes per stage row (one swizzle span)
+constexpr int kThreads = 192;
+constexpr long long kWaitBudget = 2000000000LL;  // ~1 s of SM clocks per wait
+constexpr int kSmemLimit = 232448;             // opt-in dynamic shared memory per block
+
+struct TcArgs {
+  RowMap rows;
+  int N, K;
+  const float* bias;
+  const float* col_scale;
+  void* out;
+  int64_t ldo;
+  int out_kind;
+  int gelu;
+  float out_scale;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: true when the phase of the given parity completed; false after the clock
+// budget or once another role of the CTA has given up (*abort set).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
+                                          int* err) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitBudget) {
+      atomicOr(err, kErrTimeout);
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B
+// apart (stride byte offset), leading byte offset unused for this layout, version 1.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = BN.
+template <bool FP8, int BN>
+__device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (FP8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+template <bool FP8>
+__device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t id,
+                                          uint32_t accum) {
+  if (FP8) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(id), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(id), "r"(accum)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float gelu_fast(float x) {
+  const float u = 0.7978845608028654f * fmaf(0.044715f * x * x, x, x);
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+  return 0.5f * x * (1.0f + t);
+}
+
+template <int BN>
+struct Cfg {
+  static constexpr int kStageBytes = (BM + BN) * kRowBytes;
+  static constexpr int kStages0 = (kSmemLimit - 2048) / kStageBytes;
+  static constexpr int kStages = kStages0 > 8 ? 8 : kStages0;
+  static constexpr int kAccStride = (BN + 31) / 32 * 32;
+  static constexpr int kTmemCols = (2 * kAccStride <= 32) ? 32 : (2 * kAccStride <= 64) ? 64
+                                   : (2 * kAccStride <= 128) ? 128 : (2 * kAccStride <= 256) ? 256 : 512;
+  static constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 1024 /*barriers*/;
+};
+
+template <bool FP8, int BN>
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs g) {
+  using C = Cfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;                                   // kStages x 16 KB
+  uint8_t* sB = smem + C::kStages * BM * kRowBytes;     // kStages x BN*128 B
+  uint64_t* bars = (uint64_t*)(smem + C::kStages * C::kStageBytes);
+  // bars: full[S], empty[S], tfull[2], tempty[2], drain
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * C::kStages;
+  const uint32_t tfull0 = empty0 + 8 * C::kStages, tempty0 = tfull0 + 16;
+  const uint32_t drain = tempty0 + 16;
+
+  if (threadIdx.x == 0) {
+    abort_sh = 0;
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull0 + 8 * a, 1);
+      mbar_init(tempty0 + 8 * a, 4);
+    }
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"((uint32_t)C::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  volatile int* abort = &abort_sh;
+
+  const int64_t M = valid_rows(g.rows);
+  const int64_t tiles_m = (M + BM - 1) / BM;
+  const int tiles_n = (g.N + BN - 1) / BN;
+  const int64_t ntiles = tiles_m * tiles_n;
+  const int kblocks = (g.K * (FP8 ? 1 : 2) + kRowBytes - 1) / kRowBytes;
+  const int kelems = kRowBytes / (FP8 ? 1 : 2);
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+    uint32_t it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int m0 = (int)((t / tiles_n) * BM);
+      const int n0 = (int)(t % tiles_n) * BN;
+      for (int kb = 0; kb < kblocks; ++kb, ++it) {
+        const int s = it % C::kStages;
+        const uint32_t ph = (it / C::kStages) & 1;
+        if (!mbar_wait(empty0 + 8 * s, ph ^ 1, abort, g.err)) { ok = false; break; }
+        mbar_arrive_expect_tx(full0 + 8 * s, C::kStageBytes);
+        tma_load_2d(smem_u32(sA + s * BM * kRowBytes), &tmA, full0 + 8 * s, kb * kelems, m0);
+        tma_load_2d(smem_u32(sB + s * BN * kRowBytes), &tmB, full0 + 8 * s, kb * kelems, n0);
+      }
+    }
+    // Drain: the last issued load of every stage must have landed before the CTA exits.
+    const uint32_t issued = it;
+    for (uint32_t j = (issued > (uint32_t)C::kStages ? issued - C::kStages : 0); j < issued; ++j) {
+      const int s = j % C::kStages;
+      const uint32_t ph = (j / C::kStages) & 1;
+      const long long t0 = clock64();
+      while (!mbar_try(full0 + 8 * s, ph) && clock64() - t0 < kWaitBudget) {
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t id = idesc<FP8, BN>();
+    uint32_t it = 0, j = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+      const int a = j & 1;
+      const uint32_t aph = (j >> 1) & 1;
+      if (!mbar_wait(tempty0 + 8 * a, aph ^ 1, abort, g.err)) break;
+      tc_fence_after();
+      const uint32_t dt = tmem + a * C::kAccStride;
+      for (int kb = 0; kb < kblocks; ++kb, ++it) {
+        const int s = it % C::kStages;
+        const uint32_t ph = (it / C::kStages) & 1;
+        if (!mbar_wait(full0 + 8 * s, ph, abort, g.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint64_t da = desc_sw128(smem_u32(sA + s * BM * kRowBytes));
+        const uint64_t db = desc_sw128(smem_u32(sB + s * BN * kRowBytes));
+#pragma unroll
+        for (int kk = 0; kk < kRowBytes / 32; ++kk)  // 32 bytes of K per instruction
+          mma_issue<FP8>(dt, da + 2 * kk, db + 2 * kk, id, (kb | kk) ? 1u : 0u);
+        mma_commit(empty0 + 8 * s);  // frees the stage when these MMAs have read it
+      }
+      if (ok) mma_commit(tfull0 + 8 * a);
+    }
+    // Drain: every MMA issued by this thread completes before TMEM is released.
+    mma_commit(drain);
+    const long long t0 = clock64();
+    while (!mbar_try(drain, 0) && clock64() - t0 < kWaitBudget) {
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    uint32_t j = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int a = j & 1;
+      const uint32_t aph = (j >> 1) & 1;
+      if (!mbar_wait(tfull0 + 8 * a, aph, abort, g.err)) break;
+      tc_fence_after();
+      const int64_t m0 = (t / tiles_n) * BM;
+      const int n0 = (int)(t % tiles_n) * BN;
+      const int64_t row = m0 + q * 32 + lane;
+      const bool row_ok = row < M;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * C::kAccStride + c0, v);
+        const int col0 = n0 + c0;
+        // columns this tile owns: below N and below BN (the last chunk may run past BN)
+        const int ncols = min(g.N - col0, BN - c0);
+        if (!row_ok || ncols <= 0) continue;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const bool cok = i < ncols;
+          const int col = col0 + i;
+          float x = v[i];
+          if (g.col_scale) x *= cok ? g.col_scale[col] : 0.0f;
+          x += cok ? g.bias[col] : 0.0f;
+          if (g.gelu) x = gelu_fast(x);
+          v[i] = x;
+        }
+        const bool full = ncols >= 32;
+        if (g.out_kind == kXF32) {
+          float* o = (float*)g.out + row * g.ldo + col0;
+          if (full && (g.ldo % 4 == 0)) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<float4*>(o + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+          } else {
+            for (int i = 0; i < ncols && i < 32; ++i) o[i] = v[i];
+          }
+        } else if (g.out_kind == kXBF16) {
+          __nv_bfloat16* o = (__nv_bfloat16*)g.out + row * g.ldo + col0;
+          if (full && (g.ldo % 8 == 0)) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 8) {
+              uint4 w;
+              __nv_bfloat162 h0 = __floats2bfloat162_rn(v[i], v[i + 1]);
+              __nv_bfloat162 h1 = __floats2bfloat162_rn(v[i + 2], v[i + 3]);
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[i + 4], v[i + 5]);
+              __nv_bfloat162 h3 = __floats2bfloat162_rn(v[i + 6], v[i + 7]);
+              memcpy(&w.x, &h0, 4); memcpy(&w.y, &h1, 4);
+              memcpy(&w.z, &h2, 4); memcpy(&w.w, &h3, 4);
+              *reinterpret_cast<uint4*>(o + i) = w;
+            }
+          } else {
+            for (int i = 0; i < ncols && i < 32; ++i) o[i] = __float2bfloat16_rn(v[i]);
+          }
+        } else {
+          __nv_fp8_e4m3* o = (__nv_fp8_e4m3*)g.out + row * g.ldo + col0;
+          const float sc = g.out_scale;
+          if (full && (g.ldo % 16 == 0)) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 16) {
+              uint8_t b[16];
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                __nv_fp8_e4m3 f(v[i + e] * sc);
+                b[e] = f.__x;
+              }
+              *reinterpret_cast<uint4*>(o + i) = *reinterpret_cast<uint4*>(b);
+            }
+          } else {
+            for (int i = 0; i < ncols && i < 32; ++i) o[i] = __nv_fp8_e4m3(v[i] * sc);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty0 + 8 * a);
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)C::kTmemCols)
+                 : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+template <bool FP8, int BN>
+cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream_t st) {
+  using C = Cfg<BN>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<FP8, BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const int64_t tiles = ((a.rows.nmax + BM - 1) / BM) * ((L.N + BN - 1) / BN);
+  const unsigned grid = (unsigned)(tiles < num_sms ? (tiles > 0 ? tiles : 1) : num_sms);
+  tc_gemm_kernel<FP8, BN><<<grid, kThreads, C::kSmemBytes, st>>>(L.tmA, L.tmB, a);
+  return cudaGetLastError();
+}
+
+template <bool FP8>
+cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream_t st) {
+  switch (L.BN) {
+    case 32: return launch_bn<FP8, 32>(L, a, num_sms, st);
+    case 64: return launch_bn<FP8, 64>(L, a, num_sms, st);
+    case 128: return launch_bn<FP8, 128>(L, a, num_sms, st);
+    case 160: return launch_bn<FP8, 160>(L, a, num_sms, st);
+    case 208: return launch_bn<FP8, 208>(L, a, num_sms, st);
+    case 256: return launch_bn<FP8, 256>(L, a, num_sms, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+bool tc_encode_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
+                  uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,
+                  uint32_t box_outer, char* err, size_t errlen) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    snprintf(err, errlen, "cuTensorMapEncodeTiled is not available from the driver");
+    return false;
+  }
+  if (((uintptr_t)base & 15) || (row_pitch_bytes & 15) || box_inner * elem_bytes != kRowBytes) {
+    snprintf(err, errlen, "tensor map: base/pitch not 16-byte aligned or box not 128 B");
+    return false;
+  }
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {row_pitch_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt =
+      elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    snprintf(err, errlen, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return false;
+  }
+  return true;
+}
+
+cudaError_t launch_tc_gemm(const TcLayer& L, const RowMap& rows, int num_sms, int* err,
+                           cudaStream_t st) {
+  if (rows.nmax <= 0) return cudaSuccess;
+  TcArgs a;
+  a.rows = rows;
+  a.N = L.N;
+  a.K = L.K;
+  a.bias = L.bias;
+  a.col_scale = L.col_scale;
+  a.out = L.out;
+  a.ldo = L.ldo;
+  a.out_kind = L.out_kind;
+  a.gelu = L.gelu ? 1 : 0;
+  a.out_scale = L.out_scale;
+  a.err = err;
+  return L.elem_bytes == 1 ? launch_fmt<true>(L, a, num_sms, st)
+                           : launch_fmt<false>(L, a, num_sms, st);
+}
+
+}  // namespace dfgb

@@ -1,0 +1,694 @@
+// C ABI of libdfgb (include/df.h): state creation, the fused reaction step and the stage
+// entry points. Host code only orchestrates; every step of the path runs in the kernels
+// of eos.cu, compact.cu, mlp_simt.cu and mlp_tc.cu.
+#include "dfgb_internal.cuh"
+#include "../../include/df.h"
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace dfgb;
+
+struct df_state {
+  int device = 0;
+  int num_sms = 0;
+  int n = 0, K0 = 0, L = 0;
+  std::vector<int> widths;
+  int precision = DF_FP32;
+  double T_react = 0, lambda = 0.1, dt = 0;
+  int64_t cap = 0;                       // rows per batch
+  EosParams P{};
+  double* d_spc = nullptr;
+  double* d_K = nullptr;
+  double* d_norm = nullptr;
+  int* d_err = nullptr;                  // kernel error word
+  int64_t* d_count = nullptr;            // reacting cells of the last step
+  int64_t* d_flagged = nullptr;          // flagged cells of the last step
+  int64_t* d_iters = nullptr;            // Newton iterations of the last step
+  std::vector<float*> W32;               // FP32 weights, [N x Kp8] zero padded (SIMT)
+  std::vector<int> Kp8;
+  std::vector<float*> bias;
+  std::vector<void*> Wlp;                // BF16 / FP8 weights [N x Kp16]
+  std::vector<float*> col_scale;         // FP8 dequantisation scale per output channel
+  std::vector<float> act_scale;          // FP8 quantisation scale of each layer's input
+  // batch scratch
+  void* x = nullptr;
+  int64_t ldx = 0;
+  void* act[2] = {nullptr, nullptr};
+  int64_t act_ld[2] = {0, 0};
+  float* O = nullptr;
+  int64_t ldo = 0;
+  double* h0 = nullptr;
+  int32_t* rstat = nullptr;
+  // compaction scratch, grown on demand
+  int32_t* idx = nullptr;
+  int64_t idx_cap = 0;
+  int64_t* cscr = nullptr;
+  int64_t cscr_words = 0;
+  std::vector<TcLayer> tcl;
+  std::string err;
+  // kernel timing (df_profile_enable / df_profile_read)
+  bool prof_on = false;
+  struct Rec { int fam; cudaEvent_t a, b; };
+  std::vector<Rec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  std::vector<std::string> prof_names;
+  std::vector<int64_t> prof_launches;
+  std::vector<double> prof_ms;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+const char* kVersion = "dfgb 0.1.0 (sm_103a)";
+
+df_status fail(df_state* s, df_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (s) s->err = buf; else g_create_err = buf;
+  return code;
+}
+
+df_status cuda_fail(df_state* s, cudaError_t e, const char* where) {
+  return fail(s, e == cudaErrorMemoryAllocation ? DF_ERR_OOM : DF_ERR_CUDA, "%s: %s", where,
+              cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+}
+
+int pick_bn(int N) {
+  // Per-tile cost model: BN columns of work plus a fixed ~64-column share for the A
+  // operand stream and the epilogue; pick the cheapest tiling of N.
+  const int cand[] = {256, 208, 160, 128, 64, 32};
+  int best = 32;
+  int64_t best_cost = INT64_MAX;
+  for (int bn : cand) {
+    const int64_t cost = (int64_t)((N + bn - 1) / bn) * (bn + 64);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = bn;
+    }
+  }
+  return best;
+}
+
+__global__ void cast_rows_kernel(int64_t rows, int K, const float* __restrict__ in,
+                                 int64_t ldi, void* out, int64_t ldo, int kind, float scale) {
+  const int64_t total = rows * ldo;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / ldo;
+    const int k = (int)(e % ldo);
+    const float v = (k < K) ? in[r * ldi + k] : 0.0f;
+    if (kind == kXF32) ((float*)out)[e] = v;
+    else if (kind == kXBF16) ((__nv_bfloat16*)out)[e] = __float2bfloat16_rn(v);
+    else ((__nv_fp8_e4m3*)out)[e] = __nv_fp8_e4m3(v * scale);
+  }
+}
+
+int xkind_of(int precision) {
+  return precision == DF_BF16 ? kXBF16 : precision == DF_FP8_E4M3 ? kXFP8 : kXF32;
+}
+
+size_t elem_of(int precision) {
+  return precision == DF_BF16 ? 2 : precision == DF_FP8_E4M3 ? 1 : 4;
+}
+
+void free_state(df_state* s) {
+  auto f = [](void* p) { if (p) cudaFree(p); };
+  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
+  for (auto p : s->W32) f(p);
+  for (auto p : s->bias) f(p);
+  for (auto p : s->Wlp) f(p);
+  for (auto p : s->col_scale) f(p);
+  f(s->x); f(s->act[0]); f(s->act[1]); f(s->O); f(s->h0); f(s->rstat);
+  f(s->idx); f(s->cscr);
+}
+
+cudaEvent_t prof_event(df_state* s) {
+  if (!s->prof_pool.empty()) {
+    cudaEvent_t e = s->prof_pool.back();
+    s->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int prof_family(df_state* s, const char* name) {
+  for (size_t i = 0; i < s->prof_names.size(); ++i)
+    if (s->prof_names[i] == name) return (int)i;
+  s->prof_names.push_back(name);
+  s->prof_launches.push_back(0);
+  s->prof_ms.push_back(0.0);
+  return (int)s->prof_names.size() - 1;
+}
+
+// Brackets the launches made during its lifetime with events on `st` when timing is on.
+struct ProfScope {
+  df_state* s;
+  cudaStream_t st;
+  df_state::Rec r{};
+  ProfScope(df_state* s_, const char* name, cudaStream_t st_) : s(s_), st(st_) {
+    if (!s->prof_on) return;
+    r.fam = prof_family(s, name);
+    r.a = prof_event(s);
+    r.b = prof_event(s);
+    cudaEventRecord(r.a, st);
+  }
+  ~ProfScope() {
+    if (!s->prof_on || !r.a) return;
+    cudaEventRecord(r.b, st);
+    s->prof_recs.push_back(r);
+  }
+};
+
+// The network layers a6-a7 on rows of the batch buffers: x -> act -> ... -> O.
+df_status run_mlp(df_state* s, const RowMap& rm, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  static const char* kLayer[8] = {"layer0", "layer1", "layer2", "layer3",
+                                  "layer4", "layer5", "layer6", "layer7"};
+  for (int l = 0; l < s->L; ++l) {
+    const bool last = l == s->L - 1;
+    ProfScope ps(s, kLayer[l], st);
+    if (s->precision == DF_FP32) {
+      const float* A = (l == 0) ? (const float*)s->x : (const float*)s->act[(l - 1) & 1];
+      const int64_t lda = (l == 0) ? s->ldx : s->act_ld[(l - 1) & 1];
+      float* Cout = last ? s->O : (float*)s->act[l & 1];
+      const int64_t ldc = last ? s->ldo : s->act_ld[l & 1];
+      e = launch_sgemm_bias_act(rm, s->widths[l + 1], s->Kp8[l], A, lda, s->W32[l], s->Kp8[l],
+                                s->bias[l], Cout, ldc, !last, s->num_sms, st);
+    } else {
+      e = launch_tc_gemm(s->tcl[l], rm, s->num_sms, s->d_err, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "network layer launch");
+  }
+  return DF_OK;
+}
+
+df_status check_fields(df_state* s, int64_t n, const void* a, const void* b, const void* Y,
+                       int64_t ldY) {
+  if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
+  if (n < 0) return fail(s, DF_ERR_INVALID_ARG, "n_cells < 0");
+  if (n == 0) return DF_OK;
+  if (!a || !b || !Y) return fail(s, DF_ERR_INVALID_ARG, "NULL field pointer");
+  if (ldY < n) return fail(s, DF_ERR_INVALID_ARG, "ldY (%lld) < n_cells (%lld)", (long long)ldY,
+                           (long long)n);
+  return DF_OK;
+}
+
+df_status ensure_compact(df_state* s, int64_t n) {
+  if (n > s->idx_cap) {
+    if (s->idx) cudaFree(s->idx);
+    s->idx = nullptr;
+    s->idx_cap = 0;
+    cudaError_t e = dalloc(&s->idx, (size_t)n);
+    if (e != cudaSuccess) return cuda_fail(s, e, "reacting-cell list");
+    s->idx_cap = n;
+  }
+  const int64_t w = compact_scratch_words(n);
+  if (w > s->cscr_words) {
+    if (s->cscr) cudaFree(s->cscr);
+    s->cscr = nullptr;
+    s->cscr_words = 0;
+    cudaError_t e = dalloc(&s->cscr, (size_t)w);
+    if (e != cudaSuccess) return cuda_fail(s, e, "compaction scratch");
+    s->cscr_words = w;
+  }
+  return DF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* df_version(void) { return kVersion; }
+
+const char* df_get_last_error(df_state* s) { return s ? s->err.c_str() : g_create_err.c_str(); }
+
+df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
+                          const df_options* opt, df_state** out) {
+  if (!out) return fail(nullptr, DF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mech || !mlp || !opt) return fail(nullptr, DF_ERR_INVALID_ARG, "NULL descriptor");
+  const int n = mech->n_species;
+  if (n < 1 || n > kMaxSpecies)
+    return fail(nullptr, DF_ERR_UNSUPPORTED, "n_species must be in 1..%d", kMaxSpecies);
+  if (!mech->W || !mech->Tc || !mech->pc || !mech->omega || !mech->kij || !mech->nasa)
+    return fail(nullptr, DF_ERR_INVALID_ARG, "NULL mechanism array");
+  const int L = mlp->n_layers;
+  if (L < 1 || L > 8 || !mlp->widths || !mlp->W || !mlp->b)
+    return fail(nullptr, DF_ERR_INVALID_ARG, "bad network description");
+  if (mlp->widths[0] != n + 2 || mlp->widths[L] != n)
+    return fail(nullptr, DF_ERR_INVALID_ARG, "network must map n+2 inputs to n outputs");
+  for (int l = 0; l <= L; ++l)
+    if (mlp->widths[l] < 1 || mlp->widths[l] > 8192)
+      return fail(nullptr, DF_ERR_INVALID_ARG, "layer width out of range");
+  if (!mlp->in_mean || !mlp->in_std || !mlp->out_mean || !mlp->out_std)
+    return fail(nullptr, DF_ERR_INVALID_ARG, "NULL normalisation array");
+  if (!(mlp->lambda > 0.0)) return fail(nullptr, DF_ERR_INVALID_ARG, "lambda must be > 0");
+  const double inv_l = 1.0 / mlp->lambda;
+  const int m = (int)std::lround(inv_l);
+  if (m < 1 || m > 64 || std::fabs(inv_l - m) > 1e-9 * inv_l)
+    return fail(nullptr, DF_ERR_UNSUPPORTED, "1/lambda must be an integer in 1..64");
+  if (!(mlp->dt > 0.0)) return fail(nullptr, DF_ERR_INVALID_ARG, "dt must be > 0");
+  if (opt->precision < DF_FP32 || opt->precision > DF_FP8_E4M3)
+    return fail(nullptr, DF_ERR_INVALID_ARG, "unknown precision");
+  for (int k = 0; k < n; ++k)
+    if (!(mech->W[k] > 0) || !(mech->Tc[k] > 0) || !(mech->pc[k] > 0))
+      return fail(nullptr, DF_ERR_INVALID_ARG, "W, Tc, pc must be positive");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)
+    return fail(nullptr, DF_ERR_CUDA, "no CUDA device");
+  if (opt->device < 0 || opt->device >= ndev)
+    return fail(nullptr, DF_ERR_INVALID_ARG, "device ordinal out of range");
+  DeviceGuard guard(opt->device);
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, opt->device);
+  if (opt->precision != DF_FP32 && prop.major * 10 + prop.minor < 100)
+    return fail(nullptr, DF_ERR_UNSUPPORTED, "tensor-core precisions need sm_100 or newer");
+
+  df_state* s = new df_state();
+  s->device = opt->device;
+  s->num_sms = prop.multiProcessorCount;
+  s->n = n;
+  s->K0 = n + 2;
+  s->L = L;
+  s->widths.assign(mlp->widths, mlp->widths + L + 1);
+  s->precision = opt->precision;
+  s->T_react = opt->T_react;
+  s->lambda = mlp->lambda;
+  s->dt = mlp->dt;
+  s->cap = opt->batch_cells > 0 ? round_up(opt->batch_cells, 128) : (int64_t)1 << 20;
+  cudaError_t e;
+#define CK(expr, what)                          \
+  do {                                          \
+    e = (expr);                                 \
+    if (e != cudaSuccess) {                     \
+      df_status rc = cuda_fail(nullptr, e, what); \
+      free_state(s);                            \
+      delete s;                                 \
+      return rc;                                \
+    }                                           \
+  } while (0)
+
+  // ---- equation-of-state constants (Peng & Robinson 1976, NASA-7) ----
+  std::vector<double> spc((size_t)n * kSpcStride), K((size_t)n * n);
+  for (int k = 0; k < n; ++k) {
+    const double Tc = mech->Tc[k], pc = mech->pc[k], w = mech->omega[k];
+    const double ac = 0.45724 * kR * kR * Tc * Tc / pc;
+    const double b = 0.07780 * kR * Tc / pc;
+    const double kap = 0.37464 + 1.54226 * w - 0.26992 * w * w;
+    const double sac = std::sqrt(ac);
+    double* q = &spc[(size_t)k * kSpcStride];
+    const double* a = mech->nasa + 7 * k;
+    q[0] = 1.0 / mech->W[k];
+    q[1] = sac * (1.0 + kap);
+    q[2] = sac * kap / std::sqrt(Tc);
+    q[3] = b;
+    q[4] = kR * a[5];
+    q[5] = kR * a[0];
+    q[6] = kR * a[1] / 2.0;
+    q[7] = kR * a[2] / 3.0;
+    q[8] = kR * a[3] / 4.0;
+    q[9] = kR * a[4] / 5.0;
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) K[(size_t)i * n + j] = (i == j) ? 1.0 : 1.0 - mech->kij[i * n + j];
+  std::vector<double> norm((size_t)2 * s->K0 + 2 * n);
+  for (int k = 0; k < s->K0; ++k) {
+    if (!(mlp->in_std[k] != 0.0)) {
+      delete s;
+      return fail(nullptr, DF_ERR_INVALID_ARG, "in_std must be non-zero");
+    }
+    norm[k] = mlp->in_mean[k];
+    norm[s->K0 + k] = 1.0 / mlp->in_std[k];
+  }
+  for (int k = 0; k < n; ++k) {
+    norm[2 * s->K0 + k] = mlp->out_mean[k];
+    norm[2 * s->K0 + n + k] = mlp->out_std[k];
+  }
+  CK(dalloc(&s->d_spc, spc.size()), "constants");
+  CK(dalloc(&s->d_K, K.size()), "constants");
+  CK(dalloc(&s->d_norm, norm.size()), "constants");
+  CK(cudaMemcpy(s->d_spc, spc.data(), sizeof(double) * spc.size(), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(s->d_K, K.data(), sizeof(double) * K.size(), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(s->d_norm, norm.data(), sizeof(double) * norm.size(), cudaMemcpyHostToDevice), "copy");
+  CK(dalloc(&s->d_err, 1), "error word");
+  CK(cudaMemset(s->d_err, 0, sizeof(int)), "memset");
+  CK(dalloc(&s->d_count, 1), "counters");
+  CK(dalloc(&s->d_flagged, 1), "counters");
+  CK(dalloc(&s->d_iters, 1), "counters");
+  CK(cudaMemset(s->d_iters, 0, sizeof(int64_t)), "memset");
+  CK(cudaMemset(s->d_count, 0, sizeof(int64_t)), "memset");
+  CK(cudaMemset(s->d_flagged, 0, sizeof(int64_t)), "memset");
+  EosParams& P = s->P;
+  P.n = n;
+  P.K0 = s->K0;
+  P.inv_lambda = m;
+  P.lambda = mlp->lambda;
+  P.T_react = opt->T_react;
+  P.newton_tol = opt->newton_tol > 0 ? opt->newton_tol : 1e-10;
+  P.newton_max_iter = opt->newton_max_iter > 0 ? opt->newton_max_iter : 30;
+  P.spc = s->d_spc;
+  P.Kmat = s->d_K;
+  P.norm = s->d_norm;
+  P.err = s->d_err;
+  P.flagged = s->d_flagged;
+  P.newton_iters = s->d_iters;
+
+  // ---- network weights ----
+  const bool lp = s->precision != DF_FP32;
+  const size_t eb = elem_of(s->precision);
+  for (int l = 0; l < L; ++l) {
+    const int Kl = s->widths[l], Nl = s->widths[l + 1];
+    if (!mlp->W[l] || !mlp->b[l]) {
+      free_state(s);
+      delete s;
+      return fail(nullptr, DF_ERR_INVALID_ARG, "NULL layer array");
+    }
+    float* b = nullptr;
+    CK(dalloc(&b, Nl), "bias");
+    s->bias.push_back(b);
+    CK(cudaMemcpy(b, mlp->b[l], sizeof(float) * Nl, cudaMemcpyHostToDevice), "copy");
+    if (!lp) {
+      const int kp = (int)round_up(Kl, 8);
+      std::vector<float> w((size_t)Nl * kp, 0.0f);
+      for (int r = 0; r < Nl; ++r)
+        for (int c = 0; c < Kl; ++c) w[(size_t)r * kp + c] = mlp->W[l][(size_t)r * Kl + c];
+      float* d = nullptr;
+      CK(dalloc(&d, w.size()), "weights");
+      CK(cudaMemcpy(d, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice), "copy");
+      s->W32.push_back(d);
+      s->Kp8.push_back(kp);
+    } else {
+      const int kp = (int)round_up(Kl, 16);
+      void* d = nullptr;
+      CK(cudaMalloc(&d, eb * (size_t)Nl * kp), "weights");
+      float* cs = nullptr;
+      if (s->precision == DF_BF16) {
+        std::vector<__nv_bfloat16> w((size_t)Nl * kp, __float2bfloat16_rn(0.0f));
+        for (int r = 0; r < Nl; ++r)
+          for (int c = 0; c < Kl; ++c)
+            w[(size_t)r * kp + c] = __float2bfloat16_rn(mlp->W[l][(size_t)r * Kl + c]);
+        CK(cudaMemcpy(d, w.data(), eb * w.size(), cudaMemcpyHostToDevice), "copy");
+      } else {
+        // per-output-channel scale: row max |W| maps to the e4m3 maximum 448
+        std::vector<uint8_t> w((size_t)Nl * kp, 0);
+        std::vector<float> sc(Nl);
+        for (int r = 0; r < Nl; ++r) {
+          float amax = 0.0f;
+          for (int c = 0; c < Kl; ++c) amax = std::max(amax, std::fabs(mlp->W[l][(size_t)r * Kl + c]));
+          const float ws = amax > 0 ? amax / 448.0f : 1.0f;
+          sc[r] = ws;
+          for (int c = 0; c < Kl; ++c)
+            w[(size_t)r * kp + c] = __nv_fp8_e4m3(mlp->W[l][(size_t)r * Kl + c] / ws).__x;
+        }
+        CK(cudaMemcpy(d, w.data(), w.size(), cudaMemcpyHostToDevice), "copy");
+        // dequantisation = weight scale / input activation scale
+        const float in_scale = 1.0f;
+        for (auto& v : sc) v /= in_scale;
+        CK(dalloc(&cs, Nl), "scales");
+        CK(cudaMemcpy(cs, sc.data(), sizeof(float) * Nl, cudaMemcpyHostToDevice), "copy");
+        s->act_scale.push_back(in_scale);
+      }
+      s->Wlp.push_back(d);
+      s->col_scale.push_back(cs);
+      s->Kp8.push_back(kp);
+    }
+  }
+
+  // ---- batch scratch ----
+  const int xk = xkind_of(s->precision);
+  s->ldx = round_up(s->K0, lp ? 16 : 8);
+  CK(cudaMalloc(&s->x, eb * (size_t)s->cap * s->ldx), "network input");
+  int64_t wmax[2] = {8, 8};
+  for (int l = 0; l + 1 < L; ++l)
+    wmax[l & 1] = std::max<int64_t>(wmax[l & 1], round_up(s->widths[l + 1], lp ? 16 : 8));
+  for (int b = 0; b < 2; ++b) {
+    s->act_ld[b] = wmax[b];
+    CK(cudaMalloc(&s->act[b], eb * (size_t)s->cap * wmax[b]), "activations");
+    CK(cudaMemset(s->act[b], 0, eb * (size_t)s->cap * wmax[b]), "memset");
+  }
+  s->ldo = round_up(n, 8);
+  CK(dalloc(&s->O, (size_t)s->cap * s->ldo), "network output");
+  CK(dalloc(&s->h0, (size_t)s->cap), "h0");
+  CK(dalloc(&s->rstat, (size_t)s->cap), "row status");
+
+  if (lp) {
+    char emsg[256];
+    for (int l = 0; l < L; ++l) {
+      const bool last = l == L - 1;
+      TcLayer T{};
+      T.N = s->widths[l + 1];
+      T.K = s->widths[l];
+      T.BN = pick_bn(T.N);
+      if (const char* env = getenv("DFGB_BN")) {  // tile-width override for sweeps
+        const int v = atoi(env);
+        if (v == 32 || v == 64 || v == 128 || v == 160 || v == 208 || v == 256) T.BN = v;
+      }
+      T.bias = s->bias[l];
+      T.col_scale = s->col_scale[l];
+      T.out = last ? (void*)s->O : s->act[l & 1];
+      T.ldo = last ? s->ldo : s->act_ld[l & 1];
+      T.out_kind = last ? kXF32 : xk;
+      T.gelu = !last;
+      T.out_scale = (s->precision == DF_FP8_E4M3 && !last) ? s->act_scale[l + 1] : 1.0f;
+      T.elem_bytes = (int)eb;
+      const void* Abase = (l == 0) ? s->x : s->act[(l - 1) & 1];
+      const int64_t lda = (l == 0) ? s->ldx : s->act_ld[(l - 1) & 1];
+      const uint32_t boxk = 128 / (uint32_t)eb;
+      if (!tc_encode_2d(&T.tmA, Abase, (int)eb, (uint64_t)T.K, (uint64_t)s->cap,
+                        (uint64_t)lda * eb, boxk, 128, emsg, sizeof emsg) ||
+          !tc_encode_2d(&T.tmB, s->Wlp[l], (int)eb, (uint64_t)T.K, (uint64_t)T.N,
+                        (uint64_t)s->Kp8[l] * eb, boxk, (uint32_t)T.BN, emsg, sizeof emsg)) {
+        free_state(s);
+        delete s;
+        return fail(nullptr, DF_ERR_CUDA, "%s", emsg);
+      }
+      s->tcl.push_back(T);
+    }
+  }
+  (void)xk;
+#undef CK
+  *out = s;
+  return DF_OK;
+}
+
+void df_state_destroy(df_state* s) {
+  if (!s) return;
+  DeviceGuard guard(s->device);
+  cudaDeviceSynchronize();
+  for (auto& r : s->prof_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : s->prof_pool) cudaEventDestroy(e);
+  free_state(s);
+  delete s;
+}
+
+df_status df_real_fluid_props(df_state* s, int64_t n_cells, const double* T, const double* p,
+                              const double* Y, int64_t ldY, double* rho, double* h, double* cp,
+                              double* Z, void* stream) {
+  df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
+  if (rc != DF_OK || n_cells == 0) return rc;
+  DeviceGuard guard(s->device);
+  cudaError_t e = launch_props(s->P, n_cells, T, p, Y, ldY, rho, h, cp, Z, (cudaStream_t)stream);
+  return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "real-fluid properties");
+}
+
+df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const double* p,
+                       double* Y, int64_t ldY, int32_t* cell_status, int64_t* n_active_out,
+                       void* stream) {
+  df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
+  if (rc != DF_OK) return rc;
+  if (!(std::fabs(dt - s->dt) <= 1e-12 * std::fabs(s->dt)))
+    return fail(s, DF_ERR_DT_MISMATCH, "dt %.17g differs from the network's %.17g", dt, s->dt);
+  DeviceGuard guard(s->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = ensure_compact(s, n_cells)) != DF_OK) return rc;
+  cudaError_t e = cudaMemsetAsync(s->d_flagged, 0, sizeof(int64_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_iters, 0, sizeof(int64_t), st);
+  if (e == cudaSuccess) {
+    ProfScope ps(s, "compact", st);
+    e = launch_compact(n_cells, s->T_react, T, s->idx, s->d_count, cell_status, s->cscr, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(s, e, "reacting-cell compaction");
+  const int xk = xkind_of(s->precision);
+  const float xs = s->precision == DF_FP8_E4M3 ? s->act_scale[0] : 1.0f;
+  for (int64_t row0 = 0; row0 < n_cells; row0 += s->cap) {
+    const RowMap rm{s->idx, s->d_count, row0, std::min<int64_t>(s->cap, n_cells - row0)};
+    {
+      ProfScope ps(s, "eos_pre", st);
+      e = launch_eos_pre(s->P, rm, T, p, Y, ldY, s->h0, nullptr, s->x, xk, s->ldx, xs, s->rstat, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "eos_pre launch");
+    if ((rc = run_mlp(s, rm, st)) != DF_OK) return rc;
+    {
+      ProfScope ps(s, "eos_post", st);
+      e = launch_eos_post(s->P, rm, s->O, s->ldo, s->h0, T, p, Y, ldY, s->rstat, cell_status, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "eos_post launch");
+  }
+  if (n_active_out) {
+    e = cudaMemcpyAsync(n_active_out, s->d_count, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "n_active copy");
+  }
+  return DF_OK;
+}
+
+df_status df_get_step_summary(df_state* s, void* stream, df_step_stats* stats) {
+  if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
+  DeviceGuard guard(s->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+  int64_t c = 0, f = 0, it = 0;
+  int err = 0;
+  if ((e = cudaMemcpy(&c, s->d_count, sizeof c, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(&f, s->d_flagged, sizeof f, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(&it, s->d_iters, sizeof it, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(&err, s->d_err, sizeof err, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(s, e, "summary read");
+  if (stats) {
+    stats->n_active = c;
+    stats->n_flagged = f;
+    stats->newton_iterations = it;
+  }
+  if (err & kErrTimeout) {
+    cudaMemset(s->d_err, 0, sizeof(int));
+    return fail(s, DF_ERR_TIMEOUT, "a kernel wait hit its time limit");
+  }
+  if (f > 0) return fail(s, DF_ERR_NOT_CONVERGED, "%lld cells were flagged", (long long)f);
+  return DF_OK;
+}
+
+df_status df_active_compact(df_state* s, int64_t n_cells, const double* T, int32_t* idx,
+                            int64_t* count, void* stream) {
+  if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
+  if (n_cells < 0 || !count || (n_cells > 0 && (!T || !idx)))
+    return fail(s, DF_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard guard(s->device);
+  df_status rc = ensure_compact(s, n_cells);
+  if (rc != DF_OK) return rc;
+  cudaError_t e = launch_compact(n_cells, s->T_react, T, idx, count, nullptr, s->cscr,
+                                 (cudaStream_t)stream);
+  return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "compaction");
+}
+
+df_status df_eos_pre(df_state* s, int64_t n_cells, const double* T, const double* p,
+                     const double* Y, int64_t ldY, double* h0, double* Z, float* x,
+                     int32_t* status, void* stream) {
+  df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
+  if (rc != DF_OK || n_cells == 0) return rc;
+  DeviceGuard guard(s->device);
+  const RowMap rm{nullptr, nullptr, 0, n_cells};
+  cudaError_t e = launch_eos_pre(s->P, rm, T, p, Y, ldY, h0, Z, x, kXF32, s->K0, 1.0f, status,
+                                 (cudaStream_t)stream);
+  return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "eos_pre");
+}
+
+df_status df_mlp_forward(df_state* s, int64_t n_rows, const float* x, float* O, void* stream) {
+  if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
+  if (n_rows < 0 || (n_rows > 0 && (!x || !O))) return fail(s, DF_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard guard(s->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int xk = xkind_of(s->precision);
+  const float xs = s->precision == DF_FP8_E4M3 ? s->act_scale[0] : 1.0f;
+  for (int64_t r0 = 0; r0 < n_rows; r0 += s->cap) {
+    const int64_t rows = std::min<int64_t>(s->cap, n_rows - r0);
+    const int64_t total = rows * s->ldx;
+    const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)s->num_sms * 16);
+    cast_rows_kernel<<<g, 256, 0, st>>>(rows, s->K0, x + r0 * s->K0, s->K0, s->x, s->ldx, xk, xs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(s, e, "input cast");
+    const RowMap rm{nullptr, nullptr, 0, rows};
+    df_status rc = run_mlp(s, rm, st);
+    if (rc != DF_OK) return rc;
+    e = cudaMemcpy2DAsync(O + r0 * s->n, sizeof(float) * s->n, s->O, sizeof(float) * s->ldo,
+                          sizeof(float) * s->n, (size_t)rows, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "output copy");
+  }
+  return DF_OK;
+}
+
+df_status df_eos_post(df_state* s, int64_t n_cells, const float* O, const double* h0,
+                      double* T, const double* p, double* Y, int64_t ldY, int32_t* status,
+                      void* stream) {
+  df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
+  if (rc != DF_OK || n_cells == 0) return rc;
+  if (!O || !h0) return fail(s, DF_ERR_INVALID_ARG, "NULL O or h0");
+  DeviceGuard guard(s->device);
+  const RowMap rm{nullptr, nullptr, 0, n_cells};
+  cudaError_t e = launch_eos_post(s->P, rm, O, s->n, h0, T, p, Y, ldY, nullptr, status,
+                                  (cudaStream_t)stream);
+  return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "eos_post");
+}
+
+df_status df_profile_enable(df_state* s, int32_t enable) {
+  if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
+  s->prof_on = enable != 0;
+  return DF_OK;
+}
+
+df_status df_profile_read(df_state* s, int32_t max_entries, char* names, int64_t* launches,
+                          double* total_ms, int32_t* n_entries) {
+  if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
+  if (max_entries < 0 || (max_entries > 0 && (!names || !launches || !total_ms)) || !n_entries)
+    return fail(s, DF_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard guard(s->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(s, e, "device synchronize");
+  for (auto& r : s->prof_recs) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      s->prof_launches[r.fam] += 1;
+      s->prof_ms[r.fam] += ms;
+    }
+    s->prof_pool.push_back(r.a);
+    s->prof_pool.push_back(r.b);
+  }
+  s->prof_recs.clear();
+  const int n = (int)std::min<size_t>(s->prof_names.size(), (size_t)max_entries);
+  for (int i = 0; i < n; ++i) {
+    snprintf(names + 32 * i, 32, "%s", s->prof_names[i].c_str());
+    launches[i] = s->prof_launches[i];
+    total_ms[i] = s->prof_ms[i];
+  }
+  *n_entries = n;
+  std::fill(s->prof_launches.begin(), s->prof_launches.end(), 0);
+  std::fill(s->prof_ms.begin(), s->prof_ms.end(), 0.0);
+  return DF_OK;
+}
+
+}  // extern "C"

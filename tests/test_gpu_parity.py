@@ -1,0 +1,251 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, step by step and for the
+whole reaction step. Tolerances: integer work (the reacting-cell list, status bits) is
+bit-exact; EoS outputs (Z, rho, h, cp, h0) within 1e-10 relative; the FP32 network path
+within |dY| <= 1e-6 absolute of the FP64 network; recovered T within 1e-3 K of the oracle's
+Newton fed with the GPU's own Y'."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import network as onw
+from oracle import pr_eos as ope
+from oracle import step as ostep
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EOS_RTOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def df():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2508_18969_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+DEV = "cuda:0"
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device=DEV)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def _h_scale(mech, T, p, Y):
+    """Magnitude of the terms summed into h (for a relative tolerance on a signed sum)."""
+    from oracle.thermo import species_h_molar
+    s = ope.state(mech, T, p, Y)
+    return np.sum(np.abs(Y * species_h_molar(mech.nasa, T) / mech.W[:, None]), axis=0) + \
+        np.abs(s["h_dep"] / s["W_mix"])
+
+
+WORKLOADS = [("small-fp32-4k", 4096), ("layer1d-30sp-1m", 6000), ("react30-16m", 5000)]
+
+
+# ---------------------------------------------------------------- a0
+
+@pytest.mark.parametrize("N", [0, 1, 77, 4096, 3 * 4096 + 5, 100003])
+def test_compaction_bit_exact(df, N):
+    mech, net, _, _, _ = synth.configs.build("small-fp32-4k", n_cells=8)
+    st = df.State(mech, net, T_react=600.0, batch_cells=256)
+    T = synth.Stream(N, "compact").uniform(N, 100.0, 1200.0)
+    if N > 10:
+        T[3] = np.nan
+        T[5] = 600.0
+        T[7] = np.inf
+    idx, cnt = st.active_compact(dev(T))
+    torch.cuda.synchronize()
+    want = ostep.active_cells(T, 600.0)
+    c = int(host(cnt)[0])
+    assert c == want.shape[0]
+    assert np.array_equal(host(idx)[:c].astype(np.int64), want)
+    for thr, expect in ((-1.0, N), (1e9, 0)):
+        st2 = df.State(mech, net, T_react=thr, batch_cells=256)
+        _, cnt2 = st2.active_compact(dev(np.nan_to_num(T, nan=500.0)))
+        assert int(host(cnt2)[0]) == expect
+
+
+# ---------------------------------------------------------------- a1-a5 and properties
+
+@pytest.mark.parametrize("name,N", WORKLOADS)
+def test_eos_pre_vs_oracle(df, name, N):
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    st = df.State(mech, net, batch_cells=1024)
+    h0, Z, x, s = st.eos_pre(dev(T), dev(p), dev(Y))
+    torch.cuda.synchronize()
+    o = ope.state(mech, T, p, Y)
+    assert np.array_equal(host(s), o["status"])
+    np.testing.assert_allclose(host(Z), o["Z"], rtol=EOS_RTOL)
+    scale = _h_scale(mech, T, p, Y)
+    assert np.max(np.abs(host(h0) - o["h"]) / scale) <= EOS_RTOL
+    xo = onw.normalise_inputs(net, T, p, Y)
+    np.testing.assert_allclose(host(x), xo, atol=2e-6, rtol=1e-6)
+
+
+@pytest.mark.parametrize("name,N", WORKLOADS[:2])
+def test_real_fluid_props_vs_oracle(df, name, N):
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    st = df.State(mech, net, batch_cells=1024)
+    rho, h, cp, Z = st.real_fluid_props(dev(T), dev(p), dev(Y))
+    torch.cuda.synchronize()
+    o = ope.state(mech, T, p, Y)
+    np.testing.assert_allclose(host(Z), o["Z"], rtol=EOS_RTOL)
+    np.testing.assert_allclose(host(rho), o["rho"], rtol=EOS_RTOL)
+    assert np.max(np.abs(host(h) - o["h"]) / _h_scale(mech, T, p, Y)) <= EOS_RTOL
+    np.testing.assert_allclose(host(cp), o["cp"], rtol=1e-9)
+
+
+# ---------------------------------------------------------------- a6-a7
+
+@pytest.mark.parametrize("name,N", WORKLOADS[:2])
+def test_mlp_fp32_vs_fp64(df, name, N):
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    x = onw.normalise_inputs(net, T, p, Y)
+    st = df.State(mech, net, precision=df.DF_FP32, batch_cells=1024)
+    O = st.mlp_forward(dev(x.astype(np.float32)))
+    torch.cuda.synchronize()
+    Oo = onw.mlp_forward(net, x.astype(np.float32).astype(np.float64))
+    # |dY| <= out_std * |dO| <= 1e-3 * |dO|: 1e-4 on O keeps dY two decades inside 1e-6
+    np.testing.assert_allclose(host(O), Oo, atol=1e-4, rtol=0)
+
+
+@pytest.mark.parametrize("name,N,bn", [("small-fp32-4k", 1000, None), ("layer1d-30sp-1m", 3000, None),
+                                        ("layer1d-30sp-1m", 777, "160"), ("layer1d-30sp-1m", 777, "256"),
+                                        ("layer1d-30sp-1m", 777, "128")])
+def test_mlp_bf16_vs_rounded_oracle(df, name, N, bn, monkeypatch):
+    """tcgen05 BF16 path against the FP64 network with BF16 rounding at the same points
+    (input, weights, hidden activations); differences come only from FP32 accumulation
+    order and the tanh approximation, which can move a hidden activation by one BF16 ulp."""
+    if bn:
+        monkeypatch.setenv("DFGB_BN", bn)
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    x = onw.normalise_inputs(net, T, p, Y).astype(np.float32).astype(np.float64)
+    st = df.State(mech, net, precision=df.DF_BF16, batch_cells=512)
+    O = host(st.mlp_forward(dev(x.astype(np.float32))))
+    torch.cuda.synchronize()
+    Oq = onw.mlp_forward_rounded(net, x, onw.round_to_bf16)
+    err = np.abs(O - Oq)
+    assert err.max() <= 2e-2, err.max()
+    assert err.mean() <= 1e-3, err.mean()
+    # and against the exact FP64 network: BF16 storage error only
+    Oe = onw.mlp_forward(net, x)
+    assert np.abs(O - Oe).max() <= 5e-2
+
+
+# ---------------------------------------------------------------- a8-a10
+
+@pytest.mark.parametrize("name,N", WORKLOADS[:2])
+def test_eos_post_vs_oracle(df, name, N):
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    o = ope.state(mech, T, p, Y)
+    x = onw.normalise_inputs(net, T, p, Y)
+    O = onw.mlp_forward(net, x).astype(np.float32)
+    st = df.State(mech, net, batch_cells=1024)
+    Td, Yd = dev(T), dev(Y)
+    s = st.eos_post(dev(O), dev(o["h"]), Td, dev(p), Yd)
+    torch.cuda.synchronize()
+    Yn = onw.denormalise(net, Y, O.astype(np.float64))
+    Tn, so = ostep.solve_T(mech, p, Yn, o["h"], T)
+    assert np.array_equal(host(s), so)
+    np.testing.assert_allclose(host(Yd), Yn, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(host(Td), Tn, rtol=0, atol=1e-3)
+
+
+# ---------------------------------------------------------------- whole step
+
+def _step_check(df, mech, net, T, p, Y, prec, T_react, batch, dY_tol):
+    st = df.State(mech, net, precision=prec, T_react=T_react, batch_cells=batch)
+    Td, pd, Yd = dev(T), dev(p), dev(Y)
+    status = torch.full((T.shape[0],), -1, dtype=torch.int32, device=DEV)
+    nact = torch.zeros(1, dtype=torch.int64, device=DEV)
+    st.chem_step(Td, pd, Yd, status=status, n_active=nact)
+    rc, a, f, _ = st.step_summary()
+    To, Yo, so = ostep.chem_step(mech, net, T, p, Y, net.dt, T_react=T_react)
+    Tg, Yg, sg = host(Td), host(Yd), host(status)
+    assert np.array_equal(sg, so)
+    act = ostep.active_cells(T, T_react)
+    assert a == act.shape[0] == int(host(nact)[0])
+    inact = np.setdiff1d(np.arange(T.shape[0]), act)
+    assert np.array_equal(Tg[inact], T[inact]) and np.array_equal(Yg[:, inact], Y[:, inact])
+    dY = np.abs(Yg - Yo).max()
+    assert dY <= dY_tol, dY
+    # T recovery with the GPU's own Y' (network error kept out of the Newton check)
+    ok = act[so[act] == 0]
+    h0 = ope.state(mech, T[ok], p[ok], Y[:, ok])["h"]
+    Tr, sr = ostep.solve_T(mech, p[ok], Yg[:, ok], h0, T[ok])
+    assert np.all(sr == 0)
+    assert np.abs(Tg[ok] - Tr).max() <= 1e-3
+    return dY
+
+
+@pytest.mark.parametrize("name,N,T_react,batch", [("small-fp32-4k", 4096, 0.0, 1024),
+                                                  ("small-fp32-4k", 4096, 600.0, 1000),
+                                                  ("layer1d-30sp-1m", 6000, 0.0, 2048),
+                                                  ("react30-16m", 5000, 600.0, 700)])
+def test_chem_step_fp32(df, name, N, T_react, batch):
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    _step_check(df, mech, net, T, p, Y, df.DF_FP32, T_react, batch, 1e-6)
+
+
+@pytest.mark.parametrize("name,N,T_react,batch", [("small-fp32-4k", 4096, 600.0, 1024),
+                                                  ("layer1d-30sp-1m", 6000, 0.0, 2048),
+                                                  ("react30-16m", 5000, 600.0, 700)])
+def test_chem_step_bf16(df, name, N, T_react, batch):
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    dY = _step_check(df, mech, net, T, p, Y, df.DF_BF16, T_react, batch, 1e-4)
+    print(f"BF16 {name}: max |dY| vs FP64 = {dY:.3e}")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_full_size_sampled(df, prec):
+    """The 2^20-cell mixing-layer workload in the bench's launch configuration; 2048 sampled
+    cells are recomputed by the oracle (cells are independent)."""
+    mech, net, T, p, Y = synth.configs.build("layer1d-30sp-1m")
+    N = T.shape[0]
+    st = df.State(mech, net, precision=df.DF_FP32 if prec == "fp32" else df.DF_BF16, T_react=0.0)
+    Td, pd, Yd = dev(T), dev(p), dev(Y)
+    status = torch.empty(N, dtype=torch.int32, device=DEV)
+    st.chem_step(Td, pd, Yd, status=status)
+    torch.cuda.synchronize()
+    sel = np.sort(synth.Stream(1, "sample").integers(2048, N))
+    To, Yo, so = ostep.chem_step(mech, net, T[sel], p[sel], Y[:, sel], net.dt, T_react=0.0)
+    assert np.array_equal(host(status)[sel], so)
+    dY = np.abs(host(Yd)[:, sel] - Yo).max()
+    assert dY <= (1e-6 if prec == "fp32" else 1e-4), dY
+    h0 = ope.state(mech, T[sel], p[sel], Y[:, sel])["h"]
+    Tr, _ = ostep.solve_T(mech, p[sel], host(Yd)[:, sel], h0, T[sel])
+    assert np.abs(host(Td)[sel] - Tr).max() <= 1e-3
+
+
+def test_nonfinite_cells_and_empty_call(df):
+    mech, net, T, p, Y = synth.configs.build("small-fp32-4k", n_cells=300)
+    T = T.copy(); p = p.copy(); Y = Y.copy()
+    T[3] = np.nan
+    p[5] = np.inf
+    Y[2, 7] = np.nan
+    p[9] = -1.0
+    st = df.State(mech, net, T_react=0.0, batch_cells=128)
+    Td, Yd = dev(T), dev(Y)
+    status = torch.empty(300, dtype=torch.int32, device=DEV)
+    st.chem_step(Td, dev(p), Yd, status=status)
+    rc, a, f, _ = st.step_summary()
+    To, Yo, so = ostep.chem_step(mech, net, T, p, Y, net.dt, T_react=0.0)
+    assert np.array_equal(host(status), so)
+    assert f == int(np.count_nonzero(so[ostep.active_cells(T, 0.0)]))
+    assert rc == 3  # DF_ERR_NOT_CONVERGED: flagged cells were reported
+    empty = torch.empty(0, dtype=torch.float64, device=DEV)
+    st.chem_step(empty, empty, torch.empty(9, 0, dtype=torch.float64, device=DEV))
+
+
+def test_dt_mismatch_is_rejected(df):
+    mech, net, T, p, Y = synth.configs.build("small-fp32-4k", n_cells=16)
+    st = df.State(mech, net)
+    with pytest.raises(df.DFError) as e:
+        st.chem_step(dev(T), dev(p), dev(Y), dt=2e-7)
+    assert e.value.code == 5

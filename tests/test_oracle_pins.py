@@ -330,3 +330,15 @@ def test_oracle_is_independent_of_the_cuda_package():
         for f in list(pkg.rglob("*.py")) + list(pkg.rglob("*.cu")) + list(pkg.rglob("*.cuh")):
             txt = f.read_text()
             assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_round_to_bf16_matches_torch():
+    x = synth.Stream(9, "bf16").normal(4000) * 10.0 ** synth.Stream(9, "e").uniform(4000, -6, 6)
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(nw.round_to_bf16(x), ref)
+
+
+def test_rounded_mlp_with_identity_rounding_is_the_mlp():
+    net = synth.make_network([5, 7, 6, 3], 3, 11)
+    x = synth.Stream(3, "x").uniform(40 * 5, -2, 2).reshape(40, 5)
+    np.testing.assert_array_equal(nw.mlp_forward_rounded(net, x, lambda a: a), nw.mlp_forward(net, x))
