@@ -36,14 +36,16 @@ def enthalpy_cp(mech, T, p, Y):
     return s["h"], s["cp"], s["status"]
 
 
-def solve_T(mech, p, Y, h0, T_start, tol=1e-12, max_iter=100):
+def solve_T(mech, p, Y, h0, T_start, tol=1e-12, max_iter=100, return_iters=False):
     """Newton on h(T, p, Y) = h0 with slope cp, kept inside a bracket [lo, hi] that starts
-    at [50, 5000] K and shrinks with the sign of h - h0 (h rises with T); a step that
-    leaves the bracket is replaced by bisection. Stops when |dT| <= tol * T."""
+    at [50, 5000] K and shrinks with the sign of h - h0 (h rises with T). Stops when the
+    Newton step |dT| <= tol * T; a longer step that leaves the bracket is replaced by
+    bisection."""
     T = np.clip(np.asarray(T_start, dtype=np.float64).copy(), T_LO, T_HI)
     lo = np.full_like(T, T_LO)
     hi = np.full_like(T, T_HI)
     status = np.zeros(T.shape, dtype=np.int32)
+    iters = np.zeros(T.shape, dtype=np.int64)
     todo = np.ones(T.shape, dtype=bool)
     for _ in range(max_iter):
         if not todo.any():
@@ -57,14 +59,17 @@ def solve_T(mech, p, Y, h0, T_start, tol=1e-12, max_iter=100):
         lo[idx] = np.where(f <= 0.0, np.maximum(lo[idx], T[idx]), lo[idx])
         with np.errstate(divide="ignore", invalid="ignore"):
             Tn = T[idx] - f / cp
-        out = ~np.isfinite(Tn) | (Tn <= lo[idx]) | (Tn >= hi[idx])
+        # a step within tolerance has converged; only a longer step that leaves the
+        # bracket (or is not finite) is replaced by bisection
+        done = np.isfinite(Tn) & (np.abs(Tn - T[idx]) <= tol * T[idx])
+        out = ~done & (~np.isfinite(Tn) | (Tn <= lo[idx]) | (Tn >= hi[idx]))
         Tn = np.where(out, 0.5 * (lo[idx] + hi[idx]), Tn)
-        done = np.abs(Tn - T[idx]) <= tol * T[idx]
         T[idx] = Tn
+        iters[idx] += 1
         finished = done | bad
         todo[idx[finished]] = False
     status[todo] |= NOT_CONVERGED
-    return T, status
+    return (T, status, iters) if return_iters else (T, status)
 
 
 def chem_step(mech, net, T, p, Y, dt, T_react=600.0, newton_tol=1e-12, max_iter=100,

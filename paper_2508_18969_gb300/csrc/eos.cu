@@ -357,8 +357,10 @@ __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap 
         const double cp = cp_ig(m, Tn) + q.cp_dep * m.inv;
         if (f > 0.0) hi = fmin(hi, Tn); else lo = fmax(lo, Tn);
         double Tx = Tn - f / cp;
-        if (!(Tx > lo && Tx < hi)) Tx = 0.5 * (lo + hi);
+        // a step within tolerance has converged; only a longer step that leaves the
+        // bracket (or is not finite) is replaced by bisection
         const bool done = fabs(Tx - Tn) <= P.newton_tol * Tn;
+        if (!done && !(Tx > lo && Tx < hi)) Tx = 0.5 * (lo + hi);
         Tn = Tx;
         if (done) {
           conv = true;

@@ -8,10 +8,12 @@
 // becomes a multi-stage TMA ring and two TMEM accumulators, so the epilogue of one tile
 // overlaps the MMAs of the next.
 //
-// Warp roles (192 threads, one CTA per SM):
+// Warp roles (320 threads, one CTA per SM):
 //   warp 0      TMA producer (one lane)
 //   warp 1      TMEM allocator and MMA issuer (one lane)
-//   warps 2..5  epilogue; warp w reads TMEM lanes 32*(w%4) .. 32*(w%4)+31
+//   warps 2..9  epilogue; warp w reads TMEM lanes 32*(w%4) .. 32*(w%4)+31 and every other
+//               32-column chunk; results go through a shared-memory transpose so that each
+//               warp store writes whole 16-byte units of consecutive rows
 // Every mbarrier wait is bounded by a clock budget; on expiry the CTA sets the error word,
 // drains its own copies and MMAs, frees its TMEM and returns.
 #include "dfgb_internal.cuh"
@@ -26,7 +28,9 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int kRowBytes = 128;                 // K bytes per stage row (one swizzle span)
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;                   // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kStageOut = 32 * 32 * 4;         // per-warp output staging (32 rows x 128 B)
 constexpr long long kWaitBudget = 2000000000LL;  // ~1 s of SM clocks per wait
 constexpr int kSmemLimit = 232448;             // opt-in dynamic shared memory per block
 
@@ -171,12 +175,13 @@ __device__ __forceinline__ float gelu_fast(float x) {
 template <int BN>
 struct Cfg {
   static constexpr int kStageBytes = (BM + BN) * kRowBytes;
-  static constexpr int kStages0 = (kSmemLimit - 2048) / kStageBytes;
+  static constexpr int kStages0 = (kSmemLimit - 2048 - kEpiWarps * kStageOut) / kStageBytes;
   static constexpr int kStages = kStages0 > 8 ? 8 : kStages0;
   static constexpr int kAccStride = (BN + 31) / 32 * 32;
   static constexpr int kTmemCols = (2 * kAccStride <= 32) ? 32 : (2 * kAccStride <= 64) ? 64
                                    : (2 * kAccStride <= 128) ? 128 : (2 * kAccStride <= 256) ? 256 : 512;
-  static constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 1024 /*barriers*/;
+  static constexpr int kSmemBytes =
+      kStages * kStageBytes + kEpiWarps * kStageOut + 1024 /*align*/ + 1024 /*barriers*/;
 };
 
 template <bool FP8, int BN>
@@ -187,7 +192,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;                                   // kStages x 16 KB
   uint8_t* sB = smem + C::kStages * BM * kRowBytes;     // kStages x BN*128 B
-  uint64_t* bars = (uint64_t*)(smem + C::kStages * C::kStageBytes);
+  uint8_t* sOut = smem + C::kStages * C::kStageBytes;  // kEpiWarps x 4 KB
+  uint64_t* bars = (uint64_t*)(sOut + kEpiWarps * kStageOut);
   // bars: full[S], empty[S], tfull[2], tempty[2], drain
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull0 + 8 * a, 1);
-      mbar_init(tempty0 + 8 * a, 4);
+      mbar_init(tempty0 + 8 * a, kEpiWarps);
     }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -290,80 +296,94 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     }
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int q = warp & 3;                   // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;         // which of the alternating 32-column chunks
+    uint8_t* stg = sOut + (warp - 2) * kStageOut;
+    const int esz = g.out_kind == kXF32 ? 4 : (g.out_kind == kXBF16 ? 2 : 1);
+    const int U = 2 * esz;                    // 16-byte units per 32-column row segment
+    const int RB = 32 * esz;                  // bytes per row segment
     uint32_t j = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int a = j & 1;
       const uint32_t aph = (j >> 1) & 1;
       if (!mbar_wait(tfull0 + 8 * a, aph, abort, g.err)) break;
       tc_fence_after();
-      const int64_t m0 = (t / tiles_n) * BM;
+      const int64_t m0 = (t / tiles_n) * BM + q * 32;
       const int n0 = (int)(t % tiles_n) * BN;
-      const int64_t row = m0 + q * 32 + lane;
-      const bool row_ok = row < M;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 32 * half; c0 < BN; c0 += 64) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * C::kAccStride + c0, v);
         const int col0 = n0 + c0;
         // columns this tile owns: below N and below BN (the last chunk may run past BN)
         const int ncols = min(g.N - col0, BN - c0);
-        if (!row_ok || ncols <= 0) continue;
+        if (ncols <= 0) continue;             // warp-uniform
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const bool cok = i < ncols;
-          const int col = col0 + i;
           float x = v[i];
-          if (g.col_scale) x *= cok ? g.col_scale[col] : 0.0f;
-          x += cok ? g.bias[col] : 0.0f;
+          if (g.col_scale) x *= cok ? __ldg(g.col_scale + col0 + i) : 0.0f;
+          x += cok ? __ldg(g.bias + col0 + i) : 0.0f;
           if (g.gelu) x = gelu_fast(x);
           v[i] = x;
         }
-        const bool full = ncols >= 32;
+        // registers -> staging row `lane`, 16-byte units rotated so a quarter-warp's
+        // stores hit distinct banks
+        uint4 w[8];
         if (g.out_kind == kXF32) {
-          float* o = (float*)g.out + row * g.ldo + col0;
-          if (full && (g.ldo % 4 == 0)) {
 #pragma unroll
-            for (int i = 0; i < 32; i += 4)
-              *reinterpret_cast<float4*>(o + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-          } else {
-            for (int i = 0; i < ncols && i < 32; ++i) o[i] = v[i];
-          }
+          for (int u = 0; u < 8; ++u)
+            w[u] = make_uint4(__float_as_uint(v[4 * u]), __float_as_uint(v[4 * u + 1]),
+                              __float_as_uint(v[4 * u + 2]), __float_as_uint(v[4 * u + 3]));
         } else if (g.out_kind == kXBF16) {
-          __nv_bfloat16* o = (__nv_bfloat16*)g.out + row * g.ldo + col0;
-          if (full && (g.ldo % 8 == 0)) {
 #pragma unroll
-            for (int i = 0; i < 32; i += 8) {
-              uint4 w;
-              __nv_bfloat162 h0 = __floats2bfloat162_rn(v[i], v[i + 1]);
-              __nv_bfloat162 h1 = __floats2bfloat162_rn(v[i + 2], v[i + 3]);
-              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[i + 4], v[i + 5]);
-              __nv_bfloat162 h3 = __floats2bfloat162_rn(v[i + 6], v[i + 7]);
-              memcpy(&w.x, &h0, 4); memcpy(&w.y, &h1, 4);
-              memcpy(&w.z, &h2, 4); memcpy(&w.w, &h3, 4);
-              *reinterpret_cast<uint4*>(o + i) = w;
-            }
-          } else {
-            for (int i = 0; i < ncols && i < 32; ++i) o[i] = __float2bfloat16_rn(v[i]);
+          for (int u = 0; u < 4; ++u) {
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * u], v[8 * u + 1]);
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * u + 2], v[8 * u + 3]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * u + 4], v[8 * u + 5]);
+            __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * u + 6], v[8 * u + 7]);
+            memcpy(&w[u].x, &h0, 4); memcpy(&w[u].y, &h1, 4);
+            memcpy(&w[u].z, &h2, 4); memcpy(&w[u].w, &h3, 4);
           }
         } else {
-          __nv_fp8_e4m3* o = (__nv_fp8_e4m3*)g.out + row * g.ldo + col0;
           const float sc = g.out_scale;
-          if (full && (g.ldo % 16 == 0)) {
 #pragma unroll
-            for (int i = 0; i < 32; i += 16) {
-              uint8_t b[16];
+          for (int u = 0; u < 2; ++u) {
+            uint32_t wd[4];
 #pragma unroll
-              for (int e = 0; e < 16; ++e) {
-                __nv_fp8_e4m3 f(v[i + e] * sc);
-                b[e] = f.__x;
-              }
-              *reinterpret_cast<uint4*>(o + i) = *reinterpret_cast<uint4*>(b);
+            for (int e = 0; e < 4; ++e) {
+              const __nv_fp8x4_e4m3 f(make_float4(v[16 * u + 4 * e] * sc, v[16 * u + 4 * e + 1] * sc,
+                                                  v[16 * u + 4 * e + 2] * sc, v[16 * u + 4 * e + 3] * sc));
+              wd[e] = f.__x;
             }
-          } else {
-            for (int i = 0; i < ncols && i < 32; ++i) o[i] = __nv_fp8_e4m3(v[i] * sc);
+            w[u] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
           }
         }
+        const int rot = (U == 8) ? lane : (U == 4 ? (lane >> 1) : (lane >> 2));
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u < U)
+            *reinterpret_cast<uint4*>(stg + lane * RB + ((u + rot) & (U - 1)) * 16) = w[u];
+        __syncwarp();
+        // staging -> global: lane l stores unit (l % U) of row (l / U) + k * (32 / U)
+        const int rows_per = 32 / U;
+        const int u = lane % U;
+        const int ecount = 16 / esz;           // elements per unit
+        const int ufirst = u * ecount;
+        uint8_t* gbase = (uint8_t*)g.out + (m0 * g.ldo + col0) * esz;
+        for (int k = 0; k < U; ++k) {
+          const int r = lane / U + k * rows_per;
+          if (m0 + r >= M || ufirst >= ncols) continue;
+          const int rr = (U == 8) ? r : (U == 4 ? (r >> 1) : (r >> 2));
+          const uint8_t* src = stg + r * RB + ((u + rr) & (U - 1)) * 16;
+          uint8_t* dst = gbase + (int64_t)r * g.ldo * esz + ufirst * esz;
+          if (ufirst + ecount <= ncols) {
+            *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+          } else {
+            for (int e = 0; e < (ncols - ufirst) * esz; ++e) dst[e] = src[e];
+          }
+        }
+        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();

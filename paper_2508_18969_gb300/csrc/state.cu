@@ -379,7 +379,7 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
   P.lambda = mlp->lambda;
   P.T_react = opt->T_react;
   P.newton_tol = opt->newton_tol > 0 ? opt->newton_tol : 1e-10;
-  P.newton_max_iter = opt->newton_max_iter > 0 ? opt->newton_max_iter : 30;
+  P.newton_max_iter = opt->newton_max_iter > 0 ? opt->newton_max_iter : 50;
   P.spc = s->d_spc;
   P.Kmat = s->d_K;
   P.norm = s->d_norm;

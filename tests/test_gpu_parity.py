@@ -65,9 +65,10 @@ def test_compaction_bit_exact(df, N):
     c = int(host(cnt)[0])
     assert c == want.shape[0]
     assert np.array_equal(host(idx)[:c].astype(np.int64), want)
+    T2 = np.nan_to_num(T, nan=500.0, posinf=700.0)
     for thr, expect in ((-1.0, N), (1e9, 0)):
         st2 = df.State(mech, net, T_react=thr, batch_cells=256)
-        _, cnt2 = st2.active_compact(dev(np.nan_to_num(T, nan=500.0)))
+        _, cnt2 = st2.active_compact(dev(T2))
         assert int(host(cnt2)[0]) == expect
 
 
@@ -153,7 +154,11 @@ def test_eos_post_vs_oracle(df, name, N):
     Yn = onw.denormalise(net, Y, O.astype(np.float64))
     Tn, so = ostep.solve_T(mech, p, Yn, o["h"], T)
     assert np.array_equal(host(s), so)
-    np.testing.assert_allclose(host(Yd), Yn, rtol=0, atol=1e-12)
+    # the kernel forms Y' = Y (1 + lambda du Y^-lambda)^(1/lambda) with Y^-lambda in FP32
+    # (relative error ~2e-7), which only scales the increment Y' - Y; renormalisation
+    # spreads it over the species of a cell
+    tol = 2e-6 * np.sum(np.abs(Yn - Y), axis=0, keepdims=True) + 1e-15
+    assert np.all(np.abs(host(Yd) - Yn) <= tol)
     np.testing.assert_allclose(host(Td), Tn, rtol=0, atol=1e-3)
 
 

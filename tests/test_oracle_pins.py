@@ -268,6 +268,21 @@ def test_newton_round_trip(mech30):
     np.testing.assert_allclose(Ts, T, atol=1e-8, rtol=0)
 
 
+def test_newton_started_at_the_root_stops_at_once(mech30):
+    """h(T0) = h0 exactly gives a zero Newton step, which must end the iteration (and not
+    be mistaken for a step that leaves the bracket); from a nearby start the count stays
+    small for every cell of the uniform workload."""
+    mech, net, T, p, Y = synth.configs.build("small-fp32-4k", n_cells=1024)
+    h0 = pe.state(mech, T, p, Y)["h"]
+    Ts, st, it = step.solve_T(mech, p, Y, h0, T, return_iters=True)
+    assert np.all(st == 0) and np.all(it <= 2)
+    np.testing.assert_allclose(Ts, T, rtol=1e-14)
+    x = nw.normalise_inputs(net, T, p, Y)
+    Yn = nw.denormalise(net, Y, nw.mlp_forward(net, x))
+    Ts, st, it = step.solve_T(mech, p, Yn, h0, T, tol=1e-10, return_iters=True)
+    assert np.all(st == 0) and it.max() <= 8, np.bincount(it)
+
+
 def test_zero_network_output_leaves_state():
     """A network whose read-out is identically zero (and zero output mean) predicts no
     change: Y' = Y to round-off and, by enthalpy conservation, T' = T."""
