@@ -156,6 +156,24 @@ df_status df_eos_post(df_state* s, int64_t n_cells, const float* O, const double
                       double* T, const double* p, double* Y, int64_t ldY, int32_t* status,
                       void* stream);
 
+/* ---- allocation-free compaction ----
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory, e.g. a flow solver whose pool allocator owns the whole device, or
+ * a caller on a path where cudaMalloc's implicit device-wide synchronisation is not
+ * acceptable. It does what df_active_compact does (a0: idx receives the ascending indices of
+ * cells with T > T_react, count their number; device pointers, async on `stream`) without a
+ * df_state and without allocating: its scratch is a 256 KB array in the library's device
+ * image, resident on every device that loads the library until the process exits.
+ *   - n_cells above DF_COMPACT_STATIC_MAX_CELLS is rejected with DF_ERR_INVALID_ARG; the
+ *     reason is available from df_get_last_error(NULL).
+ *   - The first call on a device looks up the array's device address (once per device, with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the one array: calls that overlap on the GPU (different streams or host
+ *     threads) race and must be serialised by the caller. */
+#define DF_COMPACT_STATIC_MAX_CELLS ((int64_t)1 << 26)
+df_status df_active_compact_static(int64_t n_cells, double T_react, const double* T,
+                                   int32_t* idx, int64_t* count, void* stream);
+
 /* ---- kernel timing ---- */
 
 /* When enabled, df_chem_step records a pair of CUDA events on its stream around each of its

@@ -20,6 +20,8 @@ STATUS_NAMES = {0: "DF_OK", 1: "DF_ERR_INVALID_ARG", 2: "DF_ERR_CUDA", 3: "DF_ER
                 4: "DF_ERR_NONFINITE_INPUT", 5: "DF_ERR_DT_MISMATCH", 6: "DF_ERR_UNSUPPORTED",
                 7: "DF_ERR_OOM", 8: "DF_ERR_TIMEOUT"}
 
+DF_COMPACT_STATIC_MAX_CELLS = 1 << 26
+
 DF_CELL_NOT_CONVERGED = 1
 DF_CELL_NO_ROOT = 2
 DF_CELL_NONFINITE = 4
@@ -66,6 +68,7 @@ SIGNATURES = {
     "df_eos_pre": (_ST, [_VP, _I64, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]),
     "df_mlp_forward": (_ST, [_VP, _I64, _VP, _VP, _VP]),
     "df_eos_post": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _VP]),
+    "df_active_compact_static": (_ST, [_I64, C.c_double, _VP, _VP, _VP, _VP]),
     "df_profile_enable": (_ST, [_VP, C.c_int32]),
     "df_profile_read": (_ST, [_VP, C.c_int32, C.c_char_p, C.POINTER(_I64), C.POINTER(C.c_double),
                               C.POINTER(C.c_int32)]),

@@ -160,5 +160,19 @@ class State:
         return st
 
 
+def active_compact_static(T, T_react: float, stream=None):
+    """Allocation-free a0 (df_active_compact_static): no state, scratch in the library's
+    static device array. Returns (idx, count) tensors; the caller allocates them here, the
+    library does not."""
+    lib = L.load()
+    N = T.shape[0]
+    idx = torch.empty(max(N, 1), dtype=torch.int32, device=T.device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=T.device)
+    rc = lib.df_active_compact_static(N, float(T_react), _ptr(T), _ptr(idx), _ptr(cnt), _stream(stream))
+    if rc != L.DF_OK:
+        raise DFError(rc, lib.df_get_last_error(None).decode())
+    return idx, cnt
+
+
 def version() -> str:
     return L.load().df_version().decode()

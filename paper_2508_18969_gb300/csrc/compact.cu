@@ -10,7 +10,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kItems = 16;                         // cells per thread per chunk
-constexpr int kChunk = kThreads * kItems;          // 4096 cells per block
+constexpr int kChunk = kCompactChunk;              // 4096 cells per block
 constexpr int kWarps = kThreads / 32;
 constexpr int kCellNonfinite = 4;
 
@@ -113,3 +113,73 @@ cudaError_t launch_compact(int64_t n, double T_react, const double* T, int32_t* 
 }
 
 }  // namespace dfgb
+
+// ---- allocation-free variant -------------------------------------------------------
+// Some callers cannot allocate device memory: a flow solver that has handed the whole
+// device to its own pool allocator, or a caller on a path where the implicit device-wide
+// synchronisation of cudaMalloc/cudaFree is not acceptable. df_active_compact_static serves
+// them: the chunk counts and offsets live in the file-scope array below (256 KB, resident on
+// every device that loads this library until the process exits), so the call allocates
+// nothing. Every call shares this one array; the count pass writes every entry the scan
+// and scatter passes read, so nothing needs clearing, but calls that overlap on the GPU
+// (other streams, other host threads) race on it.
+#include "../../include/df.h"
+
+#include <mutex>
+
+namespace {
+
+constexpr int64_t kStaticMaxCells = DF_COMPACT_STATIC_MAX_CELLS;
+constexpr int64_t kStaticWords = 2 * ((kStaticMaxCells + dfgb::kCompactChunk - 1) / dfgb::kCompactChunk);
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) int64_t g_compact_scratch[kStaticWords];
+
+std::mutex g_static_mu;
+int64_t* g_static_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_compact_scratch on the current device, looked up once per device.
+// The name is only a host-side handle; the kernel must be given this address.
+cudaError_t static_scratch(int64_t** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_compact_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = static_cast<int64_t*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+namespace dfgb {
+void set_global_error(const char* msg);  // state.cu
+}
+
+extern "C" df_status df_active_compact_static(int64_t n_cells, double T_react, const double* T,
+                                              int32_t* idx, int64_t* count, void* stream) {
+  if (n_cells < 0 || !count || (n_cells > 0 && (!T || !idx))) {
+    dfgb::set_global_error("df_active_compact_static: bad arguments");
+    return DF_ERR_INVALID_ARG;
+  }
+  if (n_cells > kStaticMaxCells) {
+    dfgb::set_global_error("df_active_compact_static: n_cells exceeds DF_COMPACT_STATIC_MAX_CELLS");
+    return DF_ERR_INVALID_ARG;
+  }
+  int64_t* scratch = nullptr;
+  cudaError_t e = static_scratch(&scratch);
+  if (e == cudaSuccess)
+    e = dfgb::launch_compact(n_cells, T_react, T, idx, count, nullptr, scratch,
+                             (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    dfgb::set_global_error(cudaGetErrorString(e));
+    return DF_ERR_CUDA;
+  }
+  return DF_OK;
+}

@@ -80,6 +80,7 @@ cudaError_t launch_props(const EosParams& P, int64_t n, const double* T, const d
                          double* Z, cudaStream_t st);
 
 // ---- launchers (compact.cu) ----
+constexpr int64_t kCompactChunk = 4096;   // cells per block of the compaction kernels
 // Stable list of cells with T > T_react. Needs scratch of compact_scratch_words(n) int64.
 int64_t compact_scratch_words(int64_t n);
 cudaError_t launch_compact(int64_t n, double T_react, const double* T, int32_t* idx,

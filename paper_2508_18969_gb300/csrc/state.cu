@@ -250,6 +250,11 @@ df_status ensure_compact(df_state* s, int64_t n) {
 
 }  // namespace
 
+namespace dfgb {
+// Error text of entry points that take no state (read with df_get_last_error(NULL)).
+void set_global_error(const char* msg) { g_create_err = msg; }
+}  // namespace dfgb
+
 extern "C" {
 
 const char* df_version(void) { return kVersion; }

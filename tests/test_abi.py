@@ -89,3 +89,12 @@ def test_entry_points_reject_null_state(lib):
     assert lib.df_real_fluid_props(None, 10, None, None, None, 10, None, None, None, None, None) == _lib.DF_ERR_INVALID_ARG
     assert lib.df_active_compact(None, 10, None, None, None, None) == _lib.DF_ERR_INVALID_ARG
     lib.df_state_destroy(None)
+
+
+def test_static_compaction_rejects_oversize_before_device_use(lib):
+    from paper_2508_18969_gb300 import _lib
+    big = _lib.DF_COMPACT_STATIC_MAX_CELLS + 1
+    rc = lib.df_active_compact_static(big, 600.0, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), None)
+    assert rc == _lib.DF_ERR_INVALID_ARG
+    assert b"DF_COMPACT_STATIC_MAX_CELLS" in lib.df_get_last_error(None)
+    assert lib.df_active_compact_static(10, 600.0, None, None, None, None) == _lib.DF_ERR_INVALID_ARG
