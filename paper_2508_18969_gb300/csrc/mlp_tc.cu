@@ -33,6 +33,7 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kStageOut = 32 * 32 * 4;         // per-warp output staging (32 rows x 128 B)
 constexpr long long kWaitBudget = 2000000000LL;  // ~1 s of SM clocks per wait
 constexpr int kSmemLimit = 232448;             // opt-in dynamic shared memory per block
+constexpr uint32_t kSuspendNs = 200000;        // try_wait may park the thread this long
 
 struct TcArgs {
   RowMap rows;
@@ -67,10 +68,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -146,9 +147,9 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// Starts loading 32 consecutive FP32 columns of this thread's TMEM lane into r; the values
+// are valid only after tmem_wait(r).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
       "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -160,9 +161,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
         "=r"(r[31])
       : "r"(taddr)
       : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Waits for this thread's outstanding TMEM loads; r is passed through so no use of it can be
+// scheduled before the wait.
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+        "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
+        "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]),
+        "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]),
+        "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]),
+        "+r"(r[31])
+      :
+      : "memory");
 }
 
 __device__ __forceinline__ float gelu_fast(float x) {
@@ -184,7 +197,90 @@ struct Cfg {
       kStages * kStageBytes + kEpiWarps * kStageOut + 1024 /*align*/ + 1024 /*barriers*/;
 };
 
-template <bool FP8, int BN>
+// One 32-column chunk of the epilogue: scale, bias, GELU, quantise, transpose through the
+// warp's staging buffer, coalesced 16-byte stores of whole row segments.
+template <int OUTK, bool GELU, bool SCALE>
+__device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const TcArgs& g, int64_t M,
+                                               int64_t m0, int col0, int ncols, uint8_t* stg,
+                                               int lane) {
+  constexpr int esz = OUTK == kXF32 ? 4 : (OUTK == kXBF16 ? 2 : 1);
+  constexpr int U = 2 * esz;     // 16-byte units per 32-column row segment
+  constexpr int RB = 32 * esz;   // bytes per row segment
+  float v[32];
+  const float4* b4 = reinterpret_cast<const float4*>(g.bias + col0);  // zero padded to 32
+  const float4* s4 = reinterpret_cast<const float4*>(g.col_scale + col0);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const float4 b = __ldg(b4 + u);
+    float4 sc = make_float4(1.f, 1.f, 1.f, 1.f);
+    if (SCALE) sc = __ldg(s4 + u);
+    float x0 = __uint_as_float(r[4 * u]), x1 = __uint_as_float(r[4 * u + 1]);
+    float x2 = __uint_as_float(r[4 * u + 2]), x3 = __uint_as_float(r[4 * u + 3]);
+    if (SCALE) { x0 *= sc.x; x1 *= sc.y; x2 *= sc.z; x3 *= sc.w; }
+    x0 += b.x; x1 += b.y; x2 += b.z; x3 += b.w;
+    if (GELU) { x0 = gelu_fast(x0); x1 = gelu_fast(x1); x2 = gelu_fast(x2); x3 = gelu_fast(x3); }
+    v[4 * u] = x0; v[4 * u + 1] = x1; v[4 * u + 2] = x2; v[4 * u + 3] = x3;
+  }
+  uint4 w[U];
+  if (OUTK == kXF32) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      w[u] = make_uint4(__float_as_uint(v[4 * u]), __float_as_uint(v[4 * u + 1]),
+                        __float_as_uint(v[4 * u + 2]), __float_as_uint(v[4 * u + 3]));
+  } else if (OUTK == kXBF16) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * u], v[8 * u + 1]);
+      __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * u + 2], v[8 * u + 3]);
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * u + 4], v[8 * u + 5]);
+      __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * u + 6], v[8 * u + 7]);
+      memcpy(&w[u].x, &h0, 4); memcpy(&w[u].y, &h1, 4);
+      memcpy(&w[u].z, &h2, 4); memcpy(&w[u].w, &h3, 4);
+    }
+  } else {
+    const float sc = g.out_scale;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      uint32_t wd[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const __nv_fp8x4_e4m3 f(make_float4(v[16 * u + 4 * e] * sc, v[16 * u + 4 * e + 1] * sc,
+                                            v[16 * u + 4 * e + 2] * sc, v[16 * u + 4 * e + 3] * sc));
+        wd[e] = f.__x;
+      }
+      w[u] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    }
+  }
+  // registers -> staging row `lane`, units rotated so a quarter-warp's stores hit distinct banks
+  const int rot = (U == 8) ? lane : (U == 4 ? (lane >> 1) : (lane >> 2));
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+    *reinterpret_cast<uint4*>(stg + lane * RB + ((u + rot) & (U - 1)) * 16) = w[u];
+  __syncwarp();
+  // staging -> global: lane l stores unit (l % U) of row (l / U) + k * (32 / U)
+  constexpr int rows_per = 32 / U;
+  constexpr int ecount = 16 / esz;
+  const int u = lane % U;
+  const int ufirst = u * ecount;
+  uint8_t* gbase = (uint8_t*)g.out + (m0 * g.ldo + col0) * esz;
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    const int rr = lane / U + k * rows_per;
+    if (m0 + rr < M && ufirst < ncols) {
+      const int rrot = (U == 8) ? rr : (U == 4 ? (rr >> 1) : (rr >> 2));
+      const uint8_t* src = stg + rr * RB + ((u + rrot) & (U - 1)) * 16;
+      uint8_t* dst = gbase + (int64_t)rr * g.ldo * esz + ufirst * esz;
+      if (ufirst + ecount <= ncols) {
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+      } else {
+        for (int e = 0; e < (ncols - ufirst) * esz; ++e) dst[e] = src[e];
+      }
+    }
+  }
+  __syncwarp();
+}
+
+template <bool FP8, int BN, int OUTK, bool GELU, bool SCALE>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs g) {
   using C = Cfg<BN>;
@@ -299,9 +395,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     const int q = warp & 3;                   // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;         // which of the alternating 32-column chunks
     uint8_t* stg = sOut + (warp - 2) * kStageOut;
-    const int esz = g.out_kind == kXF32 ? 4 : (g.out_kind == kXBF16 ? 2 : 1);
-    const int U = 2 * esz;                    // 16-byte units per 32-column row segment
-    const int RB = 32 * esz;                  // bytes per row segment
     uint32_t j = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int a = j & 1;
@@ -310,80 +403,26 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
       tc_fence_after();
       const int64_t m0 = (t / tiles_n) * BM + q * 32;
       const int n0 = (int)(t % tiles_n) * BN;
-#pragma unroll 1
-      for (int c0 = 32 * half; c0 < BN; c0 += 64) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * C::kAccStride + c0, v);
-        const int col0 = n0 + c0;
-        // columns this tile owns: below N and below BN (the last chunk may run past BN)
-        const int ncols = min(g.N - col0, BN - c0);
-        if (ncols <= 0) continue;             // warp-uniform
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const bool cok = i < ncols;
-          float x = v[i];
-          if (g.col_scale) x *= cok ? __ldg(g.col_scale + col0 + i) : 0.0f;
-          x += cok ? __ldg(g.bias + col0 + i) : 0.0f;
-          if (g.gelu) x = gelu_fast(x);
-          v[i] = x;
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + a * C::kAccStride;
+      // chunks c0 = 32*half + 64*i; TMEM loads run one chunk ahead of the math
+      uint32_t r0[32], r1[32];
+      int c0 = 32 * half;
+      if (c0 < BN) tmem_ld32(tbase + c0, r0);
+      for (; c0 < BN; c0 += 128) {
+        tmem_wait(r0);
+        const int c1 = c0 + 64;
+        if (c1 < BN) tmem_ld32(tbase + c1, r1);
+        {
+          const int ncols = min(g.N - (n0 + c0), BN - c0);
+          if (ncols > 0)
+            epilogue_chunk<OUTK, GELU, SCALE>(r0, g, M, m0, n0 + c0, ncols, stg, lane);
         }
-        // registers -> staging row `lane`, 16-byte units rotated so a quarter-warp's
-        // stores hit distinct banks
-        uint4 w[8];
-        if (g.out_kind == kXF32) {
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            w[u] = make_uint4(__float_as_uint(v[4 * u]), __float_as_uint(v[4 * u + 1]),
-                              __float_as_uint(v[4 * u + 2]), __float_as_uint(v[4 * u + 3]));
-        } else if (g.out_kind == kXBF16) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * u], v[8 * u + 1]);
-            __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * u + 2], v[8 * u + 3]);
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * u + 4], v[8 * u + 5]);
-            __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * u + 6], v[8 * u + 7]);
-            memcpy(&w[u].x, &h0, 4); memcpy(&w[u].y, &h1, 4);
-            memcpy(&w[u].z, &h2, 4); memcpy(&w[u].w, &h3, 4);
-          }
-        } else {
-          const float sc = g.out_scale;
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            uint32_t wd[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const __nv_fp8x4_e4m3 f(make_float4(v[16 * u + 4 * e] * sc, v[16 * u + 4 * e + 1] * sc,
-                                                  v[16 * u + 4 * e + 2] * sc, v[16 * u + 4 * e + 3] * sc));
-              wd[e] = f.__x;
-            }
-            w[u] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-          }
-        }
-        const int rot = (U == 8) ? lane : (U == 4 ? (lane >> 1) : (lane >> 2));
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (u < U)
-            *reinterpret_cast<uint4*>(stg + lane * RB + ((u + rot) & (U - 1)) * 16) = w[u];
-        __syncwarp();
-        // staging -> global: lane l stores unit (l % U) of row (l / U) + k * (32 / U)
-        const int rows_per = 32 / U;
-        const int u = lane % U;
-        const int ecount = 16 / esz;           // elements per unit
-        const int ufirst = u * ecount;
-        uint8_t* gbase = (uint8_t*)g.out + (m0 * g.ldo + col0) * esz;
-        for (int k = 0; k < U; ++k) {
-          const int r = lane / U + k * rows_per;
-          if (m0 + r >= M || ufirst >= ncols) continue;
-          const int rr = (U == 8) ? r : (U == 4 ? (r >> 1) : (r >> 2));
-          const uint8_t* src = stg + r * RB + ((u + rr) & (U - 1)) * 16;
-          uint8_t* dst = gbase + (int64_t)r * g.ldo * esz + ufirst * esz;
-          if (ufirst + ecount <= ncols) {
-            *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
-          } else {
-            for (int e = 0; e < (ncols - ufirst) * esz; ++e) dst[e] = src[e];
-          }
-        }
-        __syncwarp();
+        if (c1 >= BN) break;
+        tmem_wait(r1);
+        if (c1 + 64 < BN) tmem_ld32(tbase + c1 + 64, r0);
+        const int ncols = min(g.N - (n0 + c1), BN - c1);
+        if (ncols > 0)
+          epilogue_chunk<OUTK, GELU, SCALE>(r1, g, M, m0, n0 + c1, ncols, stg, lane);
       }
       tc_fence_before();
       __syncwarp();
@@ -419,32 +458,46 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-template <bool FP8, int BN>
+template <bool FP8, int BN, int OUTK, bool GELU>
 cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream_t st) {
   using C = Cfg<BN>;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<FP8, BN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         C::kSmemBytes);
+  constexpr bool SCALE = FP8;
+  auto kern = tc_gemm_kernel<FP8, BN, OUTK, GELU, SCALE>;
+  static bool attr_done[64] = {false};  // per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr_done[dev]) {
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    attr_done[dev] = true;
   }
   const int64_t tiles = ((a.rows.nmax + BM - 1) / BM) * ((L.N + BN - 1) / BN);
   const unsigned grid = (unsigned)(tiles < num_sms ? (tiles > 0 ? tiles : 1) : num_sms);
-  tc_gemm_kernel<FP8, BN><<<grid, kThreads, C::kSmemBytes, st>>>(L.tmA, L.tmB, a);
+  kern<<<grid, kThreads, C::kSmemBytes, st>>>(L.tmA, L.tmB, a);
   return cudaGetLastError();
 }
 
+// Hidden layers: GELU, output in the input precision. Last layer: linear, FP32 output.
 template <bool FP8>
 cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream_t st) {
+  constexpr int HID = FP8 ? kXFP8 : kXBF16;
+  if (L.gelu) {
+    if (L.out_kind != HID) return cudaErrorInvalidValue;
+    switch (L.BN) {
+      case 64: return launch_bn<FP8, 64, HID, true>(L, a, num_sms, st);
+      case 128: return launch_bn<FP8, 128, HID, true>(L, a, num_sms, st);
+      case 160: return launch_bn<FP8, 160, HID, true>(L, a, num_sms, st);
+      case 208: return launch_bn<FP8, 208, HID, true>(L, a, num_sms, st);
+      case 256: return launch_bn<FP8, 256, HID, true>(L, a, num_sms, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (L.out_kind != kXF32) return cudaErrorInvalidValue;
   switch (L.BN) {
-    case 32: return launch_bn<FP8, 32>(L, a, num_sms, st);
-    case 64: return launch_bn<FP8, 64>(L, a, num_sms, st);
-    case 128: return launch_bn<FP8, 128>(L, a, num_sms, st);
-    case 160: return launch_bn<FP8, 160>(L, a, num_sms, st);
-    case 208: return launch_bn<FP8, 208>(L, a, num_sms, st);
-    case 256: return launch_bn<FP8, 256>(L, a, num_sms, st);
+    case 32: return launch_bn<FP8, 32, kXF32, false>(L, a, num_sms, st);
+    case 64: return launch_bn<FP8, 64, kXF32, false>(L, a, num_sms, st);
     default: return cudaErrorInvalidValue;
   }
 }

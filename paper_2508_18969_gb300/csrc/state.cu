@@ -105,13 +105,18 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
 }
 
-int pick_bn(int N) {
-  // Per-tile cost model: BN columns of work plus a fixed ~64-column share for the A
-  // operand stream and the epilogue; pick the cheapest tiling of N.
-  const int cand[] = {256, 208, 160, 128, 64, 32};
-  int best = 32;
+// Tile width of a layer: hidden layers from the compiled set {64, 128, 160, 208, 256}, the
+// read-out layer from {32, 64}. Per-tile cost model: BN columns of work plus a fixed
+// ~64-column share for the A operand stream and the epilogue; the cheapest tiling of N wins.
+int pick_bn(int N, bool hidden) {
+  static const int hid[] = {256, 208, 160, 128, 64};
+  static const int last[] = {64, 32};
+  const int* cand = hidden ? hid : last;
+  const int nc = hidden ? 5 : 2;
+  int best = cand[nc - 1];
   int64_t best_cost = INT64_MAX;
-  for (int bn : cand) {
+  for (int i = 0; i < nc; ++i) {
+    const int bn = cand[i];
     const int64_t cost = (int64_t)((N + bn - 1) / bn) * (bn + 64);
     if (cost < best_cost) {
       best_cost = cost;
@@ -402,9 +407,12 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
       delete s;
       return fail(nullptr, DF_ERR_INVALID_ARG, "NULL layer array");
     }
+    // bias and scales are zero padded to a multiple of 32 so the epilogue loads whole chunks
+    const int64_t Npad = round_up(Nl, 32);
     float* b = nullptr;
-    CK(dalloc(&b, Nl), "bias");
+    CK(dalloc(&b, Npad), "bias");
     s->bias.push_back(b);
+    CK(cudaMemset(b, 0, sizeof(float) * Npad), "memset");
     CK(cudaMemcpy(b, mlp->b[l], sizeof(float) * Nl, cudaMemcpyHostToDevice), "copy");
     if (!lp) {
       const int kp = (int)round_up(Kl, 8);
@@ -443,7 +451,8 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
         // dequantisation = weight scale / input activation scale
         const float in_scale = 1.0f;
         for (auto& v : sc) v /= in_scale;
-        CK(dalloc(&cs, Nl), "scales");
+        CK(dalloc(&cs, Npad), "scales");
+        CK(cudaMemset(cs, 0, sizeof(float) * Npad), "memset");
         CK(cudaMemcpy(cs, sc.data(), sizeof(float) * Nl, cudaMemcpyHostToDevice), "copy");
         s->act_scale.push_back(in_scale);
       }
@@ -477,10 +486,10 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
       TcLayer T{};
       T.N = s->widths[l + 1];
       T.K = s->widths[l];
-      T.BN = pick_bn(T.N);
-      if (const char* env = getenv("DFGB_BN")) {  // tile-width override for sweeps
+      T.BN = pick_bn(T.N, !last);
+      if (const char* env = getenv("DFGB_BN")) {  // hidden-layer tile-width override (sweeps)
         const int v = atoi(env);
-        if (v == 32 || v == 64 || v == 128 || v == 160 || v == 208 || v == 256) T.BN = v;
+        if (!last && (v == 64 || v == 128 || v == 160 || v == 208 || v == 256)) T.BN = v;
       }
       T.bias = s->bias[l];
       T.col_scale = s->col_scale[l];
