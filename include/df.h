@@ -90,7 +90,8 @@ typedef struct {
 typedef struct {
   int32_t precision;          /* df_precision */
   double T_react;             /* cells with T > T_react react (K); 0 lets every cell through */
-  double newton_tol;          /* stop when |dT| <= newton_tol * T; <= 0 selects 1e-10 */
+  double newton_tol;          /* stop when the Newton step |dT| <= newton_tol * T; <= 0 selects
+                                 1e-8 (the accepted step leaves an error of O(dT^2)) */
   int32_t newton_max_iter;    /* <= 0 selects 50 */
   int32_t device;             /* CUDA device ordinal the state lives on */
   int64_t batch_cells;        /* reacting cells per internal batch; <= 0 selects 2^20 */

@@ -56,6 +56,8 @@ struct EosParams {
   const double* spc;
   const double* Kmat;
   const double* norm;
+  const float* spc2;     // spc as double-float pairs (hi, lo), [n * kSpcStride * 2]
+  const float* K2;       // Kmat as double-float pairs, [n * n * 2]
   int* err;              // device error word
   int64_t* flagged;      // device count of cells flagged by eos_post (may be NULL)
   int64_t* newton_iters; // device sum of Newton iterations (may be NULL)

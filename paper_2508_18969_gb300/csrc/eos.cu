@@ -1,16 +1,22 @@
 // Equation-of-state kernels of the reaction step: a1-a5 (eos_pre), a8-a10 (eos_post) and
 // the real-fluid property evaluation. One thread per cell; species-major (SoA) field reads
-// are coalesced across the threads of a warp. FP64 throughout except the Box-Cox features
-// that feed the network (quantised to the network's precision anyway) and the FP32
-// closed-form seed of the cubic roots, which FP64 Newton steps then polish.
+// are coalesced across the threads of a warp.
 //
 // Peng-Robinson (Sec. 2 names the EoS; equations from Peng & Robinson 1976):
 //   sqrt(a_k(T)) = sqrt(a_c,k) [1 + kappa_k (1 - sqrt(T / Tc_k))] = s_k - r_k sqrt(T),
 //   a_m = sum_ij X_i X_j sqrt(a_i a_j) (1 - k_ij) = A0 - 2 A1 sqrt(T) + A2 T
-// where A0, A1, A2 are three quadratic forms of the composition. They are computed once
-// per composition, so every Newton iteration of the T-from-h solve is O(1) in the species
-// count.
+// with three quadratic forms A0, A1, A2 of the composition, computed once per composition,
+// so each Newton iteration of the T-from-h solve is O(1) in the species count.
+//
+// Precision plan (FP64 runs at 1/64 of the FP32 rate on this GPU):
+//   * every sum over species and species pairs (W_mix, b_m, the three forms, the mixture
+//     NASA-7 coefficients) is accumulated in double-float on the FP32 pipes (~1e-14);
+//   * the cubic root, departure enthalpy, c_p and the Newton update are FP64; reciprocals
+//     start from the FP32 reciprocal and take FP64 Newton refinements;
+//   * the Box-Cox features that feed the network are FP32 (they are quantised anyway), and
+//     so is the multiplicative increment of Y' (it only scales Y' - Y).
 #include "dfgb_internal.cuh"
+#include "ddfloat.cuh"
 
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -19,6 +25,7 @@ namespace dfgb {
 namespace {
 
 constexpr double kSQ2 = 1.41421356237309504880;
+constexpr double kInvR = 1.0 / kR;
 constexpr int kThreads = 128;
 constexpr int kCellNotConverged = 1;
 constexpr int kCellNoRoot = 2;
@@ -30,77 +37,101 @@ struct Mixture {
   double e[6];       // ideal-gas mass-specific enthalpy: h_ig(T) = sum_j e_j T^j, J/kg
   double A0, A1, A2; // a_m(T) = A0 - 2 A1 sqrt(T) + A2 T
   double bm;
+  double kb;         // 1 / (2 sqrt2 b_m)
 };
 
 struct SharedConsts {
-  const double* spc;   // [n * kSpcStride]
-  const double* K;     // [n * n]
+  const f2* spc;       // [n * kSpcStride] double-float species constants
+  const f2* K;         // [n * n] 1 - k_ij
   const double* norm;  // [2 K0 + 2 n]
 };
 
-__device__ SharedConsts load_consts(const EosParams& P, double* sm) {
-  const int nspc = P.n * kSpcStride, nk = P.n * P.n, nn = 2 * P.K0 + 2 * P.n;
-  for (int i = threadIdx.x; i < nspc; i += blockDim.x) sm[i] = P.spc[i];
-  for (int i = threadIdx.x; i < nk; i += blockDim.x) sm[nspc + i] = P.Kmat[i];
-  for (int i = threadIdx.x; i < nn; i += blockDim.x) sm[nspc + nk + i] = P.norm[i];
-  __syncthreads();
-  return SharedConsts{sm, sm + nspc, sm + nspc + nk};
+// 8-byte words of shared memory the constants take: FP64 normalisation, then the
+// double-float tables (one f2 per word).
+__host__ __device__ inline int consts_words(const EosParams& P) {
+  return 2 * P.K0 + 2 * P.n + P.n * kSpcStride + P.n * P.n;
 }
 
-// Mixture coefficients of one composition (a1, a2 and the ideal-gas part of a4).
+__device__ SharedConsts load_consts(const EosParams& P, double* sm) {
+  const int nspc = P.n * kSpcStride, nk = P.n * P.n, nn = 2 * P.K0 + 2 * P.n;
+  // layout: norm (FP64) first, then the float pairs
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) sm[i] = P.norm[i];
+  float* fs = reinterpret_cast<float*>(sm + nn);
+  for (int i = threadIdx.x; i < 2 * nspc; i += blockDim.x) fs[i] = P.spc2[i];
+  for (int i = threadIdx.x; i < 2 * nk; i += blockDim.x) fs[2 * nspc + i] = P.K2[i];
+  __syncthreads();
+  return SharedConsts{reinterpret_cast<const f2*>(fs), reinterpret_cast<const f2*>(fs + 2 * nspc),
+                      sm};
+}
+
+// FP64 reciprocal: FP32 seed, two FP64 Newton steps (relative error ~1 ulp).
+__device__ __forceinline__ double drcp(double x) {
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Mixture coefficients of one composition (a1, a2 and the ideal-gas part of a4). Y is
+// FP64 mass fractions; all sums run in double-float. ws is this thread's column of a
+// shared-memory scratch [2 NM][blockDim] (entry k at ws[k * blockDim]) holding ys_k, yr_k.
 template <int NM>
-__device__ void mixture(const double (&Y)[NM], int n, const SharedConsts& c, Mixture& m) {
-  double ys[NM], yr[NM];
-  double inv = 0.0, bsum = 0.0;
-  double e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0, e4 = 0.0, e5 = 0.0;
+__device__ void mixture(const double (&Y)[NM], int n, const SharedConsts& c, f2* ws,
+                        Mixture& m) {
+  const int stride = blockDim.x;
+  f2 inv = {0.f, 0.f}, bs = {0.f, 0.f};
+  f2 e0 = {0.f, 0.f}, e1 = e0, e2 = e0, e3 = e0, e4 = e0, e5 = e0;
 #pragma unroll
   for (int k = 0; k < NM; ++k) {
-    ys[k] = 0.0;
-    yr[k] = 0.0;
     if (k < n) {
-      const double* q = c.spc + k * kSpcStride;
-      const double y = Y[k] * q[0];
-      inv += y;
-      ys[k] = y * q[1];
-      yr[k] = y * q[2];
-      bsum = fma(y, q[3], bsum);
-      e0 = fma(y, q[4], e0);
-      e1 = fma(y, q[5], e1);
-      e2 = fma(y, q[6], e2);
-      e3 = fma(y, q[7], e3);
-      e4 = fma(y, q[8], e4);
-      e5 = fma(y, q[9], e5);
+      const f2* q = c.spc + k * kSpcStride;
+      const f2 y = f2_mul(f2_from(Y[k]), q[0]);  // Y_k / W_k
+      acc_add(inv, y);
+      ws[(2 * k) * stride] = f2_mul(y, q[1]);      // ys_k = y_k s_k
+      ws[(2 * k + 1) * stride] = f2_mul(y, q[2]);  // yr_k = y_k r_k
+      acc_fma(bs, y, q[3]);
+      acc_fma(e0, y, q[4]);
+      acc_fma(e1, y, q[5]);
+      acc_fma(e2, y, q[6]);
+      acc_fma(e3, y, q[7]);
+      acc_fma(e4, y, q[8]);
+      acc_fma(e5, y, q[9]);
     }
   }
   // Symmetric quadratic forms with K_ii = 1:
-  //   F0 = sum_ij K_ij ys_i ys_j, F1 = sum_ij K_ij ys_i yr_j, F2 = sum_ij K_ij yr_i yr_j.
-  double F0 = 0.0, F1 = 0.0, F2 = 0.0;
-#pragma unroll
-  for (int i = 0; i < NM; ++i) {
-    if (i < n) {
-      double Pi = 0.0, Qi = 0.0;
-      const double* Krow = c.K + i * n;
-#pragma unroll
-      for (int j = i + 1; j < NM; ++j) {
-        if (j < n) {
-          const double K = Krow[j];
-          Pi = fma(K, ys[j], Pi);
-          Qi = fma(K, yr[j], Qi);
-        }
-      }
-      F0 = fma(ys[i], fma(2.0, Pi, ys[i]), F0);
-      F1 = fma(ys[i], yr[i] + Qi, fma(yr[i], Pi, F1));
-      F2 = fma(yr[i], fma(2.0, Qi, yr[i]), F2);
+  //   F0 = sum_ij K_ij ys_i ys_j, F1 = sum_ij K_ij ys_i yr_j, F2 = sum_ij K_ij yr_i yr_j,
+  // as sum_i ys_i (ys_i + 2 P_i) etc. with P_i = sum_{j>i} K_ij ys_j, Q_i = sum_{j>i} K_ij yr_j.
+  f2 F0 = {0.f, 0.f}, F1 = F0, F2 = F0;
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    f2 Pi = {0.f, 0.f}, Qi = {0.f, 0.f};
+    const f2* Krow = c.K + i * n;
+#pragma unroll 4
+    for (int j = i + 1; j < n; ++j) {
+      const f2 K = Krow[j];
+      acc_fma(Pi, K, ws[(2 * j) * stride]);
+      acc_fma(Qi, K, ws[(2 * j + 1) * stride]);
     }
+    Pi = f2_fin(Pi);
+    Qi = f2_fin(Qi);
+    const f2 ysi = ws[(2 * i) * stride], yri = ws[(2 * i + 1) * stride];
+    acc_fma(F0, ysi, f2_add(ysi, f2_scale2(Pi)));
+    acc_fma(F1, ysi, f2_add(yri, Qi));
+    acc_fma(F1, yri, Pi);
+    acc_fma(F2, yri, f2_add(yri, f2_scale2(Qi)));
   }
-  const double Wm = 1.0 / inv;
+  const double invd = f2_to(f2_fin(inv));
+  const double Wm = drcp(invd);
   const double W2 = Wm * Wm;
-  m.inv = inv;
-  m.e[0] = e0; m.e[1] = e1; m.e[2] = e2; m.e[3] = e3; m.e[4] = e4; m.e[5] = e5;
-  m.A0 = W2 * F0;
-  m.A1 = W2 * F1;
-  m.A2 = W2 * F2;
-  m.bm = Wm * bsum;
+  m.inv = invd;
+  m.e[0] = f2_to(f2_fin(e0)); m.e[1] = f2_to(f2_fin(e1)); m.e[2] = f2_to(f2_fin(e2));
+  m.e[3] = f2_to(f2_fin(e3)); m.e[4] = f2_to(f2_fin(e4)); m.e[5] = f2_to(f2_fin(e5));
+  m.A0 = W2 * f2_to(f2_fin(F0));
+  m.A1 = W2 * f2_to(f2_fin(F1));
+  m.A2 = W2 * f2_to(f2_fin(F2));
+  m.bm = Wm * f2_to(f2_fin(bs));
+  m.kb = drcp(2.0 * kSQ2 * m.bm);
 }
 
 __device__ __forceinline__ double h_ig(const Mixture& m, double T) {
@@ -112,29 +143,29 @@ __device__ __forceinline__ double cp_ig(const Mixture& m, double T) {
              m.e[1]);
 }
 
+// Newton steps on the cubic from an FP32-accurate seed. The step uses an FP32 reciprocal of
+// f'(Z): that scales each correction by (1 + O(1e-7)), so every step still gains ~7 digits.
 __device__ __forceinline__ double cubic_polish(double Z, double c2, double c1, double c0) {
 #pragma unroll
-  for (int it = 0; it < 3; ++it) {
+  for (int it = 0; it < 2; ++it) {
     const double f = fma(fma(Z + c2, Z, c1), Z, c0);
     const double fp = fma(fma(3.0, Z, 2.0 * c2), Z, c1);
-    if (fp != 0.0) Z -= f / fp;
+    const float fpf = (float)fp;
+    if (fpf != 0.0f) Z = fma(-f, (double)__frcp_rn(fpf), Z);
   }
   return Z;
 }
 
-__device__ __forceinline__ double log_ratio(double Z, double B) {
-  return log((Z + (1.0 + kSQ2) * B) / (Z + (1.0 - kSQ2) * B));
-}
-
 __device__ __forceinline__ double g_dep(double Z, double A, double B) {
-  return Z - 1.0 - log(Z - B) - A / (2.0 * kSQ2 * B) * log_ratio(Z, B);
+  return Z - 1.0 - log(Z - B) -
+         A * drcp(2.0 * kSQ2 * B) * log((Z + (1.0 + kSQ2) * B) * drcp(Z + (1.0 - kSQ2) * B));
 }
 
 // Compressibility (a3): the real root of
 //   Z^3 - (1 - B) Z^2 + (A - 3B^2 - 2B) Z - (AB - B^2 - B^3) = 0
 // above B with least departure Gibbs energy (ties within 1e-12 keep the larger root).
 // Seeds come from the FP32 closed form (Cardano for one real root, the trigonometric form
-// for three), each then polished by three FP64 Newton steps on the cubic.
+// for three), each polished by FP64 Newton steps on the cubic.
 __device__ double select_Z(double A, double B, int& status) {
   const double c2 = B - 1.0;
   const double c1 = A - 3.0 * B * B - 2.0 * B;
@@ -161,7 +192,8 @@ __device__ double select_Z(double A, double B, int& status) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {  // k = 0, 1, 2 give descending seeds
     const float tk = m * cosf(phi - 2.0943951023931955f * (float)k);
-    const double Z = cubic_polish((double)tk - c2 * (1.0 / 3.0), c2, c1, c0);
+    const double Z = cubic_polish(cubic_polish((double)tk - c2 * (1.0 / 3.0), c2, c1, c0), c2,
+                                  c1, c0);
     if (Z > B) {
       const double g = g_dep(Z, A, B);
       if (g < gbest - 1e-12) {
@@ -180,31 +212,35 @@ struct PRPoint {
 
 // Real-fluid state at (T, p) of a composition (a2-a4), with the departure cp if asked.
 __device__ PRPoint pr_point(const Mixture& m, double T, double p, bool want_cp, int& status) {
+  const double iT = drcp(T);
   const double t = sqrt(T);
+  const double it = t * iT;                       // 1 / sqrt(T)
   const double am = fma(-2.0 * m.A1, t, fma(m.A2, T, m.A0));
-  const double dam = m.A2 - m.A1 / t;
+  const double dam = fma(-m.A1, it, m.A2);
   const double RT = kR * T;
-  const double A = am * p / (RT * RT);
-  const double B = m.bm * p / RT;
+  const double iRT = iT * kInvR;
+  const double A = am * p * iRT * iRT;
+  const double B = m.bm * p * iRT;
   PRPoint r;
   r.Z = select_Z(A, B, status);
   const double Zp = r.Z + (1.0 + kSQ2) * B;
   const double Zm = r.Z + (1.0 - kSQ2) * B;
-  const double L = log(Zp / Zm);
-  const double k = 1.0 / (2.0 * kSQ2 * m.bm);
-  r.h_dep = RT * (r.Z - 1.0) + (T * dam - am) * k * L;
+  const double iZm = drcp(Zm);
+  const double L = log(Zp * iZm);
+  const double tdam_am = fma(T, dam, -am);
+  r.h_dep = fma(RT, r.Z - 1.0, tdam_am * m.kb * L);
   r.cp_dep = 0.0;
   if (want_cp) {
-    const double d2am = m.A1 / (2.0 * T * t);
-    const double dB = -B / T;
-    const double dA = A * (dam / am - 2.0 / T);
+    const double d2am = 0.5 * m.A1 * it * iT;
+    const double dB = -B * iT;
+    const double dA = A * fma(dam, drcp(am), -2.0 * iT);
     const double Z = r.Z;
     const double FZ = fma(3.0 * Z, Z, -2.0 * (1.0 - B) * Z) + (A - 3.0 * B * B - 2.0 * B);
     const double FA = Z - B;
     const double FB = Z * Z - (6.0 * B + 2.0) * Z - (A - 2.0 * B - 3.0 * B * B);
     const double dZ = -(FA * dA + FB * dB) / FZ;
-    const double dL = (dZ + (1.0 + kSQ2) * dB) / Zp - (dZ + (1.0 - kSQ2) * dB) / Zm;
-    r.cp_dep = kR * (Z - 1.0) + RT * dZ + k * T * d2am * L + k * (T * dam - am) * dL;
+    const double dL = (dZ + (1.0 + kSQ2) * dB) * drcp(Zp) - (dZ + (1.0 - kSQ2) * dB) * iZm;
+    r.cp_dep = kR * (Z - 1.0) + RT * dZ + m.kb * (T * d2am * L + tdam_am * dL);
   }
   return r;
 }
@@ -230,6 +266,7 @@ __global__ void __launch_bounds__(kThreads) eos_pre_kernel(EosParams P, RowMap r
     int64_t ldx, float x_scale, int32_t* __restrict__ status) {
   extern __shared__ double sm[];
   const SharedConsts c = load_consts(P, sm);
+  f2* ws = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
   const int64_t nrow = valid_rows(rows);
   const int n = P.n, K0 = P.K0;
   const double* in_mean = c.norm;
@@ -246,11 +283,27 @@ __global__ void __launch_bounds__(kThreads) eos_pre_kernel(EosParams P, RowMap r
       Yk[k] = (k < n) ? Y[k * ldY + cell] : 0.0;
       finite = finite && isfinite(Yk[k]);
     }
+    // a5 first, so the FP64 mass fractions are dead once the mixture sums take them over
+    if (x) {
+      XT* xr = x + r * ldx;
+      xr[0] = to_x<XT>(finite ? (float)((Tc - in_mean[0]) * in_is[0]) : 0.0f, x_scale);
+      xr[1] = to_x<XT>(finite ? (float)((pc - in_mean[1]) * in_is[1]) : 0.0f, x_scale);
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        if (k < n) {
+          const float y = fmaxf((float)Yk[k], 0.0f);
+          const float bc = (y > 0.0f) ? (exp2f(lam * log2f(y)) - 1.0f) / lam : -1.0f / lam;
+          const float v = (bc - (float)in_mean[2 + k]) * (float)in_is[2 + k];
+          xr[2 + k] = to_x<XT>(finite ? v : 0.0f, x_scale);
+        }
+      }
+      for (int k = K0; k < ldx; ++k) xr[k] = to_x<XT>(0.0f, x_scale);
+    }
     int st = 0;
     double h = __longlong_as_double(0x7ff8000000000000LL), Z = h;
     if (finite) {
       Mixture m;
-      mixture<NM>(Yk, n, c, m);
+      mixture<NM>(Yk, n, c, ws, m);
       const PRPoint q = pr_point(m, Tc, pc, false, st);
       Z = q.Z;
       h = h_ig(m, Tc) + q.h_dep * m.inv;
@@ -261,21 +314,6 @@ __global__ void __launch_bounds__(kThreads) eos_pre_kernel(EosParams P, RowMap r
     if (h0) h0[r] = h;
     if (Zout) Zout[r] = Z;
     if (status) status[r] = st;
-    if (x) {
-      XT* xr = x + r * ldx;
-      xr[0] = to_x<XT>(finite ? (float)((Tc - in_mean[0]) * in_is[0]) : 0.0f, x_scale);
-      xr[1] = to_x<XT>(finite ? (float)((pc - in_mean[1]) * in_is[1]) : 0.0f, x_scale);
-#pragma unroll
-      for (int k = 0; k < NM; ++k) {
-        if (k < n) {
-          const float y = fmaxf((float)Yk[k], 0.0f);
-          const float bc = (y > 0.0f) ? (exp2f(lam * log2f(y)) - 1.0f) / lam : -1.0f / lam;
-          const float v = (float)(((double)bc - in_mean[2 + k]) * in_is[2 + k]);
-          xr[2 + k] = to_x<XT>(finite ? v : 0.0f, x_scale);
-        }
-      }
-      for (int k = K0; k < ldx; ++k) xr[k] = to_x<XT>(0.0f, x_scale);
-    }
   }
 }
 
@@ -289,7 +327,8 @@ __device__ __forceinline__ double ipow(double b, int m) {
   return r;
 }
 
-// a8-a10 for the valid rows of a batch.
+// a8-a10 for the valid rows of a batch. The new mass fractions are parked in shared memory
+// (one column per thread) until the Newton solve decides whether the cell is written.
 template <int NM>
 __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap rows,
     const float* __restrict__ O, int64_t ldo, const double* __restrict__ h0,
@@ -297,12 +336,17 @@ __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap 
     const int32_t* __restrict__ pre_status, int32_t* __restrict__ cell_status) {
   extern __shared__ double sm[];
   const SharedConsts c = load_consts(P, sm);
+  // after the constants: mixture scratch [2 NM][blockDim] f2, parking area [NM][blockDim] FP64
+  f2* ws = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
+  double* ypark = sm + consts_words(P) + 2 * NM * blockDim.x;
   const int64_t nrow = valid_rows(rows);
   const int n = P.n, K0 = P.K0;
   const double* out_mean = c.norm + 2 * K0;
   const double* out_std = c.norm + 2 * K0 + n;
   const double lam = P.lambda;
+  const float lamf = (float)P.lambda;
   const int mpow = P.inv_lambda;
+  const float mf = (float)P.inv_lambda;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrow;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cell = row_cell(rows, r);
@@ -318,15 +362,20 @@ __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap 
       if (k < n) {
         const double y = Y[k * ldY + cell];
         finite = finite && isfinite(y);
-        const double ldu = lam * fma(out_std[k], (double)Or[k], out_mean[k]);  // lambda du
+        const float ldu = lamf * fmaf((float)out_std[k], Or[k], (float)out_mean[k]);  // lambda du
         double yn;
         if (y >= 1e-30) {
           // Y' = (Y^lambda + lambda du)^(1/lambda) = Y (1 + eps)^m, eps = lambda du Y^-lambda;
-          // Y^-lambda only scales the small increment, so FP32 suffices for it.
-          const double eps = ldu * (double)exp2f(-(float)lam * log2f((float)y));
-          yn = (eps > -1.0) ? y * ipow(1.0 + eps, mpow) : 0.0;
+          // the increment delta = (1 + eps)^m - 1 only scales Y' - Y, so FP32 suffices.
+          const float eps = ldu * exp2f(-lamf * log2f((float)y));
+          if (eps <= -1.0f) {
+            yn = 0.0;
+          } else {
+            const float lg = mf * log1pf(eps);
+            yn = (lg < 80.0f) ? fma(y, (double)expm1f(lg), y) : y * ipow(1.0 + (double)eps, mpow);
+          }
         } else {
-          const double base = ((y > 0.0) ? pow(y, lam) : 0.0) + ldu;
+          const double base = ((y > 0.0) ? pow(y, lam) : 0.0) + (double)ldu;
           yn = (base > 0.0) ? ipow(base, mpow) : 0.0;
         }
         Yn[k] = yn;
@@ -337,11 +386,14 @@ __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap 
     double Tn = Told;
     int iters = 0;
     if (st == 0) {
-      const double iS = 1.0 / S;
+      const double iS = drcp(S);
 #pragma unroll
-      for (int k = 0; k < NM; ++k) Yn[k] *= iS;
+      for (int k = 0; k < NM; ++k) {
+        Yn[k] *= iS;
+        if (k < n) ypark[k * blockDim.x + threadIdx.x] = Yn[k];
+      }
       Mixture m;
-      mixture<NM>(Yn, n, c, m);
+      mixture<NM>(Yn, n, c, ws, m);
       double lo = kTLo, hi = kTHi;
       Tn = fmin(fmax(Told, lo), hi);
       bool conv = false;
@@ -356,7 +408,9 @@ __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap 
         const double f = h_ig(m, Tn) + q.h_dep * m.inv - h0c;
         const double cp = cp_ig(m, Tn) + q.cp_dep * m.inv;
         if (f > 0.0) hi = fmin(hi, Tn); else lo = fmax(lo, Tn);
-        double Tx = Tn - f / cp;
+        // an FP32 reciprocal of cp scales the step by 1 + O(1e-7): convergence stays quadratic
+        // down to ~1e-7 relative steps and is then linear with ratio ~1e-7
+        double Tx = fma(-f, (double)__frcp_rn((float)cp), Tn);
         // a step within tolerance has converged; only a longer step that leaves the
         // bracket (or is not finite) is replaced by bisection
         const bool done = fabs(Tx - Tn) <= P.newton_tol * Tn;
@@ -374,7 +428,7 @@ __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap 
       T[cell] = Tn;
 #pragma unroll
       for (int k = 0; k < NM; ++k)
-        if (k < n) Y[k * ldY + cell] = Yn[k];
+        if (k < n) Y[k * ldY + cell] = ypark[k * blockDim.x + threadIdx.x];
     }
     if (cell_status) cell_status[cell] = st;
     if (st && P.flagged) atomicAdd((unsigned long long*)P.flagged, 1ull);
@@ -393,6 +447,7 @@ __global__ void __launch_bounds__(kThreads) props_kernel(EosParams P, int64_t nc
     int64_t ldY, double* rho, double* h, double* cp, double* Zo) {
   extern __shared__ double sm[];
   const SharedConsts c = load_consts(P, sm);
+  f2* ws = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
   const int n = P.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncell;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -401,7 +456,7 @@ __global__ void __launch_bounds__(kThreads) props_kernel(EosParams P, int64_t nc
 #pragma unroll
     for (int k = 0; k < NM; ++k) Yk[k] = (k < n) ? Y[k * ldY + i] : 0.0;
     Mixture m;
-    mixture<NM>(Yk, n, c, m);
+    mixture<NM>(Yk, n, c, ws, m);
     int st = 0;
     const PRPoint q = pr_point(m, Tc, pc, cp != nullptr, st);
     if (rho) rho[i] = pc / (m.inv * q.Z * kR * Tc);
@@ -411,8 +466,26 @@ __global__ void __launch_bounds__(kThreads) props_kernel(EosParams P, int64_t nc
   }
 }
 
-size_t consts_smem(const EosParams& P) {
-  return sizeof(double) * (size_t)(P.n * kSpcStride + P.n * P.n + 2 * P.K0 + 2 * P.n);
+// Dynamic shared memory of an EoS block: constants, the per-thread mixture scratch
+// (2 NM double-float words) and, for eos_post, the parking area of Y' (NM doubles).
+size_t eos_smem(const EosParams& P, int NM, bool park) {
+  return sizeof(double) * ((size_t)consts_words(P) + (size_t)(2 * NM + (park ? NM : 0)) * kThreads);
+}
+
+// Opts a kernel into more than 48 KB of dynamic shared memory, once per device.
+template <auto Kern>
+cudaError_t smem_optin() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!done[dev]) {
+    e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    done[dev] = true;
+  }
+  return cudaSuccess;
 }
 
 int grid_for(int64_t nmax) {
@@ -425,25 +498,50 @@ int grid_for(int64_t nmax) {
   return (int)(need < cap ? need : cap);
 }
 
+template <int NM, typename XT>
+cudaError_t pre_launch(const EosParams& P, const RowMap& rows, const double* T, const double* p,
+                       const double* Y, int64_t ldY, double* h0, double* Z, XT* x, int64_t ldx,
+                       float xs, int32_t* status, cudaStream_t st) {
+  cudaError_t e = smem_optin<eos_pre_kernel<NM, XT>>();
+  if (e != cudaSuccess) return e;
+  eos_pre_kernel<NM, XT><<<grid_for(rows.nmax), kThreads, eos_smem(P, NM, false), st>>>(
+      P, rows, T, p, Y, ldY, h0, Z, x, ldx, xs, status);
+  return cudaGetLastError();
+}
+
 template <int NM>
 cudaError_t pre_nm(const EosParams& P, const RowMap& rows, const double* T, const double* p,
                    const double* Y, int64_t ldY, double* h0, double* Z, void* x, int xkind,
                    int64_t ldx, float xs, int32_t* status, cudaStream_t st) {
-  const size_t smem = consts_smem(P);
-  const int g = grid_for(rows.nmax);
   switch (xkind) {
     case kXBF16:
-      eos_pre_kernel<NM, __nv_bfloat16><<<g, kThreads, smem, st>>>(
-          P, rows, T, p, Y, ldY, h0, Z, (__nv_bfloat16*)x, ldx, xs, status);
-      break;
+      return pre_launch<NM>(P, rows, T, p, Y, ldY, h0, Z, (__nv_bfloat16*)x, ldx, xs, status, st);
     case kXFP8:
-      eos_pre_kernel<NM, __nv_fp8_e4m3><<<g, kThreads, smem, st>>>(
-          P, rows, T, p, Y, ldY, h0, Z, (__nv_fp8_e4m3*)x, ldx, xs, status);
-      break;
+      return pre_launch<NM>(P, rows, T, p, Y, ldY, h0, Z, (__nv_fp8_e4m3*)x, ldx, xs, status, st);
     default:
-      eos_pre_kernel<NM, float><<<g, kThreads, smem, st>>>(P, rows, T, p, Y, ldY, h0, Z,
-                                                            (float*)x, ldx, xs, status);
+      return pre_launch<NM>(P, rows, T, p, Y, ldY, h0, Z, (float*)x, ldx, xs, status, st);
   }
+}
+
+template <int NM>
+cudaError_t post_nm(const EosParams& P, const RowMap& rows, const float* O, int64_t ldo,
+                    const double* h0, double* T, const double* p, double* Y, int64_t ldY,
+                    const int32_t* pre_status, int32_t* cell_status, cudaStream_t st) {
+  cudaError_t e = smem_optin<eos_post_kernel<NM>>();
+  if (e != cudaSuccess) return e;
+  eos_post_kernel<NM><<<grid_for(rows.nmax), kThreads, eos_smem(P, NM, true), st>>>(
+      P, rows, O, ldo, h0, T, p, Y, ldY, pre_status, cell_status);
+  return cudaGetLastError();
+}
+
+template <int NM>
+cudaError_t props_nm(const EosParams& P, int64_t n, const double* T, const double* p,
+                     const double* Y, int64_t ldY, double* rho, double* h, double* cp, double* Z,
+                     cudaStream_t st) {
+  cudaError_t e = smem_optin<props_kernel<NM>>();
+  if (e != cudaSuccess) return e;
+  props_kernel<NM><<<grid_for(n), kThreads, eos_smem(P, NM, false), st>>>(P, n, T, p, Y, ldY,
+                                                                           rho, h, cp, Z);
   return cudaGetLastError();
 }
 
@@ -464,28 +562,17 @@ cudaError_t launch_eos_post(const EosParams& P, const RowMap& rows, const float*
                             int64_t ldY, const int32_t* pre_status, int32_t* cell_status,
                             cudaStream_t st) {
   if (rows.nmax <= 0) return cudaSuccess;
-  const size_t smem = consts_smem(P);
-  const int g = grid_for(rows.nmax);
   if (P.n <= 16)
-    eos_post_kernel<16><<<g, kThreads, smem, st>>>(P, rows, O, ldo, h0, T, p, Y, ldY,
-                                                   pre_status, cell_status);
-  else
-    eos_post_kernel<32><<<g, kThreads, smem, st>>>(P, rows, O, ldo, h0, T, p, Y, ldY,
-                                                   pre_status, cell_status);
-  return cudaGetLastError();
+    return post_nm<16>(P, rows, O, ldo, h0, T, p, Y, ldY, pre_status, cell_status, st);
+  return post_nm<32>(P, rows, O, ldo, h0, T, p, Y, ldY, pre_status, cell_status, st);
 }
 
 cudaError_t launch_props(const EosParams& P, int64_t n, const double* T, const double* p,
                          const double* Y, int64_t ldY, double* rho, double* h, double* cp,
                          double* Z, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const size_t smem = consts_smem(P);
-  const int g = grid_for(n);
-  if (P.n <= 16)
-    props_kernel<16><<<g, kThreads, smem, st>>>(P, n, T, p, Y, ldY, rho, h, cp, Z);
-  else
-    props_kernel<32><<<g, kThreads, smem, st>>>(P, n, T, p, Y, ldY, rho, h, cp, Z);
-  return cudaGetLastError();
+  if (P.n <= 16) return props_nm<16>(P, n, T, p, Y, ldY, rho, h, cp, Z, st);
+  return props_nm<32>(P, n, T, p, Y, ldY, rho, h, cp, Z, st);
 }
 
 }  // namespace dfgb

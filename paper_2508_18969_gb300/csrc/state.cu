@@ -29,6 +29,8 @@ struct df_state {
   double* d_spc = nullptr;
   double* d_K = nullptr;
   double* d_norm = nullptr;
+  float* d_spc2 = nullptr;               // double-float copies of the EoS tables
+  float* d_K2 = nullptr;
   int* d_err = nullptr;                  // kernel error word
   int64_t* d_count = nullptr;            // reacting cells of the last step
   int64_t* d_flagged = nullptr;          // flagged cells of the last step
@@ -150,7 +152,7 @@ size_t elem_of(int precision) {
 
 void free_state(df_state* s) {
   auto f = [](void* p) { if (p) cudaFree(p); };
-  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
+  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
   for (auto p : s->W32) f(p);
   for (auto p : s->bias) f(p);
   for (auto p : s->Wlp) f(p);
@@ -374,6 +376,21 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
   CK(cudaMemcpy(s->d_spc, spc.data(), sizeof(double) * spc.size(), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(s->d_K, K.data(), sizeof(double) * K.size(), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(s->d_norm, norm.data(), sizeof(double) * norm.size(), cudaMemcpyHostToDevice), "copy");
+  // double-float (hi, lo) copies: x = hi + lo with hi = fl32(x), lo = fl32(x - hi)
+  auto split = [](const std::vector<double>& v) {
+    std::vector<float> o(2 * v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      const float h = (float)v[i];
+      o[2 * i] = h;
+      o[2 * i + 1] = (float)(v[i] - (double)h);
+    }
+    return o;
+  };
+  const std::vector<float> spc2 = split(spc), K2 = split(K);
+  CK(dalloc(&s->d_spc2, spc2.size()), "constants");
+  CK(dalloc(&s->d_K2, K2.size()), "constants");
+  CK(cudaMemcpy(s->d_spc2, spc2.data(), sizeof(float) * spc2.size(), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(s->d_K2, K2.data(), sizeof(float) * K2.size(), cudaMemcpyHostToDevice), "copy");
   CK(dalloc(&s->d_err, 1), "error word");
   CK(cudaMemset(s->d_err, 0, sizeof(int)), "memset");
   CK(dalloc(&s->d_count, 1), "counters");
@@ -388,11 +405,13 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
   P.inv_lambda = m;
   P.lambda = mlp->lambda;
   P.T_react = opt->T_react;
-  P.newton_tol = opt->newton_tol > 0 ? opt->newton_tol : 1e-10;
+  P.newton_tol = opt->newton_tol > 0 ? opt->newton_tol : 1e-8;
   P.newton_max_iter = opt->newton_max_iter > 0 ? opt->newton_max_iter : 50;
   P.spc = s->d_spc;
   P.Kmat = s->d_K;
   P.norm = s->d_norm;
+  P.spc2 = s->d_spc2;
+  P.K2 = s->d_K2;
   P.err = s->d_err;
   P.flagged = s->d_flagged;
   P.newton_iters = s->d_iters;
