@@ -59,7 +59,8 @@ typedef int32_t df_status;
 typedef enum {
   DF_FP32 = 0,      /* SIMT FP32 GEMMs, accurate tanh: the plain FP32 step */
   DF_BF16 = 1,      /* tcgen05 BF16 GEMMs, FP32 accumulation, BF16 activations */
-  DF_FP8_E4M3 = 2   /* tcgen05 FP8 e4m3 GEMMs, per-output-channel weight scales */
+  DF_FP8_E4M3 = 2   /* tcgen05 FP8 e4m3 GEMMs, FP32 accumulation; weights e4m3(W/s_c) with
+                       per-output-channel s_c = max|W_c|/448, activations e4m3(32 v) */
 } df_precision;
 
 /* Mechanism constants (host pointers, deep-copied by df_state_create). */

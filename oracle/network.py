@@ -87,3 +87,45 @@ def mlp_forward_rounded(net, x, rnd):
         z = h @ rnd(net.W[l]).T + net.b[l][None, :]
         h = rnd(gelu_tanh(z)) if l < L - 1 else z
     return h
+
+
+E4M3_MAX = 448.0
+
+
+def round_to_e4m3(a):
+    """Round to the nearest FP8 e4m3 value (ties to even, saturating at +-448), via binary32:
+    the value a kernel gets when it converts an FP32 number with satfinite rounding.
+    e4m3: 3 mantissa bits, exponent bias 7, normals down to 2^-6, subnormals in steps of
+    2^-9. Returned as float64."""
+    f = np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float64)
+    mag = np.abs(f)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        e = np.floor(np.log2(np.where(mag > 0, mag, 1.0)))
+    e = np.clip(e, -6.0, 8.0)                 # below 2^-6 the quantum stays 2^-9
+    q = np.exp2(e - 3.0)
+    r = np.round(mag / q) * q                 # numpy rounds half to even
+    r = np.minimum(r, E4M3_MAX)
+    out = np.copysign(r, f)
+    return np.where(np.isnan(f), np.nan, out)
+
+
+def fp8_weight_rounding(W):
+    """Per-output-channel scaled e4m3 weights: row scale s = max|W_row| / 448, stored
+    e4m3(W / s), represented value e4m3(W / s) * s (binary32 scale)."""
+    W = np.asarray(W, dtype=np.float64)
+    amax = np.max(np.abs(W), axis=1, keepdims=True)
+    s = np.where(amax > 0, (amax.astype(np.float32) / np.float32(E4M3_MAX)).astype(np.float64), 1.0)
+    return round_to_e4m3(W / s) * s
+
+
+def mlp_forward_fp8(net, x, act_scale):
+    """MLP forward as an FP8 path stores it: input and hidden activations as e4m3(v * s) / s
+    with a static per-tensor scale s = act_scale, weights with per-output-channel scales;
+    sums and GELU in FP64."""
+    rq = lambda v: round_to_e4m3(np.asarray(v) * act_scale) / act_scale
+    h = rq(np.asarray(x, dtype=np.float64))
+    L = net.n_layers
+    for l in range(L):
+        z = h @ fp8_weight_rounding(net.W[l]).T + net.b[l][None, :]
+        h = rq(gelu_tanh(z)) if l < L - 1 else z
+    return h

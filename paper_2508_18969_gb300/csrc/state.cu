@@ -70,6 +70,10 @@ struct df_state {
 namespace {
 
 thread_local std::string g_create_err;
+// FP8 activations (network input and hidden layers) are stored as e4m3(v * 32): the inputs are
+// Z-scores and the hidden activations GELU outputs, both O(1-10), so x32 keeps them between
+// e4m3's smallest normal (2^-6) and its maximum (448).
+constexpr float kFp8ActScale = 32.0f;
 const char* kVersion = "dfgb 0.1.0 (sm_103a)";
 
 df_status fail(df_state* s, df_status code, const char* fmt, ...) {
@@ -468,7 +472,7 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
         }
         CK(cudaMemcpy(d, w.data(), w.size(), cudaMemcpyHostToDevice), "copy");
         // dequantisation = weight scale / input activation scale
-        const float in_scale = 1.0f;
+        const float in_scale = kFp8ActScale;
         for (auto& v : sc) v /= in_scale;
         CK(dalloc(&cs, Npad), "scales");
         CK(cudaMemset(cs, 0, sizeof(float) * Npad), "memset");

@@ -258,3 +258,35 @@ def test_dt_mismatch_is_rejected(df):
     with pytest.raises(df.DFError) as e:
         st.chem_step(dev(T), dev(p), dev(Y), dt=2e-7)
     assert e.value.code == 5
+
+
+# ---------------------------------------------------------------- FP8 e4m3
+
+@pytest.mark.parametrize("name,N,bn", [("small-fp32-4k", 1000, None), ("layer1d-30sp-1m", 3000, None),
+                                        ("layer1d-30sp-1m", 777, "256")])
+def test_mlp_fp8_vs_rounded_oracle(df, name, N, bn, monkeypatch):
+    """tcgen05 FP8 path against the FP64 network with e4m3 rounding at the same points
+    (input and hidden activations x32, per-output-channel weight scales). A hidden
+    activation whose FP32 accumulation lands on the other side of an e4m3 rounding boundary
+    differs by one e4m3 step (6-12 %), so the bound is on the maximum and the mean."""
+    if bn:
+        monkeypatch.setenv("DFGB_BN", bn)
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    x = onw.normalise_inputs(net, T, p, Y).astype(np.float32).astype(np.float64)
+    st = df.State(mech, net, precision=df.DF_FP8_E4M3, batch_cells=512)
+    O = host(st.mlp_forward(dev(x.astype(np.float32))))
+    torch.cuda.synchronize()
+    Oq = onw.mlp_forward_fp8(net, x, 32.0)
+    err = np.abs(O - Oq)
+    print(f"FP8 {name}: max {err.max():.3e} mean {err.mean():.3e} vs rounded oracle; "
+          f"max {np.abs(O - onw.mlp_forward(net, x)).max():.3e} vs exact")
+    assert err.max() <= 0.1, err.max()
+    assert err.mean() <= 5e-3, err.mean()
+
+
+@pytest.mark.parametrize("name,N,T_react,batch", [("layer1d-30sp-1m", 6000, 0.0, 2048),
+                                                  ("react30-16m", 5000, 600.0, 700)])
+def test_chem_step_fp8(df, name, N, T_react, batch):
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    dY = _step_check(df, mech, net, T, p, Y, df.DF_FP8_E4M3, T_react, batch, 1e-3)
+    print(f"FP8 {name}: max |dY| vs FP64 = {dY:.3e}")

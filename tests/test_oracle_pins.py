@@ -357,3 +357,13 @@ def test_rounded_mlp_with_identity_rounding_is_the_mlp():
     net = synth.make_network([5, 7, 6, 3], 3, 11)
     x = synth.Stream(3, "x").uniform(40 * 5, -2, 2).reshape(40, 5)
     np.testing.assert_array_equal(nw.mlp_forward_rounded(net, x, lambda a: a), nw.mlp_forward(net, x))
+
+
+def test_round_to_e4m3_matches_torch():
+    x = synth.Stream(10, "fp8").normal(6000) * 10.0 ** synth.Stream(10, "e").uniform(6000, -4, 2.3)
+    x = x[np.abs(x) <= 440.0]
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(nw.round_to_e4m3(x), ref)
+    # saturation and the representable extremes
+    assert nw.round_to_e4m3(1e6) == 448.0 and nw.round_to_e4m3(-500.0) == -448.0
+    assert nw.round_to_e4m3(2.0 ** -9) == 2.0 ** -9 and nw.round_to_e4m3(2.0 ** -11) == 0.0
