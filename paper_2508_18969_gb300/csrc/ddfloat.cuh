@@ -18,14 +18,51 @@ struct f2 {
 
 __device__ __forceinline__ f2 f2_make(float h, float l) { return f2{h, l}; }
 
-// Exact split of an FP64 number into hi + lo (lo carries the next 24 bits).
-__device__ __forceinline__ f2 f2_from(double x) {
-  const float h = __double2float_rn(x);
-  const float l = __double2float_rn(x - (double)h);
-  return f2{h, l};
+// Conversions between FP64 and FP32 done with integer operations: on this GPU the
+// F2F conversions run on the FP64 pipe, which is the scarce one. Values outside the ranges
+// handled by the bit manipulation (zero, very small or very large magnitudes, inf, NaN) take
+// the ordinary conversion instructions.
+
+// Exact FP32 -> FP64.
+__device__ __forceinline__ double f_to_d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 255u) return (double)f;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
 }
 
-__device__ __forceinline__ double f2_to(f2 a) { return (double)a.h + (double)a.l; }
+// FP64 -> FP32 by truncation of the significand (relative error < 2^-23); used for seeds and
+// for inputs whose FP32 rounding error is irrelevant.
+__device__ __forceinline__ float d_to_f_trunc(double x) {
+  const unsigned hi32 = (unsigned)__double2hiint(x);
+  const int e = (int)((hi32 >> 20) & 0x7FFu);
+  if (e < 897 || e > 1150) return __double2float_rn(x);
+  const unsigned lo32 = (unsigned)__double2loint(x);
+  return __uint_as_float((hi32 & 0x80000000u) | ((unsigned)(e - 896) << 23) |
+                         ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29));
+}
+
+// Split of an FP64 number into hi + lo: hi is x with its significand cut to 24 bits (exact),
+// lo the remaining 29 bits rounded to 24 (x == hi + lo to ~2^-53 relative).
+__device__ __forceinline__ f2 f2_from(double x) {
+  const unsigned hi32 = (unsigned)__double2hiint(x);
+  const int e = (int)((hi32 >> 20) & 0x7FFu);
+  if (e >= 897 && e <= 1100) {
+    const unsigned sign = hi32 & 0x80000000u;
+    const unsigned lo32 = (unsigned)__double2loint(x);
+    const unsigned hb = sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
+    // remainder r * 2^(e - 1075), formed as r * 2^-64 * 2^(e - 1011) to stay in range
+    float l = __fmul_rn(__fmul_rn(__uint2float_rn(lo32 & 0x1FFFFFFFu), 5.421010862427522e-20f),
+                        __int_as_float((e - 884) << 23));
+    l = __uint_as_float(__float_as_uint(l) | sign);
+    return f2{__uint_as_float(hb), l};
+  }
+  const float h = __double2float_rn(x);
+  return f2{h, __double2float_rn(x - (double)h)};
+}
+
+__device__ __forceinline__ double f2_to(f2 a) { return f_to_d(a.h) + f_to_d(a.l); }
 
 // TwoSum (Knuth): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {

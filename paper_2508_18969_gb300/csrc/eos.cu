@@ -44,12 +44,13 @@ struct SharedConsts {
   const f2* spc;       // [n * kSpcStride] double-float species constants
   const f2* K;         // [n * n] 1 - k_ij
   const double* norm;  // [2 K0 + 2 n]
+  const float* normf;  // the same in FP32 (for the FP32 feature and increment arithmetic)
 };
 
 // 8-byte words of shared memory the constants take: FP64 normalisation, then the
 // double-float tables (one f2 per word).
 __host__ __device__ inline int consts_words(const EosParams& P) {
-  return 2 * P.K0 + 2 * P.n + P.n * kSpcStride + P.n * P.n;
+  return 2 * P.K0 + 2 * P.n + P.n * kSpcStride + P.n * P.n + (P.K0 + P.n + 1);
 }
 
 __device__ SharedConsts load_consts(const EosParams& P, double* sm) {
@@ -59,14 +60,16 @@ __device__ SharedConsts load_consts(const EosParams& P, double* sm) {
   float* fs = reinterpret_cast<float*>(sm + nn);
   for (int i = threadIdx.x; i < 2 * nspc; i += blockDim.x) fs[i] = P.spc2[i];
   for (int i = threadIdx.x; i < 2 * nk; i += blockDim.x) fs[2 * nspc + i] = P.K2[i];
+  float* nf = fs + 2 * nspc + 2 * nk;
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) nf[i] = (float)P.norm[i];
   __syncthreads();
   return SharedConsts{reinterpret_cast<const f2*>(fs), reinterpret_cast<const f2*>(fs + 2 * nspc),
-                      sm};
+                      sm, nf};
 }
 
 // FP64 reciprocal: FP32 seed, two FP64 Newton steps (relative error ~1 ulp).
 __device__ __forceinline__ double drcp(double x) {
-  double r = (double)__frcp_rn((float)x);
+  double r = f_to_d(__frcp_rn(d_to_f_trunc(x)));
   double e = fma(-x, r, 1.0);
   r = fma(r, e, r);
   e = fma(-x, r, 1.0);
@@ -150,8 +153,8 @@ __device__ __forceinline__ double cubic_polish(double Z, double c2, double c1, d
   for (int it = 0; it < 2; ++it) {
     const double f = fma(fma(Z + c2, Z, c1), Z, c0);
     const double fp = fma(fma(3.0, Z, 2.0 * c2), Z, c1);
-    const float fpf = (float)fp;
-    if (fpf != 0.0f) Z = fma(-f, (double)__frcp_rn(fpf), Z);
+    const float fpf = d_to_f_trunc(fp);
+    if (fpf != 0.0f) Z = fma(-f, f_to_d(__frcp_rn(fpf)), Z);
   }
   return Z;
 }
@@ -174,17 +177,17 @@ __device__ double select_Z(double A, double B, int& status) {
   const double Q = 2.0 * c2 * c2 * c2 * (1.0 / 27.0) - c2 * c1 * (1.0 / 3.0) + c0;
   const double disc = 0.25 * Q * Q + P * P * P * (1.0 / 27.0);
   if (disc > 0.0) {
-    const float qf = (float)Q, pf = (float)P;
-    const float sq = sqrtf((float)disc);
+    const float qf = d_to_f_trunc(Q), pf = d_to_f_trunc(P);
+    const float sq = sqrtf(d_to_f_trunc(disc));
     const float u = cbrtf(-0.5f * qf - copysignf(sq, qf));
     const float t = (u != 0.0f) ? u - pf / (3.0f * u) : 0.0f;
-    const double Z = cubic_polish((double)t - c2 * (1.0 / 3.0), c2, c1, c0);
+    const double Z = cubic_polish(f_to_d(t) - c2 * (1.0 / 3.0), c2, c1, c0);
     if (!(Z > B)) status |= kCellNoRoot;
     return Z;
   }
-  const float pf = (float)P;
+  const float pf = d_to_f_trunc(P);
   const float m = (pf < 0.0f) ? 2.0f * sqrtf(-pf / 3.0f) : 0.0f;
-  float cphi = (pf < 0.0f) ? (3.0f * (float)Q / (2.0f * pf)) * sqrtf(-3.0f / pf) : 0.0f;
+  float cphi = (pf < 0.0f) ? (3.0f * d_to_f_trunc(Q) / (2.0f * pf)) * sqrtf(-3.0f / pf) : 0.0f;
   cphi = fminf(fmaxf(cphi, -1.0f), 1.0f);
   const float phi = acosf(cphi) * (1.0f / 3.0f);
   double best = __longlong_as_double(0x7ff8000000000000LL);
@@ -192,7 +195,7 @@ __device__ double select_Z(double A, double B, int& status) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {  // k = 0, 1, 2 give descending seeds
     const float tk = m * cosf(phi - 2.0943951023931955f * (float)k);
-    const double Z = cubic_polish(cubic_polish((double)tk - c2 * (1.0 / 3.0), c2, c1, c0), c2,
+    const double Z = cubic_polish(cubic_polish(f_to_d(tk) - c2 * (1.0 / 3.0), c2, c1, c0), c2,
                                   c1, c0);
     if (Z > B) {
       const double g = g_dep(Z, A, B);
@@ -269,8 +272,6 @@ __global__ void __launch_bounds__(kThreads) eos_pre_kernel(EosParams P, RowMap r
   f2* ws = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
   const int64_t nrow = valid_rows(rows);
   const int n = P.n, K0 = P.K0;
-  const double* in_mean = c.norm;
-  const double* in_is = c.norm + K0;
   const float lam = (float)P.lambda;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrow;
        r += (int64_t)gridDim.x * blockDim.x) {
@@ -286,14 +287,16 @@ __global__ void __launch_bounds__(kThreads) eos_pre_kernel(EosParams P, RowMap r
     // a5 first, so the FP64 mass fractions are dead once the mixture sums take them over
     if (x) {
       XT* xr = x + r * ldx;
-      xr[0] = to_x<XT>(finite ? (float)((Tc - in_mean[0]) * in_is[0]) : 0.0f, x_scale);
-      xr[1] = to_x<XT>(finite ? (float)((pc - in_mean[1]) * in_is[1]) : 0.0f, x_scale);
+      const float* mf = c.normf;        // in_mean
+      const float* isf = c.normf + K0;  // 1 / in_std
+      xr[0] = to_x<XT>(finite ? (d_to_f_trunc(Tc) - mf[0]) * isf[0] : 0.0f, x_scale);
+      xr[1] = to_x<XT>(finite ? (d_to_f_trunc(pc) - mf[1]) * isf[1] : 0.0f, x_scale);
 #pragma unroll
       for (int k = 0; k < NM; ++k) {
         if (k < n) {
-          const float y = fmaxf((float)Yk[k], 0.0f);
+          const float y = fmaxf(d_to_f_trunc(Yk[k]), 0.0f);
           const float bc = (y > 0.0f) ? (exp2f(lam * log2f(y)) - 1.0f) / lam : -1.0f / lam;
-          const float v = (bc - (float)in_mean[2 + k]) * (float)in_is[2 + k];
+          const float v = (bc - mf[2 + k]) * isf[2 + k];
           xr[2 + k] = to_x<XT>(finite ? v : 0.0f, x_scale);
         }
       }
@@ -341,8 +344,8 @@ __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap 
   double* ypark = sm + consts_words(P) + 2 * NM * blockDim.x;
   const int64_t nrow = valid_rows(rows);
   const int n = P.n, K0 = P.K0;
-  const double* out_mean = c.norm + 2 * K0;
-  const double* out_std = c.norm + 2 * K0 + n;
+  const float* out_mean = c.normf + 2 * K0;
+  const float* out_std = c.normf + 2 * K0 + n;
   const double lam = P.lambda;
   const float lamf = (float)P.lambda;
   const int mpow = P.inv_lambda;
@@ -362,20 +365,20 @@ __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap 
       if (k < n) {
         const double y = Y[k * ldY + cell];
         finite = finite && isfinite(y);
-        const float ldu = lamf * fmaf((float)out_std[k], Or[k], (float)out_mean[k]);  // lambda du
+        const float ldu = lamf * fmaf(out_std[k], Or[k], out_mean[k]);  // lambda du
         double yn;
         if (y >= 1e-30) {
           // Y' = (Y^lambda + lambda du)^(1/lambda) = Y (1 + eps)^m, eps = lambda du Y^-lambda;
           // the increment delta = (1 + eps)^m - 1 only scales Y' - Y, so FP32 suffices.
-          const float eps = ldu * exp2f(-lamf * log2f((float)y));
+          const float eps = ldu * exp2f(-lamf * log2f(d_to_f_trunc(y)));
           if (eps <= -1.0f) {
             yn = 0.0;
           } else {
             const float lg = mf * log1pf(eps);
-            yn = (lg < 80.0f) ? fma(y, (double)expm1f(lg), y) : y * ipow(1.0 + (double)eps, mpow);
+            yn = (lg < 80.0f) ? fma(y, f_to_d(expm1f(lg)), y) : y * ipow(1.0 + f_to_d(eps), mpow);
           }
         } else {
-          const double base = ((y > 0.0) ? pow(y, lam) : 0.0) + (double)ldu;
+          const double base = ((y > 0.0) ? pow(y, lam) : 0.0) + f_to_d(ldu);
           yn = (base > 0.0) ? ipow(base, mpow) : 0.0;
         }
         Yn[k] = yn;
@@ -396,25 +399,32 @@ __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap 
       mixture<NM>(Yn, n, c, ws, m);
       double lo = kTLo, hi = kTHi;
       Tn = fmin(fmax(Told, lo), hi);
-      bool conv = false;
+      bool conv = false, need_cp = true;
+      double icp = 0.0;
       for (int it = 0; it < P.newton_max_iter; ++it) {
         ++iters;
         int s2 = 0;
-        const PRPoint q = pr_point(m, Tn, pc, true, s2);
+        const PRPoint q = pr_point(m, Tn, pc, need_cp, s2);
         if (s2) {
           st |= s2;
           break;
         }
         const double f = h_ig(m, Tn) + q.h_dep * m.inv - h0c;
-        const double cp = cp_ig(m, Tn) + q.cp_dep * m.inv;
+        // Chord steps: the slope of the first iteration is reused while the iterates stay
+        // close (each step contracts the error by ~|1 - cp(T)/cp(T0)| ~ 1e-5 there); an FP32
+        // reciprocal of cp scales the step by 1 + O(1e-7) on top.
+        if (need_cp) icp = f_to_d(__frcp_rn(d_to_f_trunc(cp_ig(m, Tn) + q.cp_dep * m.inv)));
         if (f > 0.0) hi = fmin(hi, Tn); else lo = fmax(lo, Tn);
-        // an FP32 reciprocal of cp scales the step by 1 + O(1e-7): convergence stays quadratic
-        // down to ~1e-7 relative steps and is then linear with ratio ~1e-7
-        double Tx = fma(-f, (double)__frcp_rn((float)cp), Tn);
+        double Tx = fma(-f, icp, Tn);
         // a step within tolerance has converged; only a longer step that leaves the
-        // bracket (or is not finite) is replaced by bisection
+        // bracket (or is not finite) is replaced by bisection, after which the slope is
+        // evaluated afresh
         const bool done = fabs(Tx - Tn) <= P.newton_tol * Tn;
-        if (!done && !(Tx > lo && Tx < hi)) Tx = 0.5 * (lo + hi);
+        need_cp = false;
+        if (!done && !(Tx > lo && Tx < hi)) {
+          Tx = 0.5 * (lo + hi);
+          need_cp = true;
+        }
         Tn = Tx;
         if (done) {
           conv = true;
