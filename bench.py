@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=16384, help="cells of the CPU oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch", type=int, default=0, help="reacting cells per internal batch")
     return ap.parse_args()
 
 
@@ -222,8 +223,8 @@ def run_ours(args):
     N = args.cells or w.n_cells
     mech, net, T, p, Y = synth.configs.build(args.workload, n_cells=N, field_seed=w.seed + rank)
     prec = {"bf16": df.DF_BF16, "fp32": df.DF_FP32, "fp8": df.DF_FP8_E4M3}[args.precision]
-    st = df.State(mech, net, precision=prec, T_react=w.T_react, device=local,
-                  batch_cells=min(N, 1 << 20))
+    batch = args.batch or min(N, 1 << 22)
+    st = df.State(mech, net, precision=prec, T_react=w.T_react, device=local, batch_cells=batch)
     Td = torch.tensor(T, device=dev)
     pd = torch.tensor(p, device=dev)
     Yd = torch.tensor(Y, device=dev).contiguous()
@@ -259,6 +260,22 @@ def run_ours(args):
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = max_over_ranks(world, ms, local)
     value = world * N / (ms_max * 1e-3)
+
+    # the same step replayed as one CUDA graph (df_graph_*), timed the same way
+    g = st.graph(Td, pd, Yd, status=status)
+    for _ in range(2):
+        g.launch()
+    torch.cuda.synchronize()
+    barrier(world)
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        g.launch()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = max_over_ranks(world, g0.elapsed_time(g1) / args.steps, local)
+    g.close()
 
     # end to end: host (pinned) fields in, device step, host fields out, every step
     e2e = None
@@ -298,7 +315,7 @@ def run_ours(args):
     fp32 = None
     if prec != df.DF_FP32 and args.fp32_steps > 0:
         s32 = df.State(mech, net, precision=df.DF_FP32, T_react=w.T_react, device=local,
-                       batch_cells=min(N, 1 << 20))
+                       batch_cells=batch)
         s32.chem_step(Td, pd, Yd, status=status)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -320,61 +337,71 @@ def run_ours(args):
 
     # roofline of the dominant kernel family (CUDA-event times recorded on the launch stream)
     pk, pk_src = peaks()
-    rows = n_act  # reacting cells per step (one batch at this size)
+    rows = n_act  # reacting cells per step
     fl = layer_flops(w.widths, rows)
     iters_per_cell = iters / max(n_act, 1)
     pre_f, post_f = eos_fp64_flops(mech.n, iters_per_cell)
     fams = {k: (v[0], v[1]) for k, v in prof.items()}
+    roofs = {}
+    for fam, (launches, tot) in fams.items():
+        avg_s = tot / args.steps * 1e-3   # family time per step (all batches of the step)
+        if fam.startswith("layer") and prec != df.DF_FP32:
+            l = int(fam[5:])
+            peak = pk["bf16_tflops_sustained"] * (2.0 if prec == df.DF_FP8_E4M3 else 1.0)
+            ach = fl[l] / avg_s / 1e12
+            roofs[fam] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                          "frac": ach / peak, "traffic": None, "kernel": f"tc_gemm {fam}",
+                          "peak_source": f"bf16_tflops_sustained ({pk_src})" +
+                          (" x2 nominal fp8/bf16 ratio" if prec == df.DF_FP8_E4M3 else "")}
+        elif fam.startswith("layer"):
+            l = int(fam[5:])
+            peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            ach = fl[l] / avg_s / 1e12
+            roofs[fam] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                          "frac": ach / peak, "traffic": None, "kernel": f"sgemm {fam}",
+                          "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"}
+        elif fam in ("eos_pre", "eos_post"):
+            # FP64-equivalent flops of the method; the kernels run the O(n^2) sums in
+            # double-float on the FP32 pipes (~12 FP32 instructions per FP64-equivalent
+            # multiply-add), so the ALU ceiling is the FP32 issue rate divided by 12, x2 flops
+            per = pre_f if fam == "eos_pre" else post_f
+            peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 12.0 * 2.0 / 1e12
+            ach = per * rows / avg_s / 1e12
+            roofs[fam] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                          "frac": ach / peak, "traffic": None, "kernel": fam,
+                          "peak_source": "double-float on FP32 pipes: 152 SMs x 128 lanes x max "
+                                         "SM clock / 12 instr per FP64-equivalent FMA x 2 flop"}
+        else:
+            ach = (12.0 * N) / avg_s / 1e9
+            roofs[fam] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                          "frac": ach / pk["hbm_gbs"], "traffic": None, "kernel": fam,
+                          "peak_source": f"hbm_gbs ({pk_src})"}
     dom = max(fams, key=lambda k: fams[k][1])
-    launches, tot = fams[dom]
-    avg_s = tot / launches * 1e-3
-    if dom.startswith("layer") and prec != df.DF_FP32:
-        l = int(dom[5:])
-        peak = pk["bf16_tflops_sustained"] * (2.0 if prec == df.DF_FP8_E4M3 else 1.0)
-        ach = fl[l] / avg_s / 1e12
-        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "kernel": f"tc_gemm {dom}",
-                "peak_source": f"bf16_tflops_sustained ({pk_src})" + (" x2 nominal fp8/bf16" if prec == df.DF_FP8_E4M3 else "")}
-    elif dom.startswith("layer"):
-        l = int(dom[5:])
-        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        ach = fl[l] / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": f"sgemm {dom}",
-                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"}
-    elif dom in ("eos_pre", "eos_post"):
-        per = pre_f if dom == "eos_pre" else post_f
-        peak = 1.25
-        ach = per * rows / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": dom,
-                "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300 table), algorithmic FP64 flops"}
-    else:
-        ach = (12.0 * N) / avg_s / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": None, "kernel": dom,
-                "peak_source": f"hbm_gbs ({pk_src})"}
+    roof = roofs[dom]
 
     cpu = None
     errs = None
     if not args.no_cpu_baseline:
         cpu, errs = cpu_oracle_leg(mech, net, T, p, Y, sel, w.T_react, gpu_first)
 
-    kpl = 3 + 1 + len(w.widths) - 1 + 1   # compaction (3) + eos_pre + layers + eos_post
-    nb = (N + (1 << 20) - 1) // (1 << 20)
+    kpl = len(w.widths) - 1 + 2            # per batch: eos_pre + layers + eos_post
+    nb = (N + batch - 1) // batch
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"bf16": "bf16+f64", "fp32": "f32+f64", "fp8": "fp8e4m3+f64"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": args.workload, "n_cells": N, "n_species": mech.n,
+        "config": {"workload": args.workload, "n_cells": N, "n_species": mech.n, "batch_cells": batch,
                    "network": "-".join(str(x) for x in w.widths), "precision": args.precision,
                    "reacting_cells": int(n_act), "T_react_K": w.T_react,
                    "l2": "inputs larger than L2 (fields 8*(2+n)*N bytes, activations GBs)"},
         "clocks": clk.summary(),
         "e2e": e2e,
-        "gpu_launches": int(kpl * nb * args.steps),
+        "gpu_launches": int((3 + kpl * nb) * args.steps),
+        "graph_ms_per_step": graph_ms,
+        "graph_value": world * N / (graph_ms * 1e-3),
         "roofline": roof,
+        "roofline_by_family": roofs,
         "cpu_baseline": cpu,
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in fams.items()},
         "newton_iterations_per_cell": iters_per_cell,

@@ -122,6 +122,22 @@ df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const
                        double* Y, int64_t ldY, int32_t* cell_status, int64_t* n_active_out,
                        void* stream);
 
+/* ---- CUDA-graph execution of the step ----
+ * A df_graph is one df_chem_step with fixed arguments (sizes, dt and the device buffers T, p,
+ * Y, cell_status, n_active_out) captured into an executable CUDA graph, so a time loop replays
+ * the whole step (compaction, EoS, every network layer, Newton) with one launch. The state and
+ * the buffers must outlive the graph; the graph reads and writes whatever the buffers hold
+ * when it runs. df_graph_create runs no kernel: it first makes sure the state's scratch fits
+ * n_cells (allocating if needed), then captures on an internal stream. */
+typedef struct df_graph df_graph;
+df_status df_graph_create(df_state* s, int64_t n_cells, double dt, double* T, const double* p,
+                          double* Y, int64_t ldY, int32_t* cell_status, int64_t* n_active_out,
+                          df_graph** out);
+/* Enqueues one replay of the captured step on `stream`. */
+df_status df_graph_launch(df_graph* g, void* stream);
+/* Destroys the graph (synchronising with its last replay). NULL is a no-op. */
+void df_graph_destroy(df_graph* g);
+
 /* Statistics of the last df_chem_step on a state. */
 typedef struct {
   int64_t n_active;           /* reacting cells */

@@ -69,6 +69,9 @@ SIGNATURES = {
     "df_mlp_forward": (_ST, [_VP, _I64, _VP, _VP, _VP]),
     "df_eos_post": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _VP]),
     "df_active_compact_static": (_ST, [_I64, C.c_double, _VP, _VP, _VP, _VP]),
+    "df_graph_create": (_ST, [_VP, _I64, C.c_double, _VP, _VP, _VP, _I64, _VP, _VP, C.POINTER(_VP)]),
+    "df_graph_launch": (_ST, [_VP, _VP]),
+    "df_graph_destroy": (None, [_VP]),
     "df_profile_enable": (_ST, [_VP, C.c_int32]),
     "df_profile_read": (_ST, [_VP, C.c_int32, C.c_char_p, C.POINTER(_I64), C.POINTER(C.c_double),
                               C.POINTER(C.c_int32)]),

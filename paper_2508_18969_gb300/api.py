@@ -95,6 +95,10 @@ class State:
                                            _ptr(T), _ptr(p), _ptr(Y), Y.stride(0), _ptr(status),
                                            _ptr(n_active), _stream(stream)))
 
+    def graph(self, T, p, Y, dt=None, status=None, n_active=None):
+        """A Graph replaying df_chem_step on these exact buffers (see df_graph_create)."""
+        return Graph(self, T, p, Y, dt, status, n_active)
+
     def step_summary(self, stream=None):
         """(status code, reacting cells, flagged cells, Newton iterations) of the last step."""
         s = L.StepStats()
@@ -158,6 +162,38 @@ class State:
         self._check(self._lib.df_eos_post(self.h, N, _ptr(O.contiguous()), _ptr(h0), _ptr(T),
                                           _ptr(p), _ptr(Y), Y.stride(0), _ptr(st), _stream(stream)))
         return st
+
+
+class Graph:
+    """One captured df_chem_step (df_graph_*); launch() replays it."""
+
+    def __init__(self, state, T, p, Y, dt, status, n_active):
+        self._lib = state._lib
+        self._state = state
+        self._bufs = (T, p, Y, status, n_active)  # keep the captured buffers alive
+        h = C.c_void_p()
+        rc = self._lib.df_graph_create(state.h, T.shape[0], state.dt if dt is None else float(dt),
+                                       _ptr(T), _ptr(p), _ptr(Y), Y.stride(0), _ptr(status),
+                                       _ptr(n_active), C.byref(h))
+        if rc != L.DF_OK:
+            raise DFError(rc, self._lib.df_get_last_error(state.h).decode())
+        self.h = h
+
+    def launch(self, stream=None):
+        rc = self._lib.df_graph_launch(self.h, _stream(stream))
+        if rc != L.DF_OK:
+            raise DFError(rc, self._lib.df_get_last_error(self._state.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.df_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def active_compact_static(T, T_react: float, stream=None):

@@ -80,6 +80,9 @@ cudaError_t launch_eos_post(const EosParams& P, const RowMap& rows, const float*
 cudaError_t launch_props(const EosParams& P, int64_t n, const double* T, const double* p,
                          const double* Y, int64_t ldY, double* rho, double* h, double* cp,
                          double* Z, cudaStream_t st);
+// Sets, on the current device, the kernel attributes the EoS launches of this configuration
+// need (done once per device; later launches and graph captures then set none).
+cudaError_t prepare_eos(const EosParams& P, int xkind);
 
 // ---- launchers (compact.cu) ----
 constexpr int64_t kCompactChunk = 4096;   // cells per block of the compaction kernels
@@ -114,5 +117,6 @@ bool tc_encode_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t i
                   uint32_t box_outer, char* err, size_t errlen);
 cudaError_t launch_tc_gemm(const TcLayer& L, const RowMap& rows, int num_sms, int* err,
                            cudaStream_t st);
+cudaError_t prepare_tc(const TcLayer& L);
 
 }  // namespace dfgb

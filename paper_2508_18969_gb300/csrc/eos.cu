@@ -567,6 +567,21 @@ cudaError_t launch_eos_pre(const EosParams& P, const RowMap& rows, const double*
   return pre_nm<32>(P, rows, T, p, Y, ldY, h0, Z, x, xkind, ldx, x_scale, status, st);
 }
 
+template <int NM>
+cudaError_t prepare_nm(int xkind) {
+  cudaError_t e = xkind == kXBF16  ? smem_optin<eos_pre_kernel<NM, __nv_bfloat16>>()
+                  : xkind == kXFP8 ? smem_optin<eos_pre_kernel<NM, __nv_fp8_e4m3>>()
+                                   : smem_optin<eos_pre_kernel<NM, float>>();
+  if (e == cudaSuccess) e = smem_optin<eos_pre_kernel<NM, float>>();  // stage entry point
+  if (e == cudaSuccess) e = smem_optin<eos_post_kernel<NM>>();
+  if (e == cudaSuccess) e = smem_optin<props_kernel<NM>>();
+  return e;
+}
+
+cudaError_t prepare_eos(const EosParams& P, int xkind) {
+  return P.n <= 16 ? prepare_nm<16>(xkind) : prepare_nm<32>(xkind);
+}
+
 cudaError_t launch_eos_post(const EosParams& P, const RowMap& rows, const float* O, int64_t ldo,
                             const double* h0, double* T, const double* p, double* Y,
                             int64_t ldY, const int32_t* pre_status, int32_t* cell_status,

@@ -458,21 +458,31 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
+// Opts the kernel instance into its dynamic shared memory, once per device.
+template <bool FP8, int BN, int OUTK, bool GELU>
+cudaError_t tc_attr() {
+  static bool attr_done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr_done[dev]) {
+    e = cudaFuncSetAttribute(tc_gemm_kernel<FP8, BN, OUTK, GELU, FP8>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN>::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_done[dev] = true;
+  }
+  return cudaSuccess;
+}
+
 template <bool FP8, int BN, int OUTK, bool GELU>
 cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream_t st) {
   using C = Cfg<BN>;
   constexpr bool SCALE = FP8;
   auto kern = tc_gemm_kernel<FP8, BN, OUTK, GELU, SCALE>;
-  static bool attr_done[64] = {false};  // per device
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (!attr_done[dev]) {
-    cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr_done[dev] = true;
-  }
+  cudaError_t e0 = tc_attr<FP8, BN, OUTK, GELU>();
+  if (e0 != cudaSuccess) return e0;
+  if (num_sms <= 0) return cudaSuccess;  // attribute set-up only
   const int64_t tiles = ((a.rows.nmax + BM - 1) / BM) * ((L.N + BN - 1) / BN);
   const unsigned grid = (unsigned)(tiles < num_sms ? (tiles > 0 ? tiles : 1) : num_sms);
   kern<<<grid, kThreads, C::kSmemBytes, st>>>(L.tmA, L.tmB, a);
@@ -530,6 +540,11 @@ bool tc_encode_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t i
     return false;
   }
   return true;
+}
+
+cudaError_t prepare_tc(const TcLayer& L) {
+  TcArgs a{};
+  return L.elem_bytes == 1 ? launch_fmt<true>(L, a, 0, nullptr) : launch_fmt<false>(L, a, 0, nullptr);
 }
 
 cudaError_t launch_tc_gemm(const TcLayer& L, const RowMap& rows, int num_sms, int* err,

@@ -536,7 +536,9 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
       s->tcl.push_back(T);
     }
   }
-  (void)xk;
+  // one-time per-device kernel attributes, so that no later call (or graph capture) sets any
+  CK(prepare_eos(s->P, xk), "kernel attributes");
+  for (const TcLayer& T : s->tcl) CK(prepare_tc(T), "kernel attributes");
 #undef CK
   *out = s;
   return DF_OK;
@@ -603,6 +605,73 @@ df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const
     if (e != cudaSuccess) return cuda_fail(s, e, "n_active copy");
   }
   return DF_OK;
+}
+
+struct df_graph {
+  df_state* s = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+df_status df_graph_create(df_state* s, int64_t n_cells, double dt, double* T, const double* p,
+                          double* Y, int64_t ldY, int32_t* cell_status, int64_t* n_active_out,
+                          df_graph** out) {
+  if (!out) return fail(s, DF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
+  if (rc != DF_OK) return rc;
+  DeviceGuard guard(s->device);
+  // everything that may allocate or set function attributes happens outside the capture
+  if ((rc = ensure_compact(s, n_cells)) != DF_OK) return rc;
+  const bool prof = s->prof_on;
+  s->prof_on = false;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    s->prof_on = prof;
+    return cuda_fail(s, e, "capture stream");
+  }
+  // kernel attributes were set by df_state_create, so the capture records launches only
+  df_graph* g = new df_graph();
+  g->s = s;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = df_chem_step(s, n_cells, dt, T, p, Y, ldY, cell_status, n_active_out, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
+    if (rc == DF_OK && e2 != cudaSuccess) rc = cuda_fail(s, e2, "end capture");
+  } else {
+    rc = cuda_fail(s, e, "begin capture");
+  }
+  if (rc == DF_OK) {
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) rc = cuda_fail(s, e, "graph instantiate");
+  }
+  cudaStreamDestroy(cs);
+  s->prof_on = prof;
+  if (rc != DF_OK) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return DF_OK;
+}
+
+df_status df_graph_launch(df_graph* g, void* stream) {
+  if (!g) return fail(nullptr, DF_ERR_INVALID_ARG, "graph is NULL");
+  DeviceGuard guard(g->s->device);
+  cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+  return e == cudaSuccess ? DF_OK : cuda_fail(g->s, e, "graph launch");
+}
+
+void df_graph_destroy(df_graph* g) {
+  if (!g) return;
+  DeviceGuard guard(g->s->device);
+  cudaDeviceSynchronize();
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
 }
 
 df_status df_get_step_summary(df_state* s, void* stream, df_step_stats* stats) {
