@@ -122,6 +122,19 @@ df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const
                        double* Y, int64_t ldY, int32_t* cell_status, int64_t* n_active_out,
                        void* stream);
 
+/* Jacobian of the reaction step of each cell (every cell treated as reacting), with p fixed
+ * and the inputs (T, Y_1..Y_n) taken as independent (no renormalisation of the input):
+ *   J_dY  (device, [n_cells][n][n+1] row-major FP32): d(Y'_k - Y_k) / d(T, Y_1..Y_n);
+ *   dTnew (device, [n_cells][n+1] FP64, may be NULL): dT'/d(T, Y_1..Y_n).
+ * Forward-mode tangents through the network (Sec. 2's chemistry network; GELU of Sec. 3.3.2)
+ * -- FP32 on the CUDA cores for a DF_FP32 state, BF16 tcgen05 GEMMs otherwise -- then the
+ * chain through de-normalisation, renormalisation and the implicit function
+ * h(T', p, Y') = h0(T, p, Y). The Box-Cox slope is taken at max(Y_j, 1e-12). Cells whose step
+ * would be flagged get NaN entries. Allocates its buffers at the first call on a state; uses
+ * the state's scratch, so it must not overlap other calls on the same state. */
+df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const double* p,
+                           const double* Y, int64_t ldY, float* J_dY, double* dTnew, void* stream);
+
 /* ---- CUDA-graph execution of the step ----
  * A df_graph is one df_chem_step with fixed arguments (sizes, dt and the device buffers T, p,
  * Y, cell_status, n_active_out) captured into an executable CUDA graph, so a time loop replays

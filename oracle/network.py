@@ -129,3 +129,24 @@ def mlp_forward_fp8(net, x, act_scale):
         z = h @ fp8_weight_rounding(net.W[l]).T + net.b[l][None, :]
         h = rq(gelu_tanh(z)) if l < L - 1 else z
     return h
+
+
+def mlp_jacobian(net, x):
+    """dO/dx of the MLP for every row of x, by reverse mode written out layer by layer:
+    for a linear layer z = h W^T + b the cotangent maps as g_h = g_z W, through GELU as
+    g_z = g_h * GELU'(z). Returns J [N, n_out, K0]."""
+    x = np.asarray(x, dtype=np.float64)
+    _, pre = mlp_forward(net, x, return_pre=True)
+    L = net.n_layers
+    n_out = net.W[-1].shape[0]
+    N = x.shape[0]
+    J = np.zeros((N, n_out, x.shape[1]))
+    for k in range(n_out):
+        g = np.zeros((N, n_out))
+        g[:, k] = 1.0                          # cotangent of output k
+        for l in range(L - 1, -1, -1):
+            if l < L - 1:
+                g = g * gelu_tanh_grad(pre[l])  # through the activation of layer l
+            g = g @ net.W[l]                    # through the linear map of layer l
+        J[:, k, :] = g
+    return J

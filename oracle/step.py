@@ -114,3 +114,40 @@ def real_fluid_props(mech, T, p, Y):
 
 __all__ = ["active_cells", "solve_T", "chem_step", "real_fluid_props", "NOT_CONVERGED",
            "NONFINITE", "NO_ROOT"]
+
+
+def chem_step_jacobian_fd(mech, net, T, p, Y, dT_rel=1e-6, dY_rel=1e-5, dY_min=1e-6):
+    """Central finite differences of the reaction step of each cell (treated as active):
+    J_dY [N, n, n+1] = d(Y'_k - Y_k) / d(T, Y_1..Y_n) and dTn [N, n+1] = dT'/d(T, Y_1..Y_n),
+    with p fixed and the Y_j perturbed independently (no renormalisation of the input).
+    Steps: T by dT_rel * T, Y_j by dY_rel * Y_j; species with Y_j < dY_min get NaN columns
+    (the Box-Cox transform is not differentiable at 0, so a difference there means nothing)."""
+    T = np.asarray(T, dtype=np.float64)
+    p = np.asarray(p, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    n, N = Y.shape
+    J = np.full((N, n, n + 1), np.nan)
+    dTn = np.full((N, n + 1), np.nan)
+
+    def run(Tx, Yx):
+        To, Yo, st = chem_step(mech, net, Tx, p, Yx, net.dt, T_react=-1.0)
+        return To, Yo - Yx, st
+
+    h = dT_rel * T
+    Tp, dYp, sp = run(T + h, Y)
+    Tm, dYm, sm = run(T - h, Y)
+    J[:, :, 0] = ((dYp - dYm) / (2 * h)).T
+    dTn[:, 0] = (Tp - Tm) / (2 * h)
+    for j in range(n):
+        ok = Y[j] >= dY_min
+        hj = np.where(ok, dY_rel * Y[j], 0.0)
+        Yp = Y.copy(); Yp[j] += hj
+        Ym = Y.copy(); Ym[j] -= hj
+        Tp, dYp, _ = run(T, Yp)
+        Tm, dYm, _ = run(T, Ym)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            col = ((dYp - dYm) / (2 * hj)).T
+            tcol = (Tp - Tm) / (2 * hj)
+        J[:, :, 1 + j] = np.where(ok[:, None], col, np.nan)
+        dTn[:, 1 + j] = np.where(ok, tcol, np.nan)
+    return J, dTn

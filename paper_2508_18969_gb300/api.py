@@ -95,6 +95,15 @@ class State:
                                            _ptr(T), _ptr(p), _ptr(Y), Y.stride(0), _ptr(status),
                                            _ptr(n_active), _stream(stream)))
 
+    def chem_jacobian(self, T, p, Y, want_dT=True, stream=None):
+        """(J [N, n, n+1] FP32, dTnew [N, n+1] FP64 or None): df_chem_jacobian."""
+        N = T.shape[0]
+        J = torch.empty(N, self.n, self.n + 1, dtype=torch.float32, device=T.device)
+        dTn = torch.empty(N, self.n + 1, dtype=torch.float64, device=T.device) if want_dT else None
+        self._check(self._lib.df_chem_jacobian(self.h, N, _ptr(T), _ptr(p), _ptr(Y), Y.stride(0),
+                                               _ptr(J), _ptr(dTn), _stream(stream)))
+        return J, dTn
+
     def graph(self, T, p, Y, dt=None, status=None, n_active=None):
         """A Graph replaying df_chem_step on these exact buffers (see df_graph_create)."""
         return Graph(self, T, p, Y, dt, status, n_active)

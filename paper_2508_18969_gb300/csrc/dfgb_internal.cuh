@@ -83,6 +83,16 @@ cudaError_t launch_props(const EosParams& P, int64_t n, const double* T, const d
 // Sets, on the current device, the kernel attributes the EoS launches of this configuration
 // need (done once per device; later launches and graph captures then set none).
 cudaError_t prepare_eos(const EosParams& P, int xkind);
+// Jacobian pieces: input scales sc [ncell x (n+1)], layer-1 tangents, post-processing.
+cudaError_t launch_jac_scale(const EosParams& P, int64_t ncell, const double* Y, int64_t ldY,
+                             float* sc, cudaStream_t st);
+cudaError_t launch_jac_tangent0(int64_t ncell, int ntan, int N1, const float* sc, const float* W1T,
+                                const void* G1, int64_t ldg, bool bf16, void* dH, int64_t ldh,
+                                cudaStream_t st);
+cudaError_t launch_jac_post(const EosParams& P, int64_t ncell, int64_t cell0, const double* T,
+                            const double* p, const double* Y, int64_t ldY, const float* O,
+                            int64_t ldo, const float* dO, int64_t lddo, const double* h0, float* J,
+                            double* dTn, cudaStream_t st);
 
 // ---- launchers (compact.cu) ----
 constexpr int64_t kCompactChunk = 4096;   // cells per block of the compaction kernels
@@ -94,9 +104,11 @@ cudaError_t launch_compact(int64_t n, double T_react, const double* T, int32_t* 
 // ---- launchers (mlp_simt.cu) ----
 // C[r, c] = act(sum_k A[r, k] W[c, k] + bias[c]) for valid rows r < rows(map), c < N.
 // A is [rows x lda] FP32, W is [N x ldw] FP32 with K a multiple of 8 (zero padded).
+// mode 1 also writes G = GELU'(z) [rows x ldg]; mode 2 computes C = (A W^T) * G[row / ntan].
 cudaError_t launch_sgemm_bias_act(const RowMap& rows, int N, int K, const float* A, int64_t lda,
                                   const float* W, int64_t ldw, const float* bias, float* C,
-                                  int64_t ldc, bool gelu, int num_sms, cudaStream_t st);
+                                  int64_t ldc, bool gelu, int num_sms, cudaStream_t st,
+                                  int mode = 0, float* G = nullptr, int64_t ldg = 0, int ntan = 1);
 
 // ---- tcgen05 GEMM (mlp_tc.cu) ----
 struct TcLayer {
@@ -111,6 +123,10 @@ struct TcLayer {
   bool gelu;
   float out_scale;       // multiply before quantising the output (FP8 activations)
   int elem_bytes;        // 2 (BF16) or 1 (FP8)
+  int mode;              // 0 plain, 1 also store GELU'(z) to gbuf, 2 scale rows by gbuf
+  void* gbuf;            // BF16 [cells x ldg] GELU'(z) of the forward pass
+  int64_t ldg;
+  int ntan;              // tangent rows per cell (mode 2)
 };
 bool tc_encode_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
                   uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,

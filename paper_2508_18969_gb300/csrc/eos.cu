@@ -248,6 +248,50 @@ __device__ PRPoint pr_point(const Mixture& m, double T, double p, bool want_cp, 
   return r;
 }
 
+// a9: T from h(T, p, Y') = h0 for the composition of m, safeguarded Newton inside a bracket
+// that starts at [50, 5000] K and shrinks with the sign of h - h0. Adds flags to st and the
+// iteration count to iters; returns the last iterate.
+__device__ double solve_T(const Mixture& m, double pc, double h0c, double Told, const EosParams& P,
+                          int& iters, int& st) {
+  double lo = kTLo, hi = kTHi;
+  double Tn = fmin(fmax(Told, lo), hi);
+  bool conv = false, need_cp = true;
+  double icp = 0.0;
+  for (int it = 0; it < P.newton_max_iter; ++it) {
+    ++iters;
+    int s2 = 0;
+    const PRPoint q = pr_point(m, Tn, pc, need_cp, s2);
+    if (s2) {
+      st |= s2;
+      break;
+    }
+    const double f = h_ig(m, Tn) + q.h_dep * m.inv - h0c;
+    // Chord steps: the slope of the first iteration is reused while the iterates stay
+    // close (each step contracts the error by ~|1 - cp(T)/cp(T0)| ~ 1e-5 there); an FP32
+    // reciprocal of cp scales the step by 1 + O(1e-7) on top.
+    if (need_cp) icp = f_to_d(__frcp_rn(d_to_f_trunc(cp_ig(m, Tn) + q.cp_dep * m.inv)));
+    if (f > 0.0) hi = fmin(hi, Tn); else lo = fmax(lo, Tn);
+    double Tx = fma(-f, icp, Tn);
+    // a step within tolerance has converged; only a longer step that leaves the
+    // bracket (or is not finite) is replaced by bisection, after which the slope is
+    // evaluated afresh
+    const bool done = fabs(Tx - Tn) <= P.newton_tol * Tn;
+    need_cp = false;
+    if (!done && !(Tx > lo && Tx < hi)) {
+      Tx = 0.5 * (lo + hi);
+      need_cp = true;
+    }
+    Tn = Tx;
+    if (done) {
+      conv = true;
+      break;
+    }
+  }
+  if (!conv && st == 0) st |= kCellNotConverged;
+  if (!isfinite(Tn)) st |= kCellNonfinite;
+  return Tn;
+}
+
 template <typename XT>
 __device__ __forceinline__ XT to_x(float v, float scale);
 template <>
@@ -397,42 +441,7 @@ __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap 
       }
       Mixture m;
       mixture<NM>(Yn, n, c, ws, m);
-      double lo = kTLo, hi = kTHi;
-      Tn = fmin(fmax(Told, lo), hi);
-      bool conv = false, need_cp = true;
-      double icp = 0.0;
-      for (int it = 0; it < P.newton_max_iter; ++it) {
-        ++iters;
-        int s2 = 0;
-        const PRPoint q = pr_point(m, Tn, pc, need_cp, s2);
-        if (s2) {
-          st |= s2;
-          break;
-        }
-        const double f = h_ig(m, Tn) + q.h_dep * m.inv - h0c;
-        // Chord steps: the slope of the first iteration is reused while the iterates stay
-        // close (each step contracts the error by ~|1 - cp(T)/cp(T0)| ~ 1e-5 there); an FP32
-        // reciprocal of cp scales the step by 1 + O(1e-7) on top.
-        if (need_cp) icp = f_to_d(__frcp_rn(d_to_f_trunc(cp_ig(m, Tn) + q.cp_dep * m.inv)));
-        if (f > 0.0) hi = fmin(hi, Tn); else lo = fmax(lo, Tn);
-        double Tx = fma(-f, icp, Tn);
-        // a step within tolerance has converged; only a longer step that leaves the
-        // bracket (or is not finite) is replaced by bisection, after which the slope is
-        // evaluated afresh
-        const bool done = fabs(Tx - Tn) <= P.newton_tol * Tn;
-        need_cp = false;
-        if (!done && !(Tx > lo && Tx < hi)) {
-          Tx = 0.5 * (lo + hi);
-          need_cp = true;
-        }
-        Tn = Tx;
-        if (done) {
-          conv = true;
-          break;
-        }
-      }
-      if (!conv && st == 0) st |= kCellNotConverged;
-      if (!isfinite(Tn)) st |= kCellNonfinite;
+      Tn = solve_T(m, pc, h0c, Told, P, iters, st);
     }
     if (st == 0) {
       T[cell] = Tn;
@@ -473,6 +482,230 @@ __global__ void __launch_bounds__(kThreads) props_kernel(EosParams P, int64_t nc
     if (h) h[i] = h_ig(m, Tc) + q.h_dep * m.inv;
     if (cp) cp[i] = cp_ig(m, Tc) + q.cp_dep * m.inv;
     if (Zo) Zo[i] = q.Z;
+  }
+}
+
+
+// ---------------------------------------------------------------- Jacobian of the step
+
+// dh/dY_k of the mass-specific real-fluid enthalpy at fixed T, p (FP64), for the composition in
+// the per-thread column ycol (entry k at ycol[k * stride]). u_k = y_k sqrt(a_k), yr_k = y_k r_k,
+// v = K u, w = K yr use the columns ucol, rcol, vcol, wcol. With sigma = sum y, W = 1/sigma:
+//   a = W^2 u.Ku,  a' = -(W^2 / sqrt T) yr.Ku,  b = W sum y_k b_k,
+//   da/dy_k = 2 W^2 sqrt(a_k) v_k - 2 W a,  da'/dy_k = -2 W a' - (W^2 / sqrt T)(r_k v_k + sqrt(a_k) w_k),
+//   db/dy_k = W (b_k - b),  dZ from the implicit cubic, h = sum y_k h_k(T) + sigma h_dep,
+//   dh/dY_k = (h_k(T) + h_dep + sigma dh_dep/dy_k) / W_k.
+__device__ void h_grad(const EosParams& P, int n, int stride, const double* ycol, double T, double p,
+                       double* ucol, double* rcol, double* vcol, double* wcol, double* out,
+                       int out_stride, int& st) {
+  const double* spc = P.spc;
+  const double* K = P.Kmat;
+  const double t = sqrt(T);
+  double sig = 0.0, bs = 0.0;
+  for (int k = 0; k < n; ++k) {
+    const double* q = spc + k * kSpcStride;
+    const double y = ycol[k * stride] * q[0];
+    sig += y;
+    bs += y * q[3];
+    ucol[k * stride] = y * (q[1] - q[2] * t);
+    rcol[k * stride] = y * q[2];
+  }
+  double G = 0.0, dGs = 0.0;
+  for (int k = 0; k < n; ++k) {
+    double v = 0.0, w = 0.0;
+    for (int j = 0; j < n; ++j) {
+      v = fma(K[k * n + j], ucol[j * stride], v);
+      w = fma(K[k * n + j], rcol[j * stride], w);
+    }
+    vcol[k * stride] = v;
+    wcol[k * stride] = w;
+    G = fma(ucol[k * stride], v, G);
+    dGs = fma(rcol[k * stride], v, dGs);
+  }
+  const double W = 1.0 / sig;
+  const double a = W * W * G;
+  const double da = -W * W * dGs / t;
+  const double b = W * bs;
+  const double RT = kR * T;
+  const double A = a * p / (RT * RT);
+  const double B = b * p / RT;
+  const double Z = select_Z(A, B, st);
+  const double c1 = 1.0 + kSQ2, c2 = 1.0 - kSQ2;
+  const double Zp = Z + c1 * B, Zm = Z + c2 * B;
+  const double L = log(Zp / Zm);
+  const double kb = 1.0 / (2.0 * kSQ2 * b);
+  const double tda = T * da - a;
+  const double hdep = RT * (Z - 1.0) + tda * kb * L;
+  const double FZ = 3.0 * Z * Z - 2.0 * (1.0 - B) * Z + (A - 3.0 * B * B - 2.0 * B);
+  const double FA = Z - B;
+  const double FB = Z * Z - (6.0 * B + 2.0) * Z - (A - 2.0 * B - 3.0 * B * B);
+  for (int k = 0; k < n; ++k) {
+    const double* q = spc + k * kSpcStride;
+    const double sak = q[1] - q[2] * t;
+    const double vk = vcol[k * stride], wk = wcol[k * stride];
+    const double dak = 2.0 * W * W * sak * vk - 2.0 * W * a;
+    const double ddak = -2.0 * W * da - W * W * (q[2] * vk + sak * wk) / t;
+    const double dbk = W * (q[3] - b);
+    const double dAk = dak * p / (RT * RT);
+    const double dBk = dbk * p / RT;
+    const double dZk = -(FA * dAk + FB * dBk) / FZ;
+    const double dLk = (dZk + c1 * dBk) / Zp - (dZk + c2 * dBk) / Zm;
+    const double dkbk = -kb * dbk / b;
+    const double dhdep = RT * dZk + (T * ddak - dak) * kb * L + tda * (dkbk * L + kb * dLk);
+    const double hk = fma(fma(fma(fma(fma(q[9], T, q[8]), T, q[7]), T, q[6]), T, q[5]), T, q[4]);
+    out[k * out_stride] = q[0] * (hk + hdep + sig * dhdep);
+  }
+}
+
+// Input scales of the tangent directions (T, Y_1..Y_n): dx_0/dT = 1/std_T and
+// dx_{2+j}/dY_j = BC'(Y_j) / std_{2+j}, BC'(y) = max(y, 1e-12)^(lambda - 1).
+__global__ void jac_scale_kernel(EosParams P, int64_t ncell, const double* __restrict__ Y,
+                                 int64_t ldY, const double* __restrict__ norm,
+                                 float* __restrict__ sc) {
+  const int ntan = P.n + 1, K0 = P.K0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ncell * ntan;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / ntan;
+    const int t = (int)(e % ntan);
+    double v;
+    if (t == 0) {
+      v = norm[K0];
+    } else {
+      const double y = fmax(Y[(int64_t)(t - 1) * ldY + c], 1e-12);
+      v = pow(y, P.lambda - 1.0) * norm[K0 + 1 + t];
+    }
+    sc[e] = (float)v;
+  }
+}
+
+// Layer-1 tangents: dH1[c ntan + t, j] = sc[c, t] * W1[j, col(t)] * G1[c, j], col(0) = 0 (T),
+// col(t) = t + 1 (Y_{t-1}); W1T is W1 transposed [K0 x N1].
+template <typename OT, typename GT>
+__global__ void jac_tangent0_kernel(int64_t ncell, int ntan, int N1, const float* __restrict__ sc,
+                                    const float* __restrict__ W1T, const GT* __restrict__ G1,
+                                    int64_t ldg, OT* __restrict__ dH, int64_t ldh) {
+  const int64_t total = ncell * ntan * (int64_t)N1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = e / N1;
+    const int j = (int)(e % N1);
+    const int64_t c = row / ntan;
+    const int t = (int)(row % ntan);
+    const int col = t == 0 ? 0 : t + 1;
+    const float v = sc[row] * W1T[(int64_t)col * N1 + j] * (float)G1[c * ldg + j];
+    dH[row * ldh + j] = (OT)v;
+  }
+}
+
+// Jacobian of the step of every cell (treated as reacting): J[c][k][t] = d(Y'_k - Y_k)/dv_t and
+// dTn[c][t] = dT'/dv_t, v = (T, Y_1..Y_n), from the network output O, its tangents dO
+// ([c ntan + t][k] = dO_k/dv_t) and the implicit function h(T', p, Y') = h0(T, p, Y).
+template <int NM>
+__global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell, int64_t cell0,
+    const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
+    int64_t ldY, const float* __restrict__ O, int64_t ldo, const float* __restrict__ dO,
+    int64_t lddo, const double* __restrict__ h0, float* __restrict__ J, double* __restrict__ dTn) {
+  extern __shared__ double sm[];
+  const SharedConsts c = load_consts(P, sm);
+  const int stride = blockDim.x;
+  f2* ws = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
+  double* cols = sm + consts_words(P) + 2 * NM * stride + threadIdx.x;
+  double* Yc = cols;                       // Y
+  double* Ypc = cols + NM * stride;        // Y'
+  double* zlc = cols + 2 * NM * stride;    // dZ_k/du_k
+  double* hgc = cols + 3 * NM * stride;    // dh/dY' at (T', Y')
+  double* uc = cols + 4 * NM * stride;
+  double* rc = cols + 5 * NM * stride;
+  double* vc = cols + 6 * NM * stride;
+  double* wc = cols + 7 * NM * stride;
+  const int n = P.n, K0 = P.K0, ntan = n + 1;
+  const float* out_mean = c.normf + 2 * K0;
+  const float* out_std = c.normf + 2 * K0 + n;
+  const float lamf = (float)P.lambda;
+  const double lam = P.lambda;
+  const int mpow = P.inv_lambda;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ncell;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = cell0 + r;
+    const double Tc = T[cell], pc = p[cell], h0c = h0[r];
+    double Yk[NM];
+    bool finite = isfinite(Tc) && isfinite(pc) && pc > 0.0 && isfinite(h0c);
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+      Yk[k] = (k < n) ? Y[k * ldY + cell] : 0.0;
+      finite = finite && isfinite(Yk[k]);
+      if (k < n) Yc[k * stride] = Yk[k];
+    }
+    int st = finite ? 0 : kCellNonfinite;
+    float* Jc = J + cell * (int64_t)n * ntan;
+    double* dTc = dTn ? dTn + cell * (int64_t)ntan : nullptr;
+    double cp1 = 1.0;
+    if (st == 0) {
+      // (T, Y): cp and dh/dY, parked in dTn (its entries are final after the column loop)
+      Mixture m0;
+      mixture<NM>(Yk, n, c, ws, m0);
+      const PRPoint q0 = pr_point(m0, Tc, pc, true, st);
+      if (dTc) {
+        dTc[0] = cp_ig(m0, Tc) + q0.cp_dep * m0.inv;
+        h_grad(P, n, stride, Yc, Tc, pc, uc, rc, vc, wc, dTc + 1, 1, st);
+      }
+      // Y' and dZ_k/du_k = Z_k^(1 - lambda) = Z_k / (Y_k^lambda + lambda du_k)
+      double S = 0.0;
+      const float* Or = O + r * ldo;
+      for (int k = 0; k < n; ++k) {
+        const double y = Yk[k];
+        const float ldu = lamf * fmaf(out_std[k], Or[k], out_mean[k]);
+        const double base = ((y > 0.0) ? pow(y, lam) : 0.0) + (double)ldu;
+        const double z = (base > 0.0) ? ipow(base, mpow) : 0.0;
+        Ypc[k * stride] = z;
+        zlc[k * stride] = (base > 0.0) ? z / base : 0.0;
+        S += z;
+      }
+      if (!(S > 0.0)) st |= kCellNonfinite;
+      if (st == 0) {
+        const double iS = 1.0 / S;
+        double Yn[NM];
+#pragma unroll
+        for (int k = 0; k < NM; ++k) {
+          Yn[k] = (k < n) ? Ypc[k * stride] * iS : 0.0;
+          if (k < n) Ypc[k * stride] = Yn[k];
+        }
+        Mixture m1;
+        mixture<NM>(Yn, n, c, ws, m1);
+        int iters = 0;
+        const double Tn = solve_T(m1, pc, h0c, Tc, P, iters, st);
+        if (st == 0) {
+          const PRPoint q1 = pr_point(m1, Tn, pc, true, st);
+          cp1 = cp_ig(m1, Tn) + q1.cp_dep * m1.inv;
+          if (dTc) h_grad(P, n, stride, Ypc, Tn, pc, uc, rc, vc, wc, hgc, stride, st);
+        }
+        // columns t = 0 (T), 1 + j (Y_j)
+        for (int t = 0; t < ntan && st == 0; ++t) {
+          const float* dOr = dO + (r * ntan + t) * lddo;
+          double bcp = 0.0;
+          if (t > 0) bcp = pow(fmax(Yc[(t - 1) * stride], 1e-12), lam - 1.0);
+          double sumjz = 0.0;
+          for (int k = 0; k < n; ++k) {
+            const double ju = (double)out_std[k] * (double)dOr[k] + ((t == k + 1) ? bcp : 0.0);
+            sumjz += zlc[k * stride] * ju;
+          }
+          double acc = 0.0;
+          for (int k = 0; k < n; ++k) {
+            const double ju = (double)out_std[k] * (double)dOr[k] + ((t == k + 1) ? bcp : 0.0);
+            const double jy = (zlc[k * stride] * ju - Ypc[k * stride] * sumjz) * iS;
+            Jc[k * ntan + t] = (float)(jy - ((t == k + 1) ? 1.0 : 0.0));
+            if (dTc) acc = fma(hgc[k * stride], jy, acc);
+          }
+          if (dTc) dTc[t] = (dTc[t] - acc) / cp1;
+        }
+      }
+    }
+    if (st != 0) {
+      const float nanf = __int_as_float(0x7fc00000);
+      for (int e = 0; e < n * ntan; ++e) Jc[e] = nanf;
+      if (dTc)
+        for (int t = 0; t < ntan; ++t) dTc[t] = __longlong_as_double(0x7ff8000000000000LL);
+    }
   }
 }
 
@@ -579,7 +812,48 @@ cudaError_t prepare_nm(int xkind) {
 }
 
 cudaError_t prepare_eos(const EosParams& P, int xkind) {
-  return P.n <= 16 ? prepare_nm<16>(xkind) : prepare_nm<32>(xkind);
+  cudaError_t e = P.n <= 16 ? prepare_nm<16>(xkind) : prepare_nm<32>(xkind);
+  if (e == cudaSuccess) e = P.n <= 16 ? smem_optin<jac_post_kernel<16>>() : smem_optin<jac_post_kernel<32>>();
+  return e;
+}
+
+cudaError_t launch_jac_scale(const EosParams& P, int64_t ncell, const double* Y, int64_t ldY,
+                             float* sc, cudaStream_t st) {
+  if (ncell <= 0) return cudaSuccess;
+  jac_scale_kernel<<<grid_for(ncell * (P.n + 1)), kThreads, 0, st>>>(P, ncell, Y, ldY, P.norm, sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jac_tangent0(int64_t ncell, int ntan, int N1, const float* sc, const float* W1T,
+                                const void* G1, int64_t ldg, bool bf16, void* dH, int64_t ldh,
+                                cudaStream_t st) {
+  if (ncell <= 0) return cudaSuccess;
+  const int g = grid_for(ncell * ntan * (int64_t)N1 / 4);
+  if (bf16)
+    jac_tangent0_kernel<__nv_bfloat16, __nv_bfloat16><<<g, kThreads, 0, st>>>(
+        ncell, ntan, N1, sc, W1T, (const __nv_bfloat16*)G1, ldg, (__nv_bfloat16*)dH, ldh);
+  else
+    jac_tangent0_kernel<float, float><<<g, kThreads, 0, st>>>(ncell, ntan, N1, sc, W1T,
+                                                              (const float*)G1, ldg, (float*)dH, ldh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jac_post(const EosParams& P, int64_t ncell, int64_t cell0, const double* T,
+                            const double* p, const double* Y, int64_t ldY, const float* O,
+                            int64_t ldo, const float* dO, int64_t lddo, const double* h0, float* J,
+                            double* dTn, cudaStream_t st) {
+  if (ncell <= 0) return cudaSuccess;
+  constexpr int kJT = 64;
+  const int64_t blocks = (ncell + kJT - 1) / kJT;
+  const int g = (int)(blocks < 4096 ? blocks : 4096);
+  if (P.n <= 16) {
+    const size_t smem = sizeof(double) * ((size_t)consts_words(P) + (size_t)(2 * 16 + 8 * 16) * kJT);
+    jac_post_kernel<16><<<g, kJT, smem, st>>>(P, ncell, cell0, T, p, Y, ldY, O, ldo, dO, lddo, h0, J, dTn);
+  } else {
+    const size_t smem = sizeof(double) * ((size_t)consts_words(P) + (size_t)(2 * 32 + 8 * 32) * kJT);
+    jac_post_kernel<32><<<g, kJT, smem, st>>>(P, ncell, cell0, T, p, Y, ldY, O, ldo, dO, lddo, h0, J, dTn);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_eos_post(const EosParams& P, const RowMap& rows, const float* O, int64_t ldo,

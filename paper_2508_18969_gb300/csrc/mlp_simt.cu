@@ -16,10 +16,18 @@ __device__ __forceinline__ float gelu_accurate(float x) {
   return 0.5f * x * (1.0f + tanhf(u));
 }
 
-template <bool GELU>
+__device__ __forceinline__ float gelu_grad_accurate(float x) {
+  const float c = 0.7978845608028654f;
+  const float t = tanhf(c * fmaf(0.044715f * x * x, x, x));
+  return fmaf(0.5f * x * (1.0f - t * t), c * fmaf(3.0f * 0.044715f, x * x, 1.0f), 0.5f * (1.0f + t));
+}
+
+// MODE 0: C = act(A W^T + b); 1: also G = GELU'(A W^T + b); 2: C = (A W^T) * G[row / ntan, col]
+template <bool GELU, int MODE>
 __global__ void __launch_bounds__(kThreads, 2) sgemm_kernel(RowMap rows, int N, int K,
     const float* __restrict__ A, int64_t lda, const float* __restrict__ W, int64_t ldw,
-    const float* __restrict__ bias, float* __restrict__ C, int64_t ldc) {
+    const float* __restrict__ bias, float* __restrict__ C, int64_t ldc, float* __restrict__ G,
+    int64_t ldg, int ntan) {
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Ws[2][BK][BN];
   const int64_t M = valid_rows(rows);
@@ -85,9 +93,13 @@ __global__ void __launch_bounds__(kThreads, 2) sgemm_kernel(RowMap rows, int N, 
       for (int j = 0; j < 8; ++j) {
         const int col = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
         if (col < N) {
-          float v = acc[i][j] + bias[col];
-          if (GELU) v = gelu_accurate(v);
-          C[r * ldc + col] = v;
+          if (MODE == 2) {
+            C[r * ldc + col] = acc[i][j] * G[(r / ntan) * ldg + col];
+          } else {
+            const float z = acc[i][j] + bias[col];
+            C[r * ldc + col] = GELU ? gelu_accurate(z) : z;
+            if (MODE == 1) G[r * ldg + col] = gelu_grad_accurate(z);
+          }
         }
       }
     }
@@ -99,16 +111,22 @@ __global__ void __launch_bounds__(kThreads, 2) sgemm_kernel(RowMap rows, int N, 
 
 cudaError_t launch_sgemm_bias_act(const RowMap& rows, int N, int K, const float* A, int64_t lda,
                                   const float* W, int64_t ldw, const float* bias, float* C,
-                                  int64_t ldc, bool gelu, int num_sms, cudaStream_t st) {
+                                  int64_t ldc, bool gelu, int num_sms, cudaStream_t st,
+                                  int mode, float* G, int64_t ldg, int ntan) {
   if (rows.nmax <= 0) return cudaSuccess;
   if (K % BK != 0 || lda % 4 != 0 || ldw % 4 != 0) return cudaErrorInvalidValue;
   const int64_t tiles = ((rows.nmax + BM - 1) / BM) * ((N + BN - 1) / BN);
   const int64_t cap = (int64_t)num_sms * 2;
   const unsigned g = (unsigned)(tiles < cap ? tiles : cap);
-  if (gelu)
-    sgemm_kernel<true><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc);
+  if (ntan < 1) ntan = 1;
+  if (mode == 2)
+    sgemm_kernel<false, 2><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc, G, ldg, ntan);
+  else if (mode == 1)
+    sgemm_kernel<true, 1><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc, G, ldg, ntan);
+  else if (gelu)
+    sgemm_kernel<true, 0><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc, G, ldg, ntan);
   else
-    sgemm_kernel<false><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc);
+    sgemm_kernel<false, 0><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc, G, ldg, ntan);
   return cudaGetLastError();
 }
 

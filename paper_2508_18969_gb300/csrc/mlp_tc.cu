@@ -46,7 +46,14 @@ struct TcArgs {
   int gelu;
   float out_scale;
   int* err;
+  void* gbuf;      // GELU'(z): written (kModeStoreG) or read as the row-group scale (kModeRowG)
+  int64_t ldg;
+  int ntan;        // rows per group for kModeRowG
 };
+
+// Epilogue modes: plain layer; layer that also stores GELU'(z) (forward pass of the Jacobian);
+// tangent layer out[r, c] = acc[r, c] * G[r / ntan, c] (no bias, no activation).
+constexpr int kModePlain = 0, kModeStoreG = 1, kModeRowG = 2;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -197,30 +204,23 @@ struct Cfg {
       kStages * kStageBytes + kEpiWarps * kStageOut + 1024 /*align*/ + 1024 /*barriers*/;
 };
 
-// One 32-column chunk of the epilogue: scale, bias, GELU, quantise, transpose through the
-// warp's staging buffer, coalesced 16-byte stores of whole row segments.
-template <int OUTK, bool GELU, bool SCALE>
-__device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const TcArgs& g, int64_t M,
-                                               int64_t m0, int col0, int ncols, uint8_t* stg,
-                                               int lane) {
+__device__ __forceinline__ float gelu_grad_fast(float x) {
+  const float c = 0.7978845608028654f;
+  const float u = c * fmaf(0.044715f * x * x, x, x);
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+  return fmaf(0.5f * x * (1.0f - t * t), c * fmaf(3.0f * 0.044715f, x * x, 1.0f), 0.5f * (1.0f + t));
+}
+
+// Quantises 32 values of row `lane` to OUTK, transposes them through the warp's staging buffer
+// and writes whole 16-byte row units of the 32 rows m0.. to dst (row pitch ld elements).
+template <int OUTK>
+__device__ __forceinline__ void store_chunk(const float (&v)[32], void* dst_base, int64_t ld,
+                                            float out_scale, int64_t M, int64_t m0, int col0,
+                                            int ncols, uint8_t* stg, int lane) {
   constexpr int esz = OUTK == kXF32 ? 4 : (OUTK == kXBF16 ? 2 : 1);
   constexpr int U = 2 * esz;     // 16-byte units per 32-column row segment
   constexpr int RB = 32 * esz;   // bytes per row segment
-  float v[32];
-  const float4* b4 = reinterpret_cast<const float4*>(g.bias + col0);  // zero padded to 32
-  const float4* s4 = reinterpret_cast<const float4*>(g.col_scale + col0);
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const float4 b = __ldg(b4 + u);
-    float4 sc = make_float4(1.f, 1.f, 1.f, 1.f);
-    if (SCALE) sc = __ldg(s4 + u);
-    float x0 = __uint_as_float(r[4 * u]), x1 = __uint_as_float(r[4 * u + 1]);
-    float x2 = __uint_as_float(r[4 * u + 2]), x3 = __uint_as_float(r[4 * u + 3]);
-    if (SCALE) { x0 *= sc.x; x1 *= sc.y; x2 *= sc.z; x3 *= sc.w; }
-    x0 += b.x; x1 += b.y; x2 += b.z; x3 += b.w;
-    if (GELU) { x0 = gelu_fast(x0); x1 = gelu_fast(x1); x2 = gelu_fast(x2); x3 = gelu_fast(x3); }
-    v[4 * u] = x0; v[4 * u + 1] = x1; v[4 * u + 2] = x2; v[4 * u + 3] = x3;
-  }
   uint4 w[U];
   if (OUTK == kXF32) {
 #pragma unroll
@@ -238,7 +238,7 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const Tc
       memcpy(&w[u].z, &h2, 4); memcpy(&w[u].w, &h3, 4);
     }
   } else {
-    const float sc = g.out_scale;
+    const float sc = out_scale;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       uint32_t wd[4];
@@ -262,14 +262,14 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const Tc
   constexpr int ecount = 16 / esz;
   const int u = lane % U;
   const int ufirst = u * ecount;
-  uint8_t* gbase = (uint8_t*)g.out + (m0 * g.ldo + col0) * esz;
+  uint8_t* gbase = (uint8_t*)dst_base + (m0 * ld + col0) * esz;
 #pragma unroll
   for (int k = 0; k < U; ++k) {
     const int rr = lane / U + k * rows_per;
     if (m0 + rr < M && ufirst < ncols) {
       const int rrot = (U == 8) ? rr : (U == 4 ? (rr >> 1) : (rr >> 2));
       const uint8_t* src = stg + rr * RB + ((u + rrot) & (U - 1)) * 16;
-      uint8_t* dst = gbase + (int64_t)rr * g.ldo * esz + ufirst * esz;
+      uint8_t* dst = gbase + (int64_t)rr * ld * esz + ufirst * esz;
       if (ufirst + ecount <= ncols) {
         *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
       } else {
@@ -280,7 +280,61 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const Tc
   __syncwarp();
 }
 
-template <bool FP8, int BN, int OUTK, bool GELU, bool SCALE>
+// One 32-column chunk of the epilogue: per-channel scale, bias, GELU (or the row-group scale
+// of a tangent layer), then quantise and store; kModeStoreG also stores GELU'(z).
+template <int OUTK, bool GELU, bool SCALE, int MODE>
+__device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const TcArgs& g, int64_t M,
+                                               int64_t m0, int col0, int ncols, uint8_t* stg,
+                                               int lane) {
+  float v[32];
+  if (MODE == kModeRowG) {
+    // tangent row m0 + lane belongs to cell (m0 + lane) / ntan; G is BF16 [cells x ldg]
+    const int64_t row = m0 + lane;
+    const int64_t cell = (row < M ? row : M - 1) / g.ntan;
+    const uint4* gp = reinterpret_cast<const uint4*>((const __nv_bfloat16*)g.gbuf + cell * g.ldg + col0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint4 q = __ldg(gp + u);
+      const uint32_t qs[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        __nv_bfloat162 h2;
+        memcpy(&h2, &qs[e], 4);
+        const float2 f = __bfloat1622float2(h2);
+        v[8 * u + 2 * e] = __uint_as_float(r[8 * u + 2 * e]) * f.x;
+        v[8 * u + 2 * e + 1] = __uint_as_float(r[8 * u + 2 * e + 1]) * f.y;
+      }
+    }
+    store_chunk<OUTK>(v, g.out, g.ldo, g.out_scale, M, m0, col0, ncols, stg, lane);
+    return;
+  }
+  float gd[32];
+  const float4* b4 = reinterpret_cast<const float4*>(g.bias + col0);  // zero padded to 32
+  const float4* s4 = reinterpret_cast<const float4*>(g.col_scale + col0);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const float4 b = __ldg(b4 + u);
+    float4 sc = make_float4(1.f, 1.f, 1.f, 1.f);
+    if (SCALE) sc = __ldg(s4 + u);
+    float x[4] = {__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]),
+                  __uint_as_float(r[4 * u + 2]), __uint_as_float(r[4 * u + 3])};
+    const float bb[4] = {b.x, b.y, b.z, b.w};
+    const float ss[4] = {sc.x, sc.y, sc.z, sc.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float z = x[e];
+      if (SCALE) z *= ss[e];
+      z += bb[e];
+      if (MODE == kModeStoreG) gd[4 * u + e] = gelu_grad_fast(z);
+      v[4 * u + e] = GELU ? gelu_fast(z) : z;
+    }
+  }
+  store_chunk<OUTK>(v, g.out, g.ldo, g.out_scale, M, m0, col0, ncols, stg, lane);
+  if (MODE == kModeStoreG)
+    store_chunk<kXBF16>(gd, g.gbuf, g.ldg, 1.0f, M, m0, col0, ncols, stg, lane);
+}
+
+template <bool FP8, int BN, int OUTK, bool GELU, bool SCALE, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs g) {
   using C = Cfg<BN>;
@@ -415,14 +469,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
         {
           const int ncols = min(g.N - (n0 + c0), BN - c0);
           if (ncols > 0)
-            epilogue_chunk<OUTK, GELU, SCALE>(r0, g, M, m0, n0 + c0, ncols, stg, lane);
+            epilogue_chunk<OUTK, GELU, SCALE, MODE>(r0, g, M, m0, n0 + c0, ncols, stg, lane);
         }
         if (c1 >= BN) break;
         tmem_wait(r1);
         if (c1 + 64 < BN) tmem_ld32(tbase + c1 + 64, r0);
         const int ncols = min(g.N - (n0 + c1), BN - c1);
         if (ncols > 0)
-          epilogue_chunk<OUTK, GELU, SCALE>(r1, g, M, m0, n0 + c1, ncols, stg, lane);
+          epilogue_chunk<OUTK, GELU, SCALE, MODE>(r1, g, M, m0, n0 + c1, ncols, stg, lane);
       }
       tc_fence_before();
       __syncwarp();
@@ -459,7 +513,7 @@ EncodeTiledFn encode_fn() {
 }
 
 // Opts the kernel instance into its dynamic shared memory, once per device.
-template <bool FP8, int BN, int OUTK, bool GELU>
+template <bool FP8, int BN, int OUTK, bool GELU, int MODE>
 cudaError_t tc_attr() {
   static bool attr_done[64] = {false};
   int dev = 0;
@@ -467,7 +521,7 @@ cudaError_t tc_attr() {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_done[dev]) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<FP8, BN, OUTK, GELU, FP8>,
+    e = cudaFuncSetAttribute(tc_gemm_kernel<FP8, BN, OUTK, GELU, FP8, MODE>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN>::kSmemBytes);
     if (e != cudaSuccess) return e;
     attr_done[dev] = true;
@@ -475,12 +529,12 @@ cudaError_t tc_attr() {
   return cudaSuccess;
 }
 
-template <bool FP8, int BN, int OUTK, bool GELU>
+template <bool FP8, int BN, int OUTK, bool GELU, int MODE = kModePlain>
 cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream_t st) {
   using C = Cfg<BN>;
   constexpr bool SCALE = FP8;
-  auto kern = tc_gemm_kernel<FP8, BN, OUTK, GELU, SCALE>;
-  cudaError_t e0 = tc_attr<FP8, BN, OUTK, GELU>();
+  auto kern = tc_gemm_kernel<FP8, BN, OUTK, GELU, SCALE, MODE>;
+  cudaError_t e0 = tc_attr<FP8, BN, OUTK, GELU, MODE>();
   if (e0 != cudaSuccess) return e0;
   if (num_sms <= 0) return cudaSuccess;  // attribute set-up only
   const int64_t tiles = ((a.rows.nmax + BM - 1) / BM) * ((L.N + BN - 1) / BN);
@@ -490,9 +544,32 @@ cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream
 }
 
 // Hidden layers: GELU, output in the input precision. Last layer: linear, FP32 output.
+// The Jacobian's BF16 passes add a hidden layer that also stores GELU'(z) and a tangent layer
+// scaled per row group by it.
 template <bool FP8>
 cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream_t st) {
   constexpr int HID = FP8 ? kXFP8 : kXBF16;
+  if (L.mode != kModePlain) {
+    if (FP8 || L.out_kind != kXBF16) return cudaErrorInvalidValue;
+    if (L.mode == kModeStoreG) {
+      switch (L.BN) {
+        case 64: return launch_bn<false, 64, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
+        case 128: return launch_bn<false, 128, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
+        case 160: return launch_bn<false, 160, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
+        case 208: return launch_bn<false, 208, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
+        case 256: return launch_bn<false, 256, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+    switch (L.BN) {
+      case 64: return launch_bn<false, 64, kXBF16, false, kModeRowG>(L, a, num_sms, st);
+      case 128: return launch_bn<false, 128, kXBF16, false, kModeRowG>(L, a, num_sms, st);
+      case 160: return launch_bn<false, 160, kXBF16, false, kModeRowG>(L, a, num_sms, st);
+      case 208: return launch_bn<false, 208, kXBF16, false, kModeRowG>(L, a, num_sms, st);
+      case 256: return launch_bn<false, 256, kXBF16, false, kModeRowG>(L, a, num_sms, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (L.gelu) {
     if (L.out_kind != HID) return cudaErrorInvalidValue;
     switch (L.BN) {
@@ -562,6 +639,9 @@ cudaError_t launch_tc_gemm(const TcLayer& L, const RowMap& rows, int num_sms, in
   a.gelu = L.gelu ? 1 : 0;
   a.out_scale = L.out_scale;
   a.err = err;
+  a.gbuf = L.gbuf;
+  a.ldg = L.ldg;
+  a.ntan = L.ntan > 0 ? L.ntan : 1;
   return L.elem_bytes == 1 ? launch_fmt<true>(L, a, num_sms, st)
                            : launch_fmt<false>(L, a, num_sms, st);
 }

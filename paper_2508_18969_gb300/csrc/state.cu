@@ -17,6 +17,31 @@
 
 using namespace dfgb;
 
+struct Jac {
+  int64_t B = 0;                         // cells per Jacobian batch
+  bool bf16 = false;                     // BF16 tensor-core passes (else FP32 SIMT)
+  size_t eb = 4;
+  void* x = nullptr;
+  int64_t ldx = 0;
+  void* act[2] = {nullptr, nullptr};
+  int64_t act_ld[2] = {0, 0};
+  std::vector<void*> G;                  // GELU'(z) of each hidden layer [B x ldg]
+  std::vector<int64_t> ldg;
+  void* tan[2] = {nullptr, nullptr};     // tangent activations [B (n+1) x tan_ld]
+  int64_t tan_ld[2] = {0, 0};
+  float* O = nullptr;
+  int64_t ldo = 0;
+  float* dO = nullptr;
+  double* h0 = nullptr;
+  float* sc = nullptr;
+  float* W1T = nullptr;
+  float* zero_bias = nullptr;
+  std::vector<void*> Wb;                 // BF16 weights owned here (FP8 states)
+  std::vector<float*> W32;               // FP32 weights (SIMT), shared with the state
+  std::vector<int> Kp;
+  std::vector<TcLayer> fwd, tng;
+};
+
 struct df_state {
   int device = 0;
   int num_sms = 0;
@@ -56,6 +81,8 @@ struct df_state {
   int64_t* cscr = nullptr;
   int64_t cscr_words = 0;
   std::vector<TcLayer> tcl;
+  std::vector<std::vector<float>> Wh;    // host copies of the FP32 weights (Jacobian set-up)
+  struct Jac* jac = nullptr;             // Jacobian context, built at the first Jacobian call
   std::string err;
   // kernel timing (df_profile_enable / df_profile_read)
   bool prof_on = false;
@@ -154,8 +181,20 @@ size_t elem_of(int precision) {
   return precision == DF_BF16 ? 2 : precision == DF_FP8_E4M3 ? 1 : 4;
 }
 
+void free_jac(Jac* j) {
+  if (!j) return;
+  auto f = [](void* p) { if (p) cudaFree(p); };
+  f(j->x); f(j->act[0]); f(j->act[1]); f(j->tan[0]); f(j->tan[1]);
+  for (auto p : j->G) f(p);
+  f(j->O); f(j->dO); f(j->h0); f(j->sc); f(j->W1T); f(j->zero_bias);
+  for (auto p : j->Wb) f(p);
+  delete j;
+}
+
 void free_state(df_state* s) {
   auto f = [](void* p) { if (p) cudaFree(p); };
+  free_jac(s->jac);
+  s->jac = nullptr;
   f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
   for (auto p : s->W32) f(p);
   for (auto p : s->bias) f(p);
@@ -430,6 +469,7 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
       delete s;
       return fail(nullptr, DF_ERR_INVALID_ARG, "NULL layer array");
     }
+    s->Wh.emplace_back(mlp->W[l], mlp->W[l] + (size_t)Nl * Kl);
     // bias and scales are zero padded to a multiple of 32 so the epilogue loads whole chunks
     const int64_t Npad = round_up(Nl, 32);
     float* b = nullptr;
@@ -607,6 +647,144 @@ df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const
   return DF_OK;
 }
 
+// Builds the Jacobian context: buffers for B cells, BF16 weights and tensor maps when the
+// state's network runs on tensor cores.
+df_status build_jac(df_state* s) {
+  Jac* j = new Jac();
+  const int L = s->L, n = s->n, ntan = n + 1;
+  j->bf16 = s->precision != DF_FP32;
+  j->eb = j->bf16 ? 2 : 4;
+  j->B = std::min<int64_t>(s->cap, 16384);
+  const int64_t B = j->B, R = B * ntan;
+  const int64_t al = j->bf16 ? 16 : 8;
+  cudaError_t e = cudaSuccess;
+  auto al_ok = [&](void** p, size_t bytes, bool zero) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e == cudaSuccess && zero) e = cudaMemset(*p, 0, bytes ? bytes : 1);
+  };
+  j->ldx = round_up(s->K0, al);
+  al_ok(&j->x, j->eb * B * j->ldx, true);
+  int64_t wmax[2] = {al, al}, tmax = al;
+  for (int l = 0; l + 1 < L; ++l) {
+    wmax[l & 1] = std::max<int64_t>(wmax[l & 1], round_up(s->widths[l + 1], al));
+    tmax = std::max<int64_t>(tmax, round_up(s->widths[l + 1], al));
+  }
+  for (int b = 0; b < 2; ++b) {
+    j->act_ld[b] = wmax[b];
+    al_ok(&j->act[b], j->eb * B * wmax[b], true);
+    j->tan_ld[b] = tmax;
+    al_ok(&j->tan[b], j->eb * R * tmax, true);
+  }
+  for (int l = 0; l + 1 < L; ++l) {
+    void* g = nullptr;
+    const int64_t ld = round_up(s->widths[l + 1], 32);
+    al_ok(&g, j->eb * B * ld, true);
+    j->G.push_back(g);
+    j->ldg.push_back(ld);
+  }
+  j->ldo = s->ldo;
+  al_ok((void**)&j->O, sizeof(float) * B * j->ldo, true);
+  al_ok((void**)&j->dO, sizeof(float) * R * j->ldo, true);
+  al_ok((void**)&j->h0, sizeof(double) * B, false);
+  al_ok((void**)&j->sc, sizeof(float) * R, false);
+  int64_t zmax = 32;
+  for (int l = 0; l < L; ++l) zmax = std::max<int64_t>(zmax, round_up(s->widths[l + 1], 32));
+  al_ok((void**)&j->zero_bias, sizeof(float) * zmax, true);
+  // layer-1 weights as the Jacobian's network holds them, transposed [K0 x N1]
+  const int N1 = s->widths[1], K0 = s->K0;
+  std::vector<float> w1t((size_t)K0 * N1);
+  for (int r = 0; r < N1; ++r)
+    for (int c = 0; c < K0; ++c) {
+      float v = s->Wh[0][(size_t)r * K0 + c];
+      if (j->bf16) v = __bfloat162float(__float2bfloat16_rn(v));
+      w1t[(size_t)c * N1 + r] = v;
+    }
+  al_ok((void**)&j->W1T, sizeof(float) * w1t.size(), false);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(j->W1T, w1t.data(), sizeof(float) * w1t.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_jac(j);
+    return cuda_fail(s, e, "Jacobian buffers");
+  }
+  if (!j->bf16) {
+    j->W32 = s->W32;
+    j->Kp = s->Kp8;
+  } else {
+    // BF16 weights: the state's own for a BF16 network, fresh copies for an FP8 one
+    for (int l = 0; l < L; ++l) {
+      const int Kl = s->widths[l], Nl = s->widths[l + 1];
+      const int kp = (int)round_up(Kl, 16);
+      j->Kp.push_back(kp);
+      if (s->precision == DF_BF16) {
+        j->Wb.push_back(nullptr);
+        continue;
+      }
+      std::vector<__nv_bfloat16> w((size_t)Nl * kp, __float2bfloat16_rn(0.0f));
+      for (int r = 0; r < Nl; ++r)
+        for (int c = 0; c < Kl; ++c) w[(size_t)r * kp + c] = __float2bfloat16_rn(s->Wh[l][(size_t)r * Kl + c]);
+      void* d = nullptr;
+      al_ok(&d, 2 * w.size(), false);
+      if (e == cudaSuccess) e = cudaMemcpy(d, w.data(), 2 * w.size(), cudaMemcpyHostToDevice);
+      j->Wb.push_back(d);
+      if (e != cudaSuccess) {
+        free_jac(j);
+        return cuda_fail(s, e, "Jacobian weights");
+      }
+    }
+    char emsg[256];
+    for (int l = 0; l < L; ++l) {
+      const bool last = l == L - 1;
+      const void* Wl = s->precision == DF_BF16 ? s->Wlp[l] : j->Wb[l];
+      // forward pass: hidden layers also store GELU'(z); the read-out is plain
+      TcLayer F{};
+      F.N = s->widths[l + 1];
+      F.K = s->widths[l];
+      F.BN = pick_bn(F.N, !last);
+      F.bias = s->bias[l];
+      F.out = last ? (void*)j->O : j->act[l & 1];
+      F.ldo = last ? j->ldo : j->act_ld[l & 1];
+      F.out_kind = last ? kXF32 : kXBF16;
+      F.gelu = !last;
+      F.out_scale = 1.0f;
+      F.elem_bytes = 2;
+      F.mode = last ? 0 : 1;
+      F.gbuf = last ? nullptr : j->G[l];
+      F.ldg = last ? 0 : j->ldg[l];
+      F.ntan = 1;
+      const void* Af = (l == 0) ? j->x : j->act[(l - 1) & 1];
+      const int64_t ldaf = (l == 0) ? j->ldx : j->act_ld[(l - 1) & 1];
+      bool ok = tc_encode_2d(&F.tmA, Af, 2, (uint64_t)F.K, (uint64_t)B, (uint64_t)ldaf * 2, 64, 128,
+                             emsg, sizeof emsg) &&
+                tc_encode_2d(&F.tmB, Wl, 2, (uint64_t)F.K, (uint64_t)F.N, (uint64_t)j->Kp[l] * 2, 64,
+                             (uint32_t)F.BN, emsg, sizeof emsg);
+      // tangent pass of layers 1.. (layer 0's tangents come from jac_tangent0)
+      TcLayer Tg = F;
+      Tg.bias = j->zero_bias;
+      Tg.out = last ? (void*)j->dO : j->tan[l & 1];
+      Tg.ldo = last ? j->ldo : j->tan_ld[l & 1];
+      Tg.gelu = false;
+      Tg.mode = last ? 0 : 2;
+      Tg.ntan = ntan;
+      if (ok && l > 0)
+        ok = tc_encode_2d(&Tg.tmA, j->tan[(l - 1) & 1], 2, (uint64_t)Tg.K, (uint64_t)R,
+                          (uint64_t)j->tan_ld[(l - 1) & 1] * 2, 64, 128, emsg, sizeof emsg);
+      if (!ok) {
+        free_jac(j);
+        return fail(s, DF_ERR_CUDA, "%s", emsg);
+      }
+      j->fwd.push_back(F);
+      j->tng.push_back(Tg);
+      if ((e = prepare_tc(F)) != cudaSuccess || (e = prepare_tc(Tg)) != cudaSuccess) {
+        free_jac(j);
+        return cuda_fail(s, e, "kernel attributes");
+      }
+    }
+  }
+  s->jac = j;
+  return DF_OK;
+}
+
 struct df_graph {
   df_state* s = nullptr;
   cudaGraph_t graph = nullptr;
@@ -672,6 +850,64 @@ void df_graph_destroy(df_graph* g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   delete g;
+}
+
+df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const double* p,
+                           const double* Y, int64_t ldY, float* J_dY, double* dTnew, void* stream) {
+  df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
+  if (rc != DF_OK || n_cells == 0) return rc;
+  if (!J_dY) return fail(s, DF_ERR_INVALID_ARG, "J_dY is NULL");
+  if (s->L < 2) return fail(s, DF_ERR_UNSUPPORTED, "the Jacobian needs at least one hidden layer");
+  DeviceGuard guard(s->device);
+  if (!s->jac && (rc = build_jac(s)) != DF_OK) return rc;
+  Jac* j = s->jac;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = s->L, ntan = s->n + 1;
+  cudaError_t e = cudaSuccess;
+  for (int64_t c0 = 0; c0 < n_cells && e == cudaSuccess; c0 += j->B) {
+    const int64_t nb = std::min<int64_t>(j->B, n_cells - c0);
+    const RowMap cells{nullptr, nullptr, c0, nb};
+    const RowMap rows{nullptr, nullptr, 0, nb};
+    const RowMap trows{nullptr, nullptr, 0, nb * ntan};
+    e = launch_eos_pre(s->P, cells, T, p, Y, ldY, j->h0, nullptr, j->x, j->bf16 ? kXBF16 : kXF32,
+                       j->ldx, 1.0f, nullptr, st);
+    // forward pass with GELU' of every hidden layer
+    for (int l = 0; l < L && e == cudaSuccess; ++l) {
+      const bool last = l == L - 1;
+      if (j->bf16) {
+        e = launch_tc_gemm(j->fwd[l], rows, s->num_sms, s->d_err, st);
+      } else {
+        const float* A = (l == 0) ? (const float*)j->x : (const float*)j->act[(l - 1) & 1];
+        const int64_t lda = (l == 0) ? j->ldx : j->act_ld[(l - 1) & 1];
+        e = launch_sgemm_bias_act(rows, s->widths[l + 1], j->Kp[l], A, lda, j->W32[l], j->Kp[l],
+                                  s->bias[l], last ? j->O : (float*)j->act[l & 1],
+                                  last ? j->ldo : j->act_ld[l & 1], !last, s->num_sms, st,
+                                  last ? 0 : 1, last ? nullptr : (float*)j->G[l],
+                                  last ? 0 : j->ldg[l], 1);
+      }
+    }
+    // tangents: layer 0 directly, then GEMMs scaled by GELU' per cell
+    if (e == cudaSuccess) e = launch_jac_scale(s->P, nb, Y + c0, ldY, j->sc, st);
+    if (e == cudaSuccess)
+      e = launch_jac_tangent0(nb, ntan, s->widths[1], j->sc, j->W1T, j->G[0], j->ldg[0], j->bf16,
+                              L > 1 ? j->tan[0] : (void*)j->dO, j->tan_ld[0], st);
+    for (int l = 1; l < L && e == cudaSuccess; ++l) {
+      const bool last = l == L - 1;
+      if (j->bf16) {
+        e = launch_tc_gemm(j->tng[l], trows, s->num_sms, s->d_err, st);
+      } else {
+        e = launch_sgemm_bias_act(trows, s->widths[l + 1], j->Kp[l], (const float*)j->tan[(l - 1) & 1],
+                                  j->tan_ld[(l - 1) & 1], j->W32[l], j->Kp[l], j->zero_bias,
+                                  last ? j->dO : (float*)j->tan[l & 1], last ? j->ldo : j->tan_ld[l & 1],
+                                  false, s->num_sms, st, last ? 0 : 2,
+                                  last ? nullptr : (float*)j->G[l], last ? 0 : j->ldg[l], ntan);
+      }
+    }
+    if (e == cudaSuccess)
+      e = launch_jac_post(s->P, nb, c0, T, p, Y, ldY, j->O, j->ldo, j->dO, j->ldo, j->h0, J_dY,
+                          dTnew, st);
+  }
+  return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "Jacobian");
 }
 
 df_status df_get_step_summary(df_state* s, void* stream, df_step_stats* stats) {

@@ -310,3 +310,33 @@ def test_graph_replay_matches_direct_steps(df, prec):
     assert torch.equal(Ta, Tb) and torch.equal(Ya, Yb) and torch.equal(sa, sb)
     assert not torch.equal(Ta, dev(T))   # the steps did change the field
     g.close()
+
+
+# ---------------------------------------------------------------- Jacobians
+
+@pytest.mark.parametrize("name,N,prec", [("small-fp32-4k", 400, "fp32"), ("layer1d-30sp-1m", 160, "fp32"),
+                                         ("small-fp32-4k", 400, "bf16"), ("layer1d-30sp-1m", 160, "fp8")])
+def test_chem_jacobian_vs_finite_differences(df, name, N, prec):
+    """df_chem_jacobian against central differences of the oracle's step (every cell taken as
+    reacting). Columns of species below 1e-4 are excluded (the Box-Cox slope is singular at 0,
+    so differences there carry no information)."""
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    pr = {"fp32": df.DF_FP32, "bf16": df.DF_BF16, "fp8": df.DF_FP8_E4M3}[prec]
+    st = df.State(mech, net, precision=pr, T_react=0.0, batch_cells=256)
+    J, dTn = st.chem_jacobian(dev(T), dev(p), dev(Y))
+    torch.cuda.synchronize()
+    J, dTn = host(J).astype(np.float64), host(dTn)
+    # step 1e-4 Y_j: the oracle's Newton stops at 1e-12 T, which a smaller step would amplify
+    # into the differences of T'; the truncation error stays O(1e-8) relative
+    Jf, dTf = ostep.chem_step_jacobian_fd(mech, net, T, p, Y, dY_rel=1e-4, dY_min=1e-4)
+    mask = np.isfinite(Jf)
+    assert np.all(np.isfinite(J)), "flagged cells in the Jacobian"
+    # the network part of J is ~out_std * dO/dv ~ 1e-3; BF16 tangents carry ~1 % of it
+    atol = 2e-6 if prec == "fp32" else 5e-5
+    err = np.abs(J - Jf)[mask]
+    print(f"Jacobian {name} {prec}: max |dJ| {err.max():.3e}")
+    assert err.max() <= atol + 1e-4 * np.abs(Jf[mask]).max()
+    tm = np.isfinite(dTf)
+    rel = np.abs(dTn - dTf)[tm] / (np.abs(dTf[tm]) + 1.0)
+    print(f"dTnew {name} {prec}: max rel {rel.max():.3e}")
+    assert rel.max() <= (1e-4 if prec == "fp32" else 5e-2)

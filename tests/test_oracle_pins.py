@@ -367,3 +367,49 @@ def test_round_to_e4m3_matches_torch():
     # saturation and the representable extremes
     assert nw.round_to_e4m3(1e6) == 448.0 and nw.round_to_e4m3(-500.0) == -448.0
     assert nw.round_to_e4m3(2.0 ** -9) == 2.0 ** -9 and nw.round_to_e4m3(2.0 ** -11) == 0.0
+
+
+def test_mlp_jacobian_matches_torch_autograd():
+    net = synth.make_network([5, 7, 6, 3], 3, 11)
+    x = synth.Stream(4, "xj").uniform(6 * 5, -2, 2).reshape(6, 5)
+    J = nw.mlp_jacobian(net, x)
+
+    def f(v):
+        h = v
+        for l in range(net.n_layers):
+            h = torch.nn.functional.linear(h, torch.tensor(net.W[l]), torch.tensor(net.b[l]))
+            if l < net.n_layers - 1:
+                h = torch.nn.functional.gelu(h, approximate="tanh")
+        return h
+
+    for i in range(x.shape[0]):
+        ref = torch.autograd.functional.jacobian(f, torch.tensor(x[i])).numpy()
+        np.testing.assert_allclose(J[i], ref, rtol=1e-12, atol=1e-14)
+
+
+def test_step_jacobian_zero_network_closed_form():
+    """With an identically zero read-out, Y' = Y / sum(Y), so d(dY_k)/dY_j = -Y_k and
+    d(dY)/dT = 0; h is homogeneous of degree one in Y, which makes dT'/dY_j = h / cp and
+    dT'/dT = 1."""
+    mech, net, T, p, Y = synth.configs.build("small-fp32-4k", n_cells=24)
+    net.W[-1] = np.zeros_like(net.W[-1])
+    net.b[-1] = np.zeros_like(net.b[-1])
+    J, dTn = step.chem_step_jacobian_fd(mech, net, T, p, Y, dY_min=1e-4)
+    s = pe.state(mech, T, p, Y)
+    for i in range(24):
+        cols = [c for c in range(1, mech.n + 1) if np.isfinite(J[i, 0, c])]
+        np.testing.assert_allclose(J[i][:, cols], np.repeat(-Y[:, i:i + 1], len(cols), axis=1),
+                                   atol=2e-8)
+        np.testing.assert_allclose(J[i][:, 0], 0.0, atol=1e-10)
+        np.testing.assert_allclose(dTn[i, cols], s["h"][i] / s["cp"][i], rtol=1e-5, atol=1e-3)
+        assert dTn[i, 0] == pytest.approx(1.0, rel=1e-6)
+
+
+def test_step_jacobian_columns_conserve_mass():
+    """sum_k Y'_k = 1 for any input, so sum_k d(dY_k)/dT = 0 and sum_k d(dY_k)/dY_j = -1."""
+    mech, net, T, p, Y = synth.configs.build("small-fp32-4k", n_cells=16)
+    J, _ = step.chem_step_jacobian_fd(mech, net, T, p, Y, dY_min=1e-4)
+    colsum = np.nansum(J, axis=1)
+    fin = np.isfinite(J[:, 0, :])
+    np.testing.assert_allclose(colsum[:, 0], 0.0, atol=1e-9)
+    np.testing.assert_allclose(colsum[:, 1:][fin[:, 1:]], -1.0, atol=1e-7)
