@@ -15,6 +15,8 @@ What the paper fixes and what it leaves open:
     (Box & Cox 1964), Newton recovery of T from conserved enthalpy, mass-action kinetics.
 
 Modules: thermo (NASA-7), pr_eos (Peng-Robinson), network (Box-Cox, normalisation, GELU,
-MLP), step (active-cell list, reaction step, real-fluid properties, T from h).
+MLP, its Jacobian), step (active-cell list, reaction step, real-fluid properties, T from h,
+finite-difference Jacobian of the step), truth (the stiff-chemistry ground truth the network
+stands in for: C, BDF, oracle/truth.c).
 """
 from . import thermo, pr_eos, network, step  # noqa: F401
