@@ -413,3 +413,41 @@ def test_step_jacobian_columns_conserve_mass():
     fin = np.isfinite(J[:, 0, :])
     np.testing.assert_allclose(colsum[:, 0], 0.0, atol=1e-9)
     np.testing.assert_allclose(colsum[:, 1:][fin[:, 1:]], -1.0, atol=1e-7)
+
+
+def test_training_gradients_match_torch_autograd():
+    from oracle import train
+    net = synth.make_network([5, 9, 7, 3], 3, 21)
+    x = synth.Stream(5, "tx").uniform(12 * 5, -2, 2).reshape(12, 5)
+    Oh = synth.Stream(5, "to").normal(12 * 3).reshape(12, 3)
+    loss, dW, db = train.loss_and_grads(net, x, Oh)
+    Wt = [torch.tensor(w, requires_grad=True) for w in net.W]
+    bt = [torch.tensor(b, requires_grad=True) for b in net.b]
+    h = torch.tensor(x)
+    for l in range(net.n_layers):
+        h = torch.nn.functional.linear(h, Wt[l], bt[l])
+        if l < net.n_layers - 1:
+            h = torch.nn.functional.gelu(h, approximate="tanh")
+    lt = ((h - torch.tensor(Oh)) ** 2).sum() / x.shape[0]
+    lt.backward()
+    assert loss == pytest.approx(lt.item(), rel=1e-13)
+    for l in range(net.n_layers):
+        np.testing.assert_allclose(dW[l], Wt[l].grad.numpy(), rtol=1e-11, atol=1e-14)
+        np.testing.assert_allclose(db[l], bt[l].grad.numpy(), rtol=1e-11, atol=1e-14)
+
+
+def test_adam_matches_torch_optim():
+    from oracle import train
+    rs = synth.Stream(6, "adam")
+    p0 = [rs.normal(12).reshape(3, 4), rs.normal(3)]
+    gs = [[rs.normal(12).reshape(3, 4), rs.normal(3)] for _ in range(3)]
+    pt = [torch.tensor(a, requires_grad=True) for a in p0]
+    opt = torch.optim.Adam(pt, lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    p, m, v = [a.copy() for a in p0], [np.zeros_like(a) for a in p0], [np.zeros_like(a) for a in p0]
+    for t, g in enumerate(gs, start=1):
+        for a, gg in zip(pt, g):
+            a.grad = torch.tensor(gg)
+        opt.step()
+        p, m, v = train.adam_step(p, g, m, v, t, lr=1e-2)
+    for a, b in zip(p, pt):
+        np.testing.assert_allclose(a, b.detach().numpy(), rtol=1e-13, atol=1e-15)
