@@ -135,6 +135,65 @@ df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const
 df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const double* p,
                            const double* Y, int64_t ldY, float* J_dY, double* dTnew, void* stream);
 
+/* ---- training of the chemistry network ----
+ * The paper trains its network offline and prints no loss; the library's reading: the network
+ * is taught the change of the Box-Cox coordinates that a stiff integration of the cell
+ * chemistry produces over dt, with the loss
+ *   L = (1/B) sum_b sum_k (O_bk - Ohat_bk)^2,  Ohat_k = (BC(Y_target,k) - BC(Y_k) - out_mean_k)
+ *                                                       / out_std_k,
+ * O the network output for the cell's normalised input (a5). Gradients by a layer-by-layer
+ * backward pass through the tanh-form GELU (Sec. 3.3.2); Adam (Kingma & Ba 2015) with bias
+ * correction updates FP32 master weights and biases, after which the working copies the
+ * reaction step reads (FP32 for a DF_FP32 state, BF16 for a DF_BF16 state) are rewritten in
+ * place, so CUDA graphs of the step stay valid. DF_FP8_E4M3 states return DF_ERR_UNSUPPORTED.
+ * The first training call on a state allocates the masters, Adam moments and batch buffers
+ * (synchronising the device); a later call with a larger batch reallocates the batch buffers.
+ * Training calls use the state's training buffers and must not overlap one another. */
+typedef struct {
+  double lr;                  /* step size, > 0 */
+  double beta1;               /* first-moment decay, 0 <= beta1 < 1 */
+  double beta2;               /* second-moment decay, 0 <= beta2 < 1 */
+  double eps;                 /* denominator guard, > 0 */
+} df_adam;
+
+/* One Adam step on `batch` states: network input from (T, p, Y) (a1-a5, FP64), targets from
+ * Y and Y_target (device, species-major like Y, same ld), forward pass, loss, backward pass,
+ * update. loss_out (device or host, may be NULL) receives L as FP32 on `stream`. The states
+ * must be valid (finite, p > 0, the PR cubic solvable): a flagged state poisons the step. */
+df_status df_train_step(df_state* s, int64_t batch, const double* T, const double* p,
+                        const double* Y, const double* Y_target, int64_t ld, const df_adam* hp,
+                        float* loss_out, void* stream);
+
+/* The building blocks of df_train_step, for a caller that forms its own loss (e.g. a
+ * torch.autograd.Function). df_mlp_forward_train is df_mlp_forward (x [n_rows * (n+2)] and
+ * O [n_rows * n] row-major FP32, device) that also keeps the activations the backward pass
+ * needs. df_mlp_backward takes dL/dO (device [n_rows * n] FP32) for the rows of the last
+ * df_mlp_forward_train (n_rows must match) and leaves dL/dW, dL/db in the state (overwriting
+ * the previous gradients); dX (device [n_rows * (n+2)] FP32, may be NULL) receives dL/dx.
+ * df_adam_step applies the stored gradients. */
+df_status df_mlp_forward_train(df_state* s, int64_t n_rows, const float* x, float* O,
+                               void* stream);
+df_status df_mlp_backward(df_state* s, int64_t n_rows, const float* dO, float* dX, void* stream);
+df_status df_adam_step(df_state* s, const df_adam* hp, void* stream);
+
+/* Copies one layer's FP32 parameters out (W [widths[l+1] * widths[l]] row-major and
+ * b [widths[l+1]], device or host pointers, either may be NULL), asynchronously on `stream`:
+ * the master weights, the last gradients, or Adam's first or second moments. */
+#define DF_PARAM_WEIGHTS 0
+#define DF_PARAM_GRADS 1
+#define DF_PARAM_ADAM_M 2
+#define DF_PARAM_ADAM_V 3
+df_status df_get_params(df_state* s, int32_t layer, int32_t which, float* W, float* b,
+                        void* stream);
+/* Number of Adam steps taken on the state (0 before training). */
+df_status df_train_get_step(df_state* s, int64_t* steps);
+
+/* Saves the master weights, biases, Adam moments and step count to a file; df_state_load
+ * restores them into a state of the same network shape (any mechanism) and rewrites the
+ * working copies. Both synchronise the device. */
+df_status df_state_save(df_state* s, const char* path);
+df_status df_state_load(df_state* s, const char* path);
+
 /* ---- CUDA-graph execution of the step ----
  * A df_graph is one df_chem_step with fixed arguments (sizes, dt and the device buffers T, p,
  * Y, cell_status, n_active_out) captured into an executable CUDA graph, so a time loop replays

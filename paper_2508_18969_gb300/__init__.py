@@ -7,4 +7,4 @@ This package is the thin Python binding of that ABI.
 """
 from ._lib import (DF_BF16, DF_FP8_E4M3, DF_FP32, DF_CELL_NO_ROOT, DF_CELL_NONFINITE,  # noqa: F401
                    DF_CELL_NOT_CONVERGED, LIB_PATH)
-from .api import DFError, State, version  # noqa: F401
+from .api import DFError, MLPEOSFunction, State, version  # noqa: F401

@@ -28,6 +28,8 @@ DF_CELL_NONFINITE = 4
 
 DF_FP32, DF_BF16, DF_FP8_E4M3 = 0, 1, 2
 
+DF_PARAM_WEIGHTS, DF_PARAM_GRADS, DF_PARAM_ADAM_M, DF_PARAM_ADAM_V = 0, 1, 2, 3
+
 _dp = C.POINTER(C.c_double)
 
 
@@ -52,6 +54,11 @@ class Options(C.Structure):
                 ("newton_max_iter", C.c_int32), ("device", C.c_int32), ("batch_cells", C.c_int64)]
 
 
+class Adam(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("eps", C.c_double)]
+
+
 _VP = C.c_void_p
 _I64 = C.c_int64
 _ST = C.c_int32
@@ -70,6 +77,14 @@ SIGNATURES = {
     "df_mlp_forward": (_ST, [_VP, _I64, _VP, _VP, _VP]),
     "df_eos_post": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _VP]),
     "df_active_compact_static": (_ST, [_I64, C.c_double, _VP, _VP, _VP, _VP]),
+    "df_train_step": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP, _I64, C.POINTER(Adam), _VP, _VP]),
+    "df_mlp_forward_train": (_ST, [_VP, _I64, _VP, _VP, _VP]),
+    "df_mlp_backward": (_ST, [_VP, _I64, _VP, _VP, _VP]),
+    "df_adam_step": (_ST, [_VP, C.POINTER(Adam), _VP]),
+    "df_get_params": (_ST, [_VP, C.c_int32, C.c_int32, _VP, _VP, _VP]),
+    "df_train_get_step": (_ST, [_VP, C.POINTER(_I64)]),
+    "df_state_save": (_ST, [_VP, C.c_char_p]),
+    "df_state_load": (_ST, [_VP, C.c_char_p]),
     "df_graph_create": (_ST, [_VP, _I64, C.c_double, _VP, _VP, _VP, _I64, _VP, _VP, C.POINTER(_VP)]),
     "df_graph_launch": (_ST, [_VP, _VP]),
     "df_graph_destroy": (None, [_VP]),

@@ -121,6 +121,64 @@ class State:
                                                   *[_ptr(o) for o in out], _stream(stream)))
         return tuple(out)
 
+    # ---- training ----
+    @staticmethod
+    def _adam(lr=1e-3, betas=(0.9, 0.999), eps=1e-8):
+        return L.Adam(float(lr), float(betas[0]), float(betas[1]), float(eps))
+
+    def train_step(self, T, p, Y, Y_target, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, loss=None,
+                   stream=None):
+        """One Adam step on the states (T, p, Y) with targets Y_target (df_train_step).
+        Returns the device FP32 loss tensor (shape [1]) the step writes."""
+        if Y_target.stride(0) != Y.stride(0):
+            raise ValueError("Y and Y_target must share their row stride")
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=T.device)
+        hp = self._adam(lr, betas, eps)
+        self._check(self._lib.df_train_step(self.h, T.shape[0], _ptr(T), _ptr(p), _ptr(Y),
+                                            _ptr(Y_target), Y.stride(0), C.byref(hp), _ptr(loss),
+                                            _stream(stream)))
+        return loss
+
+    def mlp_forward_train(self, x, stream=None):
+        x = x.contiguous()
+        O = torch.empty(x.shape[0], self.n, dtype=torch.float32, device=x.device)
+        self._check(self._lib.df_mlp_forward_train(self.h, x.shape[0], _ptr(x), _ptr(O),
+                                                   _stream(stream)))
+        return O
+
+    def mlp_backward(self, dO, want_dx=True, stream=None):
+        dO = dO.contiguous()
+        dX = torch.empty(dO.shape[0], self.K0, dtype=torch.float32, device=dO.device) if want_dx else None
+        self._check(self._lib.df_mlp_backward(self.h, dO.shape[0], _ptr(dO), _ptr(dX), _stream(stream)))
+        return dX
+
+    def adam_step(self, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, stream=None):
+        hp = self._adam(lr, betas, eps)
+        self._check(self._lib.df_adam_step(self.h, C.byref(hp), _stream(stream)))
+
+    def params(self, layer, which=L.DF_PARAM_WEIGHTS, widths=None, stream=None):
+        """(W [out, in], b [out]) FP32 device tensors of one layer: master weights, last
+        gradients or Adam moments (df_get_params)."""
+        if widths is None:
+            raise ValueError("pass the network widths")
+        W = torch.empty(widths[layer + 1], widths[layer], dtype=torch.float32, device=self.device)
+        b = torch.empty(widths[layer + 1], dtype=torch.float32, device=self.device)
+        self._check(self._lib.df_get_params(self.h, int(layer), int(which), _ptr(W), _ptr(b),
+                                            _stream(stream)))
+        return W, b
+
+    def train_steps_taken(self):
+        v = C.c_int64()
+        self._check(self._lib.df_train_get_step(self.h, C.byref(v)))
+        return v.value
+
+    def save(self, path):
+        self._check(self._lib.df_state_save(self.h, str(path).encode()))
+
+    def load(self, path):
+        self._check(self._lib.df_state_load(self.h, str(path).encode()))
+
     # ---- kernel timing ----
     def profile_enable(self, on: bool = True):
         self._check(self._lib.df_profile_enable(self.h, 1 if on else 0))
@@ -171,6 +229,23 @@ class State:
         self._check(self._lib.df_eos_post(self.h, N, _ptr(O.contiguous()), _ptr(h0), _ptr(T),
                                           _ptr(p), _ptr(Y), Y.stride(0), _ptr(st), _stream(stream)))
         return st
+
+
+class MLPEOSFunction(torch.autograd.Function):
+    """The state's network as a differentiable torch op: forward = df_mlp_forward_train,
+    backward = df_mlp_backward (returns dL/dx; dL/dW and dL/db stay in the state for
+    State.adam_step). Usage: O = MLPEOSFunction.apply(x, state)."""
+
+    @staticmethod
+    def forward(ctx, x, state):
+        ctx.state = state
+        ctx.rows = x.shape[0]
+        return state.mlp_forward_train(x.detach().float())
+
+    @staticmethod
+    def backward(ctx, dO):
+        dX = ctx.state.mlp_backward(dO.float(), want_dx=ctx.needs_input_grad[0])
+        return dX, None
 
 
 class Graph:

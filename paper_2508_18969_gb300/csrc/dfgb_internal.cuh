@@ -94,6 +94,32 @@ cudaError_t launch_jac_post(const EosParams& P, int64_t ncell, int64_t cell0, co
                             int64_t ldo, const float* dO, int64_t lddo, const double* h0, float* J,
                             double* dTn, cudaStream_t st);
 
+// ---- launchers (train.cu) ----
+// Ohat [B x ldh] FP32 (zero pads) = (BC(Yt) - BC(Y) - out_mean) / out_std of cells 0..B-1.
+cudaError_t launch_train_targets(const EosParams& P, int64_t B, const double* Y, const double* Yt,
+                                 int64_t ldY, float* Oh, int64_t ldh, cudaStream_t st);
+// Reductions of the training kernels are summed in a fixed order through a scratch buffer
+// of kTrainScratchFloats (>= kColsumChunks x widest layer for column sums), so losses and
+// gradients are reproducible run to run.
+constexpr int kTrainScratchFloats = 4096;
+constexpr int kColsumChunks = 64;
+// dO [B x ldd] (BF16 or FP32, zero pads) = 2 (O - Ohat) / B; *loss = sum (O - Ohat)^2 / B.
+cudaError_t launch_loss_grad(int64_t B, int n, const float* O, int64_t ldo, const float* Oh,
+                             int64_t ldh, void* dO, int64_t ldd, bool bf16, float* loss,
+                             float* scratch, cudaStream_t st);
+// out [C x ldo] = in^T for in [R x ldi]; rows R..Rpad-1 of the transpose are zero.
+cudaError_t launch_transpose(int64_t R, int64_t C, const void* in, int64_t ldi, void* out,
+                             int64_t ldo, int64_t Rpad, bool bf16, cudaStream_t st);
+// out[c] = sum_r in[r][c], c < C (FP32 sums of BF16 or FP32 input); scratch holds
+// kColsumChunks x C floats.
+cudaError_t launch_colsum(int64_t R, int C, const void* in, int64_t ldi, bool bf16, float* out,
+                          float* scratch, cudaStream_t st);
+cudaError_t launch_adam(int64_t count, float* w, float* m, float* v, const float* g, float lr,
+                        float b1, float b2, float eps, float c1, float c2, cudaStream_t st);
+cudaError_t launch_publish(int N, int K, const float* Wm, int64_t ldm, float* W32, int64_t ld32,
+                           void* Wb, int64_t ldb, void* WT, int64_t ldt, bool WT_bf16,
+                           cudaStream_t st);
+
 // ---- launchers (compact.cu) ----
 constexpr int64_t kCompactChunk = 4096;   // cells per block of the compaction kernels
 // Stable list of cells with T > T_react. Needs scratch of compact_scratch_words(n) int64.

@@ -1,8 +1,7 @@
 // C ABI of libdfgb (include/df.h): state creation, the fused reaction step and the stage
 // entry points. Host code only orchestrates; every step of the path runs in the kernels
 // of eos.cu, compact.cu, mlp_simt.cu and mlp_tc.cu.
-#include "dfgb_internal.cuh"
-#include "../../include/df.h"
+#include "state.cuh"
 
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -15,92 +14,10 @@
 #include <string>
 #include <vector>
 
-using namespace dfgb;
 
-struct Jac {
-  int64_t B = 0;                         // cells per Jacobian batch
-  bool bf16 = false;                     // BF16 tensor-core passes (else FP32 SIMT)
-  size_t eb = 4;
-  void* x = nullptr;
-  int64_t ldx = 0;
-  void* act[2] = {nullptr, nullptr};
-  int64_t act_ld[2] = {0, 0};
-  std::vector<void*> G;                  // GELU'(z) of each hidden layer [B x ldg]
-  std::vector<int64_t> ldg;
-  void* tan[2] = {nullptr, nullptr};     // tangent activations [B (n+1) x tan_ld]
-  int64_t tan_ld[2] = {0, 0};
-  float* O = nullptr;
-  int64_t ldo = 0;
-  float* dO = nullptr;
-  double* h0 = nullptr;
-  float* sc = nullptr;
-  float* W1T = nullptr;
-  float* zero_bias = nullptr;
-  std::vector<void*> Wb;                 // BF16 weights owned here (FP8 states)
-  std::vector<float*> W32;               // FP32 weights (SIMT), shared with the state
-  std::vector<int> Kp;
-  std::vector<TcLayer> fwd, tng;
-};
-
-struct df_state {
-  int device = 0;
-  int num_sms = 0;
-  int n = 0, K0 = 0, L = 0;
-  std::vector<int> widths;
-  int precision = DF_FP32;
-  double T_react = 0, lambda = 0.1, dt = 0;
-  int64_t cap = 0;                       // rows per batch
-  EosParams P{};
-  double* d_spc = nullptr;
-  double* d_K = nullptr;
-  double* d_norm = nullptr;
-  float* d_spc2 = nullptr;               // double-float copies of the EoS tables
-  float* d_K2 = nullptr;
-  int* d_err = nullptr;                  // kernel error word
-  int64_t* d_count = nullptr;            // reacting cells of the last step
-  int64_t* d_flagged = nullptr;          // flagged cells of the last step
-  int64_t* d_iters = nullptr;            // Newton iterations of the last step
-  std::vector<float*> W32;               // FP32 weights, [N x Kp8] zero padded (SIMT)
-  std::vector<int> Kp8;
-  std::vector<float*> bias;
-  std::vector<void*> Wlp;                // BF16 / FP8 weights [N x Kp16]
-  std::vector<float*> col_scale;         // FP8 dequantisation scale per output channel
-  std::vector<float> act_scale;          // FP8 quantisation scale of each layer's input
-  // batch scratch
-  void* x = nullptr;
-  int64_t ldx = 0;
-  void* act[2] = {nullptr, nullptr};
-  int64_t act_ld[2] = {0, 0};
-  float* O = nullptr;
-  int64_t ldo = 0;
-  double* h0 = nullptr;
-  int32_t* rstat = nullptr;
-  // compaction scratch, grown on demand
-  int32_t* idx = nullptr;
-  int64_t idx_cap = 0;
-  int64_t* cscr = nullptr;
-  int64_t cscr_words = 0;
-  std::vector<TcLayer> tcl;
-  std::vector<std::vector<float>> Wh;    // host copies of the FP32 weights (Jacobian set-up)
-  struct Jac* jac = nullptr;             // Jacobian context, built at the first Jacobian call
-  std::string err;
-  // kernel timing (df_profile_enable / df_profile_read)
-  bool prof_on = false;
-  struct Rec { int fam; cudaEvent_t a, b; };
-  std::vector<Rec> prof_recs;
-  std::vector<cudaEvent_t> prof_pool;
-  std::vector<std::string> prof_names;
-  std::vector<int64_t> prof_launches;
-  std::vector<double> prof_ms;
-};
-
-namespace {
+namespace dfgb {
 
 thread_local std::string g_create_err;
-// FP8 activations (network input and hidden layers) are stored as e4m3(v * 32): the inputs are
-// Z-scores and the hidden activations GELU outputs, both O(1-10), so x32 keeps them between
-// e4m3's smallest normal (2^-6) and its maximum (448).
-constexpr float kFp8ActScale = 32.0f;
 const char* kVersion = "dfgb 0.1.0 (sm_103a)";
 
 df_status fail(df_state* s, df_status code, const char* fmt, ...) {
@@ -116,26 +33,6 @@ df_status fail(df_state* s, df_status code, const char* fmt, ...) {
 df_status cuda_fail(df_state* s, cudaError_t e, const char* where) {
   return fail(s, e == cudaErrorMemoryAllocation ? DF_ERR_OOM : DF_ERR_CUDA, "%s: %s", where,
               cudaGetErrorString(e));
-}
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    cudaGetDevice(&prev);
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
-
-template <typename T>
-cudaError_t dalloc(T** p, size_t count) {
-  return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
 }
 
 // Tile width of a layer: hidden layers from the compiled set {64, 128, 160, 208, 256}, the
@@ -173,6 +70,15 @@ __global__ void cast_rows_kernel(int64_t rows, int K, const float* __restrict__ 
   }
 }
 
+cudaError_t launch_cast_rows(int64_t rows, int K, const float* in, int64_t ldi, void* out,
+                             int64_t ldo, int kind, float scale, int num_sms, cudaStream_t st) {
+  const int64_t total = rows * ldo;
+  if (total <= 0) return cudaSuccess;
+  const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 16);
+  cast_rows_kernel<<<g, 256, 0, st>>>(rows, K, in, ldi, out, ldo, kind, scale);
+  return cudaGetLastError();
+}
+
 int xkind_of(int precision) {
   return precision == DF_BF16 ? kXBF16 : precision == DF_FP8_E4M3 ? kXFP8 : kXF32;
 }
@@ -195,6 +101,8 @@ void free_state(df_state* s) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   free_jac(s->jac);
   s->jac = nullptr;
+  free_trn(s->trn);
+  s->trn = nullptr;
   f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
   for (auto p : s->W32) f(p);
   for (auto p : s->bias) f(p);
@@ -223,25 +131,6 @@ int prof_family(df_state* s, const char* name) {
   s->prof_ms.push_back(0.0);
   return (int)s->prof_names.size() - 1;
 }
-
-// Brackets the launches made during its lifetime with events on `st` when timing is on.
-struct ProfScope {
-  df_state* s;
-  cudaStream_t st;
-  df_state::Rec r{};
-  ProfScope(df_state* s_, const char* name, cudaStream_t st_) : s(s_), st(st_) {
-    if (!s->prof_on) return;
-    r.fam = prof_family(s, name);
-    r.a = prof_event(s);
-    r.b = prof_event(s);
-    cudaEventRecord(r.a, st);
-  }
-  ~ProfScope() {
-    if (!s->prof_on || !r.a) return;
-    cudaEventRecord(r.b, st);
-    s->prof_recs.push_back(r);
-  }
-};
 
 // The network layers a6-a7 on rows of the batch buffers: x -> act -> ... -> O.
 df_status run_mlp(df_state* s, const RowMap& rm, cudaStream_t st) {
@@ -298,9 +187,6 @@ df_status ensure_compact(df_state* s, int64_t n) {
   return DF_OK;
 }
 
-}  // namespace
-
-namespace dfgb {
 // Error text of entry points that take no state (read with df_get_last_error(NULL)).
 void set_global_error(const char* msg) { g_create_err = msg; }
 }  // namespace dfgb
@@ -859,7 +745,15 @@ df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const 
   if (!J_dY) return fail(s, DF_ERR_INVALID_ARG, "J_dY is NULL");
   if (s->L < 2) return fail(s, DF_ERR_UNSUPPORTED, "the Jacobian needs at least one hidden layer");
   DeviceGuard guard(s->device);
-  if (!s->jac && (rc = build_jac(s)) != DF_OK) return rc;
+  if (s->jac && s->jac->wver != s->wver) {  // training changed the weights
+    cudaDeviceSynchronize();
+    free_jac(s->jac);
+    s->jac = nullptr;
+  }
+  if (!s->jac) {
+    if ((rc = sync_host_weights(s)) != DF_OK || (rc = build_jac(s)) != DF_OK) return rc;
+    s->jac->wver = s->wver;
+  }
   Jac* j = s->jac;
   cudaStream_t st = (cudaStream_t)stream;
   const int L = s->L, ntan = s->n + 1;

@@ -1,0 +1,220 @@
+// Training of the chemistry network: targets, loss, the element-wise parts of the backward
+// pass and the Adam update. The GEMMs of the backward pass (weight gradients dZ^T H and input
+// gradients dZ W, the latter scaled by GELU'(z) in its epilogue) run on the same tcgen05 /
+// SIMT kernels as the forward pass; these kernels prepare their operands.
+#include "dfgb_internal.cuh"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+namespace dfgb {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxBlocks = kTrainScratchFloats;   // element-wise grids, one loss partial each
+
+__device__ __forceinline__ double boxcox(double y, double lam) {
+  return (y > 0.0 ? pow(y, lam) - 1.0 : -1.0) / lam;
+}
+
+// Ohat[b][k] = (BC(Yt_k) - BC(Y_k) - out_mean_k) / out_std_k, FP32 [B x ldh], zero pad.
+__global__ void targets_kernel(EosParams P, int64_t B, const double* __restrict__ Y,
+                               const double* __restrict__ Yt, int64_t ldY,
+                               const double* __restrict__ norm, float* __restrict__ Oh,
+                               int64_t ldh) {
+  const int n = P.n, K0 = P.K0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < B * ldh;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / ldh;
+    const int k = (int)(e % ldh);
+    float v = 0.0f;
+    if (k < n) {
+      const double du = boxcox(Yt[k * ldY + b], P.lambda) - boxcox(Y[k * ldY + b], P.lambda);
+      v = (float)((du - norm[2 * K0 + k]) / norm[2 * K0 + n + k]);
+    }
+    Oh[e] = v;
+  }
+}
+
+// dO = 2 (O - Ohat) / B (columns >= n zero); part[block] = this block's share of
+// sum (O - Ohat)^2 / B (summed in a fixed order by sum_parts_kernel, so the loss is
+// reproducible run to run).
+template <typename GT>
+__global__ void loss_grad_kernel(int64_t B, int n, const float* __restrict__ O, int64_t ldo,
+                                 const float* __restrict__ Oh, int64_t ldh, GT* __restrict__ dO,
+                                 int64_t ldd, float invB, float* __restrict__ part) {
+  __shared__ float red[kThreads / 32];
+  float acc = 0.0f;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < B * ldd;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / ldd;
+    const int k = (int)(e % ldd);
+    float g = 0.0f;
+    if (k < n) {
+      const float r = O[b * ldo + k] - Oh[b * ldh + k];
+      acc = fmaf(r * r, invB, acc);
+      g = 2.0f * r * invB;
+    }
+    dO[e] = (GT)g;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.0f;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+// out[c] = sum_{j < parts} part[j * C + c], in order of j (one thread per c).
+__global__ void sum_parts_kernel(int parts, int C, const float* __restrict__ part,
+                                 float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  float s = 0.0f;
+  for (int j = 0; j < parts; ++j) s += part[(int64_t)j * C + c];
+  out[c] = s;
+}
+
+// out[c][r] = in[r][c] for r < R, zero for R <= r < Rpad (32x32 shared-memory tiles).
+template <typename T>
+__global__ void transpose_kernel(int64_t R, int64_t C, const T* __restrict__ in, int64_t ldi,
+                                 T* __restrict__ out, int64_t ldo, int64_t Rpad) {
+  __shared__ T tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int64_t r = r0 + j, c = c0 + threadIdx.x;
+    tile[j][threadIdx.x] = (r < R && c < C) ? in[r * ldi + c] : (T)0.0f;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int64_t c = c0 + j, r = r0 + threadIdx.x;
+    if (c < C && r < Rpad) out[c * ldo + r] = tile[threadIdx.x][j];
+  }
+}
+
+// part[blockIdx.y * C + c] = sum of in[r][c] over the rows of chunk blockIdx.y.
+template <typename T>
+__global__ void colsum_kernel(int64_t R, int C, const T* __restrict__ in, int64_t ldi,
+                              float* __restrict__ part) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const int64_t per = (R + gridDim.y - 1) / gridDim.y;
+  const int64_t r0 = blockIdx.y * per, r1 = min(R, r0 + per);
+  float s = 0.0f;
+  for (int64_t r = r0; r < r1; ++r) s += (float)in[r * ldi + c];
+  part[(int64_t)blockIdx.y * C + c] = s;
+}
+
+// Adam (Kingma & Ba 2015) on one parameter array: m, v moving averages of g and g^2, bias
+// corrections c1 = 1 - b1^t, c2 = 1 - b2^t, w -= lr (m / c1) / (sqrt(v / c2) + eps).
+__global__ void adam_kernel(int64_t count, float* __restrict__ w, float* __restrict__ m,
+                            float* __restrict__ v, const float* __restrict__ g, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
+    const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// Working copies of a master weight matrix Wm [N x ldm]: FP32 [N x ld32] (SIMT), BF16
+// [N x ldb] (tensor cores), and the transposed copy [K x ldt] (FP32 or BF16) for the input
+// gradient GEMM. Any destination may be NULL. Pads stay as allocated (zero).
+__global__ void publish_kernel(int N, int K, const float* __restrict__ Wm, int64_t ldm, float* W32,
+                               int64_t ld32, __nv_bfloat16* Wb, int64_t ldb, void* WT, int64_t ldt,
+                               int WT_bf16) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)N * K;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / K), c = (int)(e % K);
+    const float w = Wm[(int64_t)r * ldm + c];
+    if (W32) W32[(int64_t)r * ld32 + c] = w;
+    if (Wb) Wb[(int64_t)r * ldb + c] = __float2bfloat16_rn(w);
+    if (WT) {
+      if (WT_bf16) ((__nv_bfloat16*)WT)[(int64_t)c * ldt + r] = __float2bfloat16_rn(w);
+      else ((float*)WT)[(int64_t)c * ldt + r] = w;
+    }
+  }
+}
+
+int blocks_for(int64_t work) {
+  int64_t b = (work + kThreads - 1) / kThreads;
+  if (b < 1) b = 1;
+  return (int)(b < kMaxBlocks ? b : kMaxBlocks);
+}
+
+}  // namespace
+
+cudaError_t launch_train_targets(const EosParams& P, int64_t B, const double* Y, const double* Yt,
+                                 int64_t ldY, float* Oh, int64_t ldh, cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  targets_kernel<<<blocks_for(B * ldh), kThreads, 0, st>>>(P, B, Y, Yt, ldY, P.norm, Oh, ldh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_grad(int64_t B, int n, const float* O, int64_t ldo, const float* Oh,
+                             int64_t ldh, void* dO, int64_t ldd, bool bf16, float* loss,
+                             float* scratch, cudaStream_t st) {
+  if (B <= 0) return cudaMemsetAsync(loss, 0, sizeof(float), st);
+  const float invB = 1.0f / (float)B;
+  const int g = blocks_for(B * ldd);
+  if (bf16)
+    loss_grad_kernel<__nv_bfloat16><<<g, kThreads, 0, st>>>(B, n, O, ldo, Oh, ldh,
+                                                            (__nv_bfloat16*)dO, ldd, invB, scratch);
+  else
+    loss_grad_kernel<float><<<g, kThreads, 0, st>>>(B, n, O, ldo, Oh, ldh, (float*)dO, ldd, invB,
+                                                    scratch);
+  sum_parts_kernel<<<1, 32, 0, st>>>(g, 1, scratch, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(int64_t R, int64_t C, const void* in, int64_t ldi, void* out,
+                             int64_t ldo, int64_t Rpad, bool bf16, cudaStream_t st) {
+  if (R <= 0 || C <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((Rpad + 31) / 32), (unsigned)((C + 31) / 32));
+  const dim3 block(32, 8);
+  if (bf16)
+    transpose_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(
+        R, C, (const __nv_bfloat16*)in, ldi, (__nv_bfloat16*)out, ldo, Rpad);
+  else
+    transpose_kernel<float><<<grid, block, 0, st>>>(R, C, (const float*)in, ldi, (float*)out, ldo,
+                                                    Rpad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colsum(int64_t R, int C, const void* in, int64_t ldi, bool bf16, float* out,
+                          float* scratch, cudaStream_t st) {
+  if (C <= 0) return cudaSuccess;
+  if (R <= 0) return cudaMemsetAsync(out, 0, sizeof(float) * C, st);
+  const int64_t chunks = std::min<int64_t>((R + 1023) / 1024, kColsumChunks);
+  const dim3 grid((unsigned)((C + 127) / 128), (unsigned)chunks);
+  if (bf16)
+    colsum_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(R, C, (const __nv_bfloat16*)in, ldi, scratch);
+  else
+    colsum_kernel<float><<<grid, 128, 0, st>>>(R, C, (const float*)in, ldi, scratch);
+  sum_parts_kernel<<<(C + 127) / 128, 128, 0, st>>>((int)chunks, C, scratch, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(int64_t count, float* w, float* m, float* v, const float* g, float lr,
+                        float b1, float b2, float eps, float c1, float c2, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  adam_kernel<<<blocks_for(count), kThreads, 0, st>>>(count, w, m, v, g, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_publish(int N, int K, const float* Wm, int64_t ldm, float* W32, int64_t ld32,
+                           void* Wb, int64_t ldb, void* WT, int64_t ldt, bool WT_bf16,
+                           cudaStream_t st) {
+  publish_kernel<<<blocks_for((int64_t)N * K), kThreads, 0, st>>>(
+      N, K, Wm, ldm, W32, ld32, (__nv_bfloat16*)Wb, ldb, WT, ldt, WT_bf16 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+}  // namespace dfgb

@@ -4,6 +4,8 @@
   layer1d-30sp-1m   30 species, 200 reactions, network 32-1600-800-400-30, 2**20 cells,
                     1D supercritical mixing layer (every cell goes through the network)
   react30-16m       same mechanism and network, 2**24 cells of which ~30 % react (T > 600 K)
+  train30-1m        same mechanism and network, 2**20 training states across the mixing layer
+                    with p ~ U[5, 20] MPa (targets come from the stiff integration)
 Seeds are 20250818 + workload number; the 16M-cell workload reuses the 30-species
 mechanism and network.
 """
@@ -35,6 +37,8 @@ WORKLOADS = {
                                 "layer1d", 20250820, 0.0),
     "react30-16m": Workload("react30-16m", 30, 200, (32, 1600, 800, 400, 30), 1 << 24,
                             "reacting", 20250820, 600.0),
+    "train30-1m": Workload("train30-1m", 30, 200, (32, 1600, 800, 400, 30), 1 << 20,
+                           "training", 20250820, 0.0),
 }
 
 
@@ -51,6 +55,8 @@ def build(name: str, n_cells: int | None = None, field_seed: int | None = None):
         T, p, Y = fields.mixing_layer_1d(mech, N, fs)
     elif w.field == "reacting":
         T, p, Y = fields.reacting_mix(mech, N, fs)
+    elif w.field == "training":
+        T, p, Y = fields.training_states(mech, N, fs + 4)
     else:
         raise KeyError(w.field)
     return mech, net, T, p, Y

@@ -84,3 +84,17 @@ def reacting_mix(mech: Mechanism, N: int, seed: int, active_fraction: float = 0.
     T = _layer_T(Zf, c)
     Y = mixing_burning_Y(mech, Zf, c, s, 1e-8, 1e-3)
     return T, np.full(N, p), Y
+
+
+def training_states(mech: Mechanism, N: int, seed: int):
+    """Training states: positions x ~ U[-1, 1] across the 1D mixing layer's profile (so cold
+    mixing, the burning zone and hot products all appear), p ~ U[5, 20] MPa, minor species
+    jittered in [1e-8, 1e-3]."""
+    s = Stream(seed, "training-states")
+    x = s.uniform(N, -1.0, 1.0)
+    Zf = 0.5 * (1.0 + np.tanh(x / 0.1))
+    c = np.exp(-(((Zf - Z_ST) / 0.1) ** 2))
+    T = _layer_T(Zf, c)
+    p = s.uniform(N, 5.0e6, 20.0e6)
+    Y = mixing_burning_Y(mech, Zf, c, s, 1e-8, 1e-3)
+    return T, p, Y
