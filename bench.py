@@ -36,14 +36,14 @@ UNIT = "cells/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp8"])
     ap.add_argument("--workload", default="layer1d-30sp-1m")
     ap.add_argument("--cells", type=int, default=0, help="override the workload's cell count")
     ap.add_argument("--fp32-steps", type=int, default=3, help="timed steps of the FP32 comparison")
-    ap.add_argument("--cpu-sample", type=int, default=16384, help="cells of the CPU oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=131072, help="cells of the CPU oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="reacting cells per internal batch")

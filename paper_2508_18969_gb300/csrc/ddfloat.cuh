@@ -20,16 +20,29 @@ __device__ __forceinline__ f2 f2_make(float h, float l) { return f2{h, l}; }
 
 // Conversions between FP64 and FP32 done with integer operations: on this GPU the
 // F2F conversions run on the FP64 pipe, which is the scarce one. Values outside the ranges
-// handled by the bit manipulation (zero, very small or very large magnitudes, inf, NaN) take
-// the ordinary conversion instructions.
+// handled by the bit manipulation (very small or very large magnitudes, inf, NaN) take the
+// ordinary conversion instructions.
 
-// Exact FP32 -> FP64.
+// Exact FP32 -> FP64 (zeros included; subnormals, inf and NaN take the conversion instruction).
 __device__ __forceinline__ double f_to_d(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xFFu;
+  if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
   if (e == 0u || e == 255u) return (double)f;
   const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
   return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// Classification of FP64 values on their bits (integer pipes).
+__device__ __forceinline__ bool d_finite(double x) {
+  return ((__double2hiint(x) >> 20) & 0x7FF) != 0x7FF;
+}
+// x > 0 (false for zeros, negative values and NaN with the sign set).
+__device__ __forceinline__ bool d_pos(double x) { return __double_as_longlong(x) > 0; }
+// x >= c for a positive finite threshold c (false for negative x and NaN with the sign set;
+// a positive NaN compares true, so test d_finite as well).
+__device__ __forceinline__ bool d_ge_pos(double x, double c) {
+  return __double_as_longlong(x) >= __double_as_longlong(c);
 }
 
 // FP64 -> FP32 by truncation of the significand (relative error < 2^-23); used for seeds and
@@ -47,10 +60,10 @@ __device__ __forceinline__ float d_to_f_trunc(double x) {
 // lo the remaining 29 bits rounded to 24 (x == hi + lo to ~2^-53 relative).
 __device__ __forceinline__ f2 f2_from(double x) {
   const unsigned hi32 = (unsigned)__double2hiint(x);
+  const unsigned lo32 = (unsigned)__double2loint(x);
   const int e = (int)((hi32 >> 20) & 0x7FFu);
   if (e >= 897 && e <= 1100) {
     const unsigned sign = hi32 & 0x80000000u;
-    const unsigned lo32 = (unsigned)__double2loint(x);
     const unsigned hb = sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
     // remainder r * 2^(e - 1075), formed as r * 2^-64 * 2^(e - 1011) to stay in range
     float l = __fmul_rn(__fmul_rn(__uint2float_rn(lo32 & 0x1FFFFFFFu), 5.421010862427522e-20f),
@@ -58,6 +71,7 @@ __device__ __forceinline__ f2 f2_from(double x) {
     l = __uint_as_float(__float_as_uint(l) | sign);
     return f2{__uint_as_float(hb), l};
   }
+  if (((hi32 & 0x7FFFFFFFu) | lo32) == 0u) return f2{__uint_as_float(hi32 & 0x80000000u), 0.0f};
   const float h = __double2float_rn(x);
   return f2{h, __double2float_rn(x - (double)h)};
 }
@@ -99,6 +113,24 @@ __device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
 }
 
 __device__ __forceinline__ f2 f2_scale2(f2 a) { return f2{2.0f * a.h, 2.0f * a.l}; }
+
+// a * b for an FP32 b.
+__device__ __forceinline__ f2 f2_mulf(f2 a, float b) {
+  const float p = __fmul_rn(a.h, b);
+  float e = __fmaf_rn(a.h, b, -p);
+  e = __fmaf_rn(a.l, b, e);
+  return f2_norm(p, e);
+}
+
+// 1 / a: FP32 reciprocal of the high part and one Newton step in double-float,
+// r = r0 + r0 (1 - a r0) (relative error ~2^-46 for a normal a).
+__device__ __forceinline__ f2 f2_rcp(f2 a) {
+  const float r0 = __frcp_rn(a.h);
+  float p, e;
+  f2_prod(a, f2{r0, 0.0f}, p, e);          // a r0 = p + e, close to 1
+  const float res = __fadd_rn(__fsub_rn(1.0f, p), -e);  // 1 - a r0, exact to ~2^-48
+  return f2_norm(r0, __fmul_rn(r0, res));
+}
 
 // Accumulator with a lazily kept low part: s += p + e.
 __device__ __forceinline__ void acc_add(f2& s, float p, float e) {

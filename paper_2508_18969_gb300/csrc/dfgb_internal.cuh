@@ -56,8 +56,12 @@ struct EosParams {
   const double* spc;
   const double* Kmat;
   const double* norm;
-  const float* spc2;     // spc as double-float pairs (hi, lo), [n * kSpcStride * 2]
-  const float* K2;       // Kmat as double-float pairs, [n * n * 2]
+  // Double-float (hi, lo) tables of the mixing sums, with 1/W folded in:
+  //   spcw2[k][j]: j = 0 1/W_k, 1 s_k/W_k, 2 r_k/W_k, 3 b_k/W_k, 4..9 hc_j/W_k;
+  //   Ks2[i][j] = (1 - k_ij) s_j / W_j,  Kr2[i][j] = (1 - k_ij) r_j / W_j.
+  const float* spcw2;    // [n * kSpcStride * 2]
+  const float* Ks2;      // [n * n * 2]
+  const float* Kr2;      // [n * n * 2]
   int* err;              // device error word
   int64_t* flagged;      // device count of cells flagged by eos_post (may be NULL)
   int64_t* newton_iters; // device sum of Newton iterations (may be NULL)

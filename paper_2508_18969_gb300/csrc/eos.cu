@@ -8,13 +8,18 @@
 // with three quadratic forms A0, A1, A2 of the composition, computed once per composition,
 // so each Newton iteration of the T-from-h solve is O(1) in the species count.
 //
-// Precision plan (FP64 runs at 1/64 of the FP32 rate on this GPU):
+// Precision plan (FP64 runs at 1/64 of the FP32 rate on this GPU, so FP64 instructions --
+// arithmetic, compares and conversions alike -- are the scarce resource):
 //   * every sum over species and species pairs (W_mix, b_m, the three forms, the mixture
-//     NASA-7 coefficients) is accumulated in double-float on the FP32 pipes (~1e-14);
-//   * the cubic root, departure enthalpy, c_p and the Newton update are FP64; reciprocals
-//     start from the FP32 reciprocal and take FP64 Newton refinements;
-//   * the Box-Cox features that feed the network are FP32 (they are quantised anyway), and
-//     so is the multiplicative increment of Y' (it only scales Y' - Y).
+//     NASA-7 coefficients) is accumulated in double-float on the FP32 pipes (~1e-14), from a
+//     per-thread shared-memory column of the mass fractions in double-float;
+//   * Y' = Y (1 + delta), its sum and the renormalisation are double-float too; delta itself
+//     is FP32 (it only scales Y' - Y);
+//   * finiteness and threshold tests look at the bits of the FP64 values, and the FP32 <-> FP64
+//     conversions are integer operations (ddfloat.cuh);
+//   * the cubic root, departure enthalpy, c_p and the Newton update are FP64; reciprocals and
+//     square roots start from FP32 values and take FP64 Newton refinements;
+//   * the Box-Cox features that feed the network are FP32 (they are quantised anyway).
 #include "dfgb_internal.cuh"
 #include "ddfloat.cuh"
 
@@ -27,6 +32,8 @@ namespace {
 constexpr double kSQ2 = 1.41421356237309504880;
 constexpr double kInvR = 1.0 / kR;
 constexpr int kThreads = 128;
+constexpr int kPreBlocks = 4;    // resident blocks per SM the register budget is sized for
+constexpr int kPostBlocks = 4;
 constexpr int kCellNotConverged = 1;
 constexpr int kCellNoRoot = 2;
 constexpr int kCellNonfinite = 4;
@@ -41,30 +48,31 @@ struct Mixture {
 };
 
 struct SharedConsts {
-  const f2* spc;       // [n * kSpcStride] double-float species constants
-  const f2* K;         // [n * n] 1 - k_ij
+  const f2* spcw;      // [n * kSpcStride] double-float species constants over W
+  const f2* Ks;        // [n * n] (1 - k_ij) s_j / W_j
+  const f2* Kr;        // [n * n] (1 - k_ij) r_j / W_j
   const double* norm;  // [2 K0 + 2 n]
   const float* normf;  // the same in FP32 (for the FP32 feature and increment arithmetic)
 };
 
 // 8-byte words of shared memory the constants take: FP64 normalisation, then the
-// double-float tables (one f2 per word).
+// double-float tables (one f2 per word), then the FP32 normalisation.
 __host__ __device__ inline int consts_words(const EosParams& P) {
-  return 2 * P.K0 + 2 * P.n + P.n * kSpcStride + P.n * P.n + (P.K0 + P.n + 1);
+  return 2 * P.K0 + 2 * P.n + P.n * kSpcStride + 2 * P.n * P.n + (P.K0 + P.n + 1);
 }
 
 __device__ SharedConsts load_consts(const EosParams& P, double* sm) {
   const int nspc = P.n * kSpcStride, nk = P.n * P.n, nn = 2 * P.K0 + 2 * P.n;
-  // layout: norm (FP64) first, then the float pairs
   for (int i = threadIdx.x; i < nn; i += blockDim.x) sm[i] = P.norm[i];
   float* fs = reinterpret_cast<float*>(sm + nn);
-  for (int i = threadIdx.x; i < 2 * nspc; i += blockDim.x) fs[i] = P.spc2[i];
-  for (int i = threadIdx.x; i < 2 * nk; i += blockDim.x) fs[2 * nspc + i] = P.K2[i];
-  float* nf = fs + 2 * nspc + 2 * nk;
+  for (int i = threadIdx.x; i < 2 * nspc; i += blockDim.x) fs[i] = P.spcw2[i];
+  for (int i = threadIdx.x; i < 2 * nk; i += blockDim.x) fs[2 * nspc + i] = P.Ks2[i];
+  for (int i = threadIdx.x; i < 2 * nk; i += blockDim.x) fs[2 * nspc + 2 * nk + i] = P.Kr2[i];
+  float* nf = fs + 2 * nspc + 4 * nk;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) nf[i] = (float)P.norm[i];
   __syncthreads();
   return SharedConsts{reinterpret_cast<const f2*>(fs), reinterpret_cast<const f2*>(fs + 2 * nspc),
-                      sm, nf};
+                      reinterpret_cast<const f2*>(fs + 2 * nspc + 2 * nk), sm, nf};
 }
 
 // FP64 reciprocal: FP32 seed, two FP64 Newton steps (relative error ~1 ulp).
@@ -76,49 +84,41 @@ __device__ __forceinline__ double drcp(double x) {
   return fma(r, e, r);
 }
 
-// Mixture coefficients of one composition (a1, a2 and the ideal-gas part of a4). Y is
-// FP64 mass fractions; all sums run in double-float. ws is this thread's column of a
-// shared-memory scratch [2 NM][blockDim] (entry k at ws[k * blockDim]) holding ys_k, yr_k.
-template <int NM>
-__device__ void mixture(const double (&Y)[NM], int n, const SharedConsts& c, f2* ws,
-                        Mixture& m) {
+// Mixture coefficients of one composition (a1, a2 and the ideal-gas part of a4), all sums in
+// double-float. ycol is this thread's column of mass fractions (entry k at ycol[k * blockDim.x]).
+// Symmetric quadratic forms with K_ii = 1, ys_i = Y_i s_i / W_i, yr_i = Y_i r_i / W_i:
+//   F0 = sum_ij K_ij ys_i ys_j = sum_i ys_i (ys_i + 2 P_i),  P_i = sum_{j>i} Ks_ij Y_j,
+//   F1 = sum_ij K_ij ys_i yr_j = sum_i ys_i (yr_i + Q_i) + yr_i P_i,  Q_i = sum_{j>i} Kr_ij Y_j,
+//   F2 = sum_ij K_ij yr_i yr_j = sum_i yr_i (yr_i + 2 Q_i).
+__device__ void mixture(const f2* ycol, int n, const SharedConsts& c, Mixture& m) {
   const int stride = blockDim.x;
   f2 inv = {0.f, 0.f}, bs = {0.f, 0.f};
   f2 e0 = {0.f, 0.f}, e1 = e0, e2 = e0, e3 = e0, e4 = e0, e5 = e0;
-#pragma unroll
-  for (int k = 0; k < NM; ++k) {
-    if (k < n) {
-      const f2* q = c.spc + k * kSpcStride;
-      const f2 y = f2_mul(f2_from(Y[k]), q[0]);  // Y_k / W_k
-      acc_add(inv, y);
-      ws[(2 * k) * stride] = f2_mul(y, q[1]);      // ys_k = y_k s_k
-      ws[(2 * k + 1) * stride] = f2_mul(y, q[2]);  // yr_k = y_k r_k
-      acc_fma(bs, y, q[3]);
-      acc_fma(e0, y, q[4]);
-      acc_fma(e1, y, q[5]);
-      acc_fma(e2, y, q[6]);
-      acc_fma(e3, y, q[7]);
-      acc_fma(e4, y, q[8]);
-      acc_fma(e5, y, q[9]);
-    }
-  }
-  // Symmetric quadratic forms with K_ii = 1:
-  //   F0 = sum_ij K_ij ys_i ys_j, F1 = sum_ij K_ij ys_i yr_j, F2 = sum_ij K_ij yr_i yr_j,
-  // as sum_i ys_i (ys_i + 2 P_i) etc. with P_i = sum_{j>i} K_ij ys_j, Q_i = sum_{j>i} K_ij yr_j.
   f2 F0 = {0.f, 0.f}, F1 = F0, F2 = F0;
 #pragma unroll 1
   for (int i = 0; i < n; ++i) {
+    const f2* q = c.spcw + i * kSpcStride;
+    const f2 y = ycol[i * stride];
+    acc_fma(inv, y, q[0]);
+    acc_fma(bs, y, q[3]);
+    acc_fma(e0, y, q[4]);
+    acc_fma(e1, y, q[5]);
+    acc_fma(e2, y, q[6]);
+    acc_fma(e3, y, q[7]);
+    acc_fma(e4, y, q[8]);
+    acc_fma(e5, y, q[9]);
     f2 Pi = {0.f, 0.f}, Qi = {0.f, 0.f};
-    const f2* Krow = c.K + i * n;
+    const f2* Ksr = c.Ks + i * n;
+    const f2* Krr = c.Kr + i * n;
 #pragma unroll 4
     for (int j = i + 1; j < n; ++j) {
-      const f2 K = Krow[j];
-      acc_fma(Pi, K, ws[(2 * j) * stride]);
-      acc_fma(Qi, K, ws[(2 * j + 1) * stride]);
+      const f2 yj = ycol[j * stride];
+      acc_fma(Pi, Ksr[j], yj);
+      acc_fma(Qi, Krr[j], yj);
     }
     Pi = f2_fin(Pi);
     Qi = f2_fin(Qi);
-    const f2 ysi = ws[(2 * i) * stride], yri = ws[(2 * i + 1) * stride];
+    const f2 ysi = f2_mul(y, q[1]), yri = f2_mul(y, q[2]);
     acc_fma(F0, ysi, f2_add(ysi, f2_scale2(Pi)));
     acc_fma(F1, ysi, f2_add(yri, Qi));
     acc_fma(F1, yri, Pi);
@@ -135,6 +135,15 @@ __device__ void mixture(const double (&Y)[NM], int n, const SharedConsts& c, f2*
   m.A2 = W2 * f2_to(f2_fin(F2));
   m.bm = Wm * f2_to(f2_fin(bs));
   m.kb = drcp(2.0 * kSQ2 * m.bm);
+}
+
+// sqrt(x) for a positive normal x: t0 = x rsqrt_32(x), then one Newton step
+// t = t0 + (x - t0^2) r / 2 with the FP32 r = rsqrt_32(x) (relative error ~2^-44).
+__device__ __forceinline__ double dsqrt_pos(double x) {
+  const float r = rsqrtf(d_to_f_trunc(x));
+  const double rd = f_to_d(r);
+  const double t0 = x * rd;
+  return fma(fma(-t0, t0, x), 0.5 * rd, t0);
 }
 
 __device__ __forceinline__ double h_ig(const Mixture& m, double T) {
@@ -216,7 +225,7 @@ struct PRPoint {
 // Real-fluid state at (T, p) of a composition (a2-a4), with the departure cp if asked.
 __device__ PRPoint pr_point(const Mixture& m, double T, double p, bool want_cp, int& status) {
   const double iT = drcp(T);
-  const double t = sqrt(T);
+  const double t = dsqrt_pos(T);
   const double it = t * iT;                       // 1 / sqrt(T)
   const double am = fma(-2.0 * m.A1, t, fma(m.A2, T, m.A0));
   const double dam = fma(-m.A1, it, m.A2);
@@ -307,54 +316,52 @@ __device__ __forceinline__ __nv_fp8_e4m3 to_x<__nv_fp8_e4m3>(float v, float scal
 
 // a1-a5 for the valid rows of a batch.
 template <int NM, typename XT>
-__global__ void __launch_bounds__(kThreads) eos_pre_kernel(EosParams P, RowMap rows,
+__global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams P, RowMap rows,
     const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
     int64_t ldY, double* __restrict__ h0, double* __restrict__ Zout, XT* __restrict__ x,
     int64_t ldx, float x_scale, int32_t* __restrict__ status) {
   extern __shared__ double sm[];
   const SharedConsts c = load_consts(P, sm);
-  f2* ws = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
+  f2* ycol = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
   const int64_t nrow = valid_rows(rows);
   const int n = P.n, K0 = P.K0;
   const float lam = (float)P.lambda;
+  const float* mf = c.normf;        // in_mean
+  const float* isf = c.normf + K0;  // 1 / in_std
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrow;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cell = row_cell(rows, r);
     const double Tc = T[cell], pc = p[cell];
-    double Yk[NM];
-    bool finite = isfinite(Tc) && isfinite(pc) && pc > 0.0 && Tc > 0.0;
-#pragma unroll
-    for (int k = 0; k < NM; ++k) {
-      Yk[k] = (k < n) ? Y[k * ldY + cell] : 0.0;
-      finite = finite && isfinite(Yk[k]);
+    bool finite = d_finite(Tc) && d_finite(pc) && d_pos(pc) && d_pos(Tc);
+    // a5 features and the double-float column of Y in one pass over the species
+    XT* xr = x ? x + r * ldx : nullptr;
+#pragma unroll 2
+    for (int k = 0; k < n; ++k) {
+      const double yd = Y[k * ldY + cell];
+      finite = finite && d_finite(yd);
+      ycol[k * blockDim.x] = f2_from(yd);
+      if (xr) {
+        const float y = fmaxf(d_to_f_trunc(yd), 0.0f);
+        const float bc = (y > 0.0f) ? (exp2f(lam * log2f(y)) - 1.0f) / lam : -1.0f / lam;
+        xr[2 + k] = to_x<XT>((bc - mf[2 + k]) * isf[2 + k], x_scale);
+      }
     }
-    // a5 first, so the FP64 mass fractions are dead once the mixture sums take them over
-    if (x) {
-      XT* xr = x + r * ldx;
-      const float* mf = c.normf;        // in_mean
-      const float* isf = c.normf + K0;  // 1 / in_std
+    if (xr) {
       xr[0] = to_x<XT>(finite ? (d_to_f_trunc(Tc) - mf[0]) * isf[0] : 0.0f, x_scale);
       xr[1] = to_x<XT>(finite ? (d_to_f_trunc(pc) - mf[1]) * isf[1] : 0.0f, x_scale);
-#pragma unroll
-      for (int k = 0; k < NM; ++k) {
-        if (k < n) {
-          const float y = fmaxf(d_to_f_trunc(Yk[k]), 0.0f);
-          const float bc = (y > 0.0f) ? (exp2f(lam * log2f(y)) - 1.0f) / lam : -1.0f / lam;
-          const float v = (bc - mf[2 + k]) * isf[2 + k];
-          xr[2 + k] = to_x<XT>(finite ? v : 0.0f, x_scale);
-        }
-      }
+      if (!finite)
+        for (int k = 0; k < n; ++k) xr[2 + k] = to_x<XT>(0.0f, x_scale);
       for (int k = K0; k < ldx; ++k) xr[k] = to_x<XT>(0.0f, x_scale);
     }
     int st = 0;
     double h = __longlong_as_double(0x7ff8000000000000LL), Z = h;
     if (finite) {
       Mixture m;
-      mixture<NM>(Yk, n, c, ws, m);
+      mixture(ycol, n, c, m);
       const PRPoint q = pr_point(m, Tc, pc, false, st);
       Z = q.Z;
       h = h_ig(m, Tc) + q.h_dep * m.inv;
-      if (!isfinite(h)) st |= kCellNonfinite;
+      if (!d_finite(h)) st |= kCellNonfinite;
     } else {
       st = kCellNonfinite;
     }
@@ -374,18 +381,18 @@ __device__ __forceinline__ double ipow(double b, int m) {
   return r;
 }
 
-// a8-a10 for the valid rows of a batch. The new mass fractions are parked in shared memory
-// (one column per thread) until the Newton solve decides whether the cell is written.
+// a8-a10 for the valid rows of a batch. Y' lives in this thread's shared-memory column (double-
+// float) from the increment to the write-back, which happens only once the Newton solve for T
+// has succeeded.
 template <int NM>
-__global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap rows,
+__global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosParams P, RowMap rows,
     const float* __restrict__ O, int64_t ldo, const double* __restrict__ h0,
     double* __restrict__ T, const double* __restrict__ p, double* __restrict__ Y, int64_t ldY,
     const int32_t* __restrict__ pre_status, int32_t* __restrict__ cell_status) {
   extern __shared__ double sm[];
   const SharedConsts c = load_consts(P, sm);
-  // after the constants: mixture scratch [2 NM][blockDim] f2, parking area [NM][blockDim] FP64
-  f2* ws = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
-  double* ypark = sm + consts_words(P) + 2 * NM * blockDim.x;
+  f2* ycol = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
+  const int stride = blockDim.x;
   const int64_t nrow = valid_rows(rows);
   const int n = P.n, K0 = P.K0;
   const float* out_mean = c.normf + 2 * K0;
@@ -399,55 +406,51 @@ __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap 
     const int64_t cell = row_cell(rows, r);
     const double Told = T[cell], pc = p[cell], h0c = h0[r];
     int st = pre_status ? pre_status[r] : 0;  // flags eos_pre raised for this row
-    double Yn[NM];
-    bool finite = isfinite(Told) && isfinite(pc) && pc > 0.0 && isfinite(h0c);
-    double S = 0.0;
+    bool finite = d_finite(Told) && d_finite(pc) && d_pos(pc) && d_finite(h0c);
+    f2 S = {0.f, 0.f};
     const float* Or = O + r * ldo;
-#pragma unroll
-    for (int k = 0; k < NM; ++k) {
-      Yn[k] = 0.0;
-      if (k < n) {
-        const double y = Y[k * ldY + cell];
-        finite = finite && isfinite(y);
-        const float ldu = lamf * fmaf(out_std[k], Or[k], out_mean[k]);  // lambda du
-        double yn;
-        if (y >= 1e-30) {
-          // Y' = (Y^lambda + lambda du)^(1/lambda) = Y (1 + eps)^m, eps = lambda du Y^-lambda;
-          // the increment delta = (1 + eps)^m - 1 only scales Y' - Y, so FP32 suffices.
-          const float eps = ldu * exp2f(-lamf * log2f(d_to_f_trunc(y)));
-          if (eps <= -1.0f) {
-            yn = 0.0;
+#pragma unroll 2
+    for (int k = 0; k < n; ++k) {
+      const double y = Y[k * ldY + cell];
+      finite = finite && d_finite(y);
+      const float ldu = lamf * fmaf(out_std[k], Or[k], out_mean[k]);  // lambda du
+      f2 yn = {0.f, 0.f};
+      if (d_ge_pos(y, 1e-30)) {
+        // Y' = (Y^lambda + lambda du)^(1/lambda) = Y (1 + eps)^m, eps = lambda du Y^-lambda;
+        // the increment delta = (1 + eps)^m - 1 only scales Y' - Y, so FP32 suffices.
+        const f2 yf = f2_from(y);
+        const float eps = ldu * exp2f(-lamf * log2f(yf.h));
+        if (eps > -1.0f) {
+          const float lg = mf * log1pf(eps);
+          if (lg < 80.0f) {
+            yn = f2_add(yf, f2_mulf(yf, expm1f(lg)));
           } else {
-            const float lg = mf * log1pf(eps);
-            yn = (lg < 80.0f) ? fma(y, f_to_d(expm1f(lg)), y) : y * ipow(1.0 + f_to_d(eps), mpow);
+            yn = f2_from(y * ipow(1.0 + f_to_d(eps), mpow));
           }
-        } else {
-          const double base = ((y > 0.0) ? pow(y, lam) : 0.0) + f_to_d(ldu);
-          yn = (base > 0.0) ? ipow(base, mpow) : 0.0;
         }
-        Yn[k] = yn;
-        S += yn;
+      } else if (d_finite(y)) {
+        // Y below 1e-30 (or not positive): the closed form in FP64
+        const double base = ((y > 0.0) ? pow(y, lam) : 0.0) + f_to_d(ldu);
+        if (base > 0.0) yn = f2_from(ipow(base, mpow));
       }
+      ycol[k * stride] = yn;
+      acc_add(S, yn);
     }
-    if (!finite || !(S > 0.0)) st |= kCellNonfinite;
+    S = f2_fin(S);
+    if (!finite || !(S.h > 0.0f) || !isfinite(S.h)) st |= kCellNonfinite;
     double Tn = Told;
     int iters = 0;
     if (st == 0) {
-      const double iS = drcp(S);
-#pragma unroll
-      for (int k = 0; k < NM; ++k) {
-        Yn[k] *= iS;
-        if (k < n) ypark[k * blockDim.x + threadIdx.x] = Yn[k];
-      }
+      const f2 iS = f2_rcp(S);
+      for (int k = 0; k < n; ++k) ycol[k * stride] = f2_mul(ycol[k * stride], iS);
       Mixture m;
-      mixture<NM>(Yn, n, c, ws, m);
+      mixture(ycol, n, c, m);
       Tn = solve_T(m, pc, h0c, Told, P, iters, st);
     }
     if (st == 0) {
       T[cell] = Tn;
-#pragma unroll
-      for (int k = 0; k < NM; ++k)
-        if (k < n) Y[k * ldY + cell] = ypark[k * blockDim.x + threadIdx.x];
+#pragma unroll 2
+      for (int k = 0; k < n; ++k) Y[k * ldY + cell] = f2_to(ycol[k * stride]);
     }
     if (cell_status) cell_status[cell] = st;
     if (st && P.flagged) atomicAdd((unsigned long long*)P.flagged, 1ull);
@@ -461,21 +464,19 @@ __global__ void __launch_bounds__(kThreads) eos_post_kernel(EosParams P, RowMap 
 }
 
 template <int NM>
-__global__ void __launch_bounds__(kThreads) props_kernel(EosParams P, int64_t ncell,
+__global__ void __launch_bounds__(kThreads, kPreBlocks) props_kernel(EosParams P, int64_t ncell,
     const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
     int64_t ldY, double* rho, double* h, double* cp, double* Zo) {
   extern __shared__ double sm[];
   const SharedConsts c = load_consts(P, sm);
-  f2* ws = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
+  f2* ycol = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
   const int n = P.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncell;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double Tc = T[i], pc = p[i];
-    double Yk[NM];
-#pragma unroll
-    for (int k = 0; k < NM; ++k) Yk[k] = (k < n) ? Y[k * ldY + i] : 0.0;
+    for (int k = 0; k < n; ++k) ycol[k * blockDim.x] = f2_from(Y[k * ldY + i]);
     Mixture m;
-    mixture<NM>(Yk, n, c, ws, m);
+    mixture(ycol, n, c, m);
     int st = 0;
     const PRPoint q = pr_point(m, Tc, pc, cp != nullptr, st);
     if (rho) rho[i] = pc / (m.inv * q.Z * kR * Tc);
@@ -643,7 +644,8 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
     if (st == 0) {
       // (T, Y): cp and dh/dY, parked in dTn (its entries are final after the column loop)
       Mixture m0;
-      mixture<NM>(Yk, n, c, ws, m0);
+      for (int k = 0; k < n; ++k) ws[k * stride] = f2_from(Yk[k]);
+      mixture(ws, n, c, m0);
       const PRPoint q0 = pr_point(m0, Tc, pc, true, st);
       if (dTc) {
         dTc[0] = cp_ig(m0, Tc) + q0.cp_dep * m0.inv;
@@ -671,7 +673,8 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
           if (k < n) Ypc[k * stride] = Yn[k];
         }
         Mixture m1;
-        mixture<NM>(Yn, n, c, ws, m1);
+        for (int k = 0; k < n; ++k) ws[k * stride] = f2_from(Yn[k]);
+        mixture(ws, n, c, m1);
         int iters = 0;
         const double Tn = solve_T(m1, pc, h0c, Tc, P, iters, st);
         if (st == 0) {
@@ -709,10 +712,10 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
   }
 }
 
-// Dynamic shared memory of an EoS block: constants, the per-thread mixture scratch
-// (2 NM double-float words) and, for eos_post, the parking area of Y' (NM doubles).
-size_t eos_smem(const EosParams& P, int NM, bool park) {
-  return sizeof(double) * ((size_t)consts_words(P) + (size_t)(2 * NM + (park ? NM : 0)) * kThreads);
+// Dynamic shared memory of an EoS block: constants and the per-thread double-float column
+// of mass fractions (n words per thread).
+size_t eos_smem(const EosParams& P) {
+  return sizeof(double) * ((size_t)consts_words(P) + (size_t)P.n * kThreads);
 }
 
 // Opts a kernel into more than 48 KB of dynamic shared memory, once per device.
@@ -747,7 +750,7 @@ cudaError_t pre_launch(const EosParams& P, const RowMap& rows, const double* T, 
                        float xs, int32_t* status, cudaStream_t st) {
   cudaError_t e = smem_optin<eos_pre_kernel<NM, XT>>();
   if (e != cudaSuccess) return e;
-  eos_pre_kernel<NM, XT><<<grid_for(rows.nmax), kThreads, eos_smem(P, NM, false), st>>>(
+  eos_pre_kernel<NM, XT><<<grid_for(rows.nmax), kThreads, eos_smem(P), st>>>(
       P, rows, T, p, Y, ldY, h0, Z, x, ldx, xs, status);
   return cudaGetLastError();
 }
@@ -772,7 +775,7 @@ cudaError_t post_nm(const EosParams& P, const RowMap& rows, const float* O, int6
                     const int32_t* pre_status, int32_t* cell_status, cudaStream_t st) {
   cudaError_t e = smem_optin<eos_post_kernel<NM>>();
   if (e != cudaSuccess) return e;
-  eos_post_kernel<NM><<<grid_for(rows.nmax), kThreads, eos_smem(P, NM, true), st>>>(
+  eos_post_kernel<NM><<<grid_for(rows.nmax), kThreads, eos_smem(P), st>>>(
       P, rows, O, ldo, h0, T, p, Y, ldY, pre_status, cell_status);
   return cudaGetLastError();
 }
@@ -783,7 +786,7 @@ cudaError_t props_nm(const EosParams& P, int64_t n, const double* T, const doubl
                      cudaStream_t st) {
   cudaError_t e = smem_optin<props_kernel<NM>>();
   if (e != cudaSuccess) return e;
-  props_kernel<NM><<<grid_for(n), kThreads, eos_smem(P, NM, false), st>>>(P, n, T, p, Y, ldY,
+  props_kernel<NM><<<grid_for(n), kThreads, eos_smem(P), st>>>(P, n, T, p, Y, ldY,
                                                                            rho, h, cp, Z);
   return cudaGetLastError();
 }

@@ -103,7 +103,7 @@ void free_state(df_state* s) {
   s->jac = nullptr;
   free_trn(s->trn);
   s->trn = nullptr;
-  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
+  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_Kr2); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
   for (auto p : s->W32) f(p);
   for (auto p : s->bias) f(p);
   for (auto p : s->Wlp) f(p);
@@ -315,11 +315,27 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
     }
     return o;
   };
-  const std::vector<float> spc2 = split(spc), K2 = split(K);
-  CK(dalloc(&s->d_spc2, spc2.size()), "constants");
-  CK(dalloc(&s->d_K2, K2.size()), "constants");
-  CK(cudaMemcpy(s->d_spc2, spc2.data(), sizeof(float) * spc2.size(), cudaMemcpyHostToDevice), "copy");
-  CK(cudaMemcpy(s->d_K2, K2.data(), sizeof(float) * K2.size(), cudaMemcpyHostToDevice), "copy");
+  // mixing-sum tables with 1/W folded in (computed in FP64, then split)
+  std::vector<double> spcw(spc.size()), Ks((size_t)n * n), Kr((size_t)n * n);
+  for (int k = 0; k < n; ++k) {
+    const double iW = spc[(size_t)k * kSpcStride];
+    spcw[(size_t)k * kSpcStride] = iW;
+    for (int j = 1; j < kSpcStride; ++j)
+      spcw[(size_t)k * kSpcStride + j] = spc[(size_t)k * kSpcStride + j] * iW;
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double* q = &spc[(size_t)j * kSpcStride];
+      Ks[(size_t)i * n + j] = K[(size_t)i * n + j] * q[1] * q[0];
+      Kr[(size_t)i * n + j] = K[(size_t)i * n + j] * q[2] * q[0];
+    }
+  const std::vector<float> spcw2 = split(spcw), Ks2 = split(Ks), Kr2 = split(Kr);
+  CK(dalloc(&s->d_spc2, spcw2.size()), "constants");
+  CK(dalloc(&s->d_K2, Ks2.size()), "constants");
+  CK(dalloc(&s->d_Kr2, Kr2.size()), "constants");
+  CK(cudaMemcpy(s->d_spc2, spcw2.data(), sizeof(float) * spcw2.size(), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(s->d_K2, Ks2.data(), sizeof(float) * Ks2.size(), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(s->d_Kr2, Kr2.data(), sizeof(float) * Kr2.size(), cudaMemcpyHostToDevice), "copy");
   CK(dalloc(&s->d_err, 1), "error word");
   CK(cudaMemset(s->d_err, 0, sizeof(int)), "memset");
   CK(dalloc(&s->d_count, 1), "counters");
@@ -339,8 +355,9 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
   P.spc = s->d_spc;
   P.Kmat = s->d_K;
   P.norm = s->d_norm;
-  P.spc2 = s->d_spc2;
-  P.K2 = s->d_K2;
+  P.spcw2 = s->d_spc2;
+  P.Ks2 = s->d_K2;
+  P.Kr2 = s->d_Kr2;
   P.err = s->d_err;
   P.flagged = s->d_flagged;
   P.newton_iters = s->d_iters;

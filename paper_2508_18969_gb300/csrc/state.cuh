@@ -50,8 +50,9 @@ struct df_state {
   double* d_spc = nullptr;
   double* d_K = nullptr;
   double* d_norm = nullptr;
-  float* d_spc2 = nullptr;               // double-float copies of the EoS tables
+  float* d_spc2 = nullptr;               // double-float mixing-sum tables (EosParams)
   float* d_K2 = nullptr;
+  float* d_Kr2 = nullptr;
   int* d_err = nullptr;                  // kernel error word
   int64_t* d_count = nullptr;            // reacting cells of the last step
   int64_t* d_flagged = nullptr;          // flagged cells of the last step
