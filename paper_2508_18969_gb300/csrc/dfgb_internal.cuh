@@ -144,6 +144,8 @@ cudaError_t launch_sgemm_bias_act(const RowMap& rows, int N, int K, const float*
 struct TcLayer {
   CUtensorMap tmA;       // activations in, box {64 (K), 128 (M)}
   CUtensorMap tmB;       // weights [N x K], box {64, BN}
+  CUtensorMap tmO;       // output [rows x ldo], box {32, 32}, swizzled (tc_encode_out)
+  CUtensorMap tmG;       // GELU'(z) [rows x ldg] BF16 of kModeStoreG, same boxes
   int N, K, BN;
   const float* bias;     // [N]
   const float* col_scale;// [N] per-output-channel dequant scale (FP8) or NULL
@@ -161,8 +163,16 @@ struct TcLayer {
 bool tc_encode_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
                   uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,
                   uint32_t box_outer, char* err, size_t errlen);
+// Encodes L.tmO (and L.tmG for mode 1) for an output buffer of `rows` rows: columns 0..N-1
+// of L.out (row pitch L.ldo elements of L.out_kind), boxes of 32 x 32. Rows of a tile beyond
+// the valid rows of a launch are written too (up to `rows`): outputs are scratch buffers.
+bool tc_encode_out(TcLayer& L, uint64_t rows, char* err, size_t errlen);
 cudaError_t launch_tc_gemm(const TcLayer& L, const RowMap& rows, int num_sms, int* err,
                            cudaStream_t st);
 cudaError_t prepare_tc(const TcLayer& L);
+// Pipeline stages of the kernel instance with this tile width and output kind, and the
+// number of epilogue warps per TMEM lane quarter (for the host's choice of tile width).
+int tc_stages(int BN, int out_kind);
+int tc_epi_warps_per_quarter();
 
 }  // namespace dfgb

@@ -18,19 +18,25 @@
 // drains its own copies and MMAs, frees its TMEM and returns.
 #include "dfgb_internal.cuh"
 
+#ifndef EPI_PER_QUARTER
+#define EPI_PER_QUARTER 3
+#endif
+
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <string.h>
 #include <stdio.h>
+
+#include <type_traits>
 
 namespace dfgb {
 namespace {
 
 constexpr int BM = 128;
 constexpr int kRowBytes = 128;                 // K bytes per stage row (one swizzle span)
-constexpr int kEpiWarps = 8;                   // two per TMEM lane quarter
+constexpr int kEpiPerQuarter = EPI_PER_QUARTER;  // epilogue warps per TMEM lane quarter
+constexpr int kEpiWarps = 4 * kEpiPerQuarter;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kStageOut = 32 * 32 * 4;         // per-warp output staging (32 rows x 128 B)
 constexpr long long kWaitBudget = 2000000000LL;  // ~1 s of SM clocks per wait
 constexpr int kSmemLimit = 232448;             // opt-in dynamic shared memory per block
 constexpr uint32_t kSuspendNs = 200000;        // try_wait may park the thread this long
@@ -185,15 +191,31 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
       : "memory");
 }
 
-__device__ __forceinline__ float gelu_fast(float x) {
-  const float u = 0.7978845608028654f * fmaf(0.044715f * x * x, x, x);
+// tanh-form GELU (Sec. 3.3.2), 0.5 x (1 + tanh(c (x + a x^3))), evaluated as
+// u = x (c + a c x^2), t = tanh(u), y = 0.5 x + 0.5 x t: two multiplies, two FMAs, one MUFU
+// tanh and one multiply per element.
+constexpr float kGeluC = 0.7978845608028654f;        // sqrt(2 / pi)
+constexpr float kGeluAC = 0.044715f * 0.7978845608028654f;
+
+__device__ __forceinline__ float tanh_fast(float u) {
   float t;
   asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
-  return 0.5f * x * (1.0f + t);
+  return t;
 }
 
-template <int BN>
+__device__ __forceinline__ float gelu_fast(float x) {
+  const float t = tanh_fast(x * fmaf(x * x, kGeluAC, kGeluC));
+  const float hx = 0.5f * x;
+  return fmaf(hx, t, hx);
+}
+
+constexpr int out_bytes(int outk) { return outk == kXF32 ? 4 : (outk == kXBF16 ? 2 : 1); }
+
+template <int BN, int OUTK>
 struct Cfg {
+  // per warp: two staging buffers of 32 rows x 32 columns (the GELU' of kModeStoreG is BF16,
+  // no wider than the output)
+  static constexpr int kStageOut = 2 * 32 * 32 * out_bytes(OUTK);
   static constexpr int kStageBytes = (BM + BN) * kRowBytes;
   static constexpr int kStages0 = (kSmemLimit - 2048 - kEpiWarps * kStageOut) / kStageBytes;
   static constexpr int kStages = kStages0 > 8 ? 8 : kStages0;
@@ -204,20 +226,47 @@ struct Cfg {
       kStages * kStageBytes + kEpiWarps * kStageOut + 1024 /*align*/ + 1024 /*barriers*/;
 };
 
+// d/dx of the tanh-form GELU: 0.5 (1 + t) + 0.5 x (1 - t^2) c (1 + 3 a x^2).
 __device__ __forceinline__ float gelu_grad_fast(float x) {
-  const float c = 0.7978845608028654f;
-  const float u = c * fmaf(0.044715f * x * x, x, x);
-  float t;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
-  return fmaf(0.5f * x * (1.0f - t * t), c * fmaf(3.0f * 0.044715f, x * x, 1.0f), 0.5f * (1.0f + t));
+  const float x2 = x * x;
+  const float t = tanh_fast(x * fmaf(x2, kGeluAC, kGeluC));
+  const float hx = 0.5f * x;
+  return fmaf(hx * fmaf(-t, t, 1.0f), fmaf(x2, 3.0f * kGeluAC, kGeluC), fmaf(0.5f, t, 0.5f));
 }
 
-// Quantises 32 values of row `lane` to OUTK, transposes them through the warp's staging buffer
-// and writes whole 16-byte row units of the 32 rows m0.. to dst (row pitch ld elements).
+// Unit position in a staging row of RB bytes under the tensor map's swizzle: the 16-byte unit u
+// of row r sits at u ^ swz(r), swz = (r >> 2) & 1 for 32-byte rows (32B swizzle), (r >> 1) & 3
+// for 64-byte rows (64B swizzle), r & 7 for 128-byte rows (128B swizzle). Rows of eight
+// consecutive lanes then cover all 32 banks.
+template <int RB>
+__device__ __forceinline__ int swz(int r) {
+  return RB == 128 ? (r & 7) : (RB == 64 ? ((r >> 1) & 3) : ((r >> 2) & 1));
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+               ::"l"((uint64_t)map), "r"(x), "r"(y), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Waits until at most one bulk store group of this thread is still reading shared memory.
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Quantises 32 values of row `lane` to OUTK, writes them into one of the warp's two staging
+// buffers (32 rows x 32 columns, swizzled) and has lane 0 issue a TMA tensor store of the box
+// at (col0, m0); the tensor map clips rows and columns outside the output. A buffer is reused
+// only after the store issued from it two calls earlier has finished reading it.
 template <int OUTK>
-__device__ __forceinline__ void store_chunk(const float (&v)[32], void* dst_base, int64_t ld,
-                                            float out_scale, int64_t M, int64_t m0, int col0,
-                                            int ncols, uint8_t* stg, int lane) {
+__device__ __forceinline__ void store_chunk(const float (&v)[32], const CUtensorMap* map,
+                                            float out_scale, int64_t m0, int col0, uint8_t* stg2,
+                                            int& buf, int lane) {
   constexpr int esz = OUTK == kXF32 ? 4 : (OUTK == kXBF16 ? 2 : 1);
   constexpr int U = 2 * esz;     // 16-byte units per 32-column row segment
   constexpr int RB = 32 * esz;   // bytes per row segment
@@ -251,41 +300,29 @@ __device__ __forceinline__ void store_chunk(const float (&v)[32], void* dst_base
       w[u] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
     }
   }
-  // registers -> staging row `lane`, units rotated so a quarter-warp's stores hit distinct banks
-  const int rot = (U == 8) ? lane : (U == 4 ? (lane >> 1) : (lane >> 2));
+  uint8_t* stg = stg2 + buf * (32 * RB);
+  if (lane == 0) bulk_wait_read1();
+  __syncwarp();
+  const int sw = swz<RB>(lane);
 #pragma unroll
   for (int u = 0; u < U; ++u)
-    *reinterpret_cast<uint4*>(stg + lane * RB + ((u + rot) & (U - 1)) * 16) = w[u];
+    *reinterpret_cast<uint4*>(stg + lane * RB + ((u ^ sw) * 16)) = w[u];
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncwarp();
-  // staging -> global: lane l stores unit (l % U) of row (l / U) + k * (32 / U)
-  constexpr int rows_per = 32 / U;
-  constexpr int ecount = 16 / esz;
-  const int u = lane % U;
-  const int ufirst = u * ecount;
-  uint8_t* gbase = (uint8_t*)dst_base + (m0 * ld + col0) * esz;
-#pragma unroll
-  for (int k = 0; k < U; ++k) {
-    const int rr = lane / U + k * rows_per;
-    if (m0 + rr < M && ufirst < ncols) {
-      const int rrot = (U == 8) ? rr : (U == 4 ? (rr >> 1) : (rr >> 2));
-      const uint8_t* src = stg + rr * RB + ((u + rrot) & (U - 1)) * 16;
-      uint8_t* dst = gbase + (int64_t)rr * ld * esz + ufirst * esz;
-      if (ufirst + ecount <= ncols) {
-        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
-      } else {
-        for (int e = 0; e < (ncols - ufirst) * esz; ++e) dst[e] = src[e];
-      }
-    }
+  if (lane == 0) {
+    tma_store_2d(map, smem_u32(stg), col0, (int)m0);
+    bulk_commit();
   }
-  __syncwarp();
+  buf ^= 1;
 }
 
 // One 32-column chunk of the epilogue: per-channel scale, bias, GELU (or the row-group scale
 // of a tangent layer), then quantise and store; kModeStoreG also stores GELU'(z).
 template <int OUTK, bool GELU, bool SCALE, int MODE>
-__device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const TcArgs& g, int64_t M,
-                                               int64_t m0, int col0, int ncols, uint8_t* stg,
-                                               int lane) {
+__device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const TcArgs& g,
+                                               const CUtensorMap* tmO, const CUtensorMap* tmG,
+                                               int64_t M, int64_t m0, int col0, uint8_t* stg,
+                                               int& buf, int lane) {
   float v[32];
   if (MODE == kModeRowG) {
     // tangent row m0 + lane belongs to cell (m0 + lane) / ntan; G is BF16 [cells x ldg]
@@ -305,10 +342,9 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const Tc
         v[8 * u + 2 * e + 1] = __uint_as_float(r[8 * u + 2 * e + 1]) * f.y;
       }
     }
-    store_chunk<OUTK>(v, g.out, g.ldo, g.out_scale, M, m0, col0, ncols, stg, lane);
+    store_chunk<OUTK>(v, tmO, g.out_scale, m0, col0, stg, buf, lane);
     return;
   }
-  float gd[32];
   const float4* b4 = reinterpret_cast<const float4*>(g.bias + col0);  // zero padded to 32
   const float4* s4 = reinterpret_cast<const float4*>(g.col_scale + col0);
 #pragma unroll
@@ -325,25 +361,36 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const Tc
       float z = x[e];
       if (SCALE) z *= ss[e];
       z += bb[e];
-      if (MODE == kModeStoreG) gd[4 * u + e] = gelu_grad_fast(z);
       v[4 * u + e] = GELU ? gelu_fast(z) : z;
     }
   }
-  store_chunk<OUTK>(v, g.out, g.ldo, g.out_scale, M, m0, col0, ncols, stg, lane);
-  if (MODE == kModeStoreG)
-    store_chunk<kXBF16>(gd, g.gbuf, g.ldg, 1.0f, M, m0, col0, ncols, stg, lane);
+  store_chunk<OUTK>(v, tmO, g.out_scale, m0, col0, stg, buf, lane);
+  if (MODE == kModeStoreG) {
+    // second pass over the same accumulators: GELU'(z), so only one 32-value array is live
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float4 b = __ldg(b4 + u);
+      const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[4 * u + e] = gelu_grad_fast(__uint_as_float(r[4 * u + e]) + bb[e]);
+    }
+    store_chunk<kXBF16>(v, tmG, 1.0f, m0, col0, stg, buf, lane);
+  }
 }
 
 template <bool FP8, int BN, int OUTK, bool GELU, bool SCALE, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
-    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs g) {
-  using C = Cfg<BN>;
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmG, TcArgs g) {
+  using C = Cfg<BN, OUTK>;
+  // a 32-column epilogue chunk is stored as one TMA box, so chunks must not straddle tiles
+  static_assert(BN % 32 == 0, "tile width must be a multiple of 32");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;                                   // kStages x 16 KB
   uint8_t* sB = smem + C::kStages * BM * kRowBytes;     // kStages x BN*128 B
-  uint8_t* sOut = smem + C::kStages * C::kStageBytes;  // kEpiWarps x 4 KB
-  uint64_t* bars = (uint64_t*)(sOut + kEpiWarps * kStageOut);
+  uint8_t* sOut = smem + C::kStages * C::kStageBytes;  // kEpiWarps x kStageOut
+  uint64_t* bars = (uint64_t*)(sOut + kEpiWarps * C::kStageOut);
   // bars: full[S], empty[S], tfull[2], tempty[2], drain
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
@@ -447,8 +494,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
     const int q = warp & 3;                   // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;         // which of the alternating 32-column chunks
-    uint8_t* stg = sOut + (warp - 2) * kStageOut;
+    const int slot = (warp - 2) >> 2;         // which of the quarter's interleaved chunks
+    constexpr int kChunkStride = 32 * kEpiPerQuarter;
+    uint8_t* stg = sOut + (warp - 2) * C::kStageOut;
+    int buf = 0;
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmO) : "memory");
+    }
     uint32_t j = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int a = j & 1;
@@ -458,30 +510,39 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
       const int64_t m0 = (t / tiles_n) * BM + q * 32;
       const int n0 = (int)(t % tiles_n) * BN;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + a * C::kAccStride;
-      // chunks c0 = 32*half + 64*i; TMEM loads run one chunk ahead of the math
+      // chunks c = 32 slot + kChunkStride i; TMEM loads run one chunk ahead of the math,
+      // except in kModeStoreG, whose two stores per chunk leave no registers for a second
+      // chunk in flight
       uint32_t r0[32], r1[32];
-      int c0 = 32 * half;
-      if (c0 < BN) tmem_ld32(tbase + c0, r0);
-      for (; c0 < BN; c0 += 128) {
-        tmem_wait(r0);
-        const int c1 = c0 + 64;
-        if (c1 < BN) tmem_ld32(tbase + c1, r1);
-        {
-          const int ncols = min(g.N - (n0 + c0), BN - c0);
-          if (ncols > 0)
-            epilogue_chunk<OUTK, GELU, SCALE, MODE>(r0, g, M, m0, n0 + c0, ncols, stg, lane);
+      int c0 = 32 * slot;
+      if constexpr (MODE == kModeStoreG) {
+        for (; c0 < BN; c0 += kChunkStride) {
+          tmem_ld32(tbase + c0, r0);
+          tmem_wait(r0);
+          if (n0 + c0 < g.N)
+            epilogue_chunk<OUTK, GELU, SCALE, MODE>(r0, g, &tmO, &tmG, M, m0, n0 + c0, stg, buf, lane);
         }
+        c0 = BN;
+      }
+      if (c0 < BN) tmem_ld32(tbase + c0, r0);
+      for (; c0 < BN; c0 += 2 * kChunkStride) {
+        tmem_wait(r0);
+        const int c1 = c0 + kChunkStride;
+        if (c1 < BN) tmem_ld32(tbase + c1, r1);
+        if (n0 + c0 < g.N)
+          epilogue_chunk<OUTK, GELU, SCALE, MODE>(r0, g, &tmO, &tmG, M, m0, n0 + c0, stg, buf, lane);
         if (c1 >= BN) break;
         tmem_wait(r1);
-        if (c1 + 64 < BN) tmem_ld32(tbase + c1 + 64, r0);
-        const int ncols = min(g.N - (n0 + c1), BN - c1);
-        if (ncols > 0)
-          epilogue_chunk<OUTK, GELU, SCALE, MODE>(r1, g, M, m0, n0 + c1, ncols, stg, lane);
+        if (c1 + kChunkStride < BN) tmem_ld32(tbase + c1 + kChunkStride, r0);
+        if (n0 + c1 < g.N)
+          epilogue_chunk<OUTK, GELU, SCALE, MODE>(r1, g, &tmO, &tmG, M, m0, n0 + c1, stg, buf, lane);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty0 + 8 * a);
     }
+    // the tensor stores must have read shared memory (and be complete) before the CTA exits
+    if (lane == 0) bulk_wait_all();
   }
   __syncwarp();
   tc_fence_before();
@@ -522,7 +583,7 @@ cudaError_t tc_attr() {
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_done[dev]) {
     e = cudaFuncSetAttribute(tc_gemm_kernel<FP8, BN, OUTK, GELU, FP8, MODE>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN>::kSmemBytes);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN, OUTK>::kSmemBytes);
     if (e != cudaSuccess) return e;
     attr_done[dev] = true;
   }
@@ -531,7 +592,7 @@ cudaError_t tc_attr() {
 
 template <bool FP8, int BN, int OUTK, bool GELU, int MODE = kModePlain>
 cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream_t st) {
-  using C = Cfg<BN>;
+  using C = Cfg<BN, OUTK>;
   constexpr bool SCALE = FP8;
   auto kern = tc_gemm_kernel<FP8, BN, OUTK, GELU, SCALE, MODE>;
   cudaError_t e0 = tc_attr<FP8, BN, OUTK, GELU, MODE>();
@@ -539,7 +600,7 @@ cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream
   if (num_sms <= 0) return cudaSuccess;  // attribute set-up only
   const int64_t tiles = ((a.rows.nmax + BM - 1) / BM) * ((L.N + BN - 1) / BN);
   const unsigned grid = (unsigned)(tiles < num_sms ? (tiles > 0 ? tiles : 1) : num_sms);
-  kern<<<grid, kThreads, C::kSmemBytes, st>>>(L.tmA, L.tmB, a);
+  kern<<<grid, kThreads, C::kSmemBytes, st>>>(L.tmA, L.tmB, L.tmO, L.mode == kModeStoreG ? L.tmG : L.tmO, a);
   return cudaGetLastError();
 }
 
@@ -556,7 +617,7 @@ cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStrea
         case 64: return launch_bn<false, 64, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
         case 128: return launch_bn<false, 128, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
         case 160: return launch_bn<false, 160, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
-        case 208: return launch_bn<false, 208, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
+        case 224: return launch_bn<false, 224, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
         case 256: return launch_bn<false, 256, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
         default: return cudaErrorInvalidValue;
       }
@@ -565,7 +626,7 @@ cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStrea
       case 64: return launch_bn<false, 64, kXBF16, false, kModeRowG>(L, a, num_sms, st);
       case 128: return launch_bn<false, 128, kXBF16, false, kModeRowG>(L, a, num_sms, st);
       case 160: return launch_bn<false, 160, kXBF16, false, kModeRowG>(L, a, num_sms, st);
-      case 208: return launch_bn<false, 208, kXBF16, false, kModeRowG>(L, a, num_sms, st);
+      case 224: return launch_bn<false, 224, kXBF16, false, kModeRowG>(L, a, num_sms, st);
       case 256: return launch_bn<false, 256, kXBF16, false, kModeRowG>(L, a, num_sms, st);
       default: return cudaErrorInvalidValue;
     }
@@ -576,7 +637,7 @@ cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStrea
       case 64: return launch_bn<FP8, 64, HID, true>(L, a, num_sms, st);
       case 128: return launch_bn<FP8, 128, HID, true>(L, a, num_sms, st);
       case 160: return launch_bn<FP8, 160, HID, true>(L, a, num_sms, st);
-      case 208: return launch_bn<FP8, 208, HID, true>(L, a, num_sms, st);
+      case 224: return launch_bn<FP8, 224, HID, true>(L, a, num_sms, st);
       case 256: return launch_bn<FP8, 256, HID, true>(L, a, num_sms, st);
       default: return cudaErrorInvalidValue;
     }
@@ -618,6 +679,67 @@ bool tc_encode_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t i
   }
   return true;
 }
+
+namespace {
+bool encode_store(CUtensorMap* map, const void* base, int out_kind, uint64_t cols, uint64_t rows,
+                  uint64_t ld_elems, char* err, size_t errlen) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    snprintf(err, errlen, "cuTensorMapEncodeTiled is not available from the driver");
+    return false;
+  }
+  const int esz = out_bytes(out_kind);
+  if (((uintptr_t)base & 15) || ((ld_elems * esz) & 15)) {
+    snprintf(err, errlen, "output tensor map: base/pitch not 16-byte aligned");
+    return false;
+  }
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {ld_elems * esz};
+  const cuuint32_t box[2] = {32, 32};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt = out_kind == kXF32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : out_kind == kXBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const CUtensorMapSwizzle sw = esz == 4 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : esz == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    snprintf(err, errlen, "cuTensorMapEncodeTiled (output) failed (%d)", (int)r);
+    return false;
+  }
+  return true;
+}
+}  // namespace
+
+bool tc_encode_out(TcLayer& L, uint64_t rows, char* err, size_t errlen) {
+  if (!encode_store(&L.tmO, L.out, L.out_kind, (uint64_t)L.N, rows, (uint64_t)L.ldo, err, errlen))
+    return false;
+  if (L.mode == kModeStoreG)
+    return encode_store(&L.tmG, L.gbuf, kXBF16, (uint64_t)L.N, rows, (uint64_t)L.ldg, err, errlen);
+  L.tmG = L.tmO;
+  return true;
+}
+
+int tc_stages(int BN, int out_kind) {
+  auto pick = [&](auto bn) -> int {
+    constexpr int B = decltype(bn)::value;
+    return out_kind == kXF32 ? Cfg<B, kXF32>::kStages
+           : out_kind == kXBF16 ? Cfg<B, kXBF16>::kStages : Cfg<B, kXFP8>::kStages;
+  };
+  switch (BN) {
+    case 32: return pick(std::integral_constant<int, 32>{});
+    case 64: return pick(std::integral_constant<int, 64>{});
+    case 128: return pick(std::integral_constant<int, 128>{});
+    case 160: return pick(std::integral_constant<int, 160>{});
+    case 224: return pick(std::integral_constant<int, 224>{});
+    case 256: return pick(std::integral_constant<int, 256>{});
+    default: return 0;
+  }
+}
+
+int tc_epi_warps_per_quarter() { return kEpiPerQuarter; }
 
 cudaError_t prepare_tc(const TcLayer& L) {
   TcArgs a{};

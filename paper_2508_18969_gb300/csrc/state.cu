@@ -35,19 +35,31 @@ df_status cuda_fail(df_state* s, cudaError_t e, const char* where) {
               cudaGetErrorString(e));
 }
 
-// Tile width of a layer: hidden layers from the compiled set {64, 128, 160, 208, 256}, the
-// read-out layer from {32, 64}. Per-tile cost model: BN columns of work plus a fixed
-// ~64-column share for the A operand stream and the epilogue; the cheapest tiling of N wins.
-int pick_bn(int N, bool hidden) {
-  static const int hid[] = {256, 208, 160, 128, 64};
+// Tile width of a layer: hidden layers from the compiled set {64, 128, 160, 224, 256}, the
+// read-out layer from {32, 64}. Cost per layer, fitted to measured tcgen05 times on this GPU:
+//   * one k-block (K <= 64 BF16, 128 FP8): the epilogue is the work; each tile costs the
+//     32-column chunks its busiest epilogue warp handles, plus half a chunk of fixed cost;
+//   * longer K: the MMAs are the work; each tile costs BN + 128 columns, x1.3 when the tile
+//     leaves the TMA ring fewer than four stages.
+int pick_bn(int N, int K, bool hidden, int out_kind) {
+  static const int hid[] = {256, 224, 160, 128, 64};
   static const int last[] = {64, 32};
   const int* cand = hidden ? hid : last;
   const int nc = hidden ? 5 : 2;
+  const bool one_kblock = K * (out_kind == kXFP8 ? 1 : 2) <= 128;
+  const int epq = tc_epi_warps_per_quarter();
   int best = cand[nc - 1];
-  int64_t best_cost = INT64_MAX;
+  double best_cost = 1e300;
   for (int i = 0; i < nc; ++i) {
     const int bn = cand[i];
-    const int64_t cost = (int64_t)((N + bn - 1) / bn) * (bn + 64);
+    const double tiles = (double)((N + bn - 1) / bn);
+    double cost;
+    if (one_kblock) {
+      const int chunks = (bn + 31) / 32;
+      cost = tiles * ((chunks + epq - 1) / epq + 0.5);
+    } else {
+      cost = tiles * (bn + 128) * (tc_stages(bn, out_kind) < 4 ? 1.3 : 1.0);
+    }
     if (cost < best_cost) {
       best_cost = cost;
       best = bn;
@@ -452,10 +464,10 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
       TcLayer T{};
       T.N = s->widths[l + 1];
       T.K = s->widths[l];
-      T.BN = pick_bn(T.N, !last);
+      T.BN = pick_bn(T.N, T.K, !last, last ? kXF32 : xk);
       if (const char* env = getenv("DFGB_BN")) {  // hidden-layer tile-width override (sweeps)
         const int v = atoi(env);
-        if (!last && (v == 64 || v == 128 || v == 160 || v == 208 || v == 256)) T.BN = v;
+        if (!last && (v == 64 || v == 128 || v == 160 || v == 224 || v == 256)) T.BN = v;
       }
       T.bias = s->bias[l];
       T.col_scale = s->col_scale[l];
@@ -471,7 +483,8 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
       if (!tc_encode_2d(&T.tmA, Abase, (int)eb, (uint64_t)T.K, (uint64_t)s->cap,
                         (uint64_t)lda * eb, boxk, 128, emsg, sizeof emsg) ||
           !tc_encode_2d(&T.tmB, s->Wlp[l], (int)eb, (uint64_t)T.K, (uint64_t)T.N,
-                        (uint64_t)s->Kp8[l] * eb, boxk, (uint32_t)T.BN, emsg, sizeof emsg)) {
+                        (uint64_t)s->Kp8[l] * eb, boxk, (uint32_t)T.BN, emsg, sizeof emsg) ||
+          !tc_encode_out(T, (uint64_t)s->cap, emsg, sizeof emsg)) {
         free_state(s);
         delete s;
         return fail(nullptr, DF_ERR_CUDA, "%s", emsg);
@@ -643,7 +656,7 @@ df_status build_jac(df_state* s) {
       TcLayer F{};
       F.N = s->widths[l + 1];
       F.K = s->widths[l];
-      F.BN = pick_bn(F.N, !last);
+      F.BN = pick_bn(F.N, F.K, !last, last ? kXF32 : kXBF16);
       F.bias = s->bias[l];
       F.out = last ? (void*)j->O : j->act[l & 1];
       F.ldo = last ? j->ldo : j->act_ld[l & 1];
@@ -660,7 +673,8 @@ df_status build_jac(df_state* s) {
       bool ok = tc_encode_2d(&F.tmA, Af, 2, (uint64_t)F.K, (uint64_t)B, (uint64_t)ldaf * 2, 64, 128,
                              emsg, sizeof emsg) &&
                 tc_encode_2d(&F.tmB, Wl, 2, (uint64_t)F.K, (uint64_t)F.N, (uint64_t)j->Kp[l] * 2, 64,
-                             (uint32_t)F.BN, emsg, sizeof emsg);
+                             (uint32_t)F.BN, emsg, sizeof emsg) &&
+                tc_encode_out(F, (uint64_t)B, emsg, sizeof emsg);
       // tangent pass of layers 1.. (layer 0's tangents come from jac_tangent0)
       TcLayer Tg = F;
       Tg.bias = j->zero_bias;
@@ -672,6 +686,7 @@ df_status build_jac(df_state* s) {
       if (ok && l > 0)
         ok = tc_encode_2d(&Tg.tmA, j->tan[(l - 1) & 1], 2, (uint64_t)Tg.K, (uint64_t)R,
                           (uint64_t)j->tan_ld[(l - 1) & 1] * 2, 64, 128, emsg, sizeof emsg);
+      if (ok) ok = tc_encode_out(Tg, (uint64_t)R, emsg, sizeof emsg);
       if (!ok) {
         free_jac(j);
         return fail(s, DF_ERR_CUDA, "%s", emsg);

@@ -116,7 +116,7 @@ void free_jac(Jac* j);
 void free_trn(Trn* t);
 // Refreshes the host weight copies from the training masters when training changed them.
 df_status sync_host_weights(df_state* s);
-int pick_bn(int N, bool hidden);
+int pick_bn(int N, int K, bool hidden, int out_kind);
 
 struct DeviceGuard {
   int prev = -1;

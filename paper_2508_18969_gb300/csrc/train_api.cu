@@ -220,7 +220,7 @@ df_status ensure_batch(df_state* s, int64_t B) {
       TcLayer F{};
       F.N = N;
       F.K = K;
-      F.BN = pick_bn(N, !last);
+      F.BN = pick_bn(N, K, !last, last ? kXF32 : kXBF16);
       F.bias = s->bias[l];
       F.out = last ? (void*)t->O : t->H[l];
       F.ldo = last ? t->ldo : t->ldh[l];
@@ -234,13 +234,14 @@ df_status ensure_batch(df_state* s, int64_t B) {
       F.ntan = 1;
       ok = encode(&F.tmA, l == 0 ? t->x : t->H[l - 1], K, B, l == 0 ? t->ldx : t->ldh[l - 1], 128,
                   emsg, sizeof emsg) &&
-           encode(&F.tmB, s->Wlp[l], K, N, s->Kp8[l], F.BN, emsg, sizeof emsg);
+           encode(&F.tmB, s->Wlp[l], K, N, s->Kp8[l], F.BN, emsg, sizeof emsg) &&
+           tc_encode_out(F, (uint64_t)B, emsg, sizeof emsg);
       // input gradient: dZ_l [B x N] times W_l, i.e. against W_l^T [K x N]; layer 0's result
       // is the FP32 gradient of the network input, the others are scaled by GELU'(Z_{l-1})
       TcLayer D{};
       D.N = K;
       D.K = N;
-      D.BN = pick_bn(K, l > 0);
+      D.BN = pick_bn(K, N, l > 0, l > 0 ? kXBF16 : kXF32);
       D.bias = t->zero_bias;
       D.out = l > 0 ? t->dZ[l - 1] : (void*)t->dX;
       D.ldo = l > 0 ? t->ldz[l - 1] : t->lddx;
@@ -254,7 +255,8 @@ df_status ensure_batch(df_state* s, int64_t B) {
       D.ntan = 1;
       if (ok)
         ok = encode(&D.tmA, t->dZ[l], N, B, t->ldz[l], 128, emsg, sizeof emsg) &&
-             encode(&D.tmB, t->WT[l], N, K, t->ldt[l], D.BN, emsg, sizeof emsg);
+             encode(&D.tmB, t->WT[l], N, K, t->ldt[l], D.BN, emsg, sizeof emsg) &&
+             tc_encode_out(D, (uint64_t)B, emsg, sizeof emsg);
       // weight gradient: dZ_l^T [N x Bp] times (H_{l-1}^T [K x Bp])^T, FP32 out
       TcLayer Wg{};
       Wg.N = K;
@@ -271,7 +273,8 @@ df_status ensure_batch(df_state* s, int64_t B) {
       Wg.ntan = 1;
       if (ok)
         ok = encode(&Wg.tmA, t->ZT, Bp, N, Bp, 128, emsg, sizeof emsg) &&
-             encode(&Wg.tmB, t->HT, Bp, K, Bp, Wg.BN, emsg, sizeof emsg);
+             encode(&Wg.tmB, t->HT, Bp, K, Bp, Wg.BN, emsg, sizeof emsg) &&
+             tc_encode_out(Wg, (uint64_t)N, emsg, sizeof emsg);
       if (!ok) break;
       t->fwd.push_back(F);
       t->dgrad.push_back(D);
