@@ -6,6 +6,8 @@
   react30-16m       same mechanism and network, 2**24 cells of which ~30 % react (T > 600 K)
   train30-1m        same mechanism and network, 2**20 training states across the mixing layer
                     with p ~ U[5, 20] MPa (targets come from the stiff integration)
+  mix3d-30sp-64m    same mechanism and network, 400^3 cells of a 3D mixing layer displaced by
+                    gradient noise, p 5-20 MPa, every cell through the network
 Seeds are 20250818 + workload number; the 16M-cell workload reuses the 30-species
 mechanism and network.
 """
@@ -39,6 +41,8 @@ WORKLOADS = {
                             "reacting", 20250820, 600.0),
     "train30-1m": Workload("train30-1m", 30, 200, (32, 1600, 800, 400, 30), 1 << 20,
                            "training", 20250820, 0.0),
+    "mix3d-30sp-64m": Workload("mix3d-30sp-64m", 30, 200, (32, 1600, 800, 400, 30), 400 ** 3,
+                               "mixing3d", 20250820, 0.0),
 }
 
 
@@ -57,6 +61,8 @@ def build(name: str, n_cells: int | None = None, field_seed: int | None = None):
         T, p, Y = fields.reacting_mix(mech, N, fs)
     elif w.field == "training":
         T, p, Y = fields.training_states(mech, N, fs + 4)
+    elif w.field == "mixing3d":
+        T, p, Y = fields.mixing_layer_3d(mech, N, fs + 5)
     else:
         raise KeyError(w.field)
     return mech, net, T, p, Y

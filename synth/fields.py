@@ -23,7 +23,9 @@ Z_ST = 0.2  # burning-zone centre in mixture fraction (near the CH4/O2 mass stoi
 
 
 def mixing_burning_Y(mech: Mechanism, Zf: np.ndarray, c: np.ndarray, stream: Stream,
-                     minor_lo: float, minor_hi: float) -> np.ndarray:
+                     minor_lo: float, minor_hi: float, minor_u: np.ndarray | None = None) -> np.ndarray:
+    """minor_u (optional, [n - 4, N] in [0, 1)) replaces the stream's draws for the minor
+    species."""
     N = Zf.shape[0]
     n = mech.n
     W = mech.W
@@ -37,7 +39,11 @@ def mixing_burning_Y(mech: Mechanism, Zf: np.ndarray, c: np.ndarray, stream: Str
     Y[2] = m * 2.0 * W[2] / W[1]
     Y[3] = m * W[3] / W[1]
     if n > 4:
-        e = stream.uniform((n - 4) * N, np.log10(minor_lo), np.log10(minor_hi)).reshape(n - 4, N)
+        lo, hi = np.log10(minor_lo), np.log10(minor_hi)
+        if minor_u is None:
+            e = stream.uniform((n - 4) * N, lo, hi).reshape(n - 4, N)
+        else:
+            e = lo + (hi - lo) * minor_u
         Y[4:] = 10.0 ** e
     Y = np.maximum(Y, 0.0)
     return Y / Y.sum(axis=0, keepdims=True)
@@ -98,3 +104,90 @@ def training_states(mech: Mechanism, N: int, seed: int):
     p = s.uniform(N, 5.0e6, 20.0e6)
     Y = mixing_burning_Y(mech, Zf, c, s, 1e-8, 1e-3)
     return T, p, Y
+
+
+def _layer3d_chunk(mech: Mechanism, N: int, seed: int, side: int, delta: float, j0: int, j1: int):
+    """(T, p, Y) of cells j0..j1-1 of the 3D mixing layer of N cells."""
+    from .noise import fractal3, permutation_table
+    G = side ** 3
+    s = Stream(seed, "mixing-layer-3d")
+    j = np.arange(j0, j1, dtype=np.int64)
+    g = (j * G) // N if N != G else j
+    ix, iy, iz = g % side, (g // side) % side, g // (side * side)
+    x = -1.0 + (ix + 0.5) * (2.0 / side)
+    y = (iy + 0.5) / side
+    z = (iz + 0.5) / side
+    nz = fractal3(3.0 * (x + 1.0), 3.0 * y, 3.0 * z, permutation_table(seed), octaves=2)
+    Zf = 0.5 * (1.0 + np.tanh((x + 0.15 * nz) / delta))
+    c = np.exp(-(((Zf - Z_ST) / 0.1) ** 2))
+    T = _layer_T(Zf, c)
+    npv = fractal3(1.5 * (x + 1.0) + 17.0, 1.5 * y + 5.0, 1.5 * z + 11.0, permutation_table(seed + 1),
+                   octaves=1)
+    p = 12.5e6 + 7.5e6 * np.clip(2.5 * npv, -1.0, 1.0)
+    nm = mech.n - 4
+    mu = None
+    if nm > 0:
+        k = np.arange(nm, dtype=np.int64)[:, None]
+        mu = s.uniform_at((k * G + g[None, :]).astype(np.uint64))
+    return T, p, mixing_burning_Y(mech, Zf, c, s, 1e-8, 1e-3, minor_u=mu)
+
+
+_SHM = {}
+
+
+def _layer3d_worker_init(names, N, n):
+    from multiprocessing import shared_memory
+    for key, shape in (("T", (N,)), ("p", (N,)), ("Y", (n, N))):
+        shm = shared_memory.SharedMemory(name=names[key])
+        _SHM[key] = (shm, np.ndarray(shape, dtype=np.float64, buffer=shm.buf))
+
+
+def _layer3d_worker(args):
+    mech, N, seed, side, delta, j0, j1 = args
+    T, p, Y = _layer3d_chunk(mech, N, seed, side, delta, j0, j1)
+    _SHM["T"][1][j0:j1] = T
+    _SHM["p"][1][j0:j1] = p
+    _SHM["Y"][1][:, j0:j1] = Y
+    return j1 - j0
+
+
+def mixing_layer_3d(mech: Mechanism, N: int, seed: int, side: int = 400, delta: float = 0.1,
+                    chunk: int = 1 << 20, workers: int | None = None):
+    """3D supercritical mixing layer on a side^3 grid over [-1, 1] x [0, 1] x [0, 1], cells
+    numbered x fastest. The 1D layer's mixture fraction Zf(x) = (1 + tanh(x / delta)) / 2 is
+    displaced by improved gradient noise (two octaves, amplitude 0.15 in x), the burning zone
+    and T follow the 1D layer, p = 12.5 MPa + 7.5 MPa * clip(2.5 n_p, -1, 1) with a second,
+    single-octave noise field n_p (so p spans 5-20 MPa), minor species jittered in [1e-8, 1e-3].
+    N < side^3 takes the evenly strided grid cells floor(j side^3 / N) with the draws those
+    cells have in the full field (every draw is indexed by the global cell number); values
+    agree up to the last-bit rounding of numpy's vectorised transcendental functions. Large fields are generated by a pool of processes
+    (spawned, so it is safe after CUDA has been initialised) writing into shared memory."""
+    import os
+    n = mech.n
+    if workers is None:
+        workers = min(len(os.sched_getaffinity(0)), 32) if N >= (1 << 23) else 1
+    ranges = [(j0, min(N, j0 + chunk)) for j0 in range(0, N, chunk)]
+    if workers <= 1 or len(ranges) <= 1:
+        T, p, Y = np.empty(N), np.empty(N), np.empty((n, N))
+        for j0, j1 in ranges:
+            T[j0:j1], p[j0:j1], Y[:, j0:j1] = _layer3d_chunk(mech, N, seed, side, delta, j0, j1)
+        return T, p, Y
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    blocks = {k: shared_memory.SharedMemory(create=True, size=8 * sz)
+              for k, sz in (("T", N), ("p", N), ("Y", n * N))}
+    try:
+        names = {k: b.name for k, b in blocks.items()}
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(workers, initializer=_layer3d_worker_init, initargs=(names, N, n)) as pool:
+            done = sum(pool.imap_unordered(
+                _layer3d_worker, [(mech, N, seed, side, delta, j0, j1) for j0, j1 in ranges]))
+        assert done == N
+        T = np.ndarray((N,), np.float64, blocks["T"].buf).copy()
+        p = np.ndarray((N,), np.float64, blocks["p"].buf).copy()
+        Y = np.ndarray((n, N), np.float64, blocks["Y"].buf).copy()
+        return T, p, Y
+    finally:
+        for b in blocks.values():
+            b.close()
+            b.unlink()

@@ -47,6 +47,17 @@ class Stream:
         with np.errstate(over="ignore"):
             return _mix(self._key + i * _GAMMA)
 
+    def bits_at(self, idx) -> np.ndarray:
+        """Values at explicit counter positions idx (0-based; does not advance the stream):
+        bits_at(range(c, c + n)) equals the next n values of a stream at counter c."""
+        i = np.asarray(idx, dtype=np.uint64) + np.uint64(1)
+        with np.errstate(over="ignore"):
+            return _mix(self._key + i * _GAMMA)
+
+    def uniform_at(self, idx, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+        u = (self.bits_at(idx) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+        return lo + (hi - lo) * u
+
     def uniform(self, n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
         """n doubles in [lo, hi): the top 53 bits scaled by 2**-53."""
         u = (self.bits(n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)

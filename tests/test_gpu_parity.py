@@ -45,7 +45,8 @@ def _h_scale(mech, T, p, Y):
         np.abs(s["h_dep"] / s["W_mix"])
 
 
-WORKLOADS = [("small-fp32-4k", 4096), ("layer1d-30sp-1m", 6000), ("react30-16m", 5000)]
+WORKLOADS = [("small-fp32-4k", 4096), ("layer1d-30sp-1m", 6000), ("react30-16m", 5000),
+             ("mix3d-30sp-64m", 5000)]
 
 
 # ---------------------------------------------------------------- a0
