@@ -113,15 +113,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_setup(args):
+def dist_setup(args=None, backend=None):
+    """(world, rank, local) from the torchrun environment; joins the process group when
+    world > 1 (NCCL when CUDA is available, else gloo: the CPU path the tests use)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -132,13 +139,21 @@ def barrier(world):
 
 
 def max_over_ranks(world, v, local):
+    """Maximum of v over all ranks (the slowest rank's time bounds the whole job)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{local}")
+    dev = f"cuda:{local}" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_scaling_value(world, cells_per_rank, ms_max):
+    """Whole-job cells/s: every rank advances its own field of cells_per_rank cells, and the
+    job takes as long as its slowest rank."""
+    return world * cells_per_rank / (ms_max * 1e-3)
 
 
 def layer_flops(widths, rows):
@@ -259,7 +274,7 @@ def run_ours(args):
     rc, n_act, n_flag, iters = st.step_summary()
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = max_over_ranks(world, ms, local)
-    value = world * N / (ms_max * 1e-3)
+    value = weak_scaling_value(world, N, ms_max)
 
     # the same step replayed as one CUDA graph (df_graph_*), timed the same way
     g = st.graph(Td, pd, Yd, status=status)
