@@ -62,6 +62,10 @@ struct EosParams {
   const float* spcw2;    // [n * kSpcStride * 2]
   const float* Ks2;      // [n * n * 2]
   const float* Kr2;      // [n * n * 2]
+  // FP32 pair corrections of the T-from-h solve: kfs[i][j] = k_ij s_j / W_j,
+  // kfr[i][j] = k_ij r_j / W_j (k_ii = 0)
+  const float* kfs;      // [n * n]
+  const float* kfr;      // [n * n]
   int* err;              // device error word
   int64_t* flagged;      // device count of cells flagged by eos_post (may be NULL)
   int64_t* newton_iters; // device sum of Newton iterations (may be NULL)

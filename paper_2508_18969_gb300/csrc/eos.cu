@@ -51,6 +51,8 @@ struct SharedConsts {
   const f2* spcw;      // [n * kSpcStride] double-float species constants over W
   const f2* Ks;        // [n * n] (1 - k_ij) s_j / W_j
   const f2* Kr;        // [n * n] (1 - k_ij) r_j / W_j
+  const float* kfs;    // [n * n] k_ij s_j / W_j (FP32; the T-from-h layout only)
+  const float* kfr;    // [n * n] k_ij r_j / W_j
   const double* norm;  // [2 K0 + 2 n]
   const float* normf;  // the same in FP32 (for the FP32 feature and increment arithmetic)
 };
@@ -72,7 +74,27 @@ __device__ SharedConsts load_consts(const EosParams& P, double* sm) {
   for (int i = threadIdx.x; i < nn; i += blockDim.x) nf[i] = (float)P.norm[i];
   __syncthreads();
   return SharedConsts{reinterpret_cast<const f2*>(fs), reinterpret_cast<const f2*>(fs + 2 * nspc),
-                      reinterpret_cast<const f2*>(fs + 2 * nspc + 2 * nk), sm, nf};
+                      reinterpret_cast<const f2*>(fs + 2 * nspc + 2 * nk), nullptr, nullptr, sm, nf};
+}
+
+// The layout of the T-from-h kernel: FP64 normalisation, double-float species table, the two
+// FP32 k_ij tables, FP32 normalisation (no double-float pair tables).
+__host__ __device__ inline int consts_words_post(const EosParams& P) {
+  return 2 * P.K0 + 2 * P.n + P.n * kSpcStride + P.n * P.n + (P.K0 + P.n + 1);
+}
+
+__device__ SharedConsts load_consts_post(const EosParams& P, double* sm) {
+  const int nspc = P.n * kSpcStride, nk = P.n * P.n, nn = 2 * P.K0 + 2 * P.n;
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) sm[i] = P.norm[i];
+  float* fs = reinterpret_cast<float*>(sm + nn);
+  for (int i = threadIdx.x; i < 2 * nspc; i += blockDim.x) fs[i] = P.spcw2[i];
+  float* ks = fs + 2 * nspc;
+  for (int i = threadIdx.x; i < nk; i += blockDim.x) ks[i] = P.kfs[i];
+  for (int i = threadIdx.x; i < nk; i += blockDim.x) ks[nk + i] = P.kfr[i];
+  float* nf = ks + 2 * nk;
+  for (int i = threadIdx.x; i < nn; i += blockDim.x) nf[i] = (float)P.norm[i];
+  __syncthreads();
+  return SharedConsts{reinterpret_cast<const f2*>(fs), nullptr, nullptr, ks, ks + nk, sm, nf};
 }
 
 // FP64 reciprocal: FP32 seed, two FP64 Newton steps (relative error ~1 ulp).
@@ -146,6 +168,59 @@ __device__ __forceinline__ double dsqrt_pos(double x) {
   return fma(fma(-t0, t0, x), 0.5 * rd, t0);
 }
 
+// mixture() for the T-from-h solve, where h(T) needs ~1e-8 relative accuracy (T' to ~1e-6 K):
+// with K = 1 - k the forms split into squares of O(n) sums, kept in double-float, and k_ij
+// corrections (k <= 0.1 of the squares) summed in FP32,
+//   F0 = S_s^2 - 2 sum_i ys_i Pk_i,  F1 = S_s S_r - sum_i (ys_i Qk_i + yr_i Pk_i),
+//   F2 = S_r^2 - 2 sum_i yr_i Qk_i,  Pk_i = sum_{j>i} k_ij ys_j,  Qk_i = sum_{j>i} k_ij yr_j.
+__device__ void mixture_post(const f2* ycol, int n, const SharedConsts& c, Mixture& m) {
+  const int stride = blockDim.x;
+  f2 inv = {0.f, 0.f}, bs = {0.f, 0.f}, Ss = {0.f, 0.f}, Sr = {0.f, 0.f};
+  f2 e0 = {0.f, 0.f}, e1 = e0, e2 = e0, e3 = e0, e4 = e0, e5 = e0;
+  float C0 = 0.f, C1 = 0.f, C2 = 0.f;
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    const f2* q = c.spcw + i * kSpcStride;
+    const f2 y = ycol[i * stride];
+    acc_fma(inv, y, q[0]);
+    acc_fma(Ss, y, q[1]);
+    acc_fma(Sr, y, q[2]);
+    acc_fma(bs, y, q[3]);
+    acc_fma(e0, y, q[4]);
+    acc_fma(e1, y, q[5]);
+    acc_fma(e2, y, q[6]);
+    acc_fma(e3, y, q[7]);
+    acc_fma(e4, y, q[8]);
+    acc_fma(e5, y, q[9]);
+    float Pk = 0.f, Qk = 0.f;
+    const float* ksr = c.kfs + i * n;
+    const float* krr = c.kfr + i * n;
+#pragma unroll 4
+    for (int j = i + 1; j < n; ++j) {
+      const float yj = ycol[j * stride].h;
+      Pk = fmaf(ksr[j], yj, Pk);
+      Qk = fmaf(krr[j], yj, Qk);
+    }
+    const float ysi = y.h * q[1].h, yri = y.h * q[2].h;
+    C0 = fmaf(ysi, Pk, C0);
+    C1 = fmaf(ysi, Qk, fmaf(yri, Pk, C1));
+    C2 = fmaf(yri, Qk, C2);
+  }
+  Ss = f2_fin(Ss);
+  Sr = f2_fin(Sr);
+  const double invd = f2_to(f2_fin(inv));
+  const double Wm = drcp(invd);
+  const double W2 = Wm * Wm;
+  m.inv = invd;
+  m.e[0] = f2_to(f2_fin(e0)); m.e[1] = f2_to(f2_fin(e1)); m.e[2] = f2_to(f2_fin(e2));
+  m.e[3] = f2_to(f2_fin(e3)); m.e[4] = f2_to(f2_fin(e4)); m.e[5] = f2_to(f2_fin(e5));
+  m.A0 = W2 * f2_to(f2_add(f2_mul(Ss, Ss), f2{-2.0f * C0, 0.f}));
+  m.A1 = W2 * f2_to(f2_add(f2_mul(Ss, Sr), f2{-C1, 0.f}));
+  m.A2 = W2 * f2_to(f2_add(f2_mul(Sr, Sr), f2{-2.0f * C2, 0.f}));
+  m.bm = Wm * f2_to(f2_fin(bs));
+  m.kb = drcp(2.0 * kSQ2 * m.bm);
+}
+
 __device__ __forceinline__ double h_ig(const Mixture& m, double T) {
   return fma(fma(fma(fma(fma(m.e[5], T, m.e[4]), T, m.e[3]), T, m.e[2]), T, m.e[1]), T, m.e[0]);
 }
@@ -155,17 +230,17 @@ __device__ __forceinline__ double cp_ig(const Mixture& m, double T) {
              m.e[1]);
 }
 
-// Newton steps on the cubic from an FP32-accurate seed. The step uses an FP32 reciprocal of
-// f'(Z): that scales each correction by (1 + O(1e-7)), so every step still gains ~7 digits.
+// One Newton step on the cubic. The step uses an FP32 reciprocal of f'(Z): that scales the
+// correction by (1 + O(1e-7)), so a step from an FP32-accurate seed still gains ~7 digits.
+__device__ __forceinline__ double cubic_step(double Z, double c2, double c1, double c0) {
+  const double f = fma(fma(Z + c2, Z, c1), Z, c0);
+  const double fp = fma(fma(3.0, Z, 2.0 * c2), Z, c1);
+  const float fpf = d_to_f_trunc(fp);
+  return fpf != 0.0f ? fma(-f, f_to_d(__frcp_rn(fpf)), Z) : Z;
+}
+
 __device__ __forceinline__ double cubic_polish(double Z, double c2, double c1, double c0) {
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const double f = fma(fma(Z + c2, Z, c1), Z, c0);
-    const double fp = fma(fma(3.0, Z, 2.0 * c2), Z, c1);
-    const float fpf = d_to_f_trunc(fp);
-    if (fpf != 0.0f) Z = fma(-f, f_to_d(__frcp_rn(fpf)), Z);
-  }
-  return Z;
+  return cubic_step(cubic_step(Z, c2, c1, c0), c2, c1, c0);
 }
 
 __device__ __forceinline__ double g_dep(double Z, double A, double B) {
@@ -177,7 +252,9 @@ __device__ __forceinline__ double g_dep(double Z, double A, double B) {
 //   Z^3 - (1 - B) Z^2 + (A - 3B^2 - 2B) Z - (AB - B^2 - B^3) = 0
 // above B with least departure Gibbs energy (ties within 1e-12 keep the larger root).
 // Seeds come from the FP32 closed form (Cardano for one real root, the trigonometric form
-// for three), each polished by FP64 Newton steps on the cubic.
+// for three), each polished by FP64 Newton steps on the cubic: two, or with FAST one, plus a
+// second where the first moved the seed by more than 1e-6 relative (a poor seed).
+template <bool FAST>
 __device__ double select_Z(double A, double B, int& status) {
   const double c2 = B - 1.0;
   const double c1 = A - 3.0 * B * B - 2.0 * B;
@@ -190,7 +267,10 @@ __device__ double select_Z(double A, double B, int& status) {
     const float sq = sqrtf(d_to_f_trunc(disc));
     const float u = cbrtf(-0.5f * qf - copysignf(sq, qf));
     const float t = (u != 0.0f) ? u - pf / (3.0f * u) : 0.0f;
-    const double Z = cubic_polish(f_to_d(t) - c2 * (1.0 / 3.0), c2, c1, c0);
+    const double Z0 = f_to_d(t) - c2 * (1.0 / 3.0);
+    double Z = cubic_step(Z0, c2, c1, c0);
+    if (!FAST || fabsf(d_to_f_trunc(Z - Z0)) > 1e-6f * fabsf(d_to_f_trunc(Z)))
+      Z = cubic_step(Z, c2, c1, c0);
     if (!(Z > B)) status |= kCellNoRoot;
     return Z;
   }
@@ -222,7 +302,10 @@ struct PRPoint {
   double Z, h_dep, cp_dep;  // molar departure enthalpy and its T-derivative at fixed p
 };
 
-// Real-fluid state at (T, p) of a composition (a2-a4), with the departure cp if asked.
+// Real-fluid state at (T, p) of a composition (a2-a4), with the departure cp if asked. With
+// FAST (the T-from-h solve, whose cp only sets the chord slope) cp is evaluated in FP32 and
+// the cubic gets one polishing step.
+template <bool FAST>
 __device__ PRPoint pr_point(const Mixture& m, double T, double p, bool want_cp, int& status) {
   const double iT = drcp(T);
   const double t = dsqrt_pos(T);
@@ -234,7 +317,7 @@ __device__ PRPoint pr_point(const Mixture& m, double T, double p, bool want_cp, 
   const double A = am * p * iRT * iRT;
   const double B = m.bm * p * iRT;
   PRPoint r;
-  r.Z = select_Z(A, B, status);
+  r.Z = select_Z<FAST>(A, B, status);
   const double Zp = r.Z + (1.0 + kSQ2) * B;
   const double Zm = r.Z + (1.0 - kSQ2) * B;
   const double iZm = drcp(Zm);
@@ -242,7 +325,23 @@ __device__ PRPoint pr_point(const Mixture& m, double T, double p, bool want_cp, 
   const double tdam_am = fma(T, dam, -am);
   r.h_dep = fma(RT, r.Z - 1.0, tdam_am * m.kb * L);
   r.cp_dep = 0.0;
-  if (want_cp) {
+  if (FAST && want_cp) {
+    // FP32: dA/dT = p (dam - 2 am / T) / (RT)^2 needs no division by am
+    const float Tf = d_to_f_trunc(T), iTf = __frcp_rn(Tf), itf = rsqrtf(Tf);
+    const float Z = d_to_f_trunc(r.Z), Af = d_to_f_trunc(A), Bf = d_to_f_trunc(B);
+    const float pf = d_to_f_trunc(p), iRTf = iTf * (float)kInvR;
+    const float d2am = 0.5f * d_to_f_trunc(m.A1) * itf * iTf;
+    const float dB = -Bf * iTf;
+    const float dA = pf * iRTf * iRTf * (d_to_f_trunc(dam) - 2.0f * d_to_f_trunc(am) * iTf);
+    const float FZ = fmaf(3.0f * Z, Z, -2.0f * (1.0f - Bf) * Z) + (Af - 3.0f * Bf * Bf - 2.0f * Bf);
+    const float FA = Z - Bf;
+    const float FB = Z * Z - (6.0f * Bf + 2.0f) * Z - (Af - 2.0f * Bf - 3.0f * Bf * Bf);
+    const float dZ = -(FA * dA + FB * dB) / FZ;
+    const float s2 = (float)kSQ2;
+    const float dL = (dZ + (1.0f + s2) * dB) / d_to_f_trunc(Zp) - (dZ + (1.0f - s2) * dB) / d_to_f_trunc(Zm);
+    r.cp_dep = f_to_d((float)kR * (Z - 1.0f) + (float)kR * Tf * dZ +
+                      d_to_f_trunc(m.kb) * (Tf * d2am * d_to_f_trunc(L) + d_to_f_trunc(tdam_am) * dL));
+  } else if (want_cp) {
     const double d2am = 0.5 * m.A1 * it * iT;
     const double dB = -B * iT;
     const double dA = A * fma(dam, drcp(am), -2.0 * iT);
@@ -260,6 +359,7 @@ __device__ PRPoint pr_point(const Mixture& m, double T, double p, bool want_cp, 
 // a9: T from h(T, p, Y') = h0 for the composition of m, safeguarded Newton inside a bracket
 // that starts at [50, 5000] K and shrinks with the sign of h - h0. Adds flags to st and the
 // iteration count to iters; returns the last iterate.
+template <bool FAST>
 __device__ double solve_T(const Mixture& m, double pc, double h0c, double Told, const EosParams& P,
                           int& iters, int& st) {
   double lo = kTLo, hi = kTHi;
@@ -269,7 +369,7 @@ __device__ double solve_T(const Mixture& m, double pc, double h0c, double Told, 
   for (int it = 0; it < P.newton_max_iter; ++it) {
     ++iters;
     int s2 = 0;
-    const PRPoint q = pr_point(m, Tn, pc, need_cp, s2);
+    const PRPoint q = pr_point<FAST>(m, Tn, pc, need_cp, s2);
     if (s2) {
       st |= s2;
       break;
@@ -358,7 +458,7 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams
     if (finite) {
       Mixture m;
       mixture(ycol, n, c, m);
-      const PRPoint q = pr_point(m, Tc, pc, false, st);
+      const PRPoint q = pr_point<false>(m, Tc, pc, false, st);
       Z = q.Z;
       h = h_ig(m, Tc) + q.h_dep * m.inv;
       if (!d_finite(h)) st |= kCellNonfinite;
@@ -390,8 +490,8 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
     double* __restrict__ T, const double* __restrict__ p, double* __restrict__ Y, int64_t ldY,
     const int32_t* __restrict__ pre_status, int32_t* __restrict__ cell_status) {
   extern __shared__ double sm[];
-  const SharedConsts c = load_consts(P, sm);
-  f2* ycol = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
+  const SharedConsts c = load_consts_post(P, sm);
+  f2* ycol = reinterpret_cast<f2*>(sm + consts_words_post(P)) + threadIdx.x;
   const int stride = blockDim.x;
   const int64_t nrow = valid_rows(rows);
   const int n = P.n, K0 = P.K0;
@@ -444,8 +544,8 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
       const f2 iS = f2_rcp(S);
       for (int k = 0; k < n; ++k) ycol[k * stride] = f2_mul(ycol[k * stride], iS);
       Mixture m;
-      mixture(ycol, n, c, m);
-      Tn = solve_T(m, pc, h0c, Told, P, iters, st);
+      mixture_post(ycol, n, c, m);
+      Tn = solve_T<true>(m, pc, h0c, Told, P, iters, st);
     }
     if (st == 0) {
       T[cell] = Tn;
@@ -478,7 +578,7 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) props_kernel(EosParams P
     Mixture m;
     mixture(ycol, n, c, m);
     int st = 0;
-    const PRPoint q = pr_point(m, Tc, pc, cp != nullptr, st);
+    const PRPoint q = pr_point<false>(m, Tc, pc, cp != nullptr, st);
     if (rho) rho[i] = pc / (m.inv * q.Z * kR * Tc);
     if (h) h[i] = h_ig(m, Tc) + q.h_dep * m.inv;
     if (cp) cp[i] = cp_ig(m, Tc) + q.cp_dep * m.inv;
@@ -530,7 +630,7 @@ __device__ void h_grad(const EosParams& P, int n, int stride, const double* ycol
   const double RT = kR * T;
   const double A = a * p / (RT * RT);
   const double B = b * p / RT;
-  const double Z = select_Z(A, B, st);
+  const double Z = select_Z<false>(A, B, st);
   const double c1 = 1.0 + kSQ2, c2 = 1.0 - kSQ2;
   const double Zp = Z + c1 * B, Zm = Z + c2 * B;
   const double L = log(Zp / Zm);
@@ -646,7 +746,7 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
       Mixture m0;
       for (int k = 0; k < n; ++k) ws[k * stride] = f2_from(Yk[k]);
       mixture(ws, n, c, m0);
-      const PRPoint q0 = pr_point(m0, Tc, pc, true, st);
+      const PRPoint q0 = pr_point<false>(m0, Tc, pc, true, st);
       if (dTc) {
         dTc[0] = cp_ig(m0, Tc) + q0.cp_dep * m0.inv;
         h_grad(P, n, stride, Yc, Tc, pc, uc, rc, vc, wc, dTc + 1, 1, st);
@@ -676,9 +776,9 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
         for (int k = 0; k < n; ++k) ws[k * stride] = f2_from(Yn[k]);
         mixture(ws, n, c, m1);
         int iters = 0;
-        const double Tn = solve_T(m1, pc, h0c, Tc, P, iters, st);
+        const double Tn = solve_T<false>(m1, pc, h0c, Tc, P, iters, st);
         if (st == 0) {
-          const PRPoint q1 = pr_point(m1, Tn, pc, true, st);
+          const PRPoint q1 = pr_point<false>(m1, Tn, pc, true, st);
           cp1 = cp_ig(m1, Tn) + q1.cp_dep * m1.inv;
           if (dTc) h_grad(P, n, stride, Ypc, Tn, pc, uc, rc, vc, wc, hgc, stride, st);
         }
@@ -716,6 +816,10 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
 // of mass fractions (n words per thread).
 size_t eos_smem(const EosParams& P) {
   return sizeof(double) * ((size_t)consts_words(P) + (size_t)P.n * kThreads);
+}
+
+size_t eos_smem_post(const EosParams& P) {
+  return sizeof(double) * ((size_t)consts_words_post(P) + (size_t)P.n * kThreads);
 }
 
 // Opts a kernel into more than 48 KB of dynamic shared memory, once per device.
@@ -775,7 +879,7 @@ cudaError_t post_nm(const EosParams& P, const RowMap& rows, const float* O, int6
                     const int32_t* pre_status, int32_t* cell_status, cudaStream_t st) {
   cudaError_t e = smem_optin<eos_post_kernel<NM>>();
   if (e != cudaSuccess) return e;
-  eos_post_kernel<NM><<<grid_for(rows.nmax), kThreads, eos_smem(P), st>>>(
+  eos_post_kernel<NM><<<grid_for(rows.nmax), kThreads, eos_smem_post(P), st>>>(
       P, rows, O, ldo, h0, T, p, Y, ldY, pre_status, cell_status);
   return cudaGetLastError();
 }

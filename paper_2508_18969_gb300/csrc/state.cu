@@ -115,7 +115,7 @@ void free_state(df_state* s) {
   s->jac = nullptr;
   free_trn(s->trn);
   s->trn = nullptr;
-  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_Kr2); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
+  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_Kr2); f(s->d_kfs); f(s->d_kfr); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
   for (auto p : s->W32) f(p);
   for (auto p : s->bias) f(p);
   for (auto p : s->Wlp) f(p);
@@ -342,6 +342,18 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
       Kr[(size_t)i * n + j] = K[(size_t)i * n + j] * q[2] * q[0];
     }
   const std::vector<float> spcw2 = split(spcw), Ks2 = split(Ks), Kr2 = split(Kr);
+  std::vector<float> kfs((size_t)n * n), kfr((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double k = (i == j) ? 0.0 : 1.0 - K[(size_t)i * n + j];
+      const double* q = &spc[(size_t)j * kSpcStride];
+      kfs[(size_t)i * n + j] = (float)(k * q[1] * q[0]);
+      kfr[(size_t)i * n + j] = (float)(k * q[2] * q[0]);
+    }
+  CK(dalloc(&s->d_kfs, kfs.size()), "constants");
+  CK(dalloc(&s->d_kfr, kfr.size()), "constants");
+  CK(cudaMemcpy(s->d_kfs, kfs.data(), sizeof(float) * kfs.size(), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(s->d_kfr, kfr.data(), sizeof(float) * kfr.size(), cudaMemcpyHostToDevice), "copy");
   CK(dalloc(&s->d_spc2, spcw2.size()), "constants");
   CK(dalloc(&s->d_K2, Ks2.size()), "constants");
   CK(dalloc(&s->d_Kr2, Kr2.size()), "constants");
@@ -370,6 +382,8 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
   P.spcw2 = s->d_spc2;
   P.Ks2 = s->d_K2;
   P.Kr2 = s->d_Kr2;
+  P.kfs = s->d_kfs;
+  P.kfr = s->d_kfr;
   P.err = s->d_err;
   P.flagged = s->d_flagged;
   P.newton_iters = s->d_iters;

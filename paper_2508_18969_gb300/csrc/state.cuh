@@ -53,6 +53,8 @@ struct df_state {
   float* d_spc2 = nullptr;               // double-float mixing-sum tables (EosParams)
   float* d_K2 = nullptr;
   float* d_Kr2 = nullptr;
+  float* d_kfs = nullptr;                // FP32 k_ij tables (EosParams)
+  float* d_kfr = nullptr;
   int* d_err = nullptr;                  // kernel error word
   int64_t* d_count = nullptr;            // reacting cells of the last step
   int64_t* d_flagged = nullptr;          // flagged cells of the last step
