@@ -78,6 +78,28 @@ __device__ __forceinline__ f2 f2_from(double x) {
 
 __device__ __forceinline__ double f2_to(f2 a) { return f_to_d(a.h) + f_to_d(a.l); }
 
+// f2 -> FP64 with integer operations only, for a normalised pair (|lo| <= ulp(hi) / 2, as
+// f2_norm leaves it): the exact sum of the two significands is formed in a 64-bit integer
+// and cut to 53 bits (truncation: relative error below 2^-52). Other pairs (zeros, subnormal,
+// inf, NaN, or a low part out of range) take f2_to.
+__device__ __forceinline__ double f2_to_int(f2 a) {
+  const unsigned uh = __float_as_uint(a.h), ul = __float_as_uint(a.l);
+  const int eh = (int)((uh >> 23) & 0xFFu), el = (int)((ul >> 23) & 0xFFu);
+  if ((ul & 0x7FFFFFFFu) == 0u) return f_to_d(a.h);
+  const int sh = 39 + el - eh;                 // scale of lo's significand against hi's << 39
+  if (eh == 0 || eh == 255 || el == 0 || el == 255 || sh > 15) return f2_to(a);
+  const unsigned long long mh = (unsigned long long)((uh & 0x7FFFFFu) | 0x800000u);
+  const unsigned long long ml = (unsigned long long)((ul & 0x7FFFFFu) | 0x800000u);
+  const unsigned long long tl = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> -sh) : 0ull);
+  unsigned long long S = mh << 39;
+  S = (((uh ^ ul) & 0x80000000u) == 0u) ? S + tl : S - tl;   // S in [2^61, 2^64)
+  const int pos = 63 - __clzll((long long)S);                 // leading bit, 61..63
+  const unsigned long long mant = (S >> (pos - 52)) & ((1ull << 52) - 1ull);
+  const unsigned e = (unsigned)(eh - 127 + pos - 62 + 1023);
+  return __hiloint2double((int)((uh & 0x80000000u) | (e << 20) | (unsigned)(mant >> 32)),
+                          (int)(unsigned)mant);
+}
+
 // TwoSum (Knuth): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);

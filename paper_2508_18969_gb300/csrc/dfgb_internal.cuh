@@ -66,6 +66,8 @@ struct EosParams {
   // kfr[i][j] = k_ij r_j / W_j (k_ii = 0)
   const float* kfs;      // [n * n]
   const float* kfr;      // [n * n]
+  // natural-log table: ln(c_j) for j < 128, then 1 / c_j, c_j = 1 + (j + 1/2) / 128
+  const double* lntab;   // [256]
   int* err;              // device error word
   int64_t* flagged;      // device count of cells flagged by eos_post (may be NULL)
   int64_t* newton_iters; // device sum of Newton iterations (may be NULL)

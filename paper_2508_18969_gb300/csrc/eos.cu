@@ -53,6 +53,7 @@ struct SharedConsts {
   const f2* Kr;        // [n * n] (1 - k_ij) r_j / W_j
   const float* kfs;    // [n * n] k_ij s_j / W_j (FP32; the T-from-h layout only)
   const float* kfr;    // [n * n] k_ij r_j / W_j
+  const double* lnt;   // [256] log table (ln c_j, then 1 / c_j)
   const double* norm;  // [2 K0 + 2 n]
   const float* normf;  // the same in FP32 (for the FP32 feature and increment arithmetic)
 };
@@ -60,11 +61,13 @@ struct SharedConsts {
 // 8-byte words of shared memory the constants take: FP64 normalisation, then the
 // double-float tables (one f2 per word), then the FP32 normalisation.
 __host__ __device__ inline int consts_words(const EosParams& P) {
-  return 2 * P.K0 + 2 * P.n + P.n * kSpcStride + 2 * P.n * P.n + (P.K0 + P.n + 1);
+  return 256 + 2 * P.K0 + 2 * P.n + P.n * kSpcStride + 2 * P.n * P.n + (P.K0 + P.n + 1);
 }
 
-__device__ SharedConsts load_consts(const EosParams& P, double* sm) {
+__device__ SharedConsts load_consts(const EosParams& P, double* sm0) {
   const int nspc = P.n * kSpcStride, nk = P.n * P.n, nn = 2 * P.K0 + 2 * P.n;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) sm0[i] = P.lntab[i];
+  double* sm = sm0 + 256;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) sm[i] = P.norm[i];
   float* fs = reinterpret_cast<float*>(sm + nn);
   for (int i = threadIdx.x; i < 2 * nspc; i += blockDim.x) fs[i] = P.spcw2[i];
@@ -74,17 +77,20 @@ __device__ SharedConsts load_consts(const EosParams& P, double* sm) {
   for (int i = threadIdx.x; i < nn; i += blockDim.x) nf[i] = (float)P.norm[i];
   __syncthreads();
   return SharedConsts{reinterpret_cast<const f2*>(fs), reinterpret_cast<const f2*>(fs + 2 * nspc),
-                      reinterpret_cast<const f2*>(fs + 2 * nspc + 2 * nk), nullptr, nullptr, sm, nf};
+                      reinterpret_cast<const f2*>(fs + 2 * nspc + 2 * nk), nullptr, nullptr, sm0,
+                      sm, nf};
 }
 
 // The layout of the T-from-h kernel: FP64 normalisation, double-float species table, the two
 // FP32 k_ij tables, FP32 normalisation (no double-float pair tables).
 __host__ __device__ inline int consts_words_post(const EosParams& P) {
-  return 2 * P.K0 + 2 * P.n + P.n * kSpcStride + P.n * P.n + (P.K0 + P.n + 1);
+  return 256 + 2 * P.K0 + 2 * P.n + P.n * kSpcStride + P.n * P.n + (P.K0 + P.n + 1);
 }
 
-__device__ SharedConsts load_consts_post(const EosParams& P, double* sm) {
+__device__ SharedConsts load_consts_post(const EosParams& P, double* sm0) {
   const int nspc = P.n * kSpcStride, nk = P.n * P.n, nn = 2 * P.K0 + 2 * P.n;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) sm0[i] = P.lntab[i];
+  double* sm = sm0 + 256;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) sm[i] = P.norm[i];
   float* fs = reinterpret_cast<float*>(sm + nn);
   for (int i = threadIdx.x; i < 2 * nspc; i += blockDim.x) fs[i] = P.spcw2[i];
@@ -94,7 +100,7 @@ __device__ SharedConsts load_consts_post(const EosParams& P, double* sm) {
   float* nf = ks + 2 * nk;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) nf[i] = (float)P.norm[i];
   __syncthreads();
-  return SharedConsts{reinterpret_cast<const f2*>(fs), nullptr, nullptr, ks, ks + nk, sm, nf};
+  return SharedConsts{reinterpret_cast<const f2*>(fs), nullptr, nullptr, ks, ks + nk, sm0, sm, nf};
 }
 
 // FP64 reciprocal: FP32 seed, two FP64 Newton steps (relative error ~1 ulp).
@@ -157,6 +163,28 @@ __device__ void mixture(const f2* ycol, int n, const SharedConsts& c, Mixture& m
   m.A2 = W2 * f2_to(f2_fin(F2));
   m.bm = Wm * f2_to(f2_fin(bs));
   m.kb = drcp(2.0 * kSQ2 * m.bm);
+}
+
+// ln(x) for a positive normal x from the shared table: x = 2^e m, m in [1, 2); with c the
+// midpoint of m's 1/128 interval, ln x = e ln2 + ln c + ln(1 + r), r = m / c - 1, |r| < 2^-8,
+// ln(1 + r) by its series to r^5 (truncation below 4e-16). Other x take the library log.
+__device__ __forceinline__ double dlog_tab(double x, const double* lnt) {
+  const int hi = __double2hiint(x);
+  const int be = (hi >> 20) & 0x7FF;
+  if (hi <= 0 || be == 0 || be == 0x7FF) return log(x);
+  const int j = (hi >> 13) & 127;
+  const double m = __hiloint2double((hi & 0x000FFFFF) | 0x3FF00000, __double2loint(x));
+  const double r = fma(m, lnt[128 + j], -1.0);
+  const double poly = r * fma(r, fma(r, fma(r, fma(r, 0.2, -0.25), 1.0 / 3.0), -0.5), 1.0);
+  const double e = f_to_d((float)(be - 1023));
+  constexpr double kLn2Hi = 6.93147180369123816490e-01, kLn2Lo = 1.90821492927058770002e-10;
+  return fma(e, kLn2Hi, lnt[j] + fma(e, kLn2Lo, poly));
+}
+
+// 1/x from the FP32 reciprocal and one FP64 Newton step (relative error ~2^-46).
+__device__ __forceinline__ double drcp1(double x) {
+  const double r = f_to_d(__frcp_rn(d_to_f_trunc(x)));
+  return fma(r, fma(-x, r, 1.0), r);
 }
 
 // sqrt(x) for a positive normal x: t0 = x rsqrt_32(x), then one Newton step
@@ -243,9 +271,9 @@ __device__ __forceinline__ double cubic_polish(double Z, double c2, double c1, d
   return cubic_step(cubic_step(Z, c2, c1, c0), c2, c1, c0);
 }
 
-__device__ __forceinline__ double g_dep(double Z, double A, double B) {
-  return Z - 1.0 - log(Z - B) -
-         A * drcp(2.0 * kSQ2 * B) * log((Z + (1.0 + kSQ2) * B) * drcp(Z + (1.0 - kSQ2) * B));
+__device__ __forceinline__ double g_dep(double Z, double A, double B, const double* lnt) {
+  return Z - 1.0 - dlog_tab(Z - B, lnt) -
+         A * drcp(2.0 * kSQ2 * B) * dlog_tab((Z + (1.0 + kSQ2) * B) * drcp(Z + (1.0 - kSQ2) * B), lnt);
 }
 
 // Compressibility (a3): the real root of
@@ -255,7 +283,7 @@ __device__ __forceinline__ double g_dep(double Z, double A, double B) {
 // for three), each polished by FP64 Newton steps on the cubic: two, or with FAST one, plus a
 // second where the first moved the seed by more than 1e-6 relative (a poor seed).
 template <bool FAST>
-__device__ double select_Z(double A, double B, int& status) {
+__device__ double select_Z(double A, double B, const double* lnt, int& status) {
   const double c2 = B - 1.0;
   const double c1 = A - 3.0 * B * B - 2.0 * B;
   const double c0 = B * B + B * B * B - A * B;
@@ -287,7 +315,7 @@ __device__ double select_Z(double A, double B, int& status) {
     const double Z = cubic_polish(cubic_polish(f_to_d(tk) - c2 * (1.0 / 3.0), c2, c1, c0), c2,
                                   c1, c0);
     if (Z > B) {
-      const double g = g_dep(Z, A, B);
+      const double g = g_dep(Z, A, B, lnt);
       if (g < gbest - 1e-12) {
         gbest = g;
         best = Z;
@@ -306,8 +334,9 @@ struct PRPoint {
 // FAST (the T-from-h solve, whose cp only sets the chord slope) cp is evaluated in FP32 and
 // the cubic gets one polishing step.
 template <bool FAST>
-__device__ PRPoint pr_point(const Mixture& m, double T, double p, bool want_cp, int& status) {
-  const double iT = drcp(T);
+__device__ PRPoint pr_point(const Mixture& m, double T, double p, bool want_cp, const double* lnt,
+                            int& status) {
+  const double iT = FAST ? drcp1(T) : drcp(T);
   const double t = dsqrt_pos(T);
   const double it = t * iT;                       // 1 / sqrt(T)
   const double am = fma(-2.0 * m.A1, t, fma(m.A2, T, m.A0));
@@ -317,11 +346,11 @@ __device__ PRPoint pr_point(const Mixture& m, double T, double p, bool want_cp, 
   const double A = am * p * iRT * iRT;
   const double B = m.bm * p * iRT;
   PRPoint r;
-  r.Z = select_Z<FAST>(A, B, status);
+  r.Z = select_Z<FAST>(A, B, lnt, status);
   const double Zp = r.Z + (1.0 + kSQ2) * B;
   const double Zm = r.Z + (1.0 - kSQ2) * B;
-  const double iZm = drcp(Zm);
-  const double L = log(Zp * iZm);
+  const double iZm = FAST ? drcp1(Zm) : drcp(Zm);
+  const double L = dlog_tab(Zp * iZm, lnt);
   const double tdam_am = fma(T, dam, -am);
   r.h_dep = fma(RT, r.Z - 1.0, tdam_am * m.kb * L);
   r.cp_dep = 0.0;
@@ -361,15 +390,16 @@ __device__ PRPoint pr_point(const Mixture& m, double T, double p, bool want_cp, 
 // iteration count to iters; returns the last iterate.
 template <bool FAST>
 __device__ double solve_T(const Mixture& m, double pc, double h0c, double Told, const EosParams& P,
-                          int& iters, int& st) {
+                          const double* lnt, int& iters, int& st) {
   double lo = kTLo, hi = kTHi;
   double Tn = fmin(fmax(Told, lo), hi);
   bool conv = false, need_cp = true;
   double icp = 0.0;
+  const float tolf = (float)P.newton_tol;
   for (int it = 0; it < P.newton_max_iter; ++it) {
     ++iters;
     int s2 = 0;
-    const PRPoint q = pr_point<FAST>(m, Tn, pc, need_cp, s2);
+    const PRPoint q = pr_point<FAST>(m, Tn, pc, need_cp, lnt, s2);
     if (s2) {
       st |= s2;
       break;
@@ -379,12 +409,15 @@ __device__ double solve_T(const Mixture& m, double pc, double h0c, double Told, 
     // close (each step contracts the error by ~|1 - cp(T)/cp(T0)| ~ 1e-5 there); an FP32
     // reciprocal of cp scales the step by 1 + O(1e-7) on top.
     if (need_cp) icp = f_to_d(__frcp_rn(d_to_f_trunc(cp_ig(m, Tn) + q.cp_dep * m.inv)));
-    if (f > 0.0) hi = fmin(hi, Tn); else lo = fmax(lo, Tn);
-    double Tx = fma(-f, icp, Tn);
-    // a step within tolerance has converged; only a longer step that leaves the
-    // bracket (or is not finite) is replaced by bisection, after which the slope is
-    // evaluated afresh
-    const bool done = fabs(Tx - Tn) <= P.newton_tol * Tn;
+    // Tn lies inside [lo, hi] (the start is clamped, later iterates are inside by
+    // construction), so the bracket update needs no min/max; the sign test reads the bit
+    if (__double2hiint(f) >= 0) hi = Tn; else lo = Tn;
+    const double step = -f * icp;
+    double Tx = Tn + step;
+    // a step within tolerance has converged (the test is a threshold, FP32 is enough); only
+    // a longer step that leaves the bracket (or is not finite) is replaced by bisection,
+    // after which the slope is evaluated afresh
+    const bool done = fabsf(d_to_f_trunc(step)) <= tolf * d_to_f_trunc(Tn);
     need_cp = false;
     if (!done && !(Tx > lo && Tx < hi)) {
       Tx = 0.5 * (lo + hi);
@@ -397,7 +430,7 @@ __device__ double solve_T(const Mixture& m, double pc, double h0c, double Told, 
     }
   }
   if (!conv && st == 0) st |= kCellNotConverged;
-  if (!isfinite(Tn)) st |= kCellNonfinite;
+  if (!d_finite(Tn)) st |= kCellNonfinite;
   return Tn;
 }
 
@@ -458,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams
     if (finite) {
       Mixture m;
       mixture(ycol, n, c, m);
-      const PRPoint q = pr_point<false>(m, Tc, pc, false, st);
+      const PRPoint q = pr_point<false>(m, Tc, pc, false, c.lnt, st);
       Z = q.Z;
       h = h_ig(m, Tc) + q.h_dep * m.inv;
       if (!d_finite(h)) st |= kCellNonfinite;
@@ -545,12 +578,12 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
       for (int k = 0; k < n; ++k) ycol[k * stride] = f2_mul(ycol[k * stride], iS);
       Mixture m;
       mixture_post(ycol, n, c, m);
-      Tn = solve_T<true>(m, pc, h0c, Told, P, iters, st);
+      Tn = solve_T<true>(m, pc, h0c, Told, P, c.lnt, iters, st);
     }
     if (st == 0) {
       T[cell] = Tn;
 #pragma unroll 2
-      for (int k = 0; k < n; ++k) Y[k * ldY + cell] = f2_to(ycol[k * stride]);
+      for (int k = 0; k < n; ++k) Y[k * ldY + cell] = f2_to_int(ycol[k * stride]);
     }
     if (cell_status) cell_status[cell] = st;
     if (st && P.flagged) atomicAdd((unsigned long long*)P.flagged, 1ull);
@@ -578,7 +611,7 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) props_kernel(EosParams P
     Mixture m;
     mixture(ycol, n, c, m);
     int st = 0;
-    const PRPoint q = pr_point<false>(m, Tc, pc, cp != nullptr, st);
+    const PRPoint q = pr_point<false>(m, Tc, pc, cp != nullptr, c.lnt, st);
     if (rho) rho[i] = pc / (m.inv * q.Z * kR * Tc);
     if (h) h[i] = h_ig(m, Tc) + q.h_dep * m.inv;
     if (cp) cp[i] = cp_ig(m, Tc) + q.cp_dep * m.inv;
@@ -630,7 +663,7 @@ __device__ void h_grad(const EosParams& P, int n, int stride, const double* ycol
   const double RT = kR * T;
   const double A = a * p / (RT * RT);
   const double B = b * p / RT;
-  const double Z = select_Z<false>(A, B, st);
+  const double Z = select_Z<false>(A, B, P.lntab, st);
   const double c1 = 1.0 + kSQ2, c2 = 1.0 - kSQ2;
   const double Zp = Z + c1 * B, Zm = Z + c2 * B;
   const double L = log(Zp / Zm);
@@ -746,7 +779,7 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
       Mixture m0;
       for (int k = 0; k < n; ++k) ws[k * stride] = f2_from(Yk[k]);
       mixture(ws, n, c, m0);
-      const PRPoint q0 = pr_point<false>(m0, Tc, pc, true, st);
+      const PRPoint q0 = pr_point<false>(m0, Tc, pc, true, c.lnt, st);
       if (dTc) {
         dTc[0] = cp_ig(m0, Tc) + q0.cp_dep * m0.inv;
         h_grad(P, n, stride, Yc, Tc, pc, uc, rc, vc, wc, dTc + 1, 1, st);
@@ -776,9 +809,9 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
         for (int k = 0; k < n; ++k) ws[k * stride] = f2_from(Yn[k]);
         mixture(ws, n, c, m1);
         int iters = 0;
-        const double Tn = solve_T<false>(m1, pc, h0c, Tc, P, iters, st);
+        const double Tn = solve_T<false>(m1, pc, h0c, Tc, P, c.lnt, iters, st);
         if (st == 0) {
-          const PRPoint q1 = pr_point<false>(m1, Tn, pc, true, st);
+          const PRPoint q1 = pr_point<false>(m1, Tn, pc, true, c.lnt, st);
           cp1 = cp_ig(m1, Tn) + q1.cp_dep * m1.inv;
           if (dTc) h_grad(P, n, stride, Ypc, Tn, pc, uc, rc, vc, wc, hgc, stride, st);
         }

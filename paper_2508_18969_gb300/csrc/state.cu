@@ -115,7 +115,7 @@ void free_state(df_state* s) {
   s->jac = nullptr;
   free_trn(s->trn);
   s->trn = nullptr;
-  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_Kr2); f(s->d_kfs); f(s->d_kfr); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
+  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_Kr2); f(s->d_kfs); f(s->d_kfr); f(s->d_lntab); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
   for (auto p : s->W32) f(p);
   for (auto p : s->bias) f(p);
   for (auto p : s->Wlp) f(p);
@@ -350,6 +350,14 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
       kfs[(size_t)i * n + j] = (float)(k * q[1] * q[0]);
       kfr[(size_t)i * n + j] = (float)(k * q[2] * q[0]);
     }
+  std::vector<double> lntab(256);
+  for (int j = 0; j < 128; ++j) {
+    const double c = 1.0 + (j + 0.5) / 128.0;
+    lntab[j] = std::log(c);
+    lntab[128 + j] = 1.0 / c;
+  }
+  CK(dalloc(&s->d_lntab, lntab.size()), "constants");
+  CK(cudaMemcpy(s->d_lntab, lntab.data(), sizeof(double) * 256, cudaMemcpyHostToDevice), "copy");
   CK(dalloc(&s->d_kfs, kfs.size()), "constants");
   CK(dalloc(&s->d_kfr, kfr.size()), "constants");
   CK(cudaMemcpy(s->d_kfs, kfs.data(), sizeof(float) * kfs.size(), cudaMemcpyHostToDevice), "copy");
@@ -384,6 +392,7 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
   P.Kr2 = s->d_Kr2;
   P.kfs = s->d_kfs;
   P.kfr = s->d_kfr;
+  P.lntab = s->d_lntab;
   P.err = s->d_err;
   P.flagged = s->d_flagged;
   P.newton_iters = s->d_iters;

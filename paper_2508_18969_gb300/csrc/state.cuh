@@ -55,6 +55,7 @@ struct df_state {
   float* d_Kr2 = nullptr;
   float* d_kfs = nullptr;                // FP32 k_ij tables (EosParams)
   float* d_kfr = nullptr;
+  double* d_lntab = nullptr;             // log table (EosParams)
   int* d_err = nullptr;                  // kernel error word
   int64_t* d_count = nullptr;            // reacting cells of the last step
   int64_t* d_flagged = nullptr;          // flagged cells of the last step
