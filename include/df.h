@@ -122,6 +122,18 @@ df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const
                        double* Y, int64_t ldY, int32_t* cell_status, int64_t* n_active_out,
                        void* stream);
 
+/* Chemical source terms for a flow solver: the same step as df_chem_step (Sec. 2: the network
+ * supplies each cell's chemical change), but T and Y are read only and the result is returned
+ * as rates:
+ *   omega (device, [n][ldw] species-major FP64, ldw >= n_cells): omega_k = rho (Y'_k - Y_k) / dt
+ *     in kg/(m^3 s), rho the real-fluid (Peng-Robinson) density at the cell's (T, p, Y);
+ *   T_new (device [n_cells], may be NULL): T' from h(T', p, Y') = h0.
+ * Cells that do not react, and flagged cells, get omega = 0 and T' = T. cell_status and
+ * n_active_out as in df_chem_step. Asynchronous. */
+df_status df_chem_source(df_state* s, int64_t n_cells, double dt, const double* T,
+                         const double* p, const double* Y, int64_t ldY, double* omega, int64_t ldw,
+                         double* T_new, int32_t* cell_status, int64_t* n_active_out, void* stream);
+
 /* Jacobian of the reaction step of each cell (every cell treated as reacting), with p fixed
  * and the inputs (T, Y_1..Y_n) taken as independent (no renormalisation of the input):
  *   J_dY  (device, [n_cells][n][n+1] row-major FP32): d(Y'_k - Y_k) / d(T, Y_1..Y_n);

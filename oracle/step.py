@@ -112,8 +112,26 @@ def real_fluid_props(mech, T, p, Y):
     return s["rho"], s["h"], s["cp"], s["Z"]
 
 
-__all__ = ["active_cells", "solve_T", "chem_step", "real_fluid_props", "NOT_CONVERGED",
-           "NONFINITE", "NO_ROOT"]
+def chem_source(mech, net, T, p, Y, dt, T_react=600.0, newton_tol=1e-12, max_iter=100):
+    """Chemical source terms of the step for a flow solver (the network supplies the chemical
+    change of each cell, Sec. 2): omega_k = rho (Y'_k - Y_k) / dt in kg/(m^3 s), rho the
+    real-fluid density at the cell's state (T, p, Y), with (T', Y') from chem_step. Cells
+    that do not react or are flagged get omega = 0 and T' = T. Returns (omega [n, N], T', status)."""
+    T = np.asarray(T, dtype=np.float64)
+    p = np.asarray(p, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    Tn, Yn, status = chem_step(mech, net, T, p, Y, dt, T_react, newton_tol, max_iter)
+    omega = np.zeros_like(Y)
+    idx = active_cells(T, T_react)
+    idx = idx[status[idx] == 0]
+    if idx.size:
+        rho = state(mech, T[idx], p[idx], Y[:, idx])["rho"]
+        omega[:, idx] = rho[None, :] * (Yn[:, idx] - Y[:, idx]) / dt
+    return omega, Tn, status
+
+
+__all__ = ["active_cells", "solve_T", "chem_step", "chem_source", "real_fluid_props",
+           "NOT_CONVERGED", "NONFINITE", "NO_ROOT"]
 
 
 def chem_step_jacobian_fd(mech, net, T, p, Y, dT_rel=1e-6, dY_rel=1e-5, dY_min=1e-6):

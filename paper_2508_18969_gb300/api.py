@@ -95,6 +95,17 @@ class State:
                                            _ptr(T), _ptr(p), _ptr(Y), Y.stride(0), _ptr(status),
                                            _ptr(n_active), _stream(stream)))
 
+    def chem_source(self, T, p, Y, dt=None, status=None, n_active=None, want_T=True, stream=None):
+        """(omega [n, N] FP64 kg/(m^3 s), T' [N] or None): df_chem_source; T, Y unchanged."""
+        N = T.shape[0]
+        om = torch.empty(self.n, N, dtype=torch.float64, device=T.device)
+        Tn = torch.empty(N, dtype=torch.float64, device=T.device) if want_T else None
+        self._check(self._lib.df_chem_source(self.h, N, self.dt if dt is None else float(dt),
+                                             _ptr(T), _ptr(p), _ptr(Y), Y.stride(0), _ptr(om),
+                                             max(N, 1), _ptr(Tn), _ptr(status), _ptr(n_active),
+                                             _stream(stream)))
+        return om, Tn
+
     def chem_jacobian(self, T, p, Y, want_dT=True, stream=None):
         """(J [N, n, n+1] FP32, dTnew [N, n+1] FP64 or None): df_chem_jacobian."""
         N = T.shape[0]

@@ -77,16 +77,25 @@ enum XKind { kXF32 = 0, kXBF16 = 1, kXFP8 = 2 };
 
 // ---- launchers (eos.cu) ----
 // status (row-indexed, may be NULL) receives the per-row flags.
+// rho (row-indexed, may be NULL) receives the real-fluid density.
 cudaError_t launch_eos_pre(const EosParams& P, const RowMap& rows, const double* T,
                            const double* p, const double* Y, int64_t ldY, double* h0,
                            double* Z, void* x, int xkind, int64_t ldx, float x_scale,
-                           int32_t* status, cudaStream_t st);
+                           int32_t* status, cudaStream_t st, double* rho = nullptr);
 // pre_status (row-indexed, may be NULL) carries eos_pre's flags; cell_status (cell-indexed,
-// may be NULL) receives the final flags.
+// may be NULL) receives the final flags. With a Source (omega non-NULL) T and Y are left alone:
+// cell columns of omega [n x ldw] receive rho (Y' - Y) / dt and T_new (may be NULL) T'.
+struct Source {
+  double* omega;
+  int64_t ldw;
+  const double* rho;     // row-indexed, from eos_pre
+  double inv_dt;
+  double* T_new;
+};
 cudaError_t launch_eos_post(const EosParams& P, const RowMap& rows, const float* O, int64_t ldo,
                             const double* h0, double* T, const double* p, double* Y,
                             int64_t ldY, const int32_t* pre_status, int32_t* cell_status,
-                            cudaStream_t st);
+                            cudaStream_t st, const Source* src = nullptr);
 cudaError_t launch_props(const EosParams& P, int64_t n, const double* T, const double* p,
                          const double* Y, int64_t ldY, double* rho, double* h, double* cp,
                          double* Z, cudaStream_t st);

@@ -452,7 +452,7 @@ template <int NM, typename XT>
 __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams P, RowMap rows,
     const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
     int64_t ldY, double* __restrict__ h0, double* __restrict__ Zout, XT* __restrict__ x,
-    int64_t ldx, float x_scale, int32_t* __restrict__ status) {
+    int64_t ldx, float x_scale, int32_t* __restrict__ status, double* __restrict__ rho) {
   extern __shared__ double sm[];
   const SharedConsts c = load_consts(P, sm);
   f2* ycol = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
@@ -495,6 +495,7 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams
       Z = q.Z;
       h = h_ig(m, Tc) + q.h_dep * m.inv;
       if (!d_finite(h)) st |= kCellNonfinite;
+      if (rho) rho[r] = pc * drcp(m.inv * Z * kR * Tc);
     } else {
       st = kCellNonfinite;
     }
@@ -521,7 +522,7 @@ template <int NM>
 __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosParams P, RowMap rows,
     const float* __restrict__ O, int64_t ldo, const double* __restrict__ h0,
     double* __restrict__ T, const double* __restrict__ p, double* __restrict__ Y, int64_t ldY,
-    const int32_t* __restrict__ pre_status, int32_t* __restrict__ cell_status) {
+    const int32_t* __restrict__ pre_status, int32_t* __restrict__ cell_status, Source src) {
   extern __shared__ double sm[];
   const SharedConsts c = load_consts_post(P, sm);
   f2* ycol = reinterpret_cast<f2*>(sm + consts_words_post(P)) + threadIdx.x;
@@ -580,7 +581,16 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
       mixture_post(ycol, n, c, m);
       Tn = solve_T<true>(m, pc, h0c, Told, P, c.lnt, iters, st);
     }
-    if (st == 0) {
+    if (st == 0 && src.omega) {
+      // source terms rho (Y' - Y) / dt; Y' - Y in double-float
+      const f2 sc = f2_from(src.rho[r] * src.inv_dt);
+#pragma unroll 2
+      for (int k = 0; k < n; ++k) {
+        const f2 d = f2_add(ycol[k * stride], f2_from(-Y[k * ldY + cell]));
+        src.omega[k * src.ldw + cell] = f2_to_int(f2_mul(d, sc));
+      }
+      if (src.T_new) src.T_new[cell] = Tn;
+    } else if (st == 0) {
       T[cell] = Tn;
 #pragma unroll 2
       for (int k = 0; k < n; ++k) Y[k * ldY + cell] = f2_to_int(ycol[k * stride]);
@@ -884,36 +894,37 @@ int grid_for(int64_t nmax) {
 template <int NM, typename XT>
 cudaError_t pre_launch(const EosParams& P, const RowMap& rows, const double* T, const double* p,
                        const double* Y, int64_t ldY, double* h0, double* Z, XT* x, int64_t ldx,
-                       float xs, int32_t* status, cudaStream_t st) {
+                       float xs, int32_t* status, cudaStream_t st, double* rho) {
   cudaError_t e = smem_optin<eos_pre_kernel<NM, XT>>();
   if (e != cudaSuccess) return e;
   eos_pre_kernel<NM, XT><<<grid_for(rows.nmax), kThreads, eos_smem(P), st>>>(
-      P, rows, T, p, Y, ldY, h0, Z, x, ldx, xs, status);
+      P, rows, T, p, Y, ldY, h0, Z, x, ldx, xs, status, rho);
   return cudaGetLastError();
 }
 
 template <int NM>
 cudaError_t pre_nm(const EosParams& P, const RowMap& rows, const double* T, const double* p,
                    const double* Y, int64_t ldY, double* h0, double* Z, void* x, int xkind,
-                   int64_t ldx, float xs, int32_t* status, cudaStream_t st) {
+                   int64_t ldx, float xs, int32_t* status, cudaStream_t st, double* rho) {
   switch (xkind) {
     case kXBF16:
-      return pre_launch<NM>(P, rows, T, p, Y, ldY, h0, Z, (__nv_bfloat16*)x, ldx, xs, status, st);
+      return pre_launch<NM>(P, rows, T, p, Y, ldY, h0, Z, (__nv_bfloat16*)x, ldx, xs, status, st, rho);
     case kXFP8:
-      return pre_launch<NM>(P, rows, T, p, Y, ldY, h0, Z, (__nv_fp8_e4m3*)x, ldx, xs, status, st);
+      return pre_launch<NM>(P, rows, T, p, Y, ldY, h0, Z, (__nv_fp8_e4m3*)x, ldx, xs, status, st, rho);
     default:
-      return pre_launch<NM>(P, rows, T, p, Y, ldY, h0, Z, (float*)x, ldx, xs, status, st);
+      return pre_launch<NM>(P, rows, T, p, Y, ldY, h0, Z, (float*)x, ldx, xs, status, st, rho);
   }
 }
 
 template <int NM>
 cudaError_t post_nm(const EosParams& P, const RowMap& rows, const float* O, int64_t ldo,
                     const double* h0, double* T, const double* p, double* Y, int64_t ldY,
-                    const int32_t* pre_status, int32_t* cell_status, cudaStream_t st) {
+                    const int32_t* pre_status, int32_t* cell_status, cudaStream_t st,
+                    const Source& src) {
   cudaError_t e = smem_optin<eos_post_kernel<NM>>();
   if (e != cudaSuccess) return e;
   eos_post_kernel<NM><<<grid_for(rows.nmax), kThreads, eos_smem_post(P), st>>>(
-      P, rows, O, ldo, h0, T, p, Y, ldY, pre_status, cell_status);
+      P, rows, O, ldo, h0, T, p, Y, ldY, pre_status, cell_status, src);
   return cudaGetLastError();
 }
 
@@ -933,11 +944,11 @@ cudaError_t props_nm(const EosParams& P, int64_t n, const double* T, const doubl
 cudaError_t launch_eos_pre(const EosParams& P, const RowMap& rows, const double* T,
                            const double* p, const double* Y, int64_t ldY, double* h0,
                            double* Z, void* x, int xkind, int64_t ldx, float x_scale,
-                           int32_t* status, cudaStream_t st) {
+                           int32_t* status, cudaStream_t st, double* rho) {
   if (rows.nmax <= 0) return cudaSuccess;
   if (P.n <= 16)
-    return pre_nm<16>(P, rows, T, p, Y, ldY, h0, Z, x, xkind, ldx, x_scale, status, st);
-  return pre_nm<32>(P, rows, T, p, Y, ldY, h0, Z, x, xkind, ldx, x_scale, status, st);
+    return pre_nm<16>(P, rows, T, p, Y, ldY, h0, Z, x, xkind, ldx, x_scale, status, st, rho);
+  return pre_nm<32>(P, rows, T, p, Y, ldY, h0, Z, x, xkind, ldx, x_scale, status, st, rho);
 }
 
 template <int NM>
@@ -999,11 +1010,12 @@ cudaError_t launch_jac_post(const EosParams& P, int64_t ncell, int64_t cell0, co
 cudaError_t launch_eos_post(const EosParams& P, const RowMap& rows, const float* O, int64_t ldo,
                             const double* h0, double* T, const double* p, double* Y,
                             int64_t ldY, const int32_t* pre_status, int32_t* cell_status,
-                            cudaStream_t st) {
+                            cudaStream_t st, const Source* src) {
   if (rows.nmax <= 0) return cudaSuccess;
+  const Source s = src ? *src : Source{nullptr, 0, nullptr, 0.0, nullptr};
   if (P.n <= 16)
-    return post_nm<16>(P, rows, O, ldo, h0, T, p, Y, ldY, pre_status, cell_status, st);
-  return post_nm<32>(P, rows, O, ldo, h0, T, p, Y, ldY, pre_status, cell_status, st);
+    return post_nm<16>(P, rows, O, ldo, h0, T, p, Y, ldY, pre_status, cell_status, st, s);
+  return post_nm<32>(P, rows, O, ldo, h0, T, p, Y, ldY, pre_status, cell_status, st, s);
 }
 
 cudaError_t launch_props(const EosParams& P, int64_t n, const double* T, const double* p,

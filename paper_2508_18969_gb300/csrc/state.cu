@@ -120,7 +120,7 @@ void free_state(df_state* s) {
   for (auto p : s->bias) f(p);
   for (auto p : s->Wlp) f(p);
   for (auto p : s->col_scale) f(p);
-  f(s->x); f(s->act[0]); f(s->act[1]); f(s->O); f(s->h0); f(s->rstat);
+  f(s->x); f(s->act[0]); f(s->act[1]); f(s->O); f(s->h0); f(s->rho_row); f(s->rstat);
   f(s->idx); f(s->cscr);
 }
 
@@ -478,6 +478,7 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
   s->ldo = round_up(n, 8);
   CK(dalloc(&s->O, (size_t)s->cap * s->ldo), "network output");
   CK(dalloc(&s->h0, (size_t)s->cap), "h0");
+  CK(dalloc(&s->rho_row, (size_t)s->cap), "rho");
   CK(dalloc(&s->rstat, (size_t)s->cap), "row status");
 
   if (lp) {
@@ -546,15 +547,20 @@ df_status df_real_fluid_props(df_state* s, int64_t n_cells, const double* T, con
   return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "real-fluid properties");
 }
 
-df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const double* p,
-                       double* Y, int64_t ldY, int32_t* cell_status, int64_t* n_active_out,
-                       void* stream) {
+}  // extern "C"
+
+namespace {
+
+// The reaction step a0-a10 in batches of the state's capacity. With src (source terms) the
+// kernels leave T and Y untouched and write omega / T_new instead.
+df_status run_step(df_state* s, int64_t n_cells, double dt, double* T, const double* p, double* Y,
+                   int64_t ldY, int32_t* cell_status, int64_t* n_active_out, cudaStream_t st,
+                   const Source* src) {
   df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
   if (rc != DF_OK) return rc;
   if (!(std::fabs(dt - s->dt) <= 1e-12 * std::fabs(s->dt)))
     return fail(s, DF_ERR_DT_MISMATCH, "dt %.17g differs from the network's %.17g", dt, s->dt);
   DeviceGuard guard(s->device);
-  cudaStream_t st = (cudaStream_t)stream;
   if ((rc = ensure_compact(s, n_cells)) != DF_OK) return rc;
   cudaError_t e = cudaMemsetAsync(s->d_flagged, 0, sizeof(int64_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_iters, 0, sizeof(int64_t), st);
@@ -569,13 +575,15 @@ df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const
     const RowMap rm{s->idx, s->d_count, row0, std::min<int64_t>(s->cap, n_cells - row0)};
     {
       ProfScope ps(s, "eos_pre", st);
-      e = launch_eos_pre(s->P, rm, T, p, Y, ldY, s->h0, nullptr, s->x, xk, s->ldx, xs, s->rstat, st);
+      e = launch_eos_pre(s->P, rm, T, p, Y, ldY, s->h0, nullptr, s->x, xk, s->ldx, xs, s->rstat, st,
+                         src ? s->rho_row : nullptr);
     }
     if (e != cudaSuccess) return cuda_fail(s, e, "eos_pre launch");
     if ((rc = run_mlp(s, rm, st)) != DF_OK) return rc;
     {
       ProfScope ps(s, "eos_post", st);
-      e = launch_eos_post(s->P, rm, s->O, s->ldo, s->h0, T, p, Y, ldY, s->rstat, cell_status, st);
+      e = launch_eos_post(s->P, rm, s->O, s->ldo, s->h0, T, p, Y, ldY, s->rstat, cell_status, st,
+                          src);
     }
     if (e != cudaSuccess) return cuda_fail(s, e, "eos_post launch");
   }
@@ -584,6 +592,41 @@ df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const
     if (e != cudaSuccess) return cuda_fail(s, e, "n_active copy");
   }
   return DF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const double* p,
+                       double* Y, int64_t ldY, int32_t* cell_status, int64_t* n_active_out,
+                       void* stream) {
+  return run_step(s, n_cells, dt, T, p, Y, ldY, cell_status, n_active_out, (cudaStream_t)stream,
+                  nullptr);
+}
+
+df_status df_chem_source(df_state* s, int64_t n_cells, double dt, const double* T,
+                         const double* p, const double* Y, int64_t ldY, double* omega, int64_t ldw,
+                         double* T_new, int32_t* cell_status, int64_t* n_active_out, void* stream) {
+  df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
+  if (rc != DF_OK) return rc;
+  if (n_cells > 0 && !omega) return fail(s, DF_ERR_INVALID_ARG, "omega is NULL");
+  if (n_cells > 0 && ldw < n_cells) return fail(s, DF_ERR_INVALID_ARG, "ldw < n_cells");
+  if (!(std::fabs(dt - s->dt) <= 1e-12 * std::fabs(s->dt)))
+    return fail(s, DF_ERR_DT_MISMATCH, "dt %.17g differs from the network's %.17g", dt, s->dt);
+  DeviceGuard guard(s->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  // cells that do not react (or get flagged) keep omega = 0 and T' = T
+  cudaError_t e = cudaSuccess;
+  if (n_cells > 0) {
+    e = cudaMemset2DAsync(omega, sizeof(double) * ldw, 0, sizeof(double) * n_cells, (size_t)s->n, st);
+    if (e == cudaSuccess && T_new)
+      e = cudaMemcpyAsync(T_new, T, sizeof(double) * n_cells, cudaMemcpyDeviceToDevice, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(s, e, "source-term initialisation");
+  const Source src{omega, ldw, s->rho_row, 1.0 / dt, T_new};
+  return run_step(s, n_cells, dt, const_cast<double*>(T), p, const_cast<double*>(Y), ldY,
+                  cell_status, n_active_out, st, &src);
 }
 
 // Builds the Jacobian context: buffers for B cells, BF16 weights and tensor maps when the

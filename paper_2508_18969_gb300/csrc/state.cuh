@@ -74,6 +74,7 @@ struct df_state {
   float* O = nullptr;
   int64_t ldo = 0;
   double* h0 = nullptr;
+  double* rho_row = nullptr;             // density of each row (source terms)
   int32_t* rstat = nullptr;
   // compaction scratch, grown on demand
   int32_t* idx = nullptr;

@@ -342,3 +342,37 @@ def test_chem_jacobian_vs_finite_differences(df, name, N, prec):
     rel = np.abs(dTn - dTf)[tm] / (np.abs(dTf[tm]) + 1.0)
     print(f"dTnew {name} {prec}: max rel {rel.max():.3e}")
     assert rel.max() <= (1e-4 if prec == "fp32" else 5e-2)
+
+
+# ---------------------------------------------------------------- source terms
+
+@pytest.mark.parametrize("name,N,T_react,prec", [("small-fp32-4k", 4096, 600.0, "fp32"),
+                                                 ("layer1d-30sp-1m", 3000, 0.0, "fp32"),
+                                                 ("react30-16m", 3000, 600.0, "bf16")])
+def test_chem_source_matches_step_and_oracle(df, name, N, T_react, prec):
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    P = df.DF_FP32 if prec == "fp32" else df.DF_BF16
+    st = df.State(mech, net, precision=P, T_react=T_react, batch_cells=1024)
+    Td, pd, Yd = dev(T), dev(p), dev(Y)
+    status = torch.full((N,), -1, dtype=torch.int32, device=DEV)
+    om, Tn = st.chem_source(Td, pd, Yd, status=status)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(Td), T) and np.array_equal(host(Yd), Y)   # inputs untouched
+    # the same step in place
+    T2, Y2 = dev(T), dev(Y)
+    st.chem_step(T2, pd, Y2)
+    torch.cuda.synchronize()
+    Ts, Ys = host(T2), host(Y2)
+    om, Tn, sg = host(om), host(Tn), host(status)
+    assert np.array_equal(Tn, Ts)
+    rho = ope.state(mech, T, p, Y)["rho"]
+    back = Y + om * net.dt / rho[None, :]
+    assert np.all(np.abs(back - Ys) <= 1e-12 * np.abs(Ys) + 1e-16)
+    inact = np.setdiff1d(np.arange(N), ostep.active_cells(T, T_react))
+    assert np.all(om[:, inact] == 0.0) and np.all(om[:, sg != 0] == 0.0)
+    # against the oracle's source terms: the step's dY bar scaled by rho / dt
+    om_o, Tn_o, so = ostep.chem_source(mech, net, T, p, Y, net.dt, T_react=T_react)
+    assert np.array_equal(sg, so)
+    dY_tol = 1e-6 if prec == "fp32" else 1e-4
+    assert np.all(np.abs(om - om_o) <= dY_tol * rho[None, :] / net.dt)
+    assert np.all(np.abs(om.sum(axis=0)) <= 1e-11 * rho / net.dt)

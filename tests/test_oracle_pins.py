@@ -451,3 +451,21 @@ def test_adam_matches_torch_optim():
         p, m, v = train.adam_step(p, g, m, v, t, lr=1e-2)
     for a, b in zip(p, pt):
         np.testing.assert_allclose(a, b.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
+def test_source_terms_conserve_mass_and_vanish_without_chemistry():
+    """omega = rho (Y' - Y) / dt: sums to zero over species (Y' is renormalised), is zero for
+    cells that do not react, and is zero everywhere for a network whose read-out is zero."""
+    mech, net, T, p, Y = synth.configs.build("small-fp32-4k", n_cells=300)
+    om, Tn, st = step.chem_source(mech, net, T, p, Y, net.dt, T_react=600.0)
+    rho = pe.state(mech, T, p, Y)["rho"]
+    assert np.all(np.abs(om.sum(axis=0)) <= 1e-12 * rho / net.dt)
+    cold = T <= 600.0
+    assert np.all(om[:, cold] == 0.0) and np.array_equal(Tn[cold], T[cold])
+    hot = ~cold & (st == 0)
+    assert np.abs(om[:, hot]).max() > 0.0
+    net.W[-1] = np.zeros_like(net.W[-1])
+    net.b[-1] = np.zeros_like(net.b[-1])
+    om0, Tn0, st0 = step.chem_source(mech, net, T, p, Y, net.dt, T_react=0.0)
+    ok = st0 == 0
+    assert np.abs(om0[:, ok]).max() <= 1e-9 * (rho[ok] / net.dt).max()
