@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="reacting cells per internal batch")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the cost model's tile widths instead of timing them (df_autotune)")
     return ap.parse_args()
 
 
@@ -239,6 +241,7 @@ def run_ours(args):
     prec = {"bf16": df.DF_BF16, "fp32": df.DF_FP32, "fp8": df.DF_FP8_E4M3}[args.precision]
     batch = args.batch or min(N, 1 << 22)
     st = df.State(mech, net, precision=prec, T_react=w.T_react, device=local, batch_cells=batch)
+    tiles = st.tiles() if args.no_autotune else st.autotune(n_rows=min(N, batch))
     Td = torch.tensor(T, device=dev)
     pd = torch.tensor(p, device=dev)
     Yd = torch.tensor(Y, device=dev).contiguous()
@@ -408,7 +411,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "n_cells": N, "n_species": mech.n, "batch_cells": batch,
                    "network": "-".join(str(x) for x in w.widths), "precision": args.precision,
-                   "reacting_cells": int(n_act), "T_react_K": w.T_react,
+                   "reacting_cells": int(n_act), "T_react_K": w.T_react, "tile_widths": tiles,
                    "l2": "inputs larger than L2 (fields 8*(2+n)*N bytes, activations GBs)"},
         "clocks": clk.summary(),
         "e2e": e2e,

@@ -87,6 +87,8 @@ SIGNATURES = {
     "df_train_get_step": (_ST, [_VP, C.POINTER(_I64)]),
     "df_state_save": (_ST, [_VP, C.c_char_p]),
     "df_state_load": (_ST, [_VP, C.c_char_p]),
+    "df_autotune": (_ST, [_VP, _I64, C.c_char_p, _VP]),
+    "df_get_tiles": (_ST, [_VP, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]),
     "df_graph_create": (_ST, [_VP, _I64, C.c_double, _VP, _VP, _VP, _I64, _VP, _VP, C.POINTER(_VP)]),
     "df_graph_launch": (_ST, [_VP, _VP]),
     "df_graph_destroy": (None, [_VP]),

@@ -190,6 +190,21 @@ class State:
     def load(self, path):
         self._check(self._lib.df_state_load(self.h, str(path).encode()))
 
+    # ---- tile widths of the tensor-core layers ----
+    def autotune(self, n_rows=0, cache_path=None, stream=None):
+        """Times every compiled tile width per layer and keeps the fastest (df_autotune)."""
+        self._check(self._lib.df_autotune(self.h, int(n_rows),
+                                          None if cache_path is None else str(cache_path).encode(),
+                                          _stream(stream)))
+        return self.tiles()
+
+    def tiles(self):
+        cap = 8
+        bn = (C.c_int32 * cap)()
+        nl = C.c_int32()
+        self._check(self._lib.df_get_tiles(self.h, bn, cap, C.byref(nl)))
+        return [int(bn[i]) for i in range(min(nl.value, cap))]
+
     # ---- kernel timing ----
     def profile_enable(self, on: bool = True):
         self._check(self._lib.df_profile_enable(self.h, 1 if on else 0))

@@ -902,6 +902,125 @@ df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const 
   return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "Jacobian");
 }
 
+// ---- tile-width autotuning ----
+
+}  // extern "C"
+
+namespace {
+
+// Re-encodes layer l's weight map for tile width bn (the only part of a layer that depends on
+// it) and sets the kernel instance's attributes.
+df_status retile(df_state* s, int l, int bn) {
+  TcLayer& T = s->tcl[l];
+  const size_t eb = elem_of(s->precision);
+  char emsg[256];
+  if (!tc_encode_2d(&T.tmB, s->Wlp[l], (int)eb, (uint64_t)T.K, (uint64_t)T.N,
+                    (uint64_t)s->Kp8[l] * eb, 128 / (uint32_t)eb, (uint32_t)bn, emsg, sizeof emsg))
+    return fail(s, DF_ERR_CUDA, "%s", emsg);
+  T.BN = bn;
+  cudaError_t e = prepare_tc(T);
+  return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "kernel attributes");
+}
+
+std::string tile_key(const df_state* s, int l, const char* dev) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s %d %d %d %d", dev, s->precision, s->widths[l], s->widths[l + 1],
+           l == s->L - 1 ? 1 : 0);
+  return buf;
+}
+
+}  // namespace
+
+extern "C" {
+
+df_status df_autotune(df_state* s, int64_t n_rows, const char* cache_path, void* stream) {
+  if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
+  if (n_rows < 0) return fail(s, DF_ERR_INVALID_ARG, "n_rows < 0");
+  if (s->precision == DF_FP32) return DF_OK;  // the SIMT layers have a single tiling
+  DeviceGuard guard(s->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, s->device);
+  std::string dev = prop.name;
+  for (char& ch : dev)
+    if (ch == ' ' || ch == '\t') ch = '_';
+  // cache: one line per layer shape, "<device> <precision> <K> <N> <last> <BN>"
+  std::vector<std::pair<std::string, int>> cache;
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char line[600];
+      while (std::fgets(line, sizeof line, f)) {
+        char d[512];
+        int prec, K, N, last, bn;
+        if (std::sscanf(line, "%511s %d %d %d %d %d", d, &prec, &K, &N, &last, &bn) == 6) {
+          char key[600];
+          snprintf(key, sizeof key, "%s %d %d %d %d", d, prec, K, N, last);
+          cache.emplace_back(key, bn);
+        }
+      }
+      std::fclose(f);
+    }
+  }
+  const int64_t rows = std::max<int64_t>(128, std::min<int64_t>(n_rows > 0 ? n_rows : s->cap, s->cap));
+  const RowMap rm{nullptr, nullptr, 0, rows};
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  df_status rc = DF_OK;
+  bool dirty = false;
+  for (int l = 0; l < s->L && rc == DF_OK && e == cudaSuccess; ++l) {
+    const bool last = l == s->L - 1;
+    const std::string key = tile_key(s, l, dev.c_str());
+    int chosen = 0;
+    for (auto& kv : cache)
+      if (kv.first == key) chosen = kv.second;
+    static const int hid[] = {64, 128, 160, 224, 256};
+    static const int rd[] = {32, 64};
+    const int* cand = last ? rd : hid;
+    const int nc = last ? 2 : 5;
+    bool known = false;
+    for (int i = 0; i < nc; ++i) known = known || cand[i] == chosen;
+    if (!known) {
+      float best = 1e30f;
+      for (int i = 0; i < nc && rc == DF_OK && e == cudaSuccess; ++i) {
+        if ((rc = retile(s, l, cand[i])) != DF_OK) break;
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_tc_gemm(s->tcl[l], rm, s->num_sms, s->d_err, st);
+        if (e == cudaSuccess) e = cudaEventRecord(a, st);
+        for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch_tc_gemm(s->tcl[l], rm, s->num_sms, s->d_err, st);
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && ms < best) {
+          best = ms;
+          chosen = cand[i];
+        }
+      }
+      cache.emplace_back(key, chosen);
+      dirty = true;
+    }
+    if (rc == DF_OK && e == cudaSuccess) rc = retile(s, l, chosen);
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(s, e, "autotune");
+  if (rc != DF_OK) return rc;
+  if (dirty && cache_path) {
+    FILE* f = std::fopen(cache_path, "w");
+    if (!f) return fail(s, DF_ERR_INVALID_ARG, "cannot write %s", cache_path);
+    for (auto& kv : cache) std::fprintf(f, "%s %d\n", kv.first.c_str(), kv.second);
+    std::fclose(f);
+  }
+  return DF_OK;
+}
+
+df_status df_get_tiles(df_state* s, int32_t* bn, int32_t max_layers, int32_t* n_layers) {
+  if (!s || !n_layers || (max_layers > 0 && !bn)) return fail(s, DF_ERR_INVALID_ARG, "bad arguments");
+  *n_layers = s->L;
+  for (int l = 0; l < s->L && l < max_layers; ++l) bn[l] = s->tcl.empty() ? 0 : s->tcl[l].BN;
+  return DF_OK;
+}
+
 df_status df_get_step_summary(df_state* s, void* stream, df_step_stats* stats) {
   if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
   DeviceGuard guard(s->device);

@@ -376,3 +376,36 @@ def test_chem_source_matches_step_and_oracle(df, name, N, T_react, prec):
     dY_tol = 1e-6 if prec == "fp32" else 1e-4
     assert np.all(np.abs(om - om_o) <= dY_tol * rho[None, :] / net.dt)
     assert np.all(np.abs(om.sum(axis=0)) <= 1e-11 * rho / net.dt)
+
+
+# ---------------------------------------------------------------- tile autotuning
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_autotune_keeps_results_and_caches(df, prec, tmp_path):
+    mech, net, T, p, Y = synth.configs.build("layer1d-30sp-1m", n_cells=5000)
+    P = df.DF_BF16 if prec == "bf16" else df.DF_FP8_E4M3
+    st = df.State(mech, net, precision=P, T_react=0.0, batch_cells=4096)
+    before = st.tiles()
+    T1, Y1 = dev(T), dev(Y)
+    st.chem_step(T1, dev(p), Y1)
+    cache = tmp_path / "tiles.txt"
+    after = st.autotune(n_rows=4096, cache_path=cache)
+    assert len(after) == net.n_layers
+    assert all(b in (64, 128, 160, 224, 256) for b in after[:-1]) and after[-1] in (32, 64)
+    T2, Y2 = dev(T), dev(Y)
+    st.chem_step(T2, dev(p), Y2)
+    torch.cuda.synchronize()
+    # the tiling changes neither the arithmetic nor its order
+    assert np.array_equal(host(T1), host(T2)) and np.array_equal(host(Y1), host(Y2))
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == net.n_layers
+    st2 = df.State(mech, net, precision=P, T_react=0.0, batch_cells=4096)
+    assert st2.autotune(n_rows=4096, cache_path=cache) == after
+    assert cache.read_text().strip().splitlines() == lines
+    print(f"{prec}: tiles {before} -> {after}")
+
+
+def test_autotune_is_a_no_op_for_fp32(df):
+    mech, net, T, p, Y = synth.configs.build("small-fp32-4k", n_cells=64)
+    st = df.State(mech, net, precision=df.DF_FP32)
+    assert st.autotune() == [0] * net.n_layers
