@@ -133,6 +133,9 @@ cudaError_t launch_transpose(int64_t R, int64_t C, const void* in, int64_t ldi, 
 // kColsumChunks x C floats.
 cudaError_t launch_colsum(int64_t R, int C, const void* in, int64_t ldi, bool bf16, float* out,
                           float* scratch, cudaStream_t st);
+// out[i] = sum_{s < splits} part[s * stride + i] (fixed order), i < count.
+cudaError_t launch_sum_splits(int splits, int64_t count, int64_t stride, const float* part,
+                              float* out, cudaStream_t st);
 cudaError_t launch_adam(int64_t count, float* w, float* m, float* v, const float* g, float lr,
                         float b1, float b2, float eps, float c1, float c2, cudaStream_t st);
 cudaError_t launch_publish(int N, int K, const float* Wm, int64_t ldm, float* W32, int64_t ld32,
@@ -174,6 +177,8 @@ struct TcLayer {
   void* gbuf;            // BF16 [cells x ldg] GELU'(z) of the forward pass
   int64_t ldg;
   int ntan;              // tangent rows per cell (mode 2)
+  int ksplit = 1;        // split-K (plain mode): split s covers k-blocks [s kbs, (s+1) kbs) and
+  int64_t split_rows = 0;  // stores its partial product at output rows + s * split_rows
 };
 bool tc_encode_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
                   uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,

@@ -55,6 +55,8 @@ struct TcArgs {
   void* gbuf;      // GELU'(z): written (kModeStoreG) or read as the row-group scale (kModeRowG)
   int64_t ldg;
   int ntan;        // rows per group for kModeRowG
+  int ksplit;      // split-K: partial products over ksplit ranges of k-blocks
+  int64_t split_rows;  // output row offset between the partial products of two splits
 };
 
 // Epilogue modes: plain layer; layer that also stores GELU'(z) (forward pass of the Jacobian);
@@ -457,9 +459,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
   const int64_t M = valid_rows(g.rows);
   const int64_t tiles_m = (M + BM - 1) / BM;
   const int tiles_n = (g.N + BN - 1) / BN;
-  const int64_t ntiles = tiles_m * tiles_n;
+  const int64_t tiles_mn = tiles_m * tiles_n;
+  const int64_t ntiles = tiles_mn * g.ksplit;   // work item t = (split, m tile, n tile)
   const int kblocks = (g.K * (FP8 ? 1 : 2) + kRowBytes - 1) / kRowBytes;
   const int kelems = kRowBytes / (FP8 ? 1 : 2);
+  const int kbs = (kblocks + g.ksplit - 1) / g.ksplit;   // k-blocks per split (host: none empty)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
@@ -468,9 +472,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     uint32_t it = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int m0 = (int)((t / tiles_n) * BM);
-      const int n0 = (int)(t % tiles_n) * BN;
-      for (int kb = 0; kb < kblocks; ++kb, ++it) {
+      const int64_t tt = t % tiles_mn;
+      const int kb0 = (int)(t / tiles_mn) * kbs, kb1 = min(kblocks, kb0 + kbs);
+      const int m0 = (int)((tt / tiles_n) * BM);
+      const int n0 = (int)(tt % tiles_n) * BN;
+      for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % C::kStages;
         const uint32_t ph = (it / C::kStages) & 1;
         if (!mbar_wait(empty0 + 8 * s, ph ^ 1, abort, g.err)) { ok = false; break; }
@@ -494,12 +500,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     uint32_t it = 0, j = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+      const int kb0 = (int)(t / tiles_mn) * kbs, kb1 = min(kblocks, kb0 + kbs);
       const int a = j & 1;
       const uint32_t aph = (j >> 1) & 1;
       if (!mbar_wait(tempty0 + 8 * a, aph ^ 1, abort, g.err)) break;
       tc_fence_after();
       const uint32_t dt = tmem + a * C::kAccStride;
-      for (int kb = 0; kb < kblocks; ++kb, ++it) {
+      for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % C::kStages;
         const uint32_t ph = (it / C::kStages) & 1;
         if (!mbar_wait(full0 + 8 * s, ph, abort, g.err)) { ok = false; break; }
@@ -508,7 +515,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
         const uint64_t db = desc_sw128(smem_u32(sB + s * BN * kRowBytes));
 #pragma unroll
         for (int kk = 0; kk < kRowBytes / 32; ++kk)  // 32 bytes of K per instruction
-          mma_issue<FP8>(dt, da + 2 * kk, db + 2 * kk, id, (kb | kk) ? 1u : 0u);
+          mma_issue<FP8>(dt, da + 2 * kk, db + 2 * kk, id, (kb != kb0 || kk) ? 1u : 0u);
         mma_commit(empty0 + 8 * s);  // frees the stage when these MMAs have read it
       }
       if (ok) mma_commit(tfull0 + 8 * a);
@@ -534,8 +541,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
       const uint32_t aph = (j >> 1) & 1;
       if (!mbar_wait(tfull0 + 8 * a, aph, abort, g.err)) break;
       tc_fence_after();
-      const int64_t m0 = (t / tiles_n) * BM + q * 32;
-      const int n0 = (int)(t % tiles_n) * BN;
+      const int64_t tt = t % tiles_mn;
+      // row of the output: the tile's rows, shifted to this split's partial product
+      const int64_t m0 = (tt / tiles_n) * BM + q * 32 + (t / tiles_mn) * g.split_rows;
+      const int n0 = (int)(tt % tiles_n) * BN;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + a * C::kAccStride;
       // chunks c = 32 slot + kChunkStride i; TMEM loads run one chunk ahead of the math,
       // except in kModeStoreG, whose two stores per chunk leave no registers for a second
@@ -625,7 +634,7 @@ cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream
   cudaError_t e0 = tc_attr<FP8, BN, OUTK, GELU, MODE>();
   if (e0 != cudaSuccess) return e0;
   if (num_sms <= 0) return cudaSuccess;  // attribute set-up only
-  const int64_t tiles = ((a.rows.nmax + BM - 1) / BM) * ((L.N + BN - 1) / BN);
+  const int64_t tiles = ((a.rows.nmax + BM - 1) / BM) * ((L.N + BN - 1) / BN) * a.ksplit;
   const unsigned grid = (unsigned)(tiles < num_sms ? (tiles > 0 ? tiles : 1) : num_sms);
   kern<<<grid, kThreads, C::kSmemBytes, st>>>(L.tmA, L.tmB, L.tmO, L.mode == kModeStoreG ? L.tmG : L.tmO, a);
   return cudaGetLastError();
@@ -791,6 +800,8 @@ cudaError_t launch_tc_gemm(const TcLayer& L, const RowMap& rows, int num_sms, in
   a.gbuf = L.gbuf;
   a.ldg = L.ldg;
   a.ntan = L.ntan > 0 ? L.ntan : 1;
+  a.ksplit = L.ksplit > 0 ? L.ksplit : 1;
+  a.split_rows = L.split_rows;
   return L.elem_bytes == 1 ? launch_fmt<true>(L, a, num_sms, st)
                            : launch_fmt<false>(L, a, num_sms, st);
 }

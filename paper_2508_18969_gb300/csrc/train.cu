@@ -14,24 +14,35 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = kTrainScratchFloats;   // element-wise grids, one loss partial each
 
-__device__ __forceinline__ double boxcox(double y, double lam) {
-  return (y > 0.0 ? pow(y, lam) - 1.0 : -1.0) / lam;
+// Change of the Box-Cox coordinate, BC(yt) - BC(y) = (yt^l - y^l) / l. For positive y and yt
+// it is formed as y^l expm1(l ln(yt / y)) / l: the ratio in FP64, the rest in FP32, which keeps
+// ~1e-7 relative accuracy of the difference itself (no cancellation of two nearly equal BCs).
+__device__ __forceinline__ float dboxcox(double y, double yt, float lam) {
+  if (y > 0.0 && yt > 0.0) {
+    const float q = (float)((yt - y) / y);
+    const float lr = (q > -0.5f && q < 1.0f) ? log1pf(q) : logf((float)(yt / y));
+    return powf((float)y, lam) * expm1f(lam * lr) / lam;
+  }
+  const float a = yt > 0.0 ? powf((float)yt, lam) : 0.0f;
+  const float b = y > 0.0 ? powf((float)y, lam) : 0.0f;
+  return (a - b) / lam;
 }
 
-// Ohat[b][k] = (BC(Yt_k) - BC(Y_k) - out_mean_k) / out_std_k, FP32 [B x ldh], zero pad.
+// Ohat[b][k] = (BC(Yt) - BC(Y) - out_mean_k) / out_std_k, FP32 [B x ldh], zero pad.
 __global__ void targets_kernel(EosParams P, int64_t B, const double* __restrict__ Y,
                                const double* __restrict__ Yt, int64_t ldY,
                                const double* __restrict__ norm, float* __restrict__ Oh,
                                int64_t ldh) {
   const int n = P.n, K0 = P.K0;
+  const float lam = (float)P.lambda;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < B * ldh;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = e / ldh;
     const int k = (int)(e % ldh);
     float v = 0.0f;
     if (k < n) {
-      const double du = boxcox(Yt[k * ldY + b], P.lambda) - boxcox(Y[k * ldY + b], P.lambda);
-      v = (float)((du - norm[2 * K0 + k]) / norm[2 * K0 + n + k]);
+      const float du = dboxcox(Y[k * ldY + b], Yt[k * ldY + b], lam);
+      v = (du - (float)norm[2 * K0 + k]) / (float)norm[2 * K0 + n + k];
     }
     Oh[e] = v;
   }
@@ -92,6 +103,17 @@ __global__ void transpose_kernel(int64_t R, int64_t C, const T* __restrict__ in,
   for (int j = threadIdx.y; j < 32; j += blockDim.y) {
     const int64_t c = c0 + j, r = r0 + threadIdx.x;
     if (c < C && r < Rpad) out[c * ldo + r] = tile[threadIdx.x][j];
+  }
+}
+
+// out[i] = sum_{s < splits} part[s * stride + i], in order of s.
+__global__ void split_sum_kernel(int splits, int64_t count, int64_t stride,
+                                 const float* __restrict__ part, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int k = 0; k < splits; ++k) s += part[k * stride + i];
+    out[i] = s;
   }
 }
 
@@ -199,6 +221,13 @@ cudaError_t launch_colsum(int64_t R, int C, const void* in, int64_t ldi, bool bf
   else
     colsum_kernel<float><<<grid, 128, 0, st>>>(R, C, (const float*)in, ldi, scratch);
   sum_parts_kernel<<<(C + 127) / 128, 128, 0, st>>>((int)chunks, C, scratch, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_splits(int splits, int64_t count, int64_t stride, const float* part,
+                              float* out, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  split_sum_kernel<<<blocks_for(count), kThreads, 0, st>>>(splits, count, stride, part, out);
   return cudaGetLastError();
 }
 

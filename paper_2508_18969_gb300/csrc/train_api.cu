@@ -41,6 +41,7 @@ struct Trn {
   void* ZT = nullptr;                    // dZ_l^T [N_l x Bp]
   void* HT = nullptr;                    // H_{l-1}^T [K_l x Bp]
   float* dX = nullptr;                   // input gradient [B x lddx]
+  float* dWp = nullptr;                  // split-K partial weight gradients [kMaxSplit x N x ldw]
   int64_t lddx = 0;
   double* h0 = nullptr;
   int32_t* rstat = nullptr;
@@ -57,7 +58,7 @@ void free_trn(Trn* t) {
     for (float* p : *v) f(p);
   for (void* p : t->WT) f(p);
   f(t->loss); f(t->scratch); f(t->zero_bias);
-  f(t->x); f(t->O); f(t->Oh); f(t->ZT); f(t->HT); f(t->dX); f(t->h0); f(t->rstat);
+  f(t->x); f(t->O); f(t->Oh); f(t->ZT); f(t->HT); f(t->dX); f(t->dWp); f(t->h0); f(t->rstat);
   for (auto v : {&t->H, &t->G, &t->dZ})
     for (void* p : *v) f(p);
   delete t;
@@ -69,13 +70,24 @@ namespace {
 
 bool trains(const df_state* s) { return s->precision == DF_FP32 || s->precision == DF_BF16; }
 
+constexpr int kMaxSplit = 16;   // split-K of the weight-gradient GEMMs
+
+// Splits of a weight-gradient GEMM over the batch: about two waves of tiles on the GPU, no
+// split empty (an empty split would store an uninitialised accumulator).
+int wgrad_splits(int64_t tiles, int kblocks, int num_sms) {
+  int S = (int)std::min<int64_t>(kMaxSplit, std::max<int64_t>(1, (2 * num_sms + tiles - 1) / tiles));
+  S = std::min(S, std::max(1, kblocks / 8));
+  while (S > 1 && (int64_t)(S - 1) * ((kblocks + S - 1) / S) >= kblocks) --S;
+  return S;
+}
+
 void free_batch(Trn* t) {
   auto f = [](void* p) { if (p) cudaFree(p); };
-  f(t->x); f(t->O); f(t->Oh); f(t->ZT); f(t->HT); f(t->dX); f(t->h0); f(t->rstat);
+  f(t->x); f(t->O); f(t->Oh); f(t->ZT); f(t->HT); f(t->dX); f(t->dWp); f(t->h0); f(t->rstat);
   for (auto v : {&t->H, &t->G, &t->dZ})
     for (void* p : *v) f(p);
   t->x = t->ZT = t->HT = nullptr;
-  t->O = t->Oh = t->dX = nullptr;
+  t->O = t->Oh = t->dX = t->dWp = nullptr;
   t->h0 = nullptr;
   t->rstat = nullptr;
   t->H.clear(); t->G.clear(); t->dZ.clear();
@@ -202,6 +214,12 @@ df_status ensure_batch(df_state* s, int64_t B) {
   zalloc(&t->HT, eb * kmax * Bp);
   t->lddx = round_up(K0, 4);
   zalloc((void**)&t->dX, sizeof(float) * B * t->lddx);
+  if (bf16) {
+    int64_t wmaxp = 0;
+    for (int l = 0; l < L; ++l)
+      wmaxp = std::max<int64_t>(wmaxp, round_up(s->widths[l + 1], 128) * t->ldw[l]);
+    zalloc((void**)&t->dWp, sizeof(float) * kMaxSplit * wmaxp);
+  }
   zalloc((void**)&t->h0, sizeof(double) * B);
   zalloc((void**)&t->rstat, sizeof(int32_t) * B);
   if (e != cudaSuccess) {
@@ -263,7 +281,7 @@ df_status ensure_batch(df_state* s, int64_t B) {
       Wg.K = (int)Bp;
       Wg.BN = K <= 32 ? 32 : 64;
       Wg.bias = t->zero_bias;
-      Wg.out = t->dW[l];
+      Wg.out = t->dWp;        // split-K partials, summed into dW afterwards
       Wg.ldo = t->ldw[l];
       Wg.out_kind = kXF32;
       Wg.gelu = false;
@@ -274,7 +292,7 @@ df_status ensure_batch(df_state* s, int64_t B) {
       if (ok)
         ok = encode(&Wg.tmA, t->ZT, Bp, N, Bp, 128, emsg, sizeof emsg) &&
              encode(&Wg.tmB, t->HT, Bp, K, Bp, Wg.BN, emsg, sizeof emsg) &&
-             tc_encode_out(Wg, (uint64_t)N, emsg, sizeof emsg);
+             tc_encode_out(Wg, (uint64_t)kMaxSplit * round_up(N, 128), emsg, sizeof emsg);
       if (!ok) break;
       t->fwd.push_back(F);
       t->dgrad.push_back(D);
@@ -342,7 +360,14 @@ cudaError_t backward(df_state* s, int64_t R, bool want_dx, cudaStream_t st) {
       if (bf16) {
         TcLayer Wg = t->wgrad[l];
         Wg.K = (int)Rp;
+        const int64_t tiles = ((N + 127) / 128) * ((K + Wg.BN - 1) / Wg.BN);
+        Wg.ksplit = wgrad_splits(tiles, (int)(Rp / 64), s->num_sms);
+        // each split owns whole 128-row tiles (a tile's store covers all its rows)
+        Wg.split_rows = round_up(N, 128);
         e = launch_tc_gemm(Wg, wrows, s->num_sms, s->d_err, st);
+        if (e == cudaSuccess)
+          e = launch_sum_splits(Wg.ksplit, (int64_t)N * t->ldw[l], Wg.split_rows * t->ldw[l],
+                                t->dWp, t->dW[l], st);
       } else {
         e = launch_sgemm_bias_act(wrows, K, (int)Rp, (const float*)t->ZT, t->Bp,
                                   (const float*)t->HT, t->Bp, t->zero_bias, t->dW[l], t->ldw[l],
