@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="reacting cells per internal batch")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the cost model's tile widths instead of timing them (df_autotune)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time every tile width per layer (df_autotune) instead of the cost model")
+    ap.add_argument("--no-autotune", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -161,6 +162,33 @@ def weak_scaling_value(world, cells_per_rank, ms_max):
     return world * cells_per_rank / (ms_max * 1e-3)
 
 
+# DRAM traffic per row (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture divided
+# by the rows of that launch; summaries in profiles/), keyed by kernel family and network, valid
+# only for the kernel source the counters were taken on (SHA-256 prefix of the file): once the
+# kernel changes, the bench reports traffic as null until it is measured again.
+MEASURED_TRAFFIC = {
+    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "345b952374ddfe4d", 3158.0),
+    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "345b952374ddfe4d", 4751.0),
+    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 296.0),
+    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 549.0),
+}
+
+
+def measured_traffic(family, network, rows_per_launch):
+    import hashlib
+    entry = MEASURED_TRAFFIC.get((family, network))
+    if entry is None:
+        return None
+    path, digest, per_row = entry
+    try:
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != digest:
+                return None
+    except OSError:
+        return None
+    return per_row * rows_per_launch
+
+
 def layer_flops(widths, rows):
     return [2.0 * widths[l] * widths[l + 1] * rows for l in range(len(widths) - 1)]
 
@@ -194,6 +222,24 @@ def cpu_oracle_leg(mech, net, T, p, Y, sel, T_react, gpu_after=None):
                "mean_abs_dT_K": float(np.abs(Tg - To).mean()),
                "cells": int(sel.shape[0])}
     return out, err
+
+
+def bdf_truth_leg(mech, net, T, p, Y, T_react, cells=2048):
+    """Times the stiff-chemistry integration the network stands in for (the C BDF of the
+    oracle, one thread per cell over the host cores) on reacting cells of the field."""
+    from oracle import step as ostep
+    from oracle import truth
+    act = ostep.active_cells(T, T_react)
+    if act.size == 0:
+        return None
+    sel = act[np.linspace(0, act.size - 1, min(cells, act.size)).astype(np.int64)]
+    t0 = time.perf_counter()
+    _, _, ok, steps, _ = truth.advance(mech, T[sel], p[sel], Y[:, sel], net.dt)
+    dt = time.perf_counter() - t0
+    return {"value": sel.size / dt, "unit": UNIT, "cells": int(sel.size), "seconds": dt,
+            "cores": len(os.sched_getaffinity(0)), "ok_fraction": float(np.mean(ok)),
+            "mean_bdf_steps": float(np.mean(steps)),
+            "what": "C BDF (orders 1-5, rtol 1e-10, atol 1e-14) of the cell chemistry over dt"}
 
 
 def run_reference(args):
@@ -244,7 +290,7 @@ def run_ours(args):
     prec = {"bf16": df.DF_BF16, "fp32": df.DF_FP32, "fp8": df.DF_FP8_E4M3}[args.precision]
     batch = args.batch or min(N, 1 << 22)
     st = df.State(mech, net, precision=prec, T_react=w.T_react, device=local, batch_cells=batch)
-    tiles = st.tiles() if args.no_autotune else st.autotune(n_rows=min(N, batch))
+    tiles = st.autotune(n_rows=min(N, batch)) if args.autotune else st.tiles()
     Td = torch.tensor(T, device=dev)
     pd = torch.tensor(p, device=dev)
     Yd = torch.tensor(Y, device=dev).contiguous()
@@ -400,13 +446,21 @@ def run_ours(args):
             roofs[fam] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                           "frac": ach / pk["hbm_gbs"], "traffic": None, "kernel": fam,
                           "peak_source": f"hbm_gbs ({pk_src})"}
+    net_str = "-".join(str(x) for x in w.widths)
+    rows_per_launch = min(int(n_act), batch)
+    for fam_name, r in roofs.items():
+        r["traffic"] = measured_traffic(fam_name, net_str, rows_per_launch)
+        if r["traffic"] is not None:
+            r["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per row x rows per launch"
     dom = max(fams, key=lambda k: fams[k][1])
     roof = roofs[dom]
 
     cpu = None
     errs = None
+    bdf = None
     if not args.no_cpu_baseline:
         cpu, errs = cpu_oracle_leg(mech, net, T, p, Y, sel, w.T_react, gpu_first)
+        bdf = bdf_truth_leg(mech, net, T, p, Y, w.T_react)
 
     kpl = len(w.widths) - 1 + 2            # per batch: eos_pre + layers + eos_post
     nb = (N + batch - 1) // batch
@@ -428,6 +482,7 @@ def run_ours(args):
         "roofline": roof,
         "roofline_by_family": roofs,
         "cpu_baseline": cpu,
+        "bdf_truth_cpu": bdf,
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in fams.items()},
         "newton_iterations_per_cell": iters_per_cell,
         "flagged_cells": int(n_flag),
