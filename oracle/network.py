@@ -38,6 +38,47 @@ def gelu_tanh_grad(x):
     return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t**2) * c * (1.0 + 3.0 * 0.044715 * x**2)
 
 
+def gelu_tanh_grad2(x):
+    """d^2 GELU / dx^2 of the tanh form, written out from the first derivative:
+    with u = c (x + a x^3), t = tanh u, u' = c (1 + 3 a x^2), u'' = 6 a c x,
+    GELU' = (1 + t)/2 + (x/2)(1 - t^2) u', GELU'' = (1 - t^2)(u' - x t u'^2 + x u''/2)."""
+    x = np.asarray(x, dtype=np.float64)
+    c, a = np.sqrt(2.0 / np.pi), 0.044715
+    t = np.tanh(c * (x + a * x**3))
+    up = c * (1.0 + 3.0 * a * x**2)
+    upp = 6.0 * a * c * x
+    return (1.0 - t**2) * (up - x * t * up**2 + 0.5 * x * upp)
+
+
+GELU_TABLE_LO, GELU_TABLE_HI, GELU_TABLE_H = -3.0, 3.0, 0.01
+
+
+def gelu_table_coeffs():
+    """Second-order table of GELU on [-3, 3] at spacing 0.01 (Sec. 3.3.2): at node
+    x_i = -3 + 0.01 i (i = 0..600) the value, slope and half curvature of the tanh form, each
+    rounded to binary32 (the precision the GPU tables hold). Returns [601, 3]."""
+    n = int(round((GELU_TABLE_HI - GELU_TABLE_LO) / GELU_TABLE_H)) + 1
+    xi = GELU_TABLE_LO + GELU_TABLE_H * np.arange(n)
+    c = np.stack([gelu_tanh(xi), gelu_tanh_grad(xi), 0.5 * gelu_tanh_grad2(xi)], axis=1)
+    return c.astype(np.float32).astype(np.float64)
+
+
+def gelu_table(x, coeffs=None):
+    """The paper's tabulated GELU (Sec. 3.3.2): 0 below -3, x above 3, and in between the
+    second-order expansion g + g' d + (g''/2) d^2 about the node at or below x (d = x - x_i).
+    The paper gives the range, the spacing and the order; expanding about the lower node is
+    this project's reading."""
+    x = np.asarray(x, dtype=np.float64)
+    if coeffs is None:
+        coeffs = gelu_table_coeffs()
+    t = (x - GELU_TABLE_LO) / GELU_TABLE_H
+    i = np.clip(np.floor(t), 0, coeffs.shape[0] - 2).astype(np.int64)
+    d = x - (GELU_TABLE_LO + GELU_TABLE_H * i)
+    c = coeffs[i]
+    y = c[..., 0] + d * (c[..., 1] + d * c[..., 2])
+    return np.where(x <= GELU_TABLE_LO, 0.0, np.where(x >= GELU_TABLE_HI, x, y))
+
+
 def normalise_inputs(net, T, p, Y):
     """Network input rows x [N, n+2] from the cell states."""
     v = np.concatenate([np.asarray(T, dtype=np.float64)[None, :],
@@ -46,15 +87,17 @@ def normalise_inputs(net, T, p, Y):
     return ((v - net.in_mean[:, None]) / net.in_std[:, None]).T
 
 
-def mlp_forward(net, x, return_pre=False):
-    """Plain layer-by-layer forward pass; x [N, K0] -> O [N, n]."""
+def mlp_forward(net, x, return_pre=False, act=None):
+    """Plain layer-by-layer forward pass; x [N, K0] -> O [N, n]. act replaces the hidden
+    activation (default: the tanh-form GELU; gelu_table for the tabulated network)."""
+    act = gelu_tanh if act is None else act
     h = np.asarray(x, dtype=np.float64)
     pre = []
     L = net.n_layers
     for l in range(L):
         z = h @ net.W[l].T + net.b[l][None, :]
         pre.append(z)
-        h = gelu_tanh(z) if l < L - 1 else z
+        h = act(z) if l < L - 1 else z
     return (h, pre) if return_pre else h
 
 

@@ -469,3 +469,28 @@ def test_source_terms_conserve_mass_and_vanish_without_chemistry():
     om0, Tn0, st0 = step.chem_source(mech, net, T, p, Y, net.dt, T_react=0.0)
     ok = st0 == 0
     assert np.abs(om0[:, ok]).max() <= 1e-9 * (rho[ok] / net.dt).max()
+
+
+def test_gelu_second_derivative_vs_finite_differences():
+    x = np.linspace(-6, 6, 241)
+    h = 1e-4
+    fd = (nw.gelu_tanh_grad(x + h) - nw.gelu_tanh_grad(x - h)) / (2 * h)
+    np.testing.assert_allclose(nw.gelu_tanh_grad2(x), fd, atol=1e-7)
+
+
+def test_tabulated_gelu_follows_its_definition_and_error_bound():
+    """The tabulated GELU (Sec. 3.3.2): exactly 0 below -3 and x above 3; inside, within the
+    remainder of a second-order expansion over one interval (largest third derivative times
+    h^3 / 6) plus the binary32 rounding of the coefficients; equal to the tanh form at the
+    nodes."""
+    x = np.linspace(-8, 8, 200001)
+    y = nw.gelu_table(x)
+    assert np.all(y[x <= -3] == 0.0) and np.array_equal(y[x >= 3], x[x >= 3])
+    inside = (x > -3) & (x < 3)
+    g3 = np.abs(np.diff(nw.gelu_tanh_grad2(np.linspace(-3, 3, 60001)))).max() / 1e-4
+    bound = g3 * 0.01**3 / 6 + 4e-7
+    assert np.abs(y[inside] - nw.gelu_tanh(x[inside])).max() <= bound
+    nodes = -3 + 0.01 * np.arange(1, 600)
+    np.testing.assert_allclose(nw.gelu_table(nodes), nw.gelu_tanh(nodes), atol=4e-7)
+    # the jumps at the ends of the table are the paper's approximation: GELU(3) - 3, GELU(-3)
+    assert abs(nw.gelu_tanh(3.0) - 3.0) > 1e-3 and abs(nw.gelu_tanh(-3.0)) > 1e-3
