@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="reacting cells per internal batch")
+    ap.add_argument("--gelu", default="tanh", choices=["tanh", "table"],
+                    help="hidden activation: hardware tanh form, or the paper's tabulation")
     ap.add_argument("--autotune", action="store_true",
                     help="time every tile width per layer (df_autotune) instead of the cost model")
     ap.add_argument("--no-autotune", action="store_true", help=argparse.SUPPRESS)
@@ -289,7 +291,9 @@ def run_ours(args):
     mech, net, T, p, Y = synth.configs.build(args.workload, n_cells=N, field_seed=w.seed + rank)
     prec = {"bf16": df.DF_BF16, "fp32": df.DF_FP32, "fp8": df.DF_FP8_E4M3}[args.precision]
     batch = args.batch or min(N, 1 << 22)
-    st = df.State(mech, net, precision=prec, T_react=w.T_react, device=local, batch_cells=batch)
+    gm = df.DF_GELU_TABLE if args.gelu == "table" else df.DF_GELU_TANH
+    st = df.State(mech, net, precision=prec, T_react=w.T_react, device=local, batch_cells=batch,
+                  gelu_mode=gm)
     tiles = st.autotune(n_rows=min(N, batch)) if args.autotune else st.tiles()
     Td = torch.tensor(T, device=dev)
     pd = torch.tensor(p, device=dev)
@@ -472,6 +476,7 @@ def run_ours(args):
         "config": {"workload": args.workload, "n_cells": N, "n_species": mech.n, "batch_cells": batch,
                    "network": "-".join(str(x) for x in w.widths), "precision": args.precision,
                    "reacting_cells": int(n_act), "T_react_K": w.T_react, "tile_widths": tiles,
+                   "gelu": args.gelu,
                    "l2": "inputs larger than L2 (fields 8*(2+n)*N bytes, activations GBs)"},
         "clocks": clk.summary(),
         "e2e": e2e,

@@ -96,7 +96,19 @@ typedef struct {
   int32_t newton_max_iter;    /* <= 0 selects 50 */
   int32_t device;             /* CUDA device ordinal the state lives on */
   int64_t batch_cells;        /* reacting cells per internal batch; <= 0 selects 2^20 */
+  int32_t gelu_mode;          /* DF_GELU_TANH (0) or DF_GELU_TABLE (1), below */
 } df_options;
+
+/* Hidden-layer activation of the network (a6). Both are the tanh form of Sec. 3.3.2:
+ *   DF_GELU_TANH   0.5 x (1 + tanh(c (x + 0.044715 x^3))), c = sqrt(2/pi), with the hardware
+ *                  tanh approximation on tensor-core paths and tanhf on the FP32 path;
+ *   DF_GELU_TABLE  the paper's tabulation: 0 for x <= -3, x for x >= 3, and in between the
+ *                  second-order expansion about the table node at or below x (nodes every 0.01,
+ *                  value, slope and half curvature in FP32). FP32 and BF16 networks, inference
+ *                  entry points only: df_state_create refuses it for DF_FP8_E4M3, and
+ *                  df_chem_jacobian and the training calls return DF_ERR_UNSUPPORTED. */
+#define DF_GELU_TANH 0
+#define DF_GELU_TABLE 1
 
 /* Creates a state on opt->device: copies the mechanism and network, derives the per-species
  * EoS constants and the low-precision weight copies, allocates scratch for one batch.

@@ -120,15 +120,17 @@ def round_to_bf16(a):
     return np.where(np.isnan(f), np.nan, out)
 
 
-def mlp_forward_rounded(net, x, rnd):
+def mlp_forward_rounded(net, x, rnd, act=None):
     """MLP forward with the input, the weights and every hidden activation passed through
     the rounding function rnd (e.g. round_to_bf16); sums and GELU stay FP64. This is the
-    network as a reduced-precision path stores it, for checking such a path element-wise."""
+    network as a reduced-precision path stores it, for checking such a path element-wise.
+    act replaces the hidden activation as in mlp_forward."""
+    act = gelu_tanh if act is None else act
     h = rnd(np.asarray(x, dtype=np.float64))
     L = net.n_layers
     for l in range(L):
         z = h @ rnd(net.W[l]).T + net.b[l][None, :]
-        h = rnd(gelu_tanh(z)) if l < L - 1 else z
+        h = rnd(act(z)) if l < L - 1 else z
     return h
 
 

@@ -6,5 +6,5 @@ runs in hand-written sm_103a CUDA kernels behind the C ABI of include/df.h (libd
 This package is the thin Python binding of that ABI.
 """
 from ._lib import (DF_BF16, DF_FP8_E4M3, DF_FP32, DF_CELL_NO_ROOT, DF_CELL_NONFINITE,  # noqa: F401
-                   DF_CELL_NOT_CONVERGED, LIB_PATH)
+                   DF_CELL_NOT_CONVERGED, DF_GELU_TABLE, DF_GELU_TANH, LIB_PATH)
 from .api import DFError, MLPEOSFunction, State, version  # noqa: F401

@@ -27,6 +27,7 @@ DF_CELL_NO_ROOT = 2
 DF_CELL_NONFINITE = 4
 
 DF_FP32, DF_BF16, DF_FP8_E4M3 = 0, 1, 2
+DF_GELU_TANH, DF_GELU_TABLE = 0, 1
 
 DF_PARAM_WEIGHTS, DF_PARAM_GRADS, DF_PARAM_ADAM_M, DF_PARAM_ADAM_V = 0, 1, 2, 3
 
@@ -51,7 +52,8 @@ class StepStats(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("T_react", C.c_double), ("newton_tol", C.c_double),
-                ("newton_max_iter", C.c_int32), ("device", C.c_int32), ("batch_cells", C.c_int64)]
+                ("newton_max_iter", C.c_int32), ("device", C.c_int32), ("batch_cells", C.c_int64),
+                ("gelu_mode", C.c_int32)]
 
 
 class Adam(C.Structure):

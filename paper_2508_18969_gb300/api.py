@@ -40,7 +40,7 @@ class State:
 
     def __init__(self, mech, net, precision: int = L.DF_FP32, T_react: float = 600.0,
                  newton_tol: float = 0.0, newton_max_iter: int = 0, device: int = 0,
-                 batch_cells: int = 0):
+                 batch_cells: int = 0, gelu_mode: int = L.DF_GELU_TANH):
         self._lib = L.load()
         self._keep = []
         d = lambda a: self._arr(np.ascontiguousarray(a, dtype=np.float64), C.c_double)
@@ -57,7 +57,7 @@ class State:
         nd = L.MlpDesc(nl, widths, Wp, bp, float(net.lam), d(net.in_mean), d(net.in_std),
                        d(net.out_mean), d(net.out_std), float(net.dt))
         opt = L.Options(int(precision), float(T_react), float(newton_tol), int(newton_max_iter),
-                        int(device), int(batch_cells))
+                        int(device), int(batch_cells), int(gelu_mode))
         h = C.c_void_p()
         rc = self._lib.df_state_create(C.byref(md), C.byref(nd), C.byref(opt), C.byref(h))
         self._keep = []

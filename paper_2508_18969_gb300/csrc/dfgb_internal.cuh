@@ -156,7 +156,26 @@ cudaError_t launch_compact(int64_t n, double T_react, const double* T, int32_t* 
 cudaError_t launch_sgemm_bias_act(const RowMap& rows, int N, int K, const float* A, int64_t lda,
                                   const float* W, int64_t ldw, const float* bias, float* C,
                                   int64_t ldc, bool gelu, int num_sms, cudaStream_t st,
-                                  int mode = 0, float* G = nullptr, int64_t ldg = 0, int ntan = 1);
+                                  int mode = 0, float* G = nullptr, int64_t ldg = 0, int ntan = 1,
+                                  const float4* gelu_table = nullptr);
+
+// The tabulated GELU (DF_GELU_TABLE): 601 nodes x_i = -3 + 0.01 i, each {GELU, GELU',
+// GELU''/2, 0} of the tanh form in FP32; 0 below -3, x above 3.
+constexpr int kGeluTableNodes = 601;
+__host__ __device__ inline float gelu_from_table(float x, const float4* tab) {
+#ifdef __CUDA_ARCH__
+  if (x <= -3.0f) return 0.0f;
+  if (x >= 3.0f) return x;
+  const float tt = (x + 3.0f) * 100.0f;
+  const int i = min((int)tt, kGeluTableNodes - 2);
+  const float d = x - fmaf(0.01f, (float)i, -3.0f);
+  const float4 c = __ldg(tab + i);
+  return fmaf(d, fmaf(d, c.z, c.y), c.x);
+#else
+  (void)x; (void)tab;
+  return 0.0f;
+#endif
+}
 
 // ---- tcgen05 GEMM (mlp_tc.cu) ----
 struct TcLayer {
@@ -177,6 +196,7 @@ struct TcLayer {
   void* gbuf;            // BF16 [cells x ldg] GELU'(z) of the forward pass
   int64_t ldg;
   int ntan;              // tangent rows per cell (mode 2)
+  const float4* gtab = nullptr;  // tabulated GELU (DF_GELU_TABLE) or NULL for the tanh form
   int ksplit = 1;        // split-K (plain mode): split s covers k-blocks [s kbs, (s+1) kbs) and
   int64_t split_rows = 0;  // stores its partial product at output rows + s * split_rows
 };

@@ -27,7 +27,7 @@ template <bool GELU, int MODE>
 __global__ void __launch_bounds__(kThreads, 2) sgemm_kernel(RowMap rows, int N, int K,
     const float* __restrict__ A, int64_t lda, const float* __restrict__ W, int64_t ldw,
     const float* __restrict__ bias, float* __restrict__ C, int64_t ldc, float* __restrict__ G,
-    int64_t ldg, int ntan) {
+    int64_t ldg, int ntan, const float4* __restrict__ gtab) {
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Ws[2][BK][BN];
   const int64_t M = valid_rows(rows);
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kThreads, 2) sgemm_kernel(RowMap rows, int N, 
             C[r * ldc + col] = acc[i][j] * G[(r / ntan) * ldg + col];
           } else {
             const float z = acc[i][j] + bias[col];
-            C[r * ldc + col] = GELU ? gelu_accurate(z) : z;
+            C[r * ldc + col] = GELU ? (gtab ? gelu_from_table(z, gtab) : gelu_accurate(z)) : z;
             if (MODE == 1) G[r * ldg + col] = gelu_grad_accurate(z);
           }
         }
@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(kThreads, 2) sgemm_kernel(RowMap rows, int N, 
 cudaError_t launch_sgemm_bias_act(const RowMap& rows, int N, int K, const float* A, int64_t lda,
                                   const float* W, int64_t ldw, const float* bias, float* C,
                                   int64_t ldc, bool gelu, int num_sms, cudaStream_t st,
-                                  int mode, float* G, int64_t ldg, int ntan) {
+                                  int mode, float* G, int64_t ldg, int ntan,
+                                  const float4* gtab) {
   if (rows.nmax <= 0) return cudaSuccess;
   if (K % BK != 0 || lda % 4 != 0 || ldw % 4 != 0) return cudaErrorInvalidValue;
   const int64_t tiles = ((rows.nmax + BM - 1) / BM) * ((N + BN - 1) / BN);
@@ -120,13 +121,13 @@ cudaError_t launch_sgemm_bias_act(const RowMap& rows, int N, int K, const float*
   const unsigned g = (unsigned)(tiles < cap ? tiles : cap);
   if (ntan < 1) ntan = 1;
   if (mode == 2)
-    sgemm_kernel<false, 2><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc, G, ldg, ntan);
+    sgemm_kernel<false, 2><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc, G, ldg, ntan, gtab);
   else if (mode == 1)
-    sgemm_kernel<true, 1><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc, G, ldg, ntan);
+    sgemm_kernel<true, 1><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc, G, ldg, ntan, gtab);
   else if (gelu)
-    sgemm_kernel<true, 0><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc, G, ldg, ntan);
+    sgemm_kernel<true, 0><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc, G, ldg, ntan, gtab);
   else
-    sgemm_kernel<false, 0><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc, G, ldg, ntan);
+    sgemm_kernel<false, 0><<<g, kThreads, 0, st>>>(rows, N, K, A, lda, W, ldw, bias, C, ldc, G, ldg, ntan, gtab);
   return cudaGetLastError();
 }
 

@@ -55,6 +55,7 @@ struct TcArgs {
   void* gbuf;      // GELU'(z): written (kModeStoreG) or read as the row-group scale (kModeRowG)
   int64_t ldg;
   int ntan;        // rows per group for kModeRowG
+  const float4* gtab;  // tabulated GELU, or NULL for the tanh form
   int ksplit;      // split-K: partial products over ksplit ranges of k-blocks
   int64_t split_rows;  // output row offset between the partial products of two splits
 };
@@ -62,6 +63,10 @@ struct TcArgs {
 // Epilogue modes: plain layer; layer that also stores GELU'(z) (forward pass of the Jacobian);
 // tangent layer out[r, c] = acc[r, c] * G[r / ntan, c] (no bias, no activation).
 constexpr int kModePlain = 0, kModeStoreG = 1, kModeRowG = 2;
+
+// Epilogue activation: none (read-out, tangent and gradient GEMMs), the tanh form with the
+// hardware tanh, or the paper's table (compiled for BF16 hidden layers only).
+constexpr int kActNone = 0, kActTanh = 1, kActTable = 2;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -343,7 +348,7 @@ __device__ __forceinline__ void store_chunk(const float (&v)[32], const CUtensor
 
 // One 32-column chunk of the epilogue: per-channel scale, bias, GELU (or the row-group scale
 // of a tangent layer), then quantise and store; kModeStoreG also stores GELU'(z).
-template <int OUTK, bool GELU, bool SCALE, int MODE>
+template <int OUTK, int ACT, bool SCALE, int MODE>
 __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const TcArgs& g,
                                                const CUtensorMap* tmO, const CUtensorMap* tmG,
                                                int64_t M, int64_t m0, int col0, uint8_t* stg,
@@ -385,9 +390,12 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const Tc
       z0 = __fadd2_rn(z0, make_float2(b.x, b.y));
       z1 = __fadd2_rn(z1, make_float2(b.z, b.w));
     }
-    if (GELU) {
+    if constexpr (ACT == kActTanh) {
       z0 = gelu_fast2(z0);
       z1 = gelu_fast2(z1);
+    } else if constexpr (ACT == kActTable) {
+      z0 = make_float2(gelu_from_table(z0.x, g.gtab), gelu_from_table(z0.y, g.gtab));
+      z1 = make_float2(gelu_from_table(z1.x, g.gtab), gelu_from_table(z1.y, g.gtab));
     }
     v[4 * u] = z0.x; v[4 * u + 1] = z0.y; v[4 * u + 2] = z1.x; v[4 * u + 3] = z1.y;
   }
@@ -407,7 +415,7 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const Tc
   }
 }
 
-template <bool FP8, int BN, int OUTK, bool GELU, bool SCALE, int MODE>
+template <bool FP8, int BN, int OUTK, int ACT, bool SCALE, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
     const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmG, TcArgs g) {
@@ -556,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
           tmem_ld32(tbase + c0, r0);
           tmem_wait(r0);
           if (n0 + c0 < g.N)
-            epilogue_chunk<OUTK, GELU, SCALE, MODE>(r0, g, &tmO, &tmG, M, m0, n0 + c0, stg, buf, lane);
+            epilogue_chunk<OUTK, ACT, SCALE, MODE>(r0, g, &tmO, &tmG, M, m0, n0 + c0, stg, buf, lane);
         }
         c0 = BN;
       }
@@ -566,12 +574,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
         const int c1 = c0 + kChunkStride;
         if (c1 < BN) tmem_ld32(tbase + c1, r1);
         if (n0 + c0 < g.N)
-          epilogue_chunk<OUTK, GELU, SCALE, MODE>(r0, g, &tmO, &tmG, M, m0, n0 + c0, stg, buf, lane);
+          epilogue_chunk<OUTK, ACT, SCALE, MODE>(r0, g, &tmO, &tmG, M, m0, n0 + c0, stg, buf, lane);
         if (c1 >= BN) break;
         tmem_wait(r1);
         if (c1 + kChunkStride < BN) tmem_ld32(tbase + c1 + kChunkStride, r0);
         if (n0 + c1 < g.N)
-          epilogue_chunk<OUTK, GELU, SCALE, MODE>(r1, g, &tmO, &tmG, M, m0, n0 + c1, stg, buf, lane);
+          epilogue_chunk<OUTK, ACT, SCALE, MODE>(r1, g, &tmO, &tmG, M, m0, n0 + c1, stg, buf, lane);
       }
       tc_fence_before();
       __syncwarp();
@@ -610,7 +618,7 @@ EncodeTiledFn encode_fn() {
 }
 
 // Opts the kernel instance into its dynamic shared memory, once per device.
-template <bool FP8, int BN, int OUTK, bool GELU, int MODE>
+template <bool FP8, int BN, int OUTK, int ACT, int MODE>
 cudaError_t tc_attr() {
   static bool attr_done[64] = {false};
   int dev = 0;
@@ -618,7 +626,7 @@ cudaError_t tc_attr() {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_done[dev]) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<FP8, BN, OUTK, GELU, FP8, MODE>,
+    e = cudaFuncSetAttribute(tc_gemm_kernel<FP8, BN, OUTK, ACT, FP8, MODE>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN, OUTK>::kSmemBytes);
     if (e != cudaSuccess) return e;
     attr_done[dev] = true;
@@ -626,12 +634,12 @@ cudaError_t tc_attr() {
   return cudaSuccess;
 }
 
-template <bool FP8, int BN, int OUTK, bool GELU, int MODE = kModePlain>
+template <bool FP8, int BN, int OUTK, int ACT, int MODE = kModePlain>
 cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream_t st) {
   using C = Cfg<BN, OUTK>;
   constexpr bool SCALE = FP8;
-  auto kern = tc_gemm_kernel<FP8, BN, OUTK, GELU, SCALE, MODE>;
-  cudaError_t e0 = tc_attr<FP8, BN, OUTK, GELU, MODE>();
+  auto kern = tc_gemm_kernel<FP8, BN, OUTK, ACT, SCALE, MODE>;
+  cudaError_t e0 = tc_attr<FP8, BN, OUTK, ACT, MODE>();
   if (e0 != cudaSuccess) return e0;
   if (num_sms <= 0) return cudaSuccess;  // attribute set-up only
   const int64_t tiles = ((a.rows.nmax + BM - 1) / BM) * ((L.N + BN - 1) / BN) * a.ksplit;
@@ -650,38 +658,49 @@ cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStrea
     if (FP8 || L.out_kind != kXBF16) return cudaErrorInvalidValue;
     if (L.mode == kModeStoreG) {
       switch (L.BN) {
-        case 64: return launch_bn<false, 64, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
-        case 128: return launch_bn<false, 128, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
-        case 160: return launch_bn<false, 160, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
-        case 224: return launch_bn<false, 224, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
-        case 256: return launch_bn<false, 256, kXBF16, true, kModeStoreG>(L, a, num_sms, st);
+        case 64: return launch_bn<false, 64, kXBF16, kActTanh, kModeStoreG>(L, a, num_sms, st);
+        case 128: return launch_bn<false, 128, kXBF16, kActTanh, kModeStoreG>(L, a, num_sms, st);
+        case 160: return launch_bn<false, 160, kXBF16, kActTanh, kModeStoreG>(L, a, num_sms, st);
+        case 224: return launch_bn<false, 224, kXBF16, kActTanh, kModeStoreG>(L, a, num_sms, st);
+        case 256: return launch_bn<false, 256, kXBF16, kActTanh, kModeStoreG>(L, a, num_sms, st);
         default: return cudaErrorInvalidValue;
       }
     }
     switch (L.BN) {
-      case 64: return launch_bn<false, 64, kXBF16, false, kModeRowG>(L, a, num_sms, st);
-      case 128: return launch_bn<false, 128, kXBF16, false, kModeRowG>(L, a, num_sms, st);
-      case 160: return launch_bn<false, 160, kXBF16, false, kModeRowG>(L, a, num_sms, st);
-      case 224: return launch_bn<false, 224, kXBF16, false, kModeRowG>(L, a, num_sms, st);
-      case 256: return launch_bn<false, 256, kXBF16, false, kModeRowG>(L, a, num_sms, st);
+      case 64: return launch_bn<false, 64, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
+      case 128: return launch_bn<false, 128, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
+      case 160: return launch_bn<false, 160, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
+      case 224: return launch_bn<false, 224, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
+      case 256: return launch_bn<false, 256, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (L.gelu && L.gtab) {
+    if (FP8 || L.out_kind != kXBF16) return cudaErrorInvalidValue;
+    switch (L.BN) {
+      case 64: return launch_bn<false, 64, kXBF16, kActTable>(L, a, num_sms, st);
+      case 128: return launch_bn<false, 128, kXBF16, kActTable>(L, a, num_sms, st);
+      case 160: return launch_bn<false, 160, kXBF16, kActTable>(L, a, num_sms, st);
+      case 224: return launch_bn<false, 224, kXBF16, kActTable>(L, a, num_sms, st);
+      case 256: return launch_bn<false, 256, kXBF16, kActTable>(L, a, num_sms, st);
       default: return cudaErrorInvalidValue;
     }
   }
   if (L.gelu) {
     if (L.out_kind != HID) return cudaErrorInvalidValue;
     switch (L.BN) {
-      case 64: return launch_bn<FP8, 64, HID, true>(L, a, num_sms, st);
-      case 128: return launch_bn<FP8, 128, HID, true>(L, a, num_sms, st);
-      case 160: return launch_bn<FP8, 160, HID, true>(L, a, num_sms, st);
-      case 224: return launch_bn<FP8, 224, HID, true>(L, a, num_sms, st);
-      case 256: return launch_bn<FP8, 256, HID, true>(L, a, num_sms, st);
+      case 64: return launch_bn<FP8, 64, HID, kActTanh>(L, a, num_sms, st);
+      case 128: return launch_bn<FP8, 128, HID, kActTanh>(L, a, num_sms, st);
+      case 160: return launch_bn<FP8, 160, HID, kActTanh>(L, a, num_sms, st);
+      case 224: return launch_bn<FP8, 224, HID, kActTanh>(L, a, num_sms, st);
+      case 256: return launch_bn<FP8, 256, HID, kActTanh>(L, a, num_sms, st);
       default: return cudaErrorInvalidValue;
     }
   }
   if (L.out_kind != kXF32) return cudaErrorInvalidValue;
   switch (L.BN) {
-    case 32: return launch_bn<FP8, 32, kXF32, false>(L, a, num_sms, st);
-    case 64: return launch_bn<FP8, 64, kXF32, false>(L, a, num_sms, st);
+    case 32: return launch_bn<FP8, 32, kXF32, kActNone>(L, a, num_sms, st);
+    case 64: return launch_bn<FP8, 64, kXF32, kActNone>(L, a, num_sms, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -800,6 +819,7 @@ cudaError_t launch_tc_gemm(const TcLayer& L, const RowMap& rows, int num_sms, in
   a.gbuf = L.gbuf;
   a.ldg = L.ldg;
   a.ntan = L.ntan > 0 ? L.ntan : 1;
+  a.gtab = L.gtab;
   a.ksplit = L.ksplit > 0 ? L.ksplit : 1;
   a.split_rows = L.split_rows;
   return L.elem_bytes == 1 ? launch_fmt<true>(L, a, num_sms, st)

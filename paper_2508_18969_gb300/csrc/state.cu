@@ -115,7 +115,7 @@ void free_state(df_state* s) {
   s->jac = nullptr;
   free_trn(s->trn);
   s->trn = nullptr;
-  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_Kr2); f(s->d_kfs); f(s->d_kfr); f(s->d_lntab); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
+  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_Kr2); f(s->d_kfs); f(s->d_kfr); f(s->d_lntab); f(s->d_gtab); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
   for (auto p : s->W32) f(p);
   for (auto p : s->bias) f(p);
   for (auto p : s->Wlp) f(p);
@@ -158,7 +158,8 @@ df_status run_mlp(df_state* s, const RowMap& rm, cudaStream_t st) {
       float* Cout = last ? s->O : (float*)s->act[l & 1];
       const int64_t ldc = last ? s->ldo : s->act_ld[l & 1];
       e = launch_sgemm_bias_act(rm, s->widths[l + 1], s->Kp8[l], A, lda, s->W32[l], s->Kp8[l],
-                                s->bias[l], Cout, ldc, !last, s->num_sms, st);
+                                s->bias[l], Cout, ldc, !last, s->num_sms, st, 0, nullptr, 0, 1,
+                                last ? nullptr : s->d_gtab);
     } else {
       e = launch_tc_gemm(s->tcl[l], rm, s->num_sms, s->d_err, st);
     }
@@ -237,6 +238,10 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
   if (!(mlp->dt > 0.0)) return fail(nullptr, DF_ERR_INVALID_ARG, "dt must be > 0");
   if (opt->precision < DF_FP32 || opt->precision > DF_FP8_E4M3)
     return fail(nullptr, DF_ERR_INVALID_ARG, "unknown precision");
+  if (opt->gelu_mode != DF_GELU_TANH && opt->gelu_mode != DF_GELU_TABLE)
+    return fail(nullptr, DF_ERR_INVALID_ARG, "unknown gelu_mode");
+  if (opt->gelu_mode == DF_GELU_TABLE && opt->precision == DF_FP8_E4M3)
+    return fail(nullptr, DF_ERR_UNSUPPORTED, "the tabulated GELU runs on FP32 and BF16 networks");
   for (int k = 0; k < n; ++k)
     if (!(mech->W[k] > 0) || !(mech->Tc[k] > 0) || !(mech->pc[k] > 0))
       return fail(nullptr, DF_ERR_INVALID_ARG, "W, Tc, pc must be positive");
@@ -259,6 +264,7 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
   s->L = L;
   s->widths.assign(mlp->widths, mlp->widths + L + 1);
   s->precision = opt->precision;
+  s->gelu_mode = opt->gelu_mode;
   s->T_react = opt->T_react;
   s->lambda = mlp->lambda;
   s->dt = mlp->dt;
@@ -350,6 +356,22 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
       kfs[(size_t)i * n + j] = (float)(k * q[1] * q[0]);
       kfr[(size_t)i * n + j] = (float)(k * q[2] * q[0]);
     }
+  if (s->gelu_mode == DF_GELU_TABLE) {
+    // value, slope and half curvature of the tanh-form GELU at x_i = -3 + 0.01 i
+    std::vector<float4> gt(kGeluTableNodes);
+    const double c = 0.79788456080286535588, a = 0.044715;  // sqrt(2 / pi)
+    for (int i = 0; i < kGeluTableNodes; ++i) {
+      const double x = -3.0 + 0.01 * i;
+      const double u = c * (x + a * x * x * x), th = std::tanh(u);
+      const double up = c * (1.0 + 3.0 * a * x * x), upp = 6.0 * a * c * x;
+      const double g0 = 0.5 * x * (1.0 + th);
+      const double g1 = 0.5 * (1.0 + th) + 0.5 * x * (1.0 - th * th) * up;
+      const double g2 = (1.0 - th * th) * (up - x * th * up * up + 0.5 * x * upp);
+      gt[i] = make_float4((float)g0, (float)g1, (float)(0.5 * g2), 0.0f);
+    }
+    CK(dalloc(&s->d_gtab, gt.size()), "gelu table");
+    CK(cudaMemcpy(s->d_gtab, gt.data(), sizeof(float4) * gt.size(), cudaMemcpyHostToDevice), "copy");
+  }
   std::vector<double> lntab(256);
   for (int j = 0; j < 128; ++j) {
     const double c = 1.0 + (j + 0.5) / 128.0;
@@ -499,6 +521,7 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
       T.ldo = last ? s->ldo : s->act_ld[l & 1];
       T.out_kind = last ? kXF32 : xk;
       T.gelu = !last;
+      T.gtab = last ? nullptr : s->d_gtab;
       T.out_scale = (s->precision == DF_FP8_E4M3 && !last) ? s->act_scale[l + 1] : 1.0f;
       T.elem_bytes = (int)eb;
       const void* Abase = (l == 0) ? s->x : s->act[(l - 1) & 1];
@@ -842,6 +865,8 @@ df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const 
   if (rc != DF_OK || n_cells == 0) return rc;
   if (!J_dY) return fail(s, DF_ERR_INVALID_ARG, "J_dY is NULL");
   if (s->L < 2) return fail(s, DF_ERR_UNSUPPORTED, "the Jacobian needs at least one hidden layer");
+  if (s->gelu_mode != DF_GELU_TANH)
+    return fail(s, DF_ERR_UNSUPPORTED, "the Jacobian needs the tanh-form GELU (DF_GELU_TANH)");
   DeviceGuard guard(s->device);
   if (s->jac && s->jac->wver != s->wver) {  // training changed the weights
     cudaDeviceSynchronize();

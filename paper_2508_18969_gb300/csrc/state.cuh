@@ -56,6 +56,8 @@ struct df_state {
   float* d_kfs = nullptr;                // FP32 k_ij tables (EosParams)
   float* d_kfr = nullptr;
   double* d_lntab = nullptr;             // log table (EosParams)
+  int gelu_mode = 0;                     // DF_GELU_TANH or DF_GELU_TABLE
+  float4* d_gtab = nullptr;              // tabulated GELU (DF_GELU_TABLE)
   int* d_err = nullptr;                  // kernel error word
   int64_t* d_count = nullptr;            // reacting cells of the last step
   int64_t* d_flagged = nullptr;          // flagged cells of the last step

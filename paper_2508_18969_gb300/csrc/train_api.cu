@@ -68,7 +68,9 @@ void free_trn(Trn* t) {
 
 namespace {
 
-bool trains(const df_state* s) { return s->precision == DF_FP32 || s->precision == DF_BF16; }
+bool trains(const df_state* s) {
+  return (s->precision == DF_FP32 || s->precision == DF_BF16) && s->gelu_mode == DF_GELU_TANH;
+}
 
 constexpr int kMaxSplit = 16;   // split-K of the weight-gradient GEMMs
 
@@ -114,7 +116,7 @@ cudaError_t publish_all(df_state* s, cudaStream_t st) {
 // Masters from the state's host weights, zero moments, transposed working copies.
 df_status ensure_params(df_state* s) {
   if (s->trn) return DF_OK;
-  if (!trains(s)) return fail(s, DF_ERR_UNSUPPORTED, "training needs a DF_FP32 or DF_BF16 state");
+  if (!trains(s)) return fail(s, DF_ERR_UNSUPPORTED, "training needs a DF_FP32 or DF_BF16 state with DF_GELU_TANH");
   Trn* t = new Trn();
   s->trn = t;
   const bool bf16 = s->precision == DF_BF16;

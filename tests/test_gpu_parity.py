@@ -409,3 +409,56 @@ def test_autotune_is_a_no_op_for_fp32(df):
     mech, net, T, p, Y = synth.configs.build("small-fp32-4k", n_cells=64)
     st = df.State(mech, net, precision=df.DF_FP32)
     assert st.autotune() == [0] * net.n_layers
+
+
+# ---------------------------------------------------------------- tabulated GELU (Sec. 3.3.2)
+
+@pytest.mark.parametrize("name,N", WORKLOADS[:2])
+def test_tabulated_gelu_mlp_fp32_vs_oracle(df, name, N):
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    x = onw.normalise_inputs(net, T, p, Y).astype(np.float32).astype(np.float64)
+    st = df.State(mech, net, precision=df.DF_FP32, batch_cells=1024, gelu_mode=df.DF_GELU_TABLE)
+    O = host(st.mlp_forward(dev(x.astype(np.float32))))
+    torch.cuda.synchronize()
+    Oo = onw.mlp_forward(net, x, act=onw.gelu_table)
+    # as the tanh-form FP32 path; the table is evaluated in FP32 (an interval index may fall
+    # on the neighbouring node, which moves the value by at most the expansion remainder)
+    np.testing.assert_allclose(O, Oo, atol=1e-4, rtol=0)
+    # the tabulation is a different activation: against the tanh-form network the outputs move
+    Ot = onw.mlp_forward(net, x)
+    print(f"{name}: max |O_table - O_tanh| (FP64 oracle) = {np.abs(Oo - Ot).max():.3e}")
+
+
+@pytest.mark.parametrize("name,N", WORKLOADS[:2])
+def test_tabulated_gelu_mlp_bf16_vs_rounded_oracle(df, name, N):
+    mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
+    x = onw.normalise_inputs(net, T, p, Y).astype(np.float32).astype(np.float64)
+    st = df.State(mech, net, precision=df.DF_BF16, batch_cells=512, gelu_mode=df.DF_GELU_TABLE)
+    O = host(st.mlp_forward(dev(x.astype(np.float32))))
+    torch.cuda.synchronize()
+    Oq = onw.mlp_forward_rounded(net, x, onw.round_to_bf16, act=onw.gelu_table)
+    err = np.abs(O - Oq)
+    assert err.max() <= 2e-2 and err.mean() <= 1e-3, (err.max(), err.mean())
+
+
+def test_tabulated_gelu_step_accuracy_and_unsupported_calls(df):
+    mech, net, T, p, Y = synth.configs.build("layer1d-30sp-1m", n_cells=6000)
+    res = {}
+    for mode in (df.DF_GELU_TANH, df.DF_GELU_TABLE):
+        st = df.State(mech, net, precision=df.DF_FP32, T_react=0.0, gelu_mode=mode)
+        Td, Yd = dev(T), dev(Y)
+        st.chem_step(Td, dev(p), Yd)
+        torch.cuda.synchronize()
+        res[mode] = (host(Td), host(Yd))
+    To, Yo, _ = ostep.chem_step(mech, net, T, p, Y, net.dt, T_react=0.0)
+    dtab = np.abs(res[df.DF_GELU_TABLE][1] - Yo).max()
+    dtanh = np.abs(res[df.DF_GELU_TANH][1] - Yo).max()
+    print(f"max |dY| vs the FP64 tanh-form oracle: tanh {dtanh:.3e}, table {dtab:.3e}")
+    assert dtanh <= 1e-6 and dtab <= 1e-4
+    st = df.State(mech, net, precision=df.DF_BF16, gelu_mode=df.DF_GELU_TABLE)
+    with pytest.raises(df.DFError) as e:
+        st.chem_jacobian(dev(T[:10]), dev(p[:10]), dev(Y[:, :10]))
+    assert e.value.code == df._lib.DF_ERR_UNSUPPORTED
+    with pytest.raises(df.DFError) as e:
+        st.train_step(dev(T[:10]), dev(p[:10]), dev(Y[:, :10]), dev(Y[:, :10]))
+    assert e.value.code == df._lib.DF_ERR_UNSUPPORTED
