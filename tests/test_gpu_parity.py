@@ -462,3 +462,37 @@ def test_tabulated_gelu_step_accuracy_and_unsupported_calls(df):
     with pytest.raises(df.DFError) as e:
         st.train_step(dev(T[:10]), dev(p[:10]), dev(Y[:, :10]), dev(Y[:, :10]))
     assert e.value.code == df._lib.DF_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------- species-count extremes
+
+def _extreme_case(n, N, seed):
+    """n species (1: a hand-made pure fluid; otherwise a generated mechanism), a random
+    network n+2 -> 48 -> 32 -> n, uniform states T in [300, 2500] K, p in [5, 20] MPa and
+    mass fractions on the simplex."""
+    from types import SimpleNamespace
+    if n == 1:
+        mech = SimpleNamespace(n=1, W=np.array([0.032]), Tc=np.array([154.6]), pc=np.array([5.04e6]),
+                               omega=np.array([0.022]), kij=np.zeros((1, 1)),
+                               nasa=np.array([[3.5, 5e-4, -1e-8, 0.0, 0.0, -1050.0, 4.0]]))
+    else:
+        mech = synth.mechanism.make_mechanism(n, 1 if n < 6 else 200, 41)
+    net = synth.network.make_network([n + 2, 48, 32, n], n, seed)
+    s = synth.Stream(seed, "extreme-states")
+    T = s.uniform(N, 300.0, 2500.0)
+    p = s.uniform(N, 5e6, 20e6)
+    Y = s.uniform(n * N, 0.0, 1.0).reshape(n, N) + 1e-6
+    return mech, net, T, p, Y / Y.sum(axis=0, keepdims=True)
+
+
+@pytest.mark.parametrize("n", [1, 5, 32])
+def test_species_count_extremes(df, n):
+    mech, net, T, p, Y = _extreme_case(n, 3001, 40 + n)
+    st = df.State(mech, net, precision=df.DF_FP32, T_react=0.0, batch_cells=1024)
+    rho, h, cp, Z = (host(a) for a in st.real_fluid_props(dev(T), dev(p), dev(Y)))
+    o = ope.state(mech, T, p, Y)
+    np.testing.assert_allclose(Z, o["Z"], rtol=EOS_RTOL)
+    assert np.all(np.abs(h - o["h"]) <= EOS_RTOL * (np.abs(o["h"]) + _h_scale(mech, T, p, Y)))
+    np.testing.assert_allclose(rho, o["rho"], rtol=EOS_RTOL)
+    _step_check(df, mech, net, T, p, Y, df.DF_FP32, 0.0, 1024, 1e-6)
+    _step_check(df, mech, net, T, p, Y, df.DF_BF16, 0.0, 1024, 1e-4)
