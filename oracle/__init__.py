@@ -17,6 +17,7 @@ What the paper fixes and what it leaves open:
 Modules: thermo (NASA-7), pr_eos (Peng-Robinson), network (Box-Cox, normalisation, GELU,
 MLP, its Jacobian), step (active-cell list, reaction step, real-fluid properties, T from h,
 finite-difference Jacobian of the step), truth (the stiff-chemistry ground truth the network
-stands in for: C, BDF, oracle/truth.c).
+stands in for: C, BDF, oracle/truth.c), solver (the sparse kernels of Sec. 3.2: LDU matrix,
+SpMV, block Gauss-Seidel, finite-volume Laplacian).
 """
-from . import thermo, pr_eos, network, step  # noqa: F401
+from . import thermo, pr_eos, network, step, solver  # noqa: F401

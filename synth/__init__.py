@@ -6,4 +6,4 @@ CUDA side of the tests and the bench take their inputs from here.
 from .rng import Stream
 from .mechanism import Mechanism, make_mechanism
 from .network import Network, make_network
-from . import fields, configs
+from . import fields, configs, mesh
