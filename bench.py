@@ -169,9 +169,9 @@ def weak_scaling_value(world, cells_per_rank, ms_max):
 # only for the kernel source the counters were taken on (SHA-256 prefix of the file): once the
 # kernel changes, the bench reports traffic as null until it is measured again.
 MEASURED_TRAFFIC = {
-    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "345b952374ddfe4d", 3158.0),
-    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "345b952374ddfe4d", 4751.0),
-    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 296.0),
+    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e08b143876a7d2e", 3158.0),
+    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e08b143876a7d2e", 4751.0),
+    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 297.0),
     ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 549.0),
 }
 
