@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="step", choices=["step", "train", "jacobian"],
+    ap.add_argument("--mode", default="step", choices=["step", "train", "jacobian", "solver"],
                     help="step: the reaction step (headline); train: Adam steps on training "
                          "states; jacobian: the step's Jacobian")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp8"])
@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="reacting cells per internal batch")
     ap.add_argument("--gelu", default="tanh", choices=["tanh", "table"],
                     help="hidden activation: hardware tanh form, or the paper's tabulation")
+    ap.add_argument("--solver-arith", default="fp64", choices=["fp64", "f2"],
+                    help="solver mode: FP64 FMAs or double-float pairs on the FP32 pipes")
+    ap.add_argument("--part-cells", type=int, default=0,
+                    help="solver mode: cells per block row (default: the workload's)")
     ap.add_argument("--autotune", action="store_true",
                     help="time every tile width per layer (df_autotune) instead of the cost model")
     ap.add_argument("--no-autotune", action="store_true", help=argparse.SUPPRESS)
@@ -249,6 +253,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.mode == "solver":
+        return run_reference_solver(args, world)
     import synth
     from oracle import step as ostep
     w = synth.configs.WORKLOADS[args.workload]
@@ -272,6 +278,33 @@ def run_reference(args):
                              "cores": len(os.sched_getaffinity(0)),
                              "sample": f"{S} cells of the workload's field recipe, evenly spread, per step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_solver(args, world):
+    """The FP64 oracle's sparse-solver step on a 64^3 instance of the mesh recipe per step."""
+    name = args.workload if args.workload in SOLVER_WORKLOADS else "mesh-8m"
+    sweeps = SOLVER_WORKLOADS[name]["sweeps"]
+    n, own, nei, pp, g, s, b = solver_problem("mesh-256k")
+    for _ in range(args.warmup):
+        solver_oracle_step(n, own, nei, pp, g, s, b, sweeps)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solver_oracle_step(n, own, nei, pp, g, s, b, sweeps)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    v = n / dt
+    unit = "cells/s"
+    line = {"impl": "reference",
+            "metric": "sparse-solver step cells/s (assembly, conversion, block Gauss-Seidel, residual)",
+            "value": v, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "sample_cells_per_step": n},
+            "cpu_baseline": {"value": v, "unit": unit, "kind": "oracle",
+                             "cores": len(os.sched_getaffinity(0)),
+                             "sample": f"the mesh recipe at 64^3 ({n} cells) per step"},
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -636,6 +669,187 @@ def run_jacobian(args):
     return 0
 
 
+# Sparse-solver workload (Sec. 3.2): a seeded 256 x 256 x 128 hexahedral mesh with random
+# extra diagonal faces, randomly numbered, decomposed into block rows of 512 cells.
+SOLVER_WORKLOADS = {
+    "mesh-8m": dict(dims=(256, 256, 128), part_cells=512, seed=7, p_extra=0.15, sweeps=2),
+    "mesh-2m": dict(dims=(128, 128, 128), part_cells=512, seed=7, p_extra=0.15, sweeps=2),
+    "mesh-256k": dict(dims=(64, 64, 64), part_cells=512, seed=7, p_extra=0.15, sweeps=2),
+}
+
+
+def solver_problem(name, seed_offset=0, part_cells=0):
+    """Mesh of the named workload, decomposed and renumbered by the library's host code:
+    (n, owner, neighbour, part_ptr, face coefficients, cell sources, right-hand side)."""
+    import synth
+    from paper_2508_18969_gb300 import solver as sol
+    w = SOLVER_WORKLOADS[name]
+    m = synth.mesh.grid_mesh(*w["dims"], seed=w["seed"] + seed_offset, p_extra=w["p_extra"])
+    parts = max(1, m.n_cells // (part_cells or w["part_cells"]))
+    new_of_old, pp = sol.mesh_decompose(m.n_cells, m.owner, m.neighbour, parts)
+    own, nei, face_old, _ = sol.mesh_renumber(m.n_cells, m.owner, m.neighbour, new_of_old)
+    s = np.empty(m.n_cells)
+    s[new_of_old] = m.cell_source
+    b = synth.mesh.rhs_vector(m.n_cells, seed=w["seed"] + seed_offset + 4)
+    return m.n_cells, own, nei, pp, np.ascontiguousarray(m.face_coeff[face_old]), s, b
+
+
+def solver_bytes(info, sweeps):
+    """Algorithmic bytes per launch of each sparse kernel: every array of the block format,
+    every vector and every LDU array moved once (the halo values once per halo cell)."""
+    n, nf, nnz_o, nh = info["n_cells"], info["n_faces"], info["nnz_offblock"], info["n_halo"]
+    nnz_b = 2 * nf - nnz_o
+    return {
+        "laplacian": 32 * nf + 20 * n,
+        "convert": 40 * nf + 24 * n,
+        "spmv": 32 * n + 10 * nnz_b + 12 * nnz_o,
+        "residual": 40 * n + 10 * nnz_b + 12 * nnz_o,
+        "gauss_seidel": 41 * n + 10 * nnz_b + 12 * nnz_o + 16 * nh,
+    }
+
+
+def solver_oracle_step(n, own, nei, pp, g, s, b, sweeps):
+    """One solver step of the FP64 oracle: assemble, build the matrix, sweep, residual."""
+    from oracle import solver as osol
+    lo, d, up = osol.fv_laplacian(n, own, nei, g, s)
+    A = osol.ldu_matrix(n, own, nei, lo, d, up)
+    x = osol.gauss_seidel(A, b, np.zeros(n), pp, sweeps)
+    return x, osol.residual(A, b, x)
+
+
+def solver_cpu_leg(sweeps, name="mesh-2m"):
+    import time
+    n, own, nei, pp, g, s, b = solver_problem(name)
+    t0 = time.perf_counter()
+    solver_oracle_step(n, own, nei, pp, g, s, b, sweeps)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "cells/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"the same recipe at {name} ({n} cells), one oracle step (scipy sparse; BLAS "
+                      "threads = default)", "seconds": dt}
+
+
+def run_solver(args):
+    """Sparse-solver step throughput (Sec. 3.2) on one GPU: face-to-cell assembly of the
+    finite-volume Laplacian, LDU -> block conversion, block Gauss-Seidel sweeps from x = 0 and
+    the residual, per step. Cells/s = cells / step time."""
+    import torch
+    import __graft_entry__ as g_
+    g_.build()
+    from paper_2508_18969_gb300 import solver as sol
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name = args.workload if args.workload in SOLVER_WORKLOADS else "mesh-8m"
+    sweeps = SOLVER_WORKLOADS[name]["sweeps"]
+    part_cells = args.part_cells or SOLVER_WORKLOADS[name]["part_cells"]
+    n, own, nei, pp, gf, sc, b = solver_problem(name, seed_offset=rank, part_cells=part_cells)
+    arith = 1 if args.solver_arith == "f2" else 0
+    S = sol.Solver(n, own, nei, pp, device=local, arithmetic=arith)
+    info = S.info()
+    f64 = dict(dtype=torch.float64, device=dev)
+    gd, sd, bd = (torch.tensor(a, **f64) for a in (gf, sc, b))
+    lo, dg, up = torch.empty(own.size, **f64), torch.empty(n, **f64), torch.empty(own.size, **f64)
+    x, r = torch.zeros(n, **f64), torch.empty(n, **f64)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        S.fv_laplacian(gd, sd, out=(lo, dg, up))
+        S.convert(lo, dg, up)
+        x.zero_()
+        S.gauss_seidel(bd, x, sweeps)
+        S.residual(bd, x, r)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = max_over_ranks(world, e0.elapsed_time(e1) / args.steps, local)
+    # per kernel: each launched alone, back to back, CUDA events on the launch stream
+    reps = 20
+    kern = {}
+    y = torch.empty(n, **f64)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        z.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(z) / reps
+
+    kern["laplacian"] = timed(lambda: S.fv_laplacian(gd, sd, out=(lo, dg, up)))
+    kern["convert"] = timed(lambda: S.convert(lo, dg, up))
+    kern["spmv"] = timed(lambda: S.spmv(x, y))
+    kern["residual"] = timed(lambda: S.residual(bd, x, r))
+    kern["gauss_seidel"] = timed(lambda: S.gauss_seidel(bd, x, 1))   # halo gather + one sweep
+    resid = float(torch.linalg.vector_norm(r).item()) / float(np.linalg.norm(b))
+    if rank != 0:
+        return 0
+    pk, pk_src = peaks()
+    by = solver_bytes(info, sweeps)
+    fam = {k: {"ms": v, "GB/s": by[k] / (v * 1e-3) / 1e9,
+               "frac": by[k] / (v * 1e-3) / 1e9 / pk["hbm_gbs"]} for k, v in kern.items()}
+    gs = fam["gauss_seidel"]
+    e2e = None
+    if not args.no_e2e:
+        hp = {k: torch.tensor(a, dtype=torch.float64).pin_memory() for k, a in
+              (("g", gf), ("s", sc), ("b", b))}
+        xh = torch.empty(n, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            gd.copy_(hp["g"], non_blocking=True)
+            sd.copy_(hp["s"], non_blocking=True)
+            bd.copy_(hp["b"], non_blocking=True)
+            step()
+            xh.copy_(x, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        z.record(stream)
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(z) / args.steps
+        e2e = {"value": n / (ems * 1e-3), "unit": "cells/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": 8 * (own.size + 2 * n), "d2h_bytes_per_step": 8 * n}
+    cpu = None if args.no_cpu_baseline else solver_cpu_leg(sweeps)
+    line = {"metric": "sparse-solver step cells/s (assembly, conversion, block Gauss-Seidel, residual)",
+            "value": weak_scaling_value(world, n, ms), "unit": "cells/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if arith == 0 else "f64 storage, double-float (2 x f32) arithmetic",
+            "data": "synthetic",
+            "config": {"workload": name, "n_cells": n, "n_faces": int(own.size),
+                       "arithmetic": args.solver_arith,
+                       "block_rows": int(info["n_parts"]), "cells_per_block_row": part_cells,
+                       "offblock_fraction_of_nnz": info["nnz_offblock"] / info["nnz"],
+                       "gauss_seidel_runs": int(info["n_runs"]), "sweeps_per_step": sweeps,
+                       "l2": "matrix and vectors larger than L2 (block format + LDU arrays ~1 GB)"},
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 4 + 2 * sweeps,
+            "roofline": {"bound": "hbm", "achieved": gs["GB/s"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": gs["frac"], "traffic": None,
+                         "kernel": "gauss_seidel (halo gather + one sweep)",
+                         "peak_source": f"hbm_gbs ({pk_src})"},
+            "kernels": fam, "algorithmic_bytes": by,
+            "relative_residual_after_step": resid,
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -644,6 +858,8 @@ def main():
         return run_train(args)
     if args.mode == "jacobian":
         return run_jacobian(args)
+    if args.mode == "solver":
+        return run_solver(args)
     return run_ours(args)
 
 

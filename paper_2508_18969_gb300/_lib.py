@@ -61,6 +61,16 @@ class Adam(C.Structure):
                 ("eps", C.c_double)]
 
 
+class SolverInfo(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("n_faces", C.c_int64), ("n_parts", C.c_int64),
+                ("nnz", C.c_int64), ("nnz_offblock", C.c_int64), ("n_halo", C.c_int64),
+                ("n_runs", C.c_int64), ("max_part", C.c_int32), ("max_runs", C.c_int32),
+                ("device_bytes", C.c_int64), ("n_chunks", C.c_int64)]
+
+
+DF_SOLVER_MAX_PART = 8192
+DF_SOLVER_FP64, DF_SOLVER_DOUBLE_FLOAT = 0, 1
+
 _VP = C.c_void_p
 _I64 = C.c_int64
 _ST = C.c_int32
@@ -98,6 +108,20 @@ SIGNATURES = {
     "df_profile_read": (_ST, [_VP, C.c_int32, C.c_char_p, C.POINTER(_I64), C.POINTER(C.c_double),
                               C.POINTER(C.c_int32)]),
     "df_get_last_error": (C.c_char_p, [_VP]),
+    # sparse-solver module (include/df_solver.h)
+    "df_mesh_decompose": (_ST, [_I64, _I64, _VP, _VP, C.c_int32, _VP, _VP]),
+    "df_mesh_renumber": (_ST, [_I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "df_solver_create": (_ST, [_I64, _I64, _VP, _VP, C.c_int32, _VP, C.c_int32, C.POINTER(_VP)]),
+    "df_solver_destroy": (None, [_VP]),
+    "df_solver_get_info": (_ST, [_VP, C.POINTER(SolverInfo)]),
+    "df_solver_set_arithmetic": (_ST, [_VP, C.c_int32]),
+    "df_solver_convert": (_ST, [_VP, _VP, _VP, _VP, _VP]),
+    "df_solver_spmv": (_ST, [_VP, _VP, _VP, _VP]),
+    "df_solver_residual": (_ST, [_VP, _VP, _VP, _VP, _VP]),
+    "df_solver_gauss_seidel": (_ST, [_VP, _VP, _VP, C.c_int32, _VP]),
+    "df_fv_laplacian": (_ST, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "df_solver_export_csr": (_ST, [_VP, _VP, _VP, _VP]),
+    "df_solver_get_last_error": (C.c_char_p, [_VP]),
     "df_version": (C.c_char_p, []),
 }
 

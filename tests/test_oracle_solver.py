@@ -169,3 +169,52 @@ def test_mesh_generator_shape():
                                                                         minlength=mesh.n_cells)
     assert deg.min() >= 3 and deg.max() <= 12
     assert 6.0 < deg.mean() < 7.5
+
+
+def test_level_sort_keeps_the_gauss_seidel_sweep():
+    """Sorting the cells of a block row stably by dependency level (1 + the highest level of
+    an earlier-numbered neighbour) keeps the order of every pair of neighbours, so the sweep
+    in the sorted numbering is the sweep in the original one, cell by cell."""
+    from collections import deque
+    mesh = smesh.grid_mesh(9, 8, 7, seed=12)
+    n = mesh.n_cells
+    rng = np.random.default_rng(7)
+    up = -rng.random(mesh.n_faces)
+    lo = up * (1.0 + 0.3 * rng.random(mesh.n_faces))
+    d = 7.0 + rng.random(n)
+    b = rng.normal(size=n)
+    nbrs = [[] for _ in range(n)]
+    for a, c in zip(mesh.owner.tolist(), mesh.neighbour.tolist()):
+        nbrs[a].append(c)
+        nbrs[c].append(a)
+    # a breadth-first numbering of the whole mesh (one block row)
+    seen, order, q = np.zeros(n, bool), [], deque([0])
+    seen[0] = True
+    while q:
+        c = q.popleft()
+        order.append(c)
+        for v in sorted(nbrs[c]):
+            if not seen[v]:
+                seen[v] = True
+                q.append(v)
+    pos = np.empty(n, np.int64)
+    pos[order] = np.arange(n)
+    level = np.zeros(n, np.int64)
+    for c in order:
+        earlier = [level[v] + 1 for v in nbrs[c] if pos[v] < pos[c]]
+        level[c] = max(earlier, default=0)
+    sorted_order = sorted(order, key=lambda c: level[c])          # stable
+    results = []
+    for numbering in (order, sorted_order):
+        new = np.empty(n, np.int64)
+        new[numbering] = np.arange(n)
+        a, c = new[mesh.owner], new[mesh.neighbour]
+        flip = a > c
+        own, nei = np.where(flip, c, a), np.where(flip, a, c)
+        A = osol.ldu_matrix(n, own, nei, np.where(flip, up, lo), d[numbering], np.where(flip, lo, up))
+        x = osol.gauss_seidel(A, b[numbering], np.zeros(n), [0, n], 2)
+        out = np.empty(n)
+        out[numbering] = x
+        results.append(out)
+    np.testing.assert_allclose(results[1], results[0], rtol=1e-13, atol=1e-15)
+    assert not np.array_equal(np.array(order), np.array(sorted_order))
