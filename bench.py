@@ -177,6 +177,9 @@ MEASURED_TRAFFIC = {
     ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e08b143876a7d2e", 4751.0),
     ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 297.0),
     ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 549.0),
+    # one block Gauss-Seidel sweep (gs_rhs_kernel + gs_sweep_kernel), per cell, FP64, 512 cells
+    # per block row (profiles/solver_kernels_mesh-2m.md)
+    ("gauss_seidel", "mesh-512"): ("paper_2508_18969_gb300/csrc/solver.cu", "1cd68a29c69cf17f", 129.8),
 }
 
 
@@ -840,7 +843,9 @@ def run_solver(args):
                        "l2": "matrix and vectors larger than L2 (block format + LDU arrays ~1 GB)"},
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 4 + 2 * sweeps,
             "roofline": {"bound": "hbm", "achieved": gs["GB/s"], "peak": pk["hbm_gbs"], "unit": "GB/s",
-                         "frac": gs["frac"], "traffic": None,
+                         "frac": gs["frac"],
+                         "traffic": measured_traffic("gauss_seidel", f"mesh-{part_cells}", n)
+                         if arith == 0 else None,
                          "kernel": "gauss_seidel (halo gather + one sweep)",
                          "peak_source": f"hbm_gbs ({pk_src})"},
             "kernels": fam, "algorithmic_bytes": by,
