@@ -18,6 +18,7 @@ Modules: thermo (NASA-7), pr_eos (Peng-Robinson), network (Box-Cox, normalisatio
 MLP, its Jacobian), step (active-cell list, reaction step, real-fluid properties, T from h,
 finite-difference Jacobian of the step), truth (the stiff-chemistry ground truth the network
 stands in for: C, BDF, oracle/truth.c), solver (the sparse kernels of Sec. 3.2: LDU matrix,
-SpMV, block Gauss-Seidel, finite-volume Laplacian).
+SpMV, block Gauss-Seidel, finite-volume Laplacian), propnet (the PRNet-style property network:
+inputs, outputs, exact properties).
 """
-from . import thermo, pr_eos, network, step, solver  # noqa: F401
+from . import thermo, pr_eos, network, step, solver, propnet  # noqa: F401

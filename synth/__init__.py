@@ -5,5 +5,5 @@ CUDA side of the tests and the bench take their inputs from here.
 """
 from .rng import Stream
 from .mechanism import Mechanism, make_mechanism
-from .network import Network, make_network
+from .network import Network, make_network, make_propnet
 from . import fields, configs, mesh

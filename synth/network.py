@@ -52,3 +52,29 @@ def make_network(widths: list[int], n_species: int, seed: int, lam: float = 0.1,
     in_std = np.concatenate([[1000.0, 5.0e6], np.full(n_species, 3.0)])
     return Network(widths=list(widths), W=Ws, b=bs, lam=lam, in_mean=in_mean, in_std=in_std,
                    out_mean=np.zeros(n_species), out_std=np.full(n_species, out_std), dt=dt)
+
+
+def make_propnet(widths: list[int], n_species: int, seed: int, lam: float = 0.1,
+                 in_mean=None, in_std=None, out_mean=None, out_std=None) -> Network:
+    """Seeded property network (PRNet-style, Sec. 2): inputs (h, p, BC(Y_1..Y_n)), any number
+    of outputs. Weights as make_network. The normalisation constants are network parameters:
+    pass the means and spreads of the data the network is meant for, else fixed defaults
+    (h ~ 0 +- 2 MJ/kg, p ~ 12.5 +- 5 MPa, BC(Y) ~ -4 +- 3; outputs 0 +- 1)."""
+    if widths[0] != n_species + 2:
+        raise ValueError("a property network reads (h, p, Y_1..Y_n)")
+    s = Stream(seed, "propnet")
+    Ws, bs = [], []
+    for fan_in, fan_out in zip(widths[:-1], widths[1:]):
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        w = s.uniform(fan_in * fan_out, -lim, lim).reshape(fan_out, fan_in)
+        Ws.append(w.astype(np.float32).astype(np.float64))
+        bs.append(s.uniform(fan_out, -0.05, 0.05).astype(np.float32).astype(np.float64))
+    m = widths[-1]
+    dflt_mean = np.concatenate([[0.0, 12.5e6], np.full(n_species, -4.0)])
+    dflt_std = np.concatenate([[2.0e6, 5.0e6], np.full(n_species, 3.0)])
+    return Network(widths=list(widths), W=Ws, b=bs, lam=lam,
+                   in_mean=np.asarray(dflt_mean if in_mean is None else in_mean, np.float64),
+                   in_std=np.asarray(dflt_std if in_std is None else in_std, np.float64),
+                   out_mean=np.asarray(np.zeros(m) if out_mean is None else out_mean, np.float64),
+                   out_std=np.asarray(np.ones(m) if out_std is None else out_std, np.float64),
+                   dt=0.0)
