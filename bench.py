@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="step", choices=["step", "train", "jacobian", "solver"],
+    ap.add_argument("--mode", default="step", choices=["step", "train", "jacobian", "solver", "propnet"],
                     help="step: the reaction step (headline); train: Adam steps on training "
                          "states; jacobian: the step's Jacobian")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp8"])
@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="reacting cells per internal batch")
     ap.add_argument("--gelu", default="tanh", choices=["tanh", "table"],
                     help="hidden activation: hardware tanh form, or the paper's tabulation")
+    ap.add_argument("--fit-steps", type=int, default=2000,
+                    help="propnet mode: Adam steps of each property network before timing")
     ap.add_argument("--solver-arith", default="fp64", choices=["fp64", "f2"],
                     help="solver mode: FP64 FMAs or double-float pairs on the FP32 pipes")
     ap.add_argument("--part-cells", type=int, default=0,
@@ -855,6 +857,187 @@ def run_solver(args):
     return 0
 
 
+# Property networks of Sec. 4.1's sizes (PRNet-style surrogates of the real-fluid state) on the
+# 30-species mechanism: density (hidden 1024-512-256) and temperature (hidden 2048-1024-512),
+# one output each; transport outputs are not modelled.
+PROPNET_WIDTHS = {"rho": [32, 1024, 512, 256, 1], "T": [32, 2048, 1024, 512, 1]}
+
+
+def run_propnet(args):
+    """Property-network throughput and accuracy: the density and temperature networks trained
+    (BF16, Adam, batch 65536) on 2^20 states of the training workload whose exact properties
+    the GPU equation of state gives, then run on 2^20 other cells; the explicit path (T from h
+    by Newton on the Peng-Robinson h(T), the reaction step's a9, from a start 10 % off) is timed
+    beside it. A step = both networks on all cells."""
+    import torch
+    import __graft_entry__ as g_
+    g_.build()
+    import paper_2508_18969_gb300 as df
+    import synth
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N = args.cells or (1 << 20)
+    mech, chem_net, T, p, Y = synth.configs.build("train30-1m", n_cells=2 * N, field_seed=31 + rank)
+    chem = df.State(mech, chem_net, precision=df.DF_BF16, T_react=0.0, device=local)
+    Td, pd, Yd = (torch.tensor(a, device=dev) for a in (T, p, Y))
+    rho, h, _, _ = chem.real_fluid_props(Td, pd, Yd)
+    props = torch.stack([rho, Td])
+    tr, te = slice(0, N), slice(N, 2 * N)
+    bc = (Yd[:, tr].clamp(min=0.0) ** 0.1 - 1.0) / 0.1
+    v = torch.cat([h[None, tr], pd[None, tr], bc], dim=0)
+    in_mean, in_std = v.mean(dim=1).cpu().numpy(), v.std(dim=1).cpu().numpy() + 1e-3
+    nets, pns = {}, {}
+    for k, (name, widths) in enumerate(PROPNET_WIDTHS.items()):
+        nets[name] = synth.make_propnet(widths, mech.n, seed=41 + k, lam=0.1, in_mean=in_mean,
+                                        in_std=in_std, out_mean=[float(props[k, tr].mean())],
+                                        out_std=[float(props[k, tr].std())])
+        pns[name] = df.PropNet(nets[name], precision=df.DF_BF16, device=local)
+    B = 65536
+    batches = [(h[i:i + B], pd[i:i + B], Yd[:, i:i + B].contiguous(), props[:, i:i + B].contiguous())
+               for i in range(0, N - B + 1, B)]
+    fit = {}
+    for k, name in enumerate(PROPNET_WIDTHS):
+        loss = None
+        first = None
+        for step in range(args.fit_steps):
+            hb, pb, Yb, tb = batches[step % len(batches)]
+            loss = pns[name].fit_step(hb, pb, Yb, tb[k:k + 1].contiguous(), lr=1e-3 if step < args.fit_steps // 2 else 3e-4)
+            if step == 0:
+                first = float(loss.item())
+        fit[name] = {"steps": args.fit_steps, "batch": B, "loss_first": first,
+                     "loss_last": float(loss.item())}
+    he, pe, Ye = h[te].contiguous(), pd[te].contiguous(), Yd[:, te].contiguous()
+    outs = {name: torch.empty(1, N, dtype=torch.float64, device=dev) for name in PROPNET_WIDTHS}
+
+    def step():
+        for name in PROPNET_WIDTHS:
+            pns[name].infer(he, pe, Ye, out=outs[name])
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    for name in PROPNET_WIDTHS:
+        pns[name].profile_read()
+        pns[name].profile_enable(True)
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = max_over_ranks(world, e0.elapsed_time(e1) / args.steps, local)
+    fam = {}
+    for name in PROPNET_WIDTHS:
+        pns[name].profile_enable(False)
+        for f, (launches, tot) in pns[name].profile_read().items():
+            fam[f"{name}:{f}"] = tot / args.steps
+    # accuracy on the held-out cells
+    rho_abs = (outs["rho"][0] - props[0, te]).abs().cpu().numpy()
+    rho_err = rho_abs / props[0, te].cpu().numpy()
+    T_err = (outs["T"][0] - props[1, te]).abs().cpu().numpy()
+    # explicit path: Newton on h(T) from a start 10 % off (eos_post with a zero network output)
+    O0 = torch.zeros(N, mech.n, dtype=torch.float32, device=dev)
+    u = torch.tensor(synth.Stream(7, "propnet-start").uniform(N, -0.1, 0.1), device=dev)
+    T_start = (props[1, te] * (1.0 + u)).contiguous()
+    Tx, Yx = T_start.clone(), Ye.clone()
+    chem.eos_post(O0, he, Tx, pe, Yx)
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        Tx.copy_(T_start)
+        chem.eos_post(O0, he, Tx, pe, Yx)
+    z.record(stream)
+    torch.cuda.synchronize()
+    explicit_ms = a.elapsed_time(z) / args.steps
+    Tx.copy_(T_start)
+    xst = chem.eos_post(O0, he, Tx, pe, Yx)
+    ok = xst == 0
+    dTx = (Tx - props[1, te]).abs()
+    explicit_flagged = int((~ok).sum().item())
+    explicit_T_err = float(dTx[ok].max().item()) if bool(ok.any()) else None
+    if rank != 0:
+        return 0
+    pk, pk_src = peaks()
+    gemm = {f: t for f, t in fam.items() if ":layer" in f}
+    dom = max(gemm, key=gemm.get)
+    name, lay = dom.split(":")
+    l = int(lay[5:])
+    wd = PROPNET_WIDTHS[name]
+    ach = 2.0 * wd[l] * wd[l + 1] * N / (gemm[dom] * 1e-3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        import time as _t
+        from oracle import propnet as opn
+        S = 16384
+        sel = np.linspace(N, 2 * N - 1, S).astype(np.int64)
+        hs, ps_, Ys = h[sel].cpu().numpy(), p[sel], Y[:, sel]
+        t0 = _t.perf_counter()
+        for nm in PROPNET_WIDTHS:
+            opn.infer(nets[nm], hs, ps_, Ys)
+        dt = _t.perf_counter() - t0
+        cpu = {"value": S / dt, "unit": "cells/s", "cores": len(os.sched_getaffinity(0)),
+               "kind": "oracle", "sample": f"{S} evenly strided cells, both networks in FP64 numpy",
+               "seconds": dt}
+    e2e = None
+    if not args.no_e2e:
+        hh, ph, Yh = (t.cpu().pin_memory() for t in (he, pe, Ye))
+        oh = {nm: torch.empty(1, N, dtype=torch.float64).pin_memory() for nm in PROPNET_WIDTHS}
+
+        def e2e_step():
+            he.copy_(hh, non_blocking=True)
+            pe.copy_(ph, non_blocking=True)
+            Ye.copy_(Yh, non_blocking=True)
+            step()
+            for nm in PROPNET_WIDTHS:
+                oh[nm].copy_(outs[nm], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        z.record(stream)
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(z) / args.steps
+        e2e = {"value": N / (ems * 1e-3), "unit": "cells/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": 8 * N * (2 + mech.n), "d2h_bytes_per_step": 16 * N}
+    q = lambda a_, f: float(np.quantile(a_, f))
+    line = {"metric": "property-network cells/s (rho and T networks of Sec. 4.1 sizes, BF16)",
+            "value": weak_scaling_value(world, N, ms), "unit": "cells/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": "train30-1m states, 2^20 training + 2^20 evaluation cells",
+                       "n_cells": N, "networks": {k: "-".join(map(str, w)) for k, w in PROPNET_WIDTHS.items()},
+                       "inputs": "h, p, Box-Cox(Y) of 30 species, Z-scored",
+                       "l2": "inputs larger than L2 (fields 8*(2+n)*N bytes, activations GBs)"},
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 2 * (2 + 4),
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops_sustained"],
+                         "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops_sustained"], "traffic": None,
+                         "kernel": f"tc_gemm {name} network {lay} ({wd[l]} -> {wd[l + 1]})",
+                         "peak_source": f"bf16_tflops_sustained ({pk_src})"},
+            "kernels_ms_per_step": fam, "fit": fit,
+            "error_vs_peng_robinson": {
+                "rho_rel_median": q(rho_err, 0.5), "rho_rel_p99": q(rho_err, 0.99), "rho_rel_max": float(rho_err.max()),
+                "rho_abs_kg_m3_median": q(rho_abs, 0.5), "rho_abs_kg_m3_p99": q(rho_abs, 0.99),
+                "rho_true_kg_m3_range": [float(props[0, te].min()), float(props[0, te].max())],
+                "T_abs_K_median": q(T_err, 0.5), "T_abs_K_p99": q(T_err, 0.99), "T_abs_K_max": float(T_err.max()),
+                "cells": N},
+            "explicit_pr_newton": {"ms_per_step": explicit_ms, "cells_per_s": N / (explicit_ms * 1e-3),
+                                   "T_abs_K_max_converged": explicit_T_err,
+                                   "flagged_cells": explicit_flagged,
+                                   "what": "eos_post: T from h by safeguarded Newton on the PR h(T), start 10 % off"},
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -865,6 +1048,8 @@ def main():
         return run_jacobian(args)
     if args.mode == "solver":
         return run_solver(args)
+    if args.mode == "propnet":
+        return run_propnet(args)
     return run_ours(args)
 
 

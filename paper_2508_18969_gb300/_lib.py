@@ -108,6 +108,11 @@ SIGNATURES = {
     "df_profile_read": (_ST, [_VP, C.c_int32, C.c_char_p, C.POINTER(_I64), C.POINTER(C.c_double),
                               C.POINTER(C.c_int32)]),
     "df_get_last_error": (C.c_char_p, [_VP]),
+    # property network (include/df_propnet.h)
+    "df_network_create": (_ST, [C.POINTER(MlpDesc), C.POINTER(Options), C.POINTER(_VP)]),
+    "df_propnet_infer": (_ST, [_VP, _I64, _VP, _VP, _VP, _I64, _VP, _I64, _VP]),
+    "df_propnet_train_step": (_ST, [_VP, _I64, _VP, _VP, _VP, _I64, _VP, _I64, C.POINTER(Adam), _VP,
+                                    _VP]),
     # sparse-solver module (include/df_solver.h)
     "df_mesh_decompose": (_ST, [_I64, _I64, _VP, _VP, C.c_int32, _VP, _VP]),
     "df_mesh_renumber": (_ST, [_I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),

@@ -66,6 +66,7 @@ class State:
         self.h = h
         self.n = int(mech.n)
         self.K0 = self.n + 2
+        self.nout = self.n
         self.dt = float(net.dt)
         self.device = torch.device("cuda", device)
 
@@ -153,7 +154,7 @@ class State:
 
     def mlp_forward_train(self, x, stream=None):
         x = x.contiguous()
-        O = torch.empty(x.shape[0], self.n, dtype=torch.float32, device=x.device)
+        O = torch.empty(x.shape[0], self.nout, dtype=torch.float32, device=x.device)
         self._check(self._lib.df_mlp_forward_train(self.h, x.shape[0], _ptr(x), _ptr(O),
                                                    _stream(stream)))
         return O
@@ -245,7 +246,7 @@ class State:
 
     def mlp_forward(self, x, stream=None):
         x = x.contiguous()
-        O = torch.empty(x.shape[0], self.n, dtype=torch.float32, device=x.device)
+        O = torch.empty(x.shape[0], self.nout, dtype=torch.float32, device=x.device)
         self._check(self._lib.df_mlp_forward(self.h, x.shape[0], _ptr(x), _ptr(O), _stream(stream)))
         return O
 

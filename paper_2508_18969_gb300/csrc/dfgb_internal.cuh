@@ -123,6 +123,15 @@ cudaError_t launch_train_targets(const EosParams& P, int64_t B, const double* Y,
 constexpr int kTrainScratchFloats = 4096;
 constexpr int kColsumChunks = 64;
 // dO [B x ldd] (BF16 or FP32, zero pads) = 2 (O - Ohat) / B; *loss = sum (O - Ohat)^2 / B.
+// Property network (propnet.cu): input rows from (h, p, Y), normalised targets, outputs.
+cudaError_t launch_prop_inputs(const double* norm, int n, double lambda, int64_t rows,
+                               const double* h, const double* p, const double* Y, int64_t ldY,
+                               void* x, int64_t ldx, int xkind, int num_sms, cudaStream_t st);
+cudaError_t launch_prop_targets(const double* norm, int K0, int m, int64_t rows, const double* t,
+                                int64_t ldt, float* Oh, int64_t ldo, int num_sms, cudaStream_t st);
+cudaError_t launch_prop_outputs(const double* norm, int K0, int m, int64_t rows, const float* O,
+                                int64_t ldo, double* out, int64_t ldout, int num_sms,
+                                cudaStream_t st);
 cudaError_t launch_loss_grad(int64_t B, int n, const float* O, int64_t ldo, const float* Oh,
                              int64_t ldh, void* dO, int64_t ldd, bool bf16, float* loss,
                              float* scratch, cudaStream_t st);

@@ -2,6 +2,7 @@
 // entry points. Host code only orchestrates; every step of the path runs in the kernels
 // of eos.cu, compact.cu, mlp_simt.cu and mlp_tc.cu.
 #include "state.cuh"
+#include "../../include/df_propnet.h"
 
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -171,6 +172,8 @@ df_status run_mlp(df_state* s, const RowMap& rm, cudaStream_t st) {
 df_status check_fields(df_state* s, int64_t n, const void* a, const void* b, const void* Y,
                        int64_t ldY) {
   if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
+  if (s->netonly)
+    return fail(s, DF_ERR_UNSUPPORTED, "the state holds a network only (df_network_create)");
   if (n < 0) return fail(s, DF_ERR_INVALID_ARG, "n_cells < 0");
   if (n == 0) return DF_OK;
   if (!a || !b || !Y) return fail(s, DF_ERR_INVALID_ARG, "NULL field pointer");
@@ -210,21 +213,25 @@ const char* df_version(void) { return kVersion; }
 
 const char* df_get_last_error(df_state* s) { return s ? s->err.c_str() : g_create_err.c_str(); }
 
-df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
-                          const df_options* opt, df_state** out) {
+// A state with the mechanism (mech != NULL: the reaction step) or with a network only
+// (mech == NULL: df_network_create; n = widths[0] - 2 composition inputs, any output width).
+static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
+                              const df_options* opt, df_state** out) {
   if (!out) return fail(nullptr, DF_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (!mech || !mlp || !opt) return fail(nullptr, DF_ERR_INVALID_ARG, "NULL descriptor");
-  const int n = mech->n_species;
-  if (n < 1 || n > kMaxSpecies)
-    return fail(nullptr, DF_ERR_UNSUPPORTED, "n_species must be in 1..%d", kMaxSpecies);
-  if (!mech->W || !mech->Tc || !mech->pc || !mech->omega || !mech->kij || !mech->nasa)
-    return fail(nullptr, DF_ERR_INVALID_ARG, "NULL mechanism array");
+  if (!mlp || !opt) return fail(nullptr, DF_ERR_INVALID_ARG, "NULL descriptor");
   const int L = mlp->n_layers;
   if (L < 1 || L > 8 || !mlp->widths || !mlp->W || !mlp->b)
     return fail(nullptr, DF_ERR_INVALID_ARG, "bad network description");
-  if (mlp->widths[0] != n + 2 || mlp->widths[L] != n)
+  const bool netonly = mech == nullptr;
+  const int n = netonly ? mlp->widths[0] - 2 : mech->n_species;
+  if (n < 1 || n > kMaxSpecies)
+    return fail(nullptr, DF_ERR_UNSUPPORTED, "n_species must be in 1..%d", kMaxSpecies);
+  if (!netonly && (!mech->W || !mech->Tc || !mech->pc || !mech->omega || !mech->kij || !mech->nasa))
+    return fail(nullptr, DF_ERR_INVALID_ARG, "NULL mechanism array");
+  if (!netonly && (mlp->widths[0] != n + 2 || mlp->widths[L] != n))
     return fail(nullptr, DF_ERR_INVALID_ARG, "network must map n+2 inputs to n outputs");
+  const int nout = mlp->widths[L];
   for (int l = 0; l <= L; ++l)
     if (mlp->widths[l] < 1 || mlp->widths[l] > 8192)
       return fail(nullptr, DF_ERR_INVALID_ARG, "layer width out of range");
@@ -235,14 +242,16 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
   const int m = (int)std::lround(inv_l);
   if (m < 1 || m > 64 || std::fabs(inv_l - m) > 1e-9 * inv_l)
     return fail(nullptr, DF_ERR_UNSUPPORTED, "1/lambda must be an integer in 1..64");
-  if (!(mlp->dt > 0.0)) return fail(nullptr, DF_ERR_INVALID_ARG, "dt must be > 0");
+  if (!netonly && !(mlp->dt > 0.0)) return fail(nullptr, DF_ERR_INVALID_ARG, "dt must be > 0");
+  if (netonly && opt->precision == DF_FP8_E4M3)
+    return fail(nullptr, DF_ERR_UNSUPPORTED, "network-only states run in FP32 or BF16");
   if (opt->precision < DF_FP32 || opt->precision > DF_FP8_E4M3)
     return fail(nullptr, DF_ERR_INVALID_ARG, "unknown precision");
   if (opt->gelu_mode != DF_GELU_TANH && opt->gelu_mode != DF_GELU_TABLE)
     return fail(nullptr, DF_ERR_INVALID_ARG, "unknown gelu_mode");
   if (opt->gelu_mode == DF_GELU_TABLE && opt->precision == DF_FP8_E4M3)
     return fail(nullptr, DF_ERR_UNSUPPORTED, "the tabulated GELU runs on FP32 and BF16 networks");
-  for (int k = 0; k < n; ++k)
+  for (int k = 0; !netonly && k < n; ++k)
     if (!(mech->W[k] > 0) || !(mech->Tc[k] > 0) || !(mech->pc[k] > 0))
       return fail(nullptr, DF_ERR_INVALID_ARG, "W, Tc, pc must be positive");
   int ndev = 0;
@@ -261,6 +270,8 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
   s->num_sms = prop.multiProcessorCount;
   s->n = n;
   s->K0 = n + 2;
+  s->nout = nout;
+  s->netonly = netonly;
   s->L = L;
   s->widths.assign(mlp->widths, mlp->widths + L + 1);
   s->precision = opt->precision;
@@ -283,7 +294,7 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
 
   // ---- equation-of-state constants (Peng & Robinson 1976, NASA-7) ----
   std::vector<double> spc((size_t)n * kSpcStride), K((size_t)n * n);
-  for (int k = 0; k < n; ++k) {
+  for (int k = 0; !netonly && k < n; ++k) {   // (a network-only state keeps zero tables)
     const double Tc = mech->Tc[k], pc = mech->pc[k], w = mech->omega[k];
     const double ac = 0.45724 * kR * kR * Tc * Tc / pc;
     const double b = 0.07780 * kR * Tc / pc;
@@ -302,9 +313,9 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
     q[8] = kR * a[3] / 4.0;
     q[9] = kR * a[4] / 5.0;
   }
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; !netonly && i < n; ++i)
     for (int j = 0; j < n; ++j) K[(size_t)i * n + j] = (i == j) ? 1.0 : 1.0 - mech->kij[i * n + j];
-  std::vector<double> norm((size_t)2 * s->K0 + 2 * n);
+  std::vector<double> norm((size_t)2 * s->K0 + 2 * nout);
   for (int k = 0; k < s->K0; ++k) {
     if (!(mlp->in_std[k] != 0.0)) {
       delete s;
@@ -313,9 +324,9 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
     norm[k] = mlp->in_mean[k];
     norm[s->K0 + k] = 1.0 / mlp->in_std[k];
   }
-  for (int k = 0; k < n; ++k) {
+  for (int k = 0; k < nout; ++k) {
     norm[2 * s->K0 + k] = mlp->out_mean[k];
-    norm[2 * s->K0 + n + k] = mlp->out_std[k];
+    norm[2 * s->K0 + nout + k] = mlp->out_std[k];
   }
   CK(dalloc(&s->d_spc, spc.size()), "constants");
   CK(dalloc(&s->d_K, K.size()), "constants");
@@ -497,7 +508,7 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
     CK(cudaMalloc(&s->act[b], eb * (size_t)s->cap * wmax[b]), "activations");
     CK(cudaMemset(s->act[b], 0, eb * (size_t)s->cap * wmax[b]), "memset");
   }
-  s->ldo = round_up(n, 8);
+  s->ldo = round_up(nout, 8);
   CK(dalloc(&s->O, (size_t)s->cap * s->ldo), "network output");
   CK(dalloc(&s->h0, (size_t)s->cap), "h0");
   CK(dalloc(&s->rho_row, (size_t)s->cap), "rho");
@@ -545,6 +556,19 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
 #undef CK
   *out = s;
   return DF_OK;
+}
+
+df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
+                          const df_options* opt, df_state** out) {
+  if (!mech) {
+    if (out) *out = nullptr;
+    return fail(nullptr, DF_ERR_INVALID_ARG, "NULL descriptor");
+  }
+  return create_state(mech, mlp, opt, out);
+}
+
+df_status df_network_create(const df_mlp_desc* mlp, const df_options* opt, df_state** out) {
+  return create_state(nullptr, mlp, opt, out);
 }
 
 void df_state_destroy(df_state* s) {
@@ -1113,9 +1137,43 @@ df_status df_mlp_forward(df_state* s, int64_t n_rows, const float* x, float* O, 
     const RowMap rm{nullptr, nullptr, 0, rows};
     df_status rc = run_mlp(s, rm, st);
     if (rc != DF_OK) return rc;
-    e = cudaMemcpy2DAsync(O + r0 * s->n, sizeof(float) * s->n, s->O, sizeof(float) * s->ldo,
-                          sizeof(float) * s->n, (size_t)rows, cudaMemcpyDeviceToDevice, st);
+    e = cudaMemcpy2DAsync(O + r0 * s->nout, sizeof(float) * s->nout, s->O, sizeof(float) * s->ldo,
+                          sizeof(float) * s->nout, (size_t)rows, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "output copy");
+  }
+  return DF_OK;
+}
+
+df_status df_propnet_infer(df_state* s, int64_t n_cells, const double* h, const double* p,
+                           const double* Y, int64_t ldY, double* out, int64_t ldout,
+                           void* stream) {
+  if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
+  if (!s->netonly) return fail(s, DF_ERR_UNSUPPORTED, "not a network-only state (df_network_create)");
+  if (n_cells < 0) return fail(s, DF_ERR_INVALID_ARG, "n_cells < 0");
+  if (n_cells == 0) return DF_OK;
+  if (!h || !p || !Y || !out) return fail(s, DF_ERR_INVALID_ARG, "NULL array");
+  if (ldY < n_cells || ldout < n_cells) return fail(s, DF_ERR_INVALID_ARG, "ldY or ldout < n_cells");
+  DeviceGuard guard(s->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int xk = xkind_of(s->precision);
+  for (int64_t r0 = 0; r0 < n_cells; r0 += s->cap) {
+    const int64_t rows = std::min<int64_t>(s->cap, n_cells - r0);
+    cudaError_t e;
+    {
+      ProfScope ps(s, "prop_inputs", st);
+      e = launch_prop_inputs(s->d_norm, s->n, s->lambda, rows, h + r0, p + r0, Y + r0, ldY, s->x,
+                             s->ldx, xk, s->num_sms, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "property-network inputs");
+    const RowMap rm{nullptr, nullptr, 0, rows};
+    df_status rc = run_mlp(s, rm, st);
+    if (rc != DF_OK) return rc;
+    {
+      ProfScope ps(s, "prop_outputs", st);
+      e = launch_prop_outputs(s->d_norm, s->K0, s->nout, rows, s->O, s->ldo, out + r0, ldout,
+                              s->num_sms, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "property-network outputs");
   }
   return DF_OK;
 }

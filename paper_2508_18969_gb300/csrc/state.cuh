@@ -42,6 +42,8 @@ struct df_state {
   int device = 0;
   int num_sms = 0;
   int n = 0, K0 = 0, L = 0;
+  int nout = 0;                          // network outputs (n for the chemistry network)
+  bool netonly = false;                  // created by df_network_create: no mechanism
   std::vector<int> widths;
   int precision = DF_FP32;
   double T_react = 0, lambda = 0.1, dt = 0;
@@ -144,7 +146,7 @@ inline cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
 }
 
-// Tile width of a layer: hidden layers from the compiled set {64, 128, 160, 208, 256}, the
+// Tile width of a layer: hidden layers from the compiled set {64, 128, 160, 224, 256}, the
 
 // Brackets the launches made during its lifetime with events on `st` when timing is on.
 struct ProfScope {

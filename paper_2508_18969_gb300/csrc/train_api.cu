@@ -11,6 +11,7 @@
 //                                             GELU' factor applied in its epilogue)
 // Every step runs in the kernels of train.cu, mlp_simt.cu and mlp_tc.cu.
 #include "state.cuh"
+#include "../../include/df_propnet.h"
 
 #include <algorithm>
 #include <cmath>
@@ -182,7 +183,7 @@ df_status ensure_batch(df_state* s, int64_t B) {
   if (e != cudaSuccess) return cuda_fail(s, e, "device synchronize");
   free_batch(t);
   B = round_up(B, 128);
-  const int L = s->L, n = s->n, K0 = s->K0;
+  const int L = s->L, K0 = s->K0;
   const bool bf16 = s->precision == DF_BF16;
   const size_t eb = bf16 ? 2 : 4;
   const int64_t al = bf16 ? 16 : 8;
@@ -209,7 +210,7 @@ df_status ensure_batch(df_state* s, int64_t B) {
     t->H.push_back(H); t->G.push_back(G); t->dZ.push_back(dZ);
     t->ldh.push_back(ldh); t->ldg.push_back(ldg); t->ldz.push_back(ldz);
   }
-  t->ldo = round_up(n, 8);
+  t->ldo = round_up(s->nout, 8);
   zalloc((void**)&t->O, sizeof(float) * B * t->ldo);
   zalloc((void**)&t->Oh, sizeof(float) * B * t->ldo);
   zalloc(&t->ZT, eb * nmax * Bp);
@@ -487,6 +488,53 @@ df_status df_train_step(df_state* s, int64_t batch, const double* T, const doubl
   return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "training step");
 }
 
+df_status df_propnet_train_step(df_state* s, int64_t batch, const double* h, const double* p,
+                                const double* Y, int64_t ldY, const double* target, int64_t ldt,
+                                const df_adam* hp, float* loss_out, void* stream) {
+  if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
+  if (!s->netonly) return fail(s, DF_ERR_UNSUPPORTED, "not a network-only state (df_network_create)");
+  if (batch < 0) return fail(s, DF_ERR_INVALID_ARG, "batch < 0");
+  if (batch > 0 && (!h || !p || !Y || !target)) return fail(s, DF_ERR_INVALID_ARG, "NULL array");
+  if (batch > 0 && (ldY < batch || ldt < batch))
+    return fail(s, DF_ERR_INVALID_ARG, "ldY or ldt < batch");
+  df_status rc = check_adam(s, hp);
+  if (rc != DF_OK) return rc;
+  DeviceGuard guard(s->device);
+  if ((rc = ensure_train(s, std::max<int64_t>(batch, 1))) != DF_OK) return rc;
+  Trn* t = s->trn;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool bf16 = s->precision == DF_BF16;
+  cudaError_t e = batch > 0 ? cudaSuccess : cudaMemsetAsync(t->loss, 0, sizeof(float), st);
+  if (batch > 0) {
+    {
+      ProfScope ps(s, "train_inputs", st);
+      e = launch_prop_inputs(s->d_norm, s->n, s->lambda, batch, h, p, Y, ldY, t->x, t->ldx,
+                             bf16 ? kXBF16 : kXF32, s->num_sms, st);
+      if (e == cudaSuccess)
+        e = launch_prop_targets(s->d_norm, s->K0, s->nout, batch, target, ldt, t->Oh, t->ldo,
+                                s->num_sms, st);
+    }
+    if (e == cudaSuccess) {
+      ProfScope ps(s, "train_forward", st);
+      e = forward(s, batch, st);
+    }
+    if (e == cudaSuccess)
+      e = launch_loss_grad(batch, s->nout, t->O, t->ldo, t->Oh, t->ldo, t->dZ[s->L - 1],
+                           t->ldz[s->L - 1], bf16, t->loss, t->scratch, st);
+    if (e == cudaSuccess) {
+      ProfScope ps(s, "train_backward", st);
+      e = backward(s, batch, false, st);
+    }
+    if (e == cudaSuccess) {
+      ProfScope ps(s, "train_adam", st);
+      e = adam(s, hp, st);
+    }
+  }
+  if (e == cudaSuccess && loss_out)
+    e = cudaMemcpyAsync(loss_out, t->loss, sizeof(float), cudaMemcpyDefault, st);
+  return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "property-network training step");
+}
+
 df_status df_mlp_forward_train(df_state* s, int64_t n_rows, const float* x, float* O,
                                void* stream) {
   if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
@@ -504,8 +552,8 @@ df_status df_mlp_forward_train(df_state* s, int64_t n_rows, const float* x, floa
                                    s->precision == DF_BF16 ? kXBF16 : kXF32, 1.0f, s->num_sms, st);
   if (e == cudaSuccess) e = forward(s, n_rows, st);
   if (e == cudaSuccess)
-    e = cudaMemcpy2DAsync(O, sizeof(float) * s->n, t->O, sizeof(float) * t->ldo,
-                          sizeof(float) * s->n, (size_t)n_rows, cudaMemcpyDeviceToDevice, st);
+    e = cudaMemcpy2DAsync(O, sizeof(float) * s->nout, t->O, sizeof(float) * t->ldo,
+                          sizeof(float) * s->nout, (size_t)n_rows, cudaMemcpyDeviceToDevice, st);
   return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "training forward pass");
 }
 
@@ -529,7 +577,7 @@ df_status df_mlp_backward(df_state* s, int64_t n_rows, const float* dO, float* d
     return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "gradient reset");
   }
   const int L = s->L;
-  cudaError_t e = launch_cast_rows(n_rows, s->n, dO, s->n, t->dZ[L - 1], t->ldz[L - 1],
+  cudaError_t e = launch_cast_rows(n_rows, s->nout, dO, s->nout, t->dZ[L - 1], t->ldz[L - 1],
                                    s->precision == DF_BF16 ? kXBF16 : kXF32, 1.0f, s->num_sms, st);
   if (e == cudaSuccess) e = backward(s, n_rows, dX != nullptr, st);
   if (e == cudaSuccess && dX)
