@@ -181,7 +181,7 @@ MEASURED_TRAFFIC = {
     ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 549.0),
     # one block Gauss-Seidel sweep (gs_rhs_kernel + gs_sweep_kernel), per cell, FP64, 512 cells
     # per block row (profiles/solver_kernels_mesh-2m.md)
-    ("gauss_seidel", "mesh-512"): ("paper_2508_18969_gb300/csrc/solver.cu", "1cd68a29c69cf17f", 129.8),
+    ("gauss_seidel", "mesh-512"): ("paper_2508_18969_gb300/csrc/solver.cu", "05bcbf99e5a03a1e", 132.1),
 }
 
 

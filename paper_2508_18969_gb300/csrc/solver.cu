@@ -19,6 +19,10 @@
 //                        the chunk (a piece of a "run", a maximal range with that property)
 //   halo_ptr, halo       cells some other block row reads, ascending (so grouped by block row)
 //   cf_ptr, cf           faces of every cell, ascending (the assembly's gather lists)
+//   order       [n]      the rows of each block row (16-bit local index) by descending number
+//                        of entries: the row order in which SpMV and Gauss-Seidel part 1 hand
+//                        rows to threads, so that a warp's rows have similar lengths and its
+//                        FP64 instructions run with few idle lanes (results do not depend on it)
 //
 // SpMV gives one CTA to a block row. A Gauss-Seidel sweep is split where its dependencies are:
 // the part of every row that uses only values from before the sweep (upper and off-block
@@ -64,6 +68,7 @@ struct SolverDev {
   const int32_t* halo = nullptr;
   const int32_t* cf_ptr = nullptr;
   const int32_t* cf = nullptr;
+  const uint16_t* order = nullptr;   // per block row: local rows by descending entry count
   int64_t n = 0, nf = 0, nnzL = 0, nnzU = 0, nnzO = 0, nh = 0;
   int t = 0;
 };
@@ -112,7 +117,8 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(SolverDev d, const doubl
   const int r0 = d.part[I], r1 = d.part[I + 1];
   if constexpr (!F2) {
     const double* __restrict__ xI = x + r0;
-    for (int r = r0 + threadIdx.x; r < r1; r += kThreads) {
+    for (int j = threadIdx.x; j < r1 - r0; j += kThreads) {
+      const int r = r0 + d.order[r0 + j];
       double s = d.dg[r] * x[r];
       const int l1 = d.lrp[r + 1];
       for (int e = d.lrp[r]; e < l1; ++e) s = fma(d.lv[e], xI[d.lc[e]], s);
@@ -127,7 +133,8 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(SolverDev d, const doubl
     float2* xs = reinterpret_cast<float2*>(spmv_smem);
     for (int i = threadIdx.x; i < r1 - r0; i += kThreads) st2(xs + i, f2_from(x[r0 + i]));
     __syncthreads();
-    for (int r = r0 + threadIdx.x; r < r1; r += kThreads) {
+    for (int j = threadIdx.x; j < r1 - r0; j += kThreads) {
+      const int r = r0 + d.order[r0 + j];
       f2 s = f2_mul(f2_from(d.dg[r]), ld2(xs + (r - r0)));
       const int l1 = d.lrp[r + 1];
       for (int e = d.lrp[r]; e < l1; ++e) acc_fma(s, f2_from(d.lv[e]), ld2(xs + d.lc[e]));
@@ -165,7 +172,8 @@ __global__ void __launch_bounds__(kThreads) gs_rhs_kernel(SolverDev d, const dou
   const int I = blockIdx.x;
   const int r0 = d.part[I], r1 = d.part[I + 1];
   const double* __restrict__ xI = x + r0;
-  for (int r = r0 + threadIdx.x; r < r1; r += kThreads) {
+  for (int j = threadIdx.x; j < r1 - r0; j += kThreads) {
+    const int r = r0 + d.order[r0 + j];
     const int u1 = d.urp[r + 1], o1 = d.orp[r + 1];
     if constexpr (F2) {
       const float2* h2 = static_cast<const float2*>(hold);
@@ -562,6 +570,21 @@ df_status df_solver_create(int64_t n_cells, int64_t n_faces, const int32_t* owne
   }
   ch_row.push_back((int32_t)n);
 
+  // row order for the thread-per-row kernels: within each block row, by descending number of
+  // (lower + upper + off-block) entries, ties in ascending row order
+  std::vector<uint16_t> order(n);
+  for (int p = 0; p < n_parts; ++p) {
+    const int32_t base = hpart[p], m = hpart[p + 1] - base;
+    std::vector<std::pair<int, int>> key(m);
+    for (int i = 0; i < m; ++i) {
+      const int32_t r = base + i;
+      const int len = (lrp[r + 1] - lrp[r]) + (urp[r + 1] - urp[r]) + (orp[r + 1] - orp[r]);
+      key[i] = {-len, i};
+    }
+    std::sort(key.begin(), key.end());
+    for (int i = 0; i < m; ++i) order[base + i] = (uint16_t)key[i].second;
+  }
+
   // halo: cells read through off-block entries, ascending; each entry's slot in it
   std::vector<int32_t> halo(oc.begin(), oc.end());
   std::sort(halo.begin(), halo.end());
@@ -626,6 +649,7 @@ df_status df_solver_create(int64_t n_cells, int64_t n_faces, const int32_t* owne
   up(&d.halo, halo);
   up(&d.cf_ptr, cf_ptr);
   up(&d.cf, cf);
+  up(&d.order, order);
   if (e == cudaSuccess) e = alloc(s, &d.lv, lc.size());
   if (e == cudaSuccess) e = alloc(s, &d.uv, uc.size());
   if (e == cudaSuccess) e = alloc(s, &d.ov, oc.size());
