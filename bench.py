@@ -260,6 +260,8 @@ def run_reference(args):
         return 0
     if args.mode == "solver":
         return run_reference_solver(args, world)
+    if args.mode == "propnet":
+        return run_reference_propnet(args, world)
     import synth
     from oracle import step as ostep
     w = synth.configs.WORKLOADS[args.workload]
@@ -309,6 +311,39 @@ def run_reference_solver(args, world):
             "cpu_baseline": {"value": v, "unit": unit, "kind": "oracle",
                              "cores": len(os.sched_getaffinity(0)),
                              "sample": f"the mesh recipe at 64^3 ({n} cells) per step"},
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_propnet(args, world):
+    """The FP64 oracle's property networks (Sec. 4.1 sizes, seeded weights) on 4096 cells of the
+    training-workload recipe per step."""
+    import synth
+    from oracle import propnet as opn
+    S = 4096
+    mech, _, T, p, Y = synth.configs.build("train30-1m", n_cells=S, field_seed=31)
+    h, props = opn.exact(mech, T, p, Y)
+    nets = [synth.make_propnet(w, mech.n, seed=41 + k, lam=0.1) for k, w in enumerate(PROPNET_WIDTHS.values())]
+    for _ in range(args.warmup):
+        for net in nets:
+            opn.infer(net, h, p, Y)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for net in nets:
+            opn.infer(net, h, p, Y)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    v = S / dt
+    unit = "cells/s"
+    line = {"impl": "reference",
+            "metric": "property-network cells/s (rho and T networks of Sec. 4.1 sizes, BF16)",
+            "value": v, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "train30-1m states", "sample_cells_per_step": S},
+            "cpu_baseline": {"value": v, "unit": unit, "kind": "oracle",
+                             "cores": len(os.sched_getaffinity(0)),
+                             "sample": f"{S} cells of the training-workload recipe per step, both networks"},
             "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
