@@ -119,6 +119,22 @@ df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
 /* Frees the state and its device memory (synchronises the device first). NULL is a no-op. */
 void df_state_destroy(df_state* s);
 
+/* One reaction step (a0-a10) of cells held in HOST memory: T [n_cells] and Y [n * ldY] are
+ * updated in place, p is read, cell_status (HOST, [n_cells], may be NULL) receives the DF_CELL_*
+ * bits. The cells go through the device in chunks of chunk_cells (0: a quarter of the cells, at
+ * least 65,536, at most the state's batch) with two device buffers: the upload of one chunk and
+ * the download of another overlap the step of a third (copies on two internal streams, the steps
+ * on `stream`), the GPU form of the paper's double buffering of data movement against
+ * computation (Sec. 3.3.3). Page-locked host memory lets the copies run asynchronously; with
+ * pageable memory CUDA stages them and they do not overlap.
+ * Stream-ordered: the work starts behind the work already on `stream`, and `stream` reaches the
+ * end of this call once every result is in host memory; synchronise it before reading T, Y or
+ * cell_status, and keep the host arrays alive until then. df_get_step_summary afterwards covers
+ * all chunks. Errors as df_chem_step. */
+df_status df_chem_step_host(df_state* s, int64_t n_cells, double dt, double* T, const double* p,
+                            double* Y, int64_t ldY, int32_t* cell_status, int64_t chunk_cells,
+                            void* stream);
+
 /* Real-fluid properties (a1-a4 without the network): rho [kg/m^3], h [J/kg], cp [J/(kg K)]
  * and Z of every cell. Any output pointer may be NULL and is then not written. */
 df_status df_real_fluid_props(df_state* s, int64_t n_cells, const double* T, const double* p,

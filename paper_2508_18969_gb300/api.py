@@ -96,6 +96,20 @@ class State:
                                            _ptr(T), _ptr(p), _ptr(Y), Y.stride(0), _ptr(status),
                                            _ptr(n_active), _stream(stream)))
 
+    def chem_step_host(self, T, p, Y, dt=None, status=None, chunk_cells=0, stream=None):
+        """df_chem_step_host: one reaction step of cells in host (CPU, ideally pinned) tensors,
+        in place on T and Y, pipelined through the device in chunks; stream-ordered on `stream`
+        (synchronise it before reading the results)."""
+        for t in (T, p, Y):
+            if t.device.type != "cpu" or t.dtype != torch.float64:
+                raise ValueError("T, p, Y must be float64 CPU tensors")
+        if status is not None and (status.device.type != "cpu" or status.dtype != torch.int32):
+            raise ValueError("status must be an int32 CPU tensor")
+        N = T.shape[0]
+        self._check(self._lib.df_chem_step_host(self.h, N, self.dt if dt is None else float(dt),
+                                                _ptr(T), _ptr(p), _ptr(Y), Y.stride(0),
+                                                _ptr(status), int(chunk_cells), _stream(stream)))
+
     def chem_source(self, T, p, Y, dt=None, status=None, n_active=None, want_T=True, stream=None):
         """(omega [n, N] FP64 kg/(m^3 s), T' [N] or None): df_chem_source; T, Y unchanged."""
         N = T.shape[0]

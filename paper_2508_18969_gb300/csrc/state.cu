@@ -123,6 +123,16 @@ void free_state(df_state* s) {
   for (auto p : s->col_scale) f(p);
   f(s->x); f(s->act[0]); f(s->act[1]); f(s->O); f(s->h0); f(s->rho_row); f(s->rstat);
   f(s->idx); f(s->cscr);
+  for (int b = 0; b < 2; ++b) {
+    f(s->hp.T[b]); f(s->hp.p[b]); f(s->hp.Y[b]); f(s->hp.st[b]);
+    if (s->hp.ev_in[b]) cudaEventDestroy(s->hp.ev_in[b]);
+    if (s->hp.ev_done[b]) cudaEventDestroy(s->hp.ev_done[b]);
+    if (s->hp.ev_out[b]) cudaEventDestroy(s->hp.ev_out[b]);
+  }
+  f(s->hp.total);
+  if (s->hp.ev_start) cudaEventDestroy(s->hp.ev_start);
+  if (s->hp.in) cudaStreamDestroy(s->hp.in);
+  if (s->hp.out) cudaStreamDestroy(s->hp.out);
 }
 
 cudaEvent_t prof_event(df_state* s) {
@@ -600,17 +610,26 @@ namespace {
 
 // The reaction step a0-a10 in batches of the state's capacity. With src (source terms) the
 // kernels leave T and Y untouched and write omega / T_new instead.
+// Reacting cells of a chunk added to the running total of df_chem_step_host.
+__global__ void add_count_kernel(const int64_t* __restrict__ c, int64_t* __restrict__ total,
+                                 int first) {
+  *total = (first ? 0 : *total) + *c;
+}
+
 df_status run_step(df_state* s, int64_t n_cells, double dt, double* T, const double* p, double* Y,
                    int64_t ldY, int32_t* cell_status, int64_t* n_active_out, cudaStream_t st,
-                   const Source* src) {
+                   const Source* src, bool keep_counters = false) {
   df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
   if (rc != DF_OK) return rc;
   if (!(std::fabs(dt - s->dt) <= 1e-12 * std::fabs(s->dt)))
     return fail(s, DF_ERR_DT_MISMATCH, "dt %.17g differs from the network's %.17g", dt, s->dt);
   DeviceGuard guard(s->device);
   if ((rc = ensure_compact(s, n_cells)) != DF_OK) return rc;
-  cudaError_t e = cudaMemsetAsync(s->d_flagged, 0, sizeof(int64_t), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_iters, 0, sizeof(int64_t), st);
+  cudaError_t e = cudaSuccess;
+  if (!keep_counters) {
+    e = cudaMemsetAsync(s->d_flagged, 0, sizeof(int64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_iters, 0, sizeof(int64_t), st);
+  }
   if (e == cudaSuccess) {
     ProfScope ps(s, "compact", st);
     e = launch_compact(n_cells, s->T_react, T, s->idx, s->d_count, cell_status, s->cscr, st);
@@ -650,6 +669,94 @@ df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const
                        void* stream) {
   return run_step(s, n_cells, dt, T, p, Y, ldY, cell_status, n_active_out, (cudaStream_t)stream,
                   nullptr);
+}
+
+df_status df_chem_step_host(df_state* s, int64_t n_cells, double dt, double* T, const double* p,
+                            double* Y, int64_t ldY, int32_t* cell_status, int64_t chunk_cells,
+                            void* stream) {
+  df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
+  if (rc != DF_OK || n_cells == 0) return rc;
+  if (chunk_cells < 0) return fail(s, DF_ERR_INVALID_ARG, "chunk_cells < 0");
+  if (!(std::fabs(dt - s->dt) <= 1e-12 * std::fabs(s->dt)))
+    return fail(s, DF_ERR_DT_MISMATCH, "dt %.17g differs from the network's %.17g", dt, s->dt);
+  DeviceGuard guard(s->device);
+  const int n = s->n;
+  // chunk: as asked, else a quarter of the cells (at least 65536, at most one batch)
+  int64_t chunk = chunk_cells > 0 ? chunk_cells
+                                   : std::max<int64_t>(65536, round_up((n_cells + 3) / 4, 128));
+  chunk = std::min(chunk, std::min(s->cap, n_cells));
+  df_state::HostPipe& hp = s->hp;
+  cudaError_t e = cudaSuccess;
+  if (hp.chunk < chunk) {
+    e = cudaDeviceSynchronize();
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      cudaFree(hp.T[b]); cudaFree(hp.p[b]); cudaFree(hp.Y[b]); cudaFree(hp.st[b]);
+      hp.T[b] = hp.p[b] = hp.Y[b] = nullptr;
+      hp.st[b] = nullptr;
+      e = dalloc(&hp.T[b], chunk);
+      if (e == cudaSuccess) e = dalloc(&hp.p[b], chunk);
+      if (e == cudaSuccess) e = dalloc(&hp.Y[b], (size_t)n * chunk);
+      if (e == cudaSuccess) e = dalloc(&hp.st[b], chunk);
+    }
+    if (e == cudaSuccess && !hp.total) e = dalloc(&hp.total, 1);
+    if (e == cudaSuccess && !hp.in) e = cudaStreamCreateWithFlags(&hp.in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !hp.out) e = cudaStreamCreateWithFlags(&hp.out, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      if (!hp.ev_in[b]) e = cudaEventCreateWithFlags(&hp.ev_in[b], cudaEventDisableTiming);
+      if (e == cudaSuccess && !hp.ev_done[b])
+        e = cudaEventCreateWithFlags(&hp.ev_done[b], cudaEventDisableTiming);
+      if (e == cudaSuccess && !hp.ev_out[b])
+        e = cudaEventCreateWithFlags(&hp.ev_out[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess && !hp.ev_start) e = cudaEventCreateWithFlags(&hp.ev_start, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      hp.chunk = 0;
+      return cuda_fail(s, e, "host-step buffers");
+    }
+    hp.chunk = chunk;
+  }
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int64_t ld = hp.chunk;
+  // the copies start behind the work already on the caller's stream
+  e = cudaEventRecord(hp.ev_start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.in, hp.ev_start, 0);
+  int64_t nchunks = 0;
+  for (int64_t c0 = 0; c0 < n_cells && e == cudaSuccess; c0 += chunk, ++nchunks) {
+    const int b = (int)(nchunks & 1);
+    const int64_t len = std::min(chunk, n_cells - c0);
+    // upload into buffer b once its previous download has finished
+    e = cudaStreamWaitEvent(hp.in, hp.ev_out[b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.T[b], T + c0, sizeof(double) * len, cudaMemcpyHostToDevice, hp.in);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.p[b], p + c0, sizeof(double) * len, cudaMemcpyHostToDevice, hp.in);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(hp.Y[b], sizeof(double) * ld, Y + c0, sizeof(double) * ldY,
+                            sizeof(double) * len, (size_t)n, cudaMemcpyHostToDevice, hp.in);
+    if (e == cudaSuccess) e = cudaEventRecord(hp.ev_in[b], hp.in);
+    // the step on the caller's stream
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, hp.ev_in[b], 0);
+    if (e != cudaSuccess) break;
+    rc = run_step(s, len, dt, hp.T[b], hp.p[b], hp.Y[b], ld, hp.st[b], nullptr, st, nullptr,
+                  nchunks > 0);
+    if (rc != DF_OK) return rc;
+    add_count_kernel<<<1, 1, 0, st>>>(s->d_count, hp.total, nchunks == 0 ? 1 : 0);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(hp.ev_done[b], st);
+    // download once the step is done
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.out, hp.ev_done[b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(T + c0, hp.T[b], sizeof(double) * len, cudaMemcpyDeviceToHost, hp.out);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(Y + c0, sizeof(double) * ldY, hp.Y[b], sizeof(double) * ld,
+                            sizeof(double) * len, (size_t)n, cudaMemcpyDeviceToHost, hp.out);
+    if (e == cudaSuccess && cell_status)
+      e = cudaMemcpyAsync(cell_status + c0, hp.st[b], sizeof(int32_t) * len, cudaMemcpyDeviceToHost, hp.out);
+    if (e == cudaSuccess) e = cudaEventRecord(hp.ev_out[b], hp.out);
+  }
+  // the caller's stream continues after the last download; the summary covers all chunks
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, hp.ev_out[(nchunks - 1) & 1], 0);
+  if (e == cudaSuccess && nchunks > 1) e = cudaStreamWaitEvent(st, hp.ev_out[nchunks & 1], 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_count, hp.total, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "host step");
 }
 
 df_status df_chem_source(df_state* s, int64_t n_cells, double dt, const double* T,

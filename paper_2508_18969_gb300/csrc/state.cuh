@@ -62,6 +62,18 @@ struct df_state {
   float4* d_gtab = nullptr;              // tabulated GELU (DF_GELU_TABLE)
   int* d_err = nullptr;                  // kernel error word
   int64_t* d_count = nullptr;            // reacting cells of the last step
+  // df_chem_step_host: device buffers of two chunks, copy streams and their events
+  struct HostPipe {
+    int64_t chunk = 0;
+    double* T[2] = {nullptr, nullptr};
+    double* p[2] = {nullptr, nullptr};
+    double* Y[2] = {nullptr, nullptr};
+    int32_t* st[2] = {nullptr, nullptr};
+    int64_t* total = nullptr;            // reacting cells summed over the chunks
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
+    cudaEvent_t ev_out[2] = {nullptr, nullptr}, ev_start = nullptr;
+  } hp;
   int64_t* d_flagged = nullptr;          // flagged cells of the last step
   int64_t* d_iters = nullptr;            // Newton iterations of the last step
   std::vector<float*> W32;               // FP32 weights, [N x Kp8] zero padded (SIMT)
