@@ -175,8 +175,8 @@ def weak_scaling_value(world, cells_per_rank, ms_max):
 # only for the kernel source the counters were taken on (SHA-256 prefix of the file): once the
 # kernel changes, the bench reports traffic as null until it is measured again.
 MEASURED_TRAFFIC = {
-    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e08b143876a7d2e", 3158.0),
-    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e08b143876a7d2e", 4751.0),
+    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "08c0caf062fdd599", 3158.0),
+    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "08c0caf062fdd599", 4756.0),
     ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 297.0),
     ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 549.0),
     # one block Gauss-Seidel sweep (gs_rhs_kernel + gs_sweep_kernel), per cell, FP64, 512 cells
@@ -368,6 +368,8 @@ def run_ours(args):
     st = df.State(mech, net, precision=prec, T_react=w.T_react, device=local, batch_cells=batch,
                   gelu_mode=gm)
     tiles = st.autotune(n_rows=min(N, batch)) if args.autotune else st.tiles()
+    # tile width per layer; "pair" marks layers on CTA pairs (256-row tiles, cta_group::2)
+    tiles = [f"{t & ~df.DF_TILE_PAIR} pair" if t & df.DF_TILE_PAIR else str(t) for t in tiles]
     Td = torch.tensor(T, device=dev)
     pd = torch.tensor(p, device=dev)
     Yd = torch.tensor(Y, device=dev).contiguous()

@@ -251,16 +251,20 @@ df_status df_graph_launch(df_graph* g, void* stream);
 void df_graph_destroy(df_graph* g);
 
 /* ---- tile-width autotuning of the tensor-core layers ----
- * df_autotune times every compiled tile width (64, 128, 160, 224, 256 output columns per CTA
- * for hidden layers, 32 and 64 for the read-out) of each network layer on n_rows rows of the
+ * df_autotune times every compiled tile (64, 128, 160, 224, 256 output columns per CTA for
+ * hidden layers, and 160, 224, 256 on CTA pairs for hidden layers of more than one k-block of
+ * 64 BF16 / 128 FP8 inputs; 32 and 64 for the read-out) of each network layer on n_rows rows of the
  * state's own buffers (<= 0 or above the batch capacity: the capacity), keeps the fastest and
  * re-encodes the layer. cache_path (may be NULL) names a text file of earlier choices, one line
  * per (device, precision, layer shape); known shapes are taken from it without timing and new
  * ones are appended. Synchronises `stream`. A no-op for DF_FP32 states. The tiling changes
  * neither the arithmetic nor its order, so results are bit-identical before and after; call
  * it before capturing graphs (a graph keeps the launch parameters it recorded).
- * df_get_tiles reports the tile width of each layer (0 for SIMT layers) in bn[0..max_layers)
- * and the number of layers in *n_layers. */
+ * df_get_tiles reports the tile of each layer (0 for SIMT layers) in bn[0..max_layers): its
+ * width, | DF_TILE_PAIR when the layer runs on CTA pairs (two CTAs of a cluster share one
+ * 256-row tile through cta_group::2 MMAs, each holding half of the tile's weight rows), and
+ * the number of layers in *n_layers. */
+#define DF_TILE_PAIR 0x1000
 df_status df_autotune(df_state* s, int64_t n_rows, const char* cache_path, void* stream);
 df_status df_get_tiles(df_state* s, int32_t* bn, int32_t max_layers, int32_t* n_layers);
 

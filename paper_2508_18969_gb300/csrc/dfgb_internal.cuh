@@ -208,6 +208,7 @@ struct TcLayer {
   const float4* gtab = nullptr;  // tabulated GELU (DF_GELU_TABLE) or NULL for the tanh form
   int ksplit = 1;        // split-K (plain mode): split s covers k-blocks [s kbs, (s+1) kbs) and
   int64_t split_rows = 0;  // stores its partial product at output rows + s * split_rows
+  bool pair = false;     // computed by CTA pairs (cta_group::2): 256-row tiles, tmB box BN/2
 };
 bool tc_encode_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
                   uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,
@@ -221,7 +222,7 @@ cudaError_t launch_tc_gemm(const TcLayer& L, const RowMap& rows, int num_sms, in
 cudaError_t prepare_tc(const TcLayer& L);
 // Pipeline stages of the kernel instance with this tile width and output kind, and the
 // number of epilogue warps per TMEM lane quarter (for the host's choice of tile width).
-int tc_stages(int BN, int out_kind);
+int tc_stages(int BN, int out_kind, bool pair = false);
 int tc_epi_warps_per_quarter();
 
 }  // namespace dfgb

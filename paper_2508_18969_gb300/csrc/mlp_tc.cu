@@ -129,11 +129,12 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
          ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = BN.
-template <bool FP8, int BN>
+// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128 (256 for a CTA pair),
+// N = BN.
+template <bool FP8, int BN, int MROWS = BM>
 __device__ constexpr uint32_t idesc() {
   return (1u << 4) | (FP8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(BN >> 3) << 17) |
-         ((uint32_t)(BM >> 4) << 24);
+         ((uint32_t)(MROWS >> 4) << 24);
 }
 
 template <bool FP8>
@@ -157,6 +158,108 @@ __device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t a, uint64_t b
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// ---- CTA pairs (cta_group::2) ----
+// Two CTAs of a cluster compute one 256-row tile: each holds its own 128 rows of A and half of
+// the tile's BN rows of W in shared memory, the even CTA issues M = 256 MMAs that read both
+// CTAs' operands and write each CTA's 128 accumulator rows into that CTA's tensor memory. Each
+// SM then streams 128 + BN/2 operand rows per k-block for BN columns of MMA work instead of
+// 128 + BN.
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Shared::cluster address of the same shared-memory offset in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_shared(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+
+// Arrival on a barrier of the peer CTA (release at cluster scope).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on a barrier that also receives arrivals from the peer CTA.
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
+                                                  volatile int* abort, int* err) {
+  if (mbar_try_cluster(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try_cluster(bar, parity)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitBudget) {
+      atomicOr(err, kErrTimeout);
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+// TMA load into this CTA's shared memory whose completion is counted on a barrier of either
+// CTA of the pair (bar_cluster: a shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map,
+                                                 uint32_t bar_cluster, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar_cluster)
+      : "memory");
+}
+
+template <bool FP8>
+__device__ __forceinline__ void mma_issue_pair(uint32_t dtmem, uint64_t a, uint64_t b,
+                                               uint32_t id, uint32_t accum) {
+  if (FP8) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(id), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(id), "r"(accum)
+        : "memory");
+  }
+}
+
+// Arrives on the barrier at this offset in both CTAs of the pair once the MMAs issued so far
+// have completed.
+__device__ __forceinline__ void mma_commit_pair_both(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar), "h"((uint16_t)3)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_pair_local(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
       : "memory");
 }
 
@@ -228,12 +331,13 @@ __device__ __forceinline__ float2 gelu_fast2(float2 x) {
 
 constexpr int out_bytes(int outk) { return outk == kXF32 ? 4 : (outk == kXBF16 ? 2 : 1); }
 
-template <int BN, int OUTK>
+template <int BN, int OUTK, bool PAIR = false>
 struct Cfg {
   // per warp: two staging buffers of 32 rows x 32 columns (the GELU' of kModeStoreG is BF16,
   // no wider than the output)
   static constexpr int kStageOut = 2 * 32 * 32 * out_bytes(OUTK);
-  static constexpr int kStageBytes = (BM + BN) * kRowBytes;
+  static constexpr int kBRows = PAIR ? BN / 2 : BN;   // rows of W this CTA holds per stage
+  static constexpr int kStageBytes = (BM + kBRows) * kRowBytes;
   static constexpr int kStages0 = (kSmemLimit - 2048 - kEpiWarps * kStageOut) / kStageBytes;
   static constexpr int kStages = kStages0 > 8 ? 8 : kStages0;
   static constexpr int kAccStride = (BN + 31) / 32 * 32;
@@ -415,17 +519,19 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const Tc
   }
 }
 
-template <bool FP8, int BN, int OUTK, int ACT, bool SCALE, int MODE>
+template <bool FP8, int BN, int OUTK, int ACT, bool SCALE, int MODE, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
     const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmG, TcArgs g) {
-  using C = Cfg<BN, OUTK>;
+  using C = Cfg<BN, OUTK, PAIR>;
   // a 32-column epilogue chunk is stored as one TMA box, so chunks must not straddle tiles
   static_assert(BN % 32 == 0, "tile width must be a multiple of 32");
+  // each CTA of a pair holds whole 8-row swizzle atoms of W
+  static_assert(!PAIR || (BN / 2) % 8 == 0, "paired tile width must split into 8-row groups");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;                                   // kStages x 16 KB
-  uint8_t* sB = smem + C::kStages * BM * kRowBytes;     // kStages x BN*128 B
+  uint8_t* sB = smem + C::kStages * BM * kRowBytes;     // kStages x kBRows*128 B
   uint8_t* sOut = smem + C::kStages * C::kStageBytes;  // kEpiWarps x kStageOut
   uint64_t* bars = (uint64_t*)(sOut + kEpiWarps * C::kStageOut);
   // bars: full[S], empty[S], tfull[2], tempty[2], drain
@@ -436,6 +542,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * C::kStages;
   const uint32_t tfull0 = empty0 + 8 * C::kStages, tempty0 = tfull0 + 16;
   const uint32_t drain = tempty0 + 16;
+  // In a pair, the even CTA (rank 0) owns the full and accumulator-empty barriers the MMAs
+  // wait on: both CTAs' loads complete on its full barriers, both CTAs' epilogues arrive on
+  // its tempty barriers. Each CTA's empty and tfull barriers receive the MMA commits.
+  const uint32_t rank = PAIR ? cluster_rank() : 0;
 
   if (threadIdx.x == 0) {
     abort_sh = 0;
@@ -445,33 +555,50 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull0 + 8 * a, 1);
-      mbar_init(tempty0 + 8 * a, kEpiWarps);
+      mbar_init(tempty0 + 8 * a, PAIR ? 2 * kEpiWarps : kEpiWarps);
     }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_base_sh)),
-                 "r"((uint32_t)C::kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (PAIR) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(&tmem_base_sh)),
+                   "r"((uint32_t)C::kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(&tmem_base_sh)),
+                   "r"((uint32_t)C::kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // the peer's barriers are initialised before any use
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
   volatile int* abort = &abort_sh;
 
   const int64_t M = valid_rows(g.rows);
   const int64_t tiles_m = (M + BM - 1) / BM;
+  // work items: (split, m tile, n tile), or for a pair (split, pair of m tiles, n tile)
+  const int64_t units_m = PAIR ? (tiles_m + 1) / 2 : tiles_m;
   const int tiles_n = (g.N + BN - 1) / BN;
-  const int64_t tiles_mn = tiles_m * tiles_n;
-  const int64_t ntiles = tiles_mn * g.ksplit;   // work item t = (split, m tile, n tile)
+  const int64_t tiles_mn = units_m * tiles_n;
+  const int64_t ntiles = tiles_mn * g.ksplit;
   const int kblocks = (g.K * (FP8 ? 1 : 2) + kRowBytes - 1) / kRowBytes;
   const int kelems = kRowBytes / (FP8 ? 1 : 2);
   const int kbs = (kblocks + g.ksplit - 1) / g.ksplit;   // k-blocks per split (host: none empty)
+  const int64_t t_first = PAIR ? (blockIdx.x >> 1) : blockIdx.x;
+  const int64_t t_step = PAIR ? (gridDim.x >> 1) : gridDim.x;
+  // first row of this CTA's part of work item tt
+  auto tile_m0 = [&](int64_t tt) -> int64_t {
+    return PAIR ? ((tt / tiles_n) * 2 + rank) * BM : (tt / tiles_n) * BM;
+  };
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
@@ -479,39 +606,65 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
     uint32_t it = 0;
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int64_t t = t_first; t < ntiles && ok; t += t_step) {
       const int64_t tt = t % tiles_mn;
       const int kb0 = (int)(t / tiles_mn) * kbs, kb1 = min(kblocks, kb0 + kbs);
-      const int m0 = (int)((tt / tiles_n) * BM);
-      const int n0 = (int)(tt % tiles_n) * BN;
+      const int m0 = (int)tile_m0(tt);
+      const int n0 = (int)(tt % tiles_n) * BN + (int)rank * C::kBRows;
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % C::kStages;
         const uint32_t ph = (it / C::kStages) & 1;
         if (!mbar_wait(empty0 + 8 * s, ph ^ 1, abort, g.err)) { ok = false; break; }
-        mbar_arrive_expect_tx(full0 + 8 * s, C::kStageBytes);
-        tma_load_2d(smem_u32(sA + s * BM * kRowBytes), &tmA, full0 + 8 * s, kb * kelems, m0);
-        tma_load_2d(smem_u32(sB + s * BN * kRowBytes), &tmB, full0 + 8 * s, kb * kelems, n0);
+        const uint32_t dA = smem_u32(sA + s * BM * kRowBytes);
+        const uint32_t dB = smem_u32(sB + s * C::kBRows * kRowBytes);
+        if constexpr (PAIR) {
+          const uint32_t full_leader = map_shared(full0 + 8 * s, 0);
+          if (rank == 0) mbar_arrive_expect_tx(full0 + 8 * s, 2 * C::kStageBytes);
+          tma_load_2d_pair(dA, &tmA, full_leader, kb * kelems, m0);
+          tma_load_2d_pair(dB, &tmB, full_leader, kb * kelems, n0);
+        } else {
+          mbar_arrive_expect_tx(full0 + 8 * s, C::kStageBytes);
+          tma_load_2d(dA, &tmA, full0 + 8 * s, kb * kelems, m0);
+          tma_load_2d(dB, &tmB, full0 + 8 * s, kb * kelems, n0);
+        }
       }
     }
-    // Drain: the last issued load of every stage must have landed before the CTA exits.
     const uint32_t issued = it;
-    for (uint32_t j = (issued > (uint32_t)C::kStages ? issued - C::kStages : 0); j < issued; ++j) {
-      const int s = j % C::kStages;
-      const uint32_t ph = (j / C::kStages) & 1;
-      const long long t0 = clock64();
-      while (!mbar_try(full0 + 8 * s, ph) && clock64() - t0 < kWaitBudget) {
+    const uint32_t first = issued > (uint32_t)C::kStages ? issued - C::kStages : 0;
+    if (!PAIR || rank == 0) {
+      // Drain: the last issued load of every stage must have landed before the CTA exits (a
+      // pair's full barriers, on the even CTA, count the odd CTA's loads too).
+      for (uint32_t j = first; j < issued; ++j) {
+        const int s = j % C::kStages;
+        const uint32_t ph = (j / C::kStages) & 1;
+        const long long t0 = clock64();
+        while (!mbar_try(full0 + 8 * s, ph) && clock64() - t0 < kWaitBudget) {
+        }
       }
     }
-  } else if (warp == 1 && lane == 0) {
+    if constexpr (PAIR) {
+      // Producer tail: the MMA commits that free the last stages arrive on this CTA's empty
+      // barriers from the even CTA; they must have arrived before this CTA exits.
+      for (uint32_t j = first; j < issued; ++j) {
+        const int s = j % C::kStages;
+        const uint32_t ph = (j / C::kStages) & 1;
+        const long long t0 = clock64();
+        while (!mbar_try_cluster(empty0 + 8 * s, ph) && clock64() - t0 < kWaitBudget) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0 && rank == 0) {
     // ---------------- MMA issuer ----------------
-    constexpr uint32_t id = idesc<FP8, BN>();
+    constexpr uint32_t id = idesc<FP8, BN, PAIR ? 2 * BM : BM>();
     uint32_t it = 0, j = 0;
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+    for (int64_t t = t_first; t < ntiles && ok; t += t_step, ++j) {
       const int kb0 = (int)(t / tiles_mn) * kbs, kb1 = min(kblocks, kb0 + kbs);
       const int a = j & 1;
       const uint32_t aph = (j >> 1) & 1;
-      if (!mbar_wait(tempty0 + 8 * a, aph ^ 1, abort, g.err)) break;
+      if (PAIR ? !mbar_wait_cluster(tempty0 + 8 * a, aph ^ 1, abort, g.err)
+               : !mbar_wait(tempty0 + 8 * a, aph ^ 1, abort, g.err))
+        break;
       tc_fence_after();
       const uint32_t dt = tmem + a * C::kAccStride;
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
@@ -520,16 +673,26 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
         if (!mbar_wait(full0 + 8 * s, ph, abort, g.err)) { ok = false; break; }
         tc_fence_after();
         const uint64_t da = desc_sw128(smem_u32(sA + s * BM * kRowBytes));
-        const uint64_t db = desc_sw128(smem_u32(sB + s * BN * kRowBytes));
+        const uint64_t db = desc_sw128(smem_u32(sB + s * C::kBRows * kRowBytes));
 #pragma unroll
-        for (int kk = 0; kk < kRowBytes / 32; ++kk)  // 32 bytes of K per instruction
-          mma_issue<FP8>(dt, da + 2 * kk, db + 2 * kk, id, (kb != kb0 || kk) ? 1u : 0u);
-        mma_commit(empty0 + 8 * s);  // frees the stage when these MMAs have read it
+        for (int kk = 0; kk < kRowBytes / 32; ++kk) {  // 32 bytes of K per instruction
+          if constexpr (PAIR)
+            mma_issue_pair<FP8>(dt, da + 2 * kk, db + 2 * kk, id, (kb != kb0 || kk) ? 1u : 0u);
+          else
+            mma_issue<FP8>(dt, da + 2 * kk, db + 2 * kk, id, (kb != kb0 || kk) ? 1u : 0u);
+        }
+        // frees the stage (in both CTAs of a pair) when these MMAs have read it
+        if constexpr (PAIR) mma_commit_pair_both(empty0 + 8 * s);
+        else mma_commit(empty0 + 8 * s);
       }
-      if (ok) mma_commit(tfull0 + 8 * a);
+      if (ok) {
+        if constexpr (PAIR) mma_commit_pair_both(tfull0 + 8 * a);
+        else mma_commit(tfull0 + 8 * a);
+      }
     }
     // Drain: every MMA issued by this thread completes before TMEM is released.
-    mma_commit(drain);
+    if constexpr (PAIR) mma_commit_pair_local(drain);
+    else mma_commit(drain);
     const long long t0 = clock64();
     while (!mbar_try(drain, 0) && clock64() - t0 < kWaitBudget) {
     }
@@ -544,21 +707,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmO) : "memory");
     }
     uint32_t j = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+    for (int64_t t = t_first; t < ntiles; t += t_step, ++j) {
       const int a = j & 1;
       const uint32_t aph = (j >> 1) & 1;
       if (!mbar_wait(tfull0 + 8 * a, aph, abort, g.err)) break;
       tc_fence_after();
       const int64_t tt = t % tiles_mn;
+      const int64_t mt = tile_m0(tt);
       // row of the output: the tile's rows, shifted to this split's partial product
-      const int64_t m0 = (tt / tiles_n) * BM + q * 32 + (t / tiles_mn) * g.split_rows;
+      const int64_t m0 = mt + q * 32 + (t / tiles_mn) * g.split_rows;
       const int n0 = (int)(tt % tiles_n) * BN;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + a * C::kAccStride;
       // chunks c = 32 slot + kChunkStride i; TMEM loads run one chunk ahead of the math,
       // except in kModeStoreG, whose two stores per chunk leave no registers for a second
-      // chunk in flight
+      // chunk in flight. The odd CTA of a pair whose m tile lies past the rows stores nothing.
       uint32_t r0[32], r1[32];
-      int c0 = 32 * slot;
+      int c0 = (PAIR && mt >= M) ? BN : 32 * slot;
       if constexpr (MODE == kModeStoreG) {
         for (; c0 < BN; c0 += kChunkStride) {
           tmem_ld32(tbase + c0, r0);
@@ -583,7 +747,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(tempty0 + 8 * a);
+      if (lane == 0) {
+        if (PAIR && rank != 0) mbar_arrive_cluster(map_shared(tempty0 + 8 * a, 0));
+        else mbar_arrive(tempty0 + 8 * a);
+      }
     }
     // the tensor stores must have read shared memory (and be complete) before the CTA exits
     if (lane == 0) bulk_wait_all();
@@ -591,11 +758,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
   __syncwarp();
   tc_fence_before();
   __syncthreads();
+  // a pair frees its tensor memory together, once neither CTA reads or writes it any more
+  if constexpr (PAIR) cluster_sync();
   tc_fence_after();
   if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)C::kTmemCols)
-                 : "memory");
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"((uint32_t)C::kTmemCols)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"((uint32_t)C::kTmemCols)
+                   : "memory");
   }
 }
 
@@ -618,34 +792,80 @@ EncodeTiledFn encode_fn() {
 }
 
 // Opts the kernel instance into its dynamic shared memory, once per device.
-template <bool FP8, int BN, int OUTK, int ACT, int MODE>
-cudaError_t tc_attr() {
+template <bool FP8, int BN, int OUTK, int ACT, int MODE, bool PAIR>
+cudaError_t tc_attr(int* max_clusters) {
   static bool attr_done[64] = {false};
+  static int clusters[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_done[dev]) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<FP8, BN, OUTK, ACT, FP8, MODE>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN, OUTK>::kSmemBytes);
+    using C = Cfg<BN, OUTK, PAIR>;
+    auto kern = tc_gemm_kernel<FP8, BN, OUTK, ACT, FP8, MODE, PAIR>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
+    if (PAIR) {
+      // how many CTA pairs fit on the GPU at once: a persistent grid of more would leave the
+      // excess pairs to a second wave
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 2;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(2, 1, 1);
+      cfg.blockDim = dim3(kThreads, 1, 1);
+      cfg.dynamicSmemBytes = C::kSmemBytes;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      e = cudaOccupancyMaxActiveClusters(&n, (const void*)kern, &cfg);
+      if (e != cudaSuccess) return e;
+      if (n <= 0) return cudaErrorInvalidConfiguration;
+      clusters[dev] = n;
+    }
     attr_done[dev] = true;
   }
+  if (max_clusters) *max_clusters = clusters[dev];
   return cudaSuccess;
 }
 
-template <bool FP8, int BN, int OUTK, int ACT, int MODE = kModePlain>
+template <bool FP8, int BN, int OUTK, int ACT, int MODE = kModePlain, bool PAIR = false>
 cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream_t st) {
-  using C = Cfg<BN, OUTK>;
+  using C = Cfg<BN, OUTK, PAIR>;
   constexpr bool SCALE = FP8;
-  auto kern = tc_gemm_kernel<FP8, BN, OUTK, ACT, SCALE, MODE>;
-  cudaError_t e0 = tc_attr<FP8, BN, OUTK, ACT, MODE>();
+  auto kern = tc_gemm_kernel<FP8, BN, OUTK, ACT, SCALE, MODE, PAIR>;
+  int max_clusters = 0;
+  cudaError_t e0 = tc_attr<FP8, BN, OUTK, ACT, MODE, PAIR>(&max_clusters);
   if (e0 != cudaSuccess) return e0;
   if (num_sms <= 0) return cudaSuccess;  // attribute set-up only
-  const int64_t tiles = ((a.rows.nmax + BM - 1) / BM) * ((L.N + BN - 1) / BN) * a.ksplit;
-  const unsigned grid = (unsigned)(tiles < num_sms ? (tiles > 0 ? tiles : 1) : num_sms);
-  kern<<<grid, kThreads, C::kSmemBytes, st>>>(L.tmA, L.tmB, L.tmO, L.mode == kModeStoreG ? L.tmG : L.tmO, a);
-  return cudaGetLastError();
+  const CUtensorMap& tmG = L.mode == kModeStoreG ? L.tmG : L.tmO;
+  const int64_t tiles_n = (L.N + BN - 1) / BN;
+  if constexpr (PAIR) {
+    if (a.ksplit > 1) return cudaErrorInvalidValue;
+    const int64_t units = ((a.rows.nmax + 2 * BM - 1) / (2 * BM)) * tiles_n;
+    const int64_t cap = std::min<int64_t>(max_clusters, num_sms / 2);
+    const int64_t nc = std::max<int64_t>(1, std::min<int64_t>(units, cap));
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * nc), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = C::kSmemBytes;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, L.tmA, L.tmB, L.tmO, tmG, a);
+  } else {
+    const int64_t tiles = ((a.rows.nmax + BM - 1) / BM) * tiles_n * a.ksplit;
+    const unsigned grid = (unsigned)(tiles < num_sms ? (tiles > 0 ? tiles : 1) : num_sms);
+    kern<<<grid, kThreads, C::kSmemBytes, st>>>(L.tmA, L.tmB, L.tmO, tmG, a);
+    return cudaGetLastError();
+  }
 }
 
 // Hidden layers: GELU, output in the input precision. Last layer: linear, FP32 output.
@@ -672,6 +892,26 @@ cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStrea
       case 160: return launch_bn<false, 160, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
       case 224: return launch_bn<false, 224, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
       case 256: return launch_bn<false, 256, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (L.pair) {
+    // CTA pairs: hidden layers with more than one k-block (the tile widths of tc_pair_widths)
+    if (!L.gelu || a.ksplit > 1) return cudaErrorInvalidValue;
+    if (L.gtab) {
+      if (FP8 || L.out_kind != kXBF16) return cudaErrorInvalidValue;
+      switch (L.BN) {
+        case 160: return launch_bn<false, 160, kXBF16, kActTable, kModePlain, true>(L, a, num_sms, st);
+        case 224: return launch_bn<false, 224, kXBF16, kActTable, kModePlain, true>(L, a, num_sms, st);
+        case 256: return launch_bn<false, 256, kXBF16, kActTable, kModePlain, true>(L, a, num_sms, st);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+    if (L.out_kind != HID) return cudaErrorInvalidValue;
+    switch (L.BN) {
+      case 160: return launch_bn<FP8, 160, HID, kActTanh, kModePlain, true>(L, a, num_sms, st);
+      case 224: return launch_bn<FP8, 224, HID, kActTanh, kModePlain, true>(L, a, num_sms, st);
+      case 256: return launch_bn<FP8, 256, HID, kActTanh, kModePlain, true>(L, a, num_sms, st);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -777,9 +1017,12 @@ bool tc_encode_out(TcLayer& L, uint64_t rows, char* err, size_t errlen) {
   return true;
 }
 
-int tc_stages(int BN, int out_kind) {
+int tc_stages(int BN, int out_kind, bool pair) {
   auto pick = [&](auto bn) -> int {
     constexpr int B = decltype(bn)::value;
+    if (pair)
+      return out_kind == kXF32 ? Cfg<B, kXF32, true>::kStages
+             : out_kind == kXBF16 ? Cfg<B, kXBF16, true>::kStages : Cfg<B, kXFP8, true>::kStages;
     return out_kind == kXF32 ? Cfg<B, kXF32>::kStages
            : out_kind == kXBF16 ? Cfg<B, kXBF16>::kStages : Cfg<B, kXFP8>::kStages;
   };

@@ -36,37 +36,51 @@ df_status cuda_fail(df_state* s, cudaError_t e, const char* where) {
               cudaGetErrorString(e));
 }
 
-// Tile width of a layer: hidden layers from the compiled set {64, 128, 160, 224, 256}, the
-// read-out layer from {32, 64}. Cost per layer, fitted to measured tcgen05 times on this GPU:
+// Tile of a tensor-core layer: BN output columns per CTA from {64, 128, 160, 224, 256} for
+// hidden layers and {32, 64} for the read-out; hidden layers of more than one k-block may also
+// run on CTA pairs (BN from {160, 224, 256} | DF_TILE_PAIR: 256-row tiles, each CTA holding
+// half of the tile's weight rows). Cost per layer, fitted to measured tcgen05 times on this GPU:
 //   * one k-block (K <= 64 BF16, 128 FP8): the epilogue is the work; each tile costs the
 //     32-column chunks its busiest epilogue warp handles, plus half a chunk of fixed cost;
-//   * longer K: the MMAs are the work; each tile costs BN + 128 columns, x1.3 when the tile
-//     leaves the TMA ring fewer than four stages.
-int pick_bn(int N, int K, bool hidden, int out_kind) {
+//   * longer K: a tile costs the larger of its MMA work (0.97 BN) and the operand rows an SM
+//     streams per k-block (128 + BN/2 on a pair; 0.8 (128 + BN) on a single CTA, whose loads
+//     stream faster per row), x1.25 when the tile leaves the TMA ring fewer than four stages.
+//     On the 1600 -> 800 layer of 2^20 rows this orders the measured times of single 160, 224
+//     and pair 160, 224, 256 tiles (2.15, 1.91, 1.82, 1.73, 1.75 ms) within 7 %.
+int pick_tile(int N, int K, bool hidden, int out_kind, bool allow_pair) {
   static const int hid[] = {256, 224, 160, 128, 64};
   static const int last[] = {64, 32};
+  static const int paired[] = {256, 224, 160};
   const int* cand = hidden ? hid : last;
   const int nc = hidden ? 5 : 2;
   const bool one_kblock = K * (out_kind == kXFP8 ? 1 : 2) <= 128;
   const int epq = tc_epi_warps_per_quarter();
   int best = cand[nc - 1];
   double best_cost = 1e300;
-  for (int i = 0; i < nc; ++i) {
-    const int bn = cand[i];
+  auto consider = [&](int bn, bool pair) {
     const double tiles = (double)((N + bn - 1) / bn);
     double cost;
     if (one_kblock) {
       const int chunks = (bn + 31) / 32;
       cost = tiles * ((chunks + epq - 1) / epq + 0.5);
     } else {
-      cost = tiles * (bn + 128) * (tc_stages(bn, out_kind) < 4 ? 1.3 : 1.0);
+      const double rows = pair ? 128.0 + bn / 2 : 0.8 * (128.0 + bn);
+      cost = tiles * std::max<double>(0.97 * bn, rows) *
+             (tc_stages(bn, out_kind, pair) < 4 ? 1.25 : 1.0);
     }
     if (cost < best_cost) {
       best_cost = cost;
-      best = bn;
+      best = pair ? (bn | DF_TILE_PAIR) : bn;
     }
-  }
+  };
+  for (int i = 0; i < nc; ++i) consider(cand[i], false);
+  if (hidden && allow_pair && !one_kblock)
+    for (int bn : paired) consider(bn, true);
   return best;
+}
+
+int pick_bn(int N, int K, bool hidden, int out_kind) {
+  return pick_tile(N, K, hidden, out_kind, false);
 }
 
 __global__ void cast_rows_kernel(int64_t rows, int K, const float* __restrict__ in,
@@ -531,10 +545,15 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
       TcLayer T{};
       T.N = s->widths[l + 1];
       T.K = s->widths[l];
-      T.BN = pick_bn(T.N, T.K, !last, last ? kXF32 : xk);
+      const int tile = pick_tile(T.N, T.K, !last, last ? kXF32 : xk, true);
+      T.BN = tile & ~DF_TILE_PAIR;
+      T.pair = (tile & DF_TILE_PAIR) != 0;
       if (const char* env = getenv("DFGB_BN")) {  // hidden-layer tile-width override (sweeps)
         const int v = atoi(env);
-        if (!last && (v == 64 || v == 128 || v == 160 || v == 224 || v == 256)) T.BN = v;
+        if (!last && (v == 64 || v == 128 || v == 160 || v == 224 || v == 256)) {
+          T.BN = v;
+          T.pair = false;
+        }
       }
       T.bias = s->bias[l];
       T.col_scale = s->col_scale[l];
@@ -551,7 +570,8 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
       if (!tc_encode_2d(&T.tmA, Abase, (int)eb, (uint64_t)T.K, (uint64_t)s->cap,
                         (uint64_t)lda * eb, boxk, 128, emsg, sizeof emsg) ||
           !tc_encode_2d(&T.tmB, s->Wlp[l], (int)eb, (uint64_t)T.K, (uint64_t)T.N,
-                        (uint64_t)s->Kp8[l] * eb, boxk, (uint32_t)T.BN, emsg, sizeof emsg) ||
+                        (uint64_t)s->Kp8[l] * eb, boxk, (uint32_t)(T.pair ? T.BN / 2 : T.BN),
+                        emsg, sizeof emsg) ||
           !tc_encode_out(T, (uint64_t)s->cap, emsg, sizeof emsg)) {
         free_state(s);
         delete s;
@@ -1064,16 +1084,20 @@ df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const 
 
 namespace {
 
-// Re-encodes layer l's weight map for tile width bn (the only part of a layer that depends on
-// it) and sets the kernel instance's attributes.
-df_status retile(df_state* s, int l, int bn) {
+// Re-encodes layer l's weight map for tile `tile` (BN, | DF_TILE_PAIR for CTA pairs: the only
+// part of a layer that depends on it) and sets the kernel instance's attributes.
+df_status retile(df_state* s, int l, int tile) {
   TcLayer& T = s->tcl[l];
   const size_t eb = elem_of(s->precision);
+  const int bn = tile & ~DF_TILE_PAIR;
+  const bool pair = (tile & DF_TILE_PAIR) != 0;
   char emsg[256];
   if (!tc_encode_2d(&T.tmB, s->Wlp[l], (int)eb, (uint64_t)T.K, (uint64_t)T.N,
-                    (uint64_t)s->Kp8[l] * eb, 128 / (uint32_t)eb, (uint32_t)bn, emsg, sizeof emsg))
+                    (uint64_t)s->Kp8[l] * eb, 128 / (uint32_t)eb, (uint32_t)(pair ? bn / 2 : bn),
+                    emsg, sizeof emsg))
     return fail(s, DF_ERR_CUDA, "%s", emsg);
   T.BN = bn;
+  T.pair = pair;
   cudaError_t e = prepare_tc(T);
   return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "kernel attributes");
 }
@@ -1130,10 +1154,12 @@ df_status df_autotune(df_state* s, int64_t n_rows, const char* cache_path, void*
     int chosen = 0;
     for (auto& kv : cache)
       if (kv.first == key) chosen = kv.second;
-    static const int hid[] = {64, 128, 160, 224, 256};
+    static const int hid[] = {64, 128, 160, 224, 256, 160 | DF_TILE_PAIR, 224 | DF_TILE_PAIR,
+                              256 | DF_TILE_PAIR};
     static const int rd[] = {32, 64};
+    const bool one_kblock = s->tcl[l].K * (int)elem_of(s->precision) <= 128;
     const int* cand = last ? rd : hid;
-    const int nc = last ? 2 : 5;
+    const int nc = last ? 2 : (one_kblock ? 5 : 8);
     bool known = false;
     for (int i = 0; i < nc; ++i) known = known || cand[i] == chosen;
     if (!known) {
@@ -1173,7 +1199,8 @@ df_status df_autotune(df_state* s, int64_t n_rows, const char* cache_path, void*
 df_status df_get_tiles(df_state* s, int32_t* bn, int32_t max_layers, int32_t* n_layers) {
   if (!s || !n_layers || (max_layers > 0 && !bn)) return fail(s, DF_ERR_INVALID_ARG, "bad arguments");
   *n_layers = s->L;
-  for (int l = 0; l < s->L && l < max_layers; ++l) bn[l] = s->tcl.empty() ? 0 : s->tcl[l].BN;
+  for (int l = 0; l < s->L && l < max_layers; ++l)
+    bn[l] = s->tcl.empty() ? 0 : (s->tcl[l].BN | (s->tcl[l].pair ? DF_TILE_PAIR : 0));
   return DF_OK;
 }
 

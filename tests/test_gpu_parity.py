@@ -391,7 +391,10 @@ def test_autotune_keeps_results_and_caches(df, prec, tmp_path):
     cache = tmp_path / "tiles.txt"
     after = st.autotune(n_rows=4096, cache_path=cache)
     assert len(after) == net.n_layers
-    assert all(b in (64, 128, 160, 224, 256) for b in after[:-1]) and after[-1] in (32, 64)
+    paired = [b & ~df.DF_TILE_PAIR for b in after[:-1] if b & df.DF_TILE_PAIR]
+    single = [b for b in after[:-1] if not b & df.DF_TILE_PAIR]
+    assert all(b in (160, 224, 256) for b in paired) and after[-1] in (32, 64)
+    assert all(b in (64, 128, 160, 224, 256) for b in single)
     T2, Y2 = dev(T), dev(Y)
     st.chem_step(T2, dev(p), Y2)
     torch.cuda.synchronize()
@@ -403,6 +406,37 @@ def test_autotune_keeps_results_and_caches(df, prec, tmp_path):
     assert st2.autotune(n_rows=4096, cache_path=cache) == after
     assert cache.read_text().strip().splitlines() == lines
     print(f"{prec}: tiles {before} -> {after}")
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8", "bf16-table"])
+def test_cta_pair_tiles_match_single_cta_tiles(df, prec, monkeypatch):
+    """Hidden layers on CTA pairs (cta_group::2 MMAs on 256-row tiles, each CTA holding half
+    of the tile's weight rows) give the same network outputs, bit for bit, as the same layers
+    on single CTAs. Batches of 1408 and 592 rows: 11 and 5 row tiles, so the last pair of each
+    batch has its second row tile past the rows. The cost model puts the 1600 -> 800 and
+    800 -> 400 layers of this network on pairs."""
+    mech, net, T, p, Y = synth.configs.build("layer1d-30sp-1m", n_cells=2000)
+    P = df.DF_FP8_E4M3 if prec == "fp8" else df.DF_BF16
+    gm = df.DF_GELU_TABLE if prec == "bf16-table" else df.DF_GELU_TANH
+    x = onw.normalise_inputs(net, T, p, Y).astype(np.float32)
+    st = df.State(mech, net, precision=P, batch_cells=1408, gelu_mode=gm)
+    tiles = st.tiles()
+    assert tiles[1] & df.DF_TILE_PAIR and tiles[2] & df.DF_TILE_PAIR, tiles
+    O_pair = host(st.mlp_forward(dev(x)))
+    monkeypatch.setenv("DFGB_BN", "224")
+    st1 = df.State(mech, net, precision=P, batch_cells=1408, gelu_mode=gm)
+    assert not any(t & df.DF_TILE_PAIR for t in st1.tiles())
+    O_single = host(st1.mlp_forward(dev(x)))
+    torch.cuda.synchronize()
+    assert np.array_equal(O_pair, O_single), np.abs(O_pair - O_single).max()
+    # and the pair path against the oracle with the same rounding points
+    xr = x.astype(np.float64)
+    Oq = (onw.mlp_forward_fp8(net, xr, 32.0) if prec == "fp8"
+          else onw.mlp_forward_rounded(net, xr, onw.round_to_bf16))
+    err = np.abs(O_pair - Oq)
+    assert err.max() <= (0.1 if prec == "fp8" else 2e-2), err.max()
+    st.close()
+    st1.close()
 
 
 def test_autotune_is_a_no_op_for_fp32(df):
