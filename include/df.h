@@ -130,7 +130,13 @@ void df_state_destroy(df_state* s);
  * Stream-ordered: the work starts behind the work already on `stream`, and `stream` reaches the
  * end of this call once every result is in host memory; synchronise it before reading T, Y or
  * cell_status, and keep the host arrays alive until then. df_get_step_summary afterwards covers
- * all chunks. Errors as df_chem_step. */
+ * all chunks. Errors as df_chem_step.
+ * chunk_cells = DF_HOST_DIRECT: no device copies; the step's kernels read and write the host
+ * arrays in place over the host link (NVLink-C2C on Grace). Every array must lie in one
+ * page-locked allocation mapped into the device's address space (cudaHostAlloc,
+ * cudaHostRegister), else DF_ERR_INVALID_ARG. The results are bit-identical to the chunked
+ * form and to df_chem_step. */
+#define DF_HOST_DIRECT (-1)
 df_status df_chem_step_host(df_state* s, int64_t n_cells, double dt, double* T, const double* p,
                             double* Y, int64_t ldY, int32_t* cell_status, int64_t chunk_cells,
                             void* stream);

@@ -28,6 +28,7 @@ DF_CELL_NONFINITE = 4
 
 DF_FP32, DF_BF16, DF_FP8_E4M3 = 0, 1, 2
 DF_GELU_TANH, DF_GELU_TABLE = 0, 1
+DF_HOST_DIRECT = -1     # df_chem_step_host: kernels access the host arrays in place
 DF_TILE_PAIR = 0x1000   # df_get_tiles: the layer runs on CTA pairs (cta_group::2)
 
 DF_PARAM_WEIGHTS, DF_PARAM_GRADS, DF_PARAM_ADAM_M, DF_PARAM_ADAM_V = 0, 1, 2, 3

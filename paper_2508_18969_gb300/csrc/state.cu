@@ -636,6 +636,37 @@ __global__ void add_count_kernel(const int64_t* __restrict__ c, int64_t* __restr
   *total = (first ? 0 : *total) + *c;
 }
 
+typedef CUresult (*PointerGetAttributeFn)(void*, CUpointer_attribute, CUdeviceptr);
+
+// Device address of `bytes` bytes of host memory at `ptr` when the whole range lies in one
+// page-locked allocation mapped into the device's address space; false otherwise.
+template <class P>
+bool host_mapped(P* ptr, size_t bytes, P** dev) {
+  static PointerGetAttributeFn get_attr = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    return (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+               ? (PointerGetAttributeFn)f
+               : nullptr;
+  }();
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer || !get_attr) return false;
+  CUdeviceptr start = 0;
+  size_t size = 0;
+  const CUdeviceptr dp = (CUdeviceptr)(uintptr_t)a.devicePointer;
+  if (get_attr(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, dp) != CUDA_SUCCESS ||
+      get_attr(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, dp) != CUDA_SUCCESS)
+    return false;
+  if (dp < start || dp + bytes > start + size) return false;
+  *dev = (P*)a.devicePointer;
+  return true;
+}
+
 df_status run_step(df_state* s, int64_t n_cells, double dt, double* T, const double* p, double* Y,
                    int64_t ldY, int32_t* cell_status, int64_t* n_active_out, cudaStream_t st,
                    const Source* src, bool keep_counters = false) {
@@ -696,11 +727,26 @@ df_status df_chem_step_host(df_state* s, int64_t n_cells, double dt, double* T, 
                             void* stream) {
   df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
   if (rc != DF_OK || n_cells == 0) return rc;
-  if (chunk_cells < 0) return fail(s, DF_ERR_INVALID_ARG, "chunk_cells < 0");
+  if (chunk_cells < 0 && chunk_cells != DF_HOST_DIRECT)
+    return fail(s, DF_ERR_INVALID_ARG, "chunk_cells < 0");
   if (!(std::fabs(dt - s->dt) <= 1e-12 * std::fabs(s->dt)))
     return fail(s, DF_ERR_DT_MISMATCH, "dt %.17g differs from the network's %.17g", dt, s->dt);
   DeviceGuard guard(s->device);
   const int n = s->n;
+  if (chunk_cells == DF_HOST_DIRECT) {
+    // the kernels read and write the host arrays in place, over the host link
+    double *dT = nullptr, *dY = nullptr;
+    const double* dp = nullptr;
+    int32_t* dst = nullptr;
+    const bool mapped =
+        host_mapped(T, sizeof(double) * n_cells, &dT) && host_mapped(p, sizeof(double) * n_cells, &dp) &&
+        host_mapped(Y, sizeof(double) * ((size_t)(n - 1) * ldY + n_cells), &dY) &&
+        (!cell_status || host_mapped(cell_status, sizeof(int32_t) * n_cells, &dst));
+    if (!mapped)
+      return fail(s, DF_ERR_INVALID_ARG,
+                  "DF_HOST_DIRECT needs T, p, Y and cell_status in page-locked, mapped host memory");
+    return run_step(s, n_cells, dt, dT, dp, dY, ldY, dst, nullptr, (cudaStream_t)stream, nullptr);
+  }
   // chunk: as asked, else a quarter of the cells (at least 65536, at most one batch)
   int64_t chunk = chunk_cells > 0 ? chunk_cells
                                    : std::max<int64_t>(65536, round_up((n_cells + 3) / 4, 128));

@@ -1,7 +1,8 @@
 """df_chem_step_host (reaction step of cells in host memory, pipelined through the device in
-chunks) against df_chem_step on the same cells: every per-cell result is computed by the same
-kernels with the same arithmetic, so T, Y and the status bits must agree bit for bit, whatever
-the chunking; the step summary covers all chunks."""
+chunks, or with the kernels reading and writing the host arrays in place) against
+df_chem_step on the same cells: every per-cell result is computed by the same kernels with the
+same arithmetic, so T, Y and the status bits must agree bit for bit, whatever the chunking;
+the step summary covers all chunks."""
 import numpy as np
 import pytest
 
@@ -20,7 +21,7 @@ def df():
     return m
 
 
-@pytest.mark.parametrize("chunk,pinned", [(0, True), (7777, True), (0, False)])
+@pytest.mark.parametrize("chunk,pinned", [(0, True), (7777, True), (0, False), (-1, True)])
 def test_host_step_equals_device_step(df, chunk, pinned):
     mech, net, T, p, Y = synth.configs.build("react30-16m", n_cells=300_001)
     st = df.State(mech, net, precision=df.DF_BF16, T_react=600.0, batch_cells=131072)
@@ -41,4 +42,21 @@ def test_host_step_equals_device_step(df, chunk, pinned):
     assert torch.equal(sh, sd.cpu())
     assert (n_act_h, n_fl_h, it_h) == (n_act_d, n_fl_d, it_d)
     assert 0 < n_act_h < T.shape[0]
+    st.close()
+
+
+def test_direct_host_access_needs_page_locked_arrays(df):
+    """DF_HOST_DIRECT refuses arrays outside page-locked, mapped host memory before any device
+    work, and leaves them untouched."""
+    mech, net, T, p, Y = synth.configs.build("react30-16m", n_cells=5000)
+    st = df.State(mech, net, precision=df.DF_BF16, T_react=600.0, batch_cells=4096)
+    Th, Yh = torch.tensor(T).pin_memory(), torch.tensor(Y).pin_memory()
+    ph = torch.tensor(p)   # pageable
+    with pytest.raises(df.DFError, match="DF_HOST_DIRECT"):
+        st.chem_step_host(Th, ph, Yh, chunk_cells=df.DF_HOST_DIRECT)
+    sh = torch.empty(T.shape[0], dtype=torch.int32)   # pageable status
+    with pytest.raises(df.DFError, match="DF_HOST_DIRECT"):
+        st.chem_step_host(Th, ph.pin_memory(), Yh, status=sh, chunk_cells=df.DF_HOST_DIRECT)
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(Th, torch.tensor(T)) and torch.equal(Yh, torch.tensor(Y))
     st.close()
