@@ -135,13 +135,13 @@ cudaError_t launch_prop_outputs(const double* norm, int K0, int m, int64_t rows,
 cudaError_t launch_loss_grad(int64_t B, int n, const float* O, int64_t ldo, const float* Oh,
                              int64_t ldh, void* dO, int64_t ldd, bool bf16, float* loss,
                              float* scratch, cudaStream_t st);
-// out [C x ldo] = in^T for in [R x ldi]; rows R..Rpad-1 of the transpose are zero.
+// out [C x ldo] = in^T for in [R x ldi]; rows R..Rpad-1 of the transpose are zero. Rpad a
+// multiple of 64, ldi and ldo even. With colsum (and scratch of scratch_floats >= C floats),
+// also colsum[c] = sum_r in[r][c], FP32, in a fixed order.
 cudaError_t launch_transpose(int64_t R, int64_t C, const void* in, int64_t ldi, void* out,
-                             int64_t ldo, int64_t Rpad, bool bf16, cudaStream_t st);
-// out[c] = sum_r in[r][c], c < C (FP32 sums of BF16 or FP32 input); scratch holds
-// kColsumChunks x C floats.
-cudaError_t launch_colsum(int64_t R, int C, const void* in, int64_t ldi, bool bf16, float* out,
-                          float* scratch, cudaStream_t st);
+                             int64_t ldo, int64_t Rpad, bool bf16, int num_sms, cudaStream_t st,
+                             float* colsum = nullptr, float* scratch = nullptr,
+                             int64_t scratch_floats = 0);
 // out[i] = sum_{s < splits} part[s * stride + i] (fixed order), i < count.
 cudaError_t launch_sum_splits(int splits, int64_t count, int64_t stride, const float* part,
                               float* out, cudaStream_t st);

@@ -843,8 +843,7 @@ cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream
   const CUtensorMap& tmG = L.mode == kModeStoreG ? L.tmG : L.tmO;
   const int64_t tiles_n = (L.N + BN - 1) / BN;
   if constexpr (PAIR) {
-    if (a.ksplit > 1) return cudaErrorInvalidValue;
-    const int64_t units = ((a.rows.nmax + 2 * BM - 1) / (2 * BM)) * tiles_n;
+    const int64_t units = ((a.rows.nmax + 2 * BM - 1) / (2 * BM)) * tiles_n * a.ksplit;
     const int64_t cap = std::min<int64_t>(max_clusters, num_sms / 2);
     const int64_t nc = std::max<int64_t>(1, std::min<int64_t>(units, cap));
     cudaLaunchAttribute at[1];
@@ -896,8 +895,16 @@ cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStrea
     }
   }
   if (L.pair) {
-    // CTA pairs: hidden layers with more than one k-block (the tile widths of tc_pair_widths)
-    if (!L.gelu || a.ksplit > 1) return cudaErrorInvalidValue;
+    // CTA pairs: hidden layers with more than one k-block, and the FP32 weight-gradient GEMMs
+    // (no activation, split-K over the batch) of training
+    if (!L.gelu) {
+      if (FP8 || L.gtab || L.out_kind != kXF32) return cudaErrorInvalidValue;
+      switch (L.BN) {
+        case 128: return launch_bn<false, 128, kXF32, kActNone, kModePlain, true>(L, a, num_sms, st);
+        case 256: return launch_bn<false, 256, kXF32, kActNone, kModePlain, true>(L, a, num_sms, st);
+        default: return cudaErrorInvalidValue;
+      }
+    }
     if (L.gtab) {
       if (FP8 || L.out_kind != kXBF16) return cudaErrorInvalidValue;
       switch (L.BN) {

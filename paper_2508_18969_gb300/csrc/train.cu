@@ -89,20 +89,93 @@ __global__ void sum_parts_kernel(int parts, int C, const float* __restrict__ par
   out[c] = s;
 }
 
-// out[c][r] = in[r][c] for r < R, zero for R <= r < Rpad (32x32 shared-memory tiles).
+// Two adjacent elements of a row: the unit of every global access of transpose_kernel.
+template <typename T> struct Pair;
+template <> struct Pair<__nv_bfloat16> {
+  using V = __nv_bfloat162;
+  static __device__ __forceinline__ float lo(V v) { return __low2float(v); }
+  static __device__ __forceinline__ float hi(V v) { return __high2float(v); }
+  static __device__ __forceinline__ V make(__nv_bfloat16 a, __nv_bfloat16 b) { return __halves2bfloat162(a, b); }
+  static __device__ __forceinline__ V zero() { return __float2bfloat162_rn(0.0f); }
+  static __device__ __forceinline__ __nv_bfloat16 first(V v) { return __low2bfloat16(v); }
+  static __device__ __forceinline__ __nv_bfloat16 second(V v) { return __high2bfloat16(v); }
+};
+template <> struct Pair<float> {
+  using V = float2;
+  static __device__ __forceinline__ float lo(V v) { return v.x; }
+  static __device__ __forceinline__ float hi(V v) { return v.y; }
+  static __device__ __forceinline__ V make(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ V zero() { return make_float2(0.0f, 0.0f); }
+  static __device__ __forceinline__ float first(V v) { return v.x; }
+  static __device__ __forceinline__ float second(V v) { return v.y; }
+};
+
+constexpr int kTp = 64;   // transpose tile: 64 rows x 64 columns, 256 threads
+
+// out[c][r] = in[r][c] for c < C, r < Rpad (zero for R <= r < Rpad). Block (x, y) takes the
+// 64-column strip x and the row tiles y, y + gridDim.y, ...; every global access moves two
+// adjacent elements of a row, 128 (BF16) or 256 (FP32) contiguous bytes per warp. The loads of
+// the next tile are issued before the stores of the current one, so that each SM keeps enough
+// bytes in flight to cover the DRAM latency of this scattered pattern. With part, the block also
+// stores the FP32 column sums of its rows, part[y * C + c], summed in a fixed order (the bias
+// gradient of the dZ transpose).
 template <typename T>
-__global__ void transpose_kernel(int64_t R, int64_t C, const T* __restrict__ in, int64_t ldi,
-                                 T* __restrict__ out, int64_t ldo, int64_t Rpad) {
-  __shared__ T tile[32][33];
-  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
-  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-    const int64_t r = r0 + j, c = c0 + threadIdx.x;
-    tile[j][threadIdx.x] = (r < R && c < C) ? in[r * ldi + c] : (T)0.0f;
+__global__ void __launch_bounds__(256, 6) transpose_kernel(int64_t R, int64_t C,
+                                                           const T* __restrict__ in, int64_t ldi,
+                                                           T* __restrict__ out, int64_t ldo,
+                                                           int64_t Rpad, float* __restrict__ part) {
+  using P = Pair<T>;
+  using V = typename P::V;
+  __shared__ T tile[kTp][kTp + 2];
+  __shared__ float red[8][kTp];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t c0 = (int64_t)blockIdx.x * kTp;
+  const int64_t c = c0 + 2 * lane;   // this thread's two columns c, c + 1 (load phase)
+  const bool col_ok = c < C, pad_hi = c + 1 >= C;
+  const int64_t ntiles = Rpad / kTp;
+  // c < C: both elements lie inside the row's pitch (ldi and c even); a pad is zeroed at use
+  const T* src = in + c;
+  V v[kTp / 8];
+  auto load = [&](int64_t tt) {
+#pragma unroll
+    for (int j = 0; j < kTp / 8; ++j) {
+      const int64_t r = tt * kTp + w + 8 * j;
+      v[j] = (r < R && col_ok) ? *reinterpret_cast<const V*>(src + r * ldi) : P::zero();
+    }
+  };
+  float s0 = 0.0f, s1 = 0.0f;
+  int64_t t = blockIdx.y;
+  if (t < ntiles) load(t);
+  for (; t < ntiles; t += gridDim.y) {
+#pragma unroll
+    for (int j = 0; j < kTp / 8; ++j) {
+      V x = v[j];
+      if (pad_hi) x = P::make(P::first(x), P::first(P::zero()));
+      s0 += P::lo(x);
+      s1 += P::hi(x);
+      tile[w + 8 * j][2 * lane] = P::first(x);
+      tile[w + 8 * j][2 * lane + 1] = P::second(x);
+    }
+    __syncthreads();
+    const int64_t r0 = t * kTp;
+    if (t + gridDim.y < ntiles) load(t + gridDim.y);
+#pragma unroll
+    for (int j = 0; j < kTp / 8; ++j) {
+      const int cl = w + 8 * j;
+      if (c0 + cl < C)
+        *reinterpret_cast<V*>(out + (c0 + cl) * ldo + r0 + 2 * lane) =
+            P::make(tile[2 * lane][cl], tile[2 * lane + 1][cl]);
+    }
+    __syncthreads();
   }
+  if (!part) return;
+  red[w][2 * lane] = s0;
+  red[w][2 * lane + 1] = s1;
   __syncthreads();
-  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-    const int64_t c = c0 + j, r = r0 + threadIdx.x;
-    if (c < C && r < Rpad) out[c * ldo + r] = tile[threadIdx.x][j];
+  if (threadIdx.x < kTp && c0 + threadIdx.x < C) {
+    float s = 0.0f;
+    for (int k = 0; k < 8; ++k) s += red[k][threadIdx.x];
+    part[(int64_t)blockIdx.y * C + c0 + threadIdx.x] = s;
   }
 }
 
@@ -117,17 +190,17 @@ __global__ void split_sum_kernel(int splits, int64_t count, int64_t stride,
   }
 }
 
-// part[blockIdx.y * C + c] = sum of in[r][c] over the rows of chunk blockIdx.y.
-template <typename T>
-__global__ void colsum_kernel(int64_t R, int C, const T* __restrict__ in, int64_t ldi,
-                              float* __restrict__ part) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// out[c] = sum_{j < parts} part[j * C + c] with one warp per c: lane l sums parts l, l + 32, ...
+// in order, then the lanes combine in a fixed butterfly, so the result is the same every run.
+__global__ void sum_parts_warp_kernel(int parts, int C, const float* __restrict__ part,
+                                      float* __restrict__ out) {
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (c >= C) return;
-  const int64_t per = (R + gridDim.y - 1) / gridDim.y;
-  const int64_t r0 = blockIdx.y * per, r1 = min(R, r0 + per);
   float s = 0.0f;
-  for (int64_t r = r0; r < r1; ++r) s += (float)in[r * ldi + c];
-  part[(int64_t)blockIdx.y * C + c] = s;
+  for (int j = lane; j < parts; j += 32) s += part[(int64_t)j * C + c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[c] = s;
 }
 
 // Adam (Kingma & Ba 2015) on one parameter array: m, v moving averages of g and g^2, bias
@@ -197,30 +270,32 @@ cudaError_t launch_loss_grad(int64_t B, int n, const float* O, int64_t ldo, cons
 }
 
 cudaError_t launch_transpose(int64_t R, int64_t C, const void* in, int64_t ldi, void* out,
-                             int64_t ldo, int64_t Rpad, bool bf16, cudaStream_t st) {
-  if (R <= 0 || C <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)((Rpad + 31) / 32), (unsigned)((C + 31) / 32));
-  const dim3 block(32, 8);
-  if (bf16)
-    transpose_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(
-        R, C, (const __nv_bfloat16*)in, ldi, (__nv_bfloat16*)out, ldo, Rpad);
-  else
-    transpose_kernel<float><<<grid, block, 0, st>>>(R, C, (const float*)in, ldi, (float*)out, ldo,
-                                                    Rpad);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_colsum(int64_t R, int C, const void* in, int64_t ldi, bool bf16, float* out,
-                          float* scratch, cudaStream_t st) {
+                             int64_t ldo, int64_t Rpad, bool bf16, int num_sms, cudaStream_t st,
+                             float* colsum, float* scratch, int64_t scratch_floats) {
   if (C <= 0) return cudaSuccess;
-  if (R <= 0) return cudaMemsetAsync(out, 0, sizeof(float) * C, st);
-  const int64_t chunks = std::min<int64_t>((R + 1023) / 1024, kColsumChunks);
-  const dim3 grid((unsigned)((C + 127) / 128), (unsigned)chunks);
+  if (Rpad <= 0 || (Rpad % kTp) || (ldi & 1) || (ldo & 1)) {
+    if (colsum && Rpad <= 0) return cudaMemsetAsync(colsum, 0, sizeof(float) * C, st);
+    return Rpad <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+  }
+  const int64_t strips = (C + kTp - 1) / kTp, ntiles = Rpad / kTp;
+  // about six blocks per SM (its resident count); with the sums, as many row groups as the
+  // scratch holds
+  int64_t groups = std::max<int64_t>(1, (6LL * std::max(num_sms, 1) + strips - 1) / strips);
+  groups = std::min(groups, ntiles);
+  if (colsum) {
+    if (!scratch || scratch_floats < C) return cudaErrorInvalidValue;
+    groups = std::min<int64_t>(groups, scratch_floats / C);
+  }
+  const dim3 grid((unsigned)strips, (unsigned)groups);
+  float* part = colsum ? scratch : nullptr;
   if (bf16)
-    colsum_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(R, C, (const __nv_bfloat16*)in, ldi, scratch);
+    transpose_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(
+        R, C, (const __nv_bfloat16*)in, ldi, (__nv_bfloat16*)out, ldo, Rpad, part);
   else
-    colsum_kernel<float><<<grid, 128, 0, st>>>(R, C, (const float*)in, ldi, scratch);
-  sum_parts_kernel<<<(C + 127) / 128, 128, 0, st>>>((int)chunks, C, scratch, out);
+    transpose_kernel<float><<<grid, 256, 0, st>>>(R, C, (const float*)in, ldi, (float*)out, ldo,
+                                                  Rpad, part);
+  if (colsum)
+    sum_parts_warp_kernel<<<(unsigned)((C + 7) / 8), 256, 0, st>>>((int)groups, (int)C, scratch, colsum);
   return cudaGetLastError();
 }
 

@@ -29,9 +29,12 @@ struct Trn {
   int64_t host_wver = 0;                 // weight version of the state's host copies
   float* loss = nullptr;                 // device loss of the last step
   float* scratch = nullptr;              // fixed-order reduction partials
+  int64_t scratch_floats = 0;
   float* zero_bias = nullptr;
   // batch buffers for up to B rows
-  int64_t B = 0, Bp = 0;                 // Bp = B rounded up to 64 (transposed pitch)
+  int64_t B = 0, Bp = 0;                 // Bp = B rounded up to 64 (transposed length)
+  int64_t ldT = 0;                       // pitch of the transposes: Bp + 64, so that rows of a
+                                         // transpose are not a power of two apart in memory
   void* x = nullptr;
   int64_t ldx = 0;
   std::vector<void*> H, G, dZ;           // hidden outputs, GELU'(Z), output gradients
@@ -96,7 +99,7 @@ void free_batch(Trn* t) {
   t->H.clear(); t->G.clear(); t->dZ.clear();
   t->ldh.clear(); t->ldg.clear(); t->ldz.clear();
   t->fwd.clear(); t->dgrad.clear(); t->wgrad.clear();
-  t->B = t->Bp = 0;
+  t->B = t->Bp = t->ldT = 0;
   t->rows = -1;
 }
 
@@ -132,8 +135,8 @@ df_status ensure_params(df_state* s) {
   int64_t wmax = 32;
   for (int l = 0; l <= s->L; ++l) wmax = std::max<int64_t>(wmax, round_up(s->widths[l], 32));
   zalloc((void**)&t->loss, sizeof(float));
-  zalloc((void**)&t->scratch,
-         sizeof(float) * std::max<int64_t>(kTrainScratchFloats, kColsumChunks * wmax));
+  t->scratch_floats = std::max<int64_t>(kTrainScratchFloats, kColsumChunks * wmax);
+  zalloc((void**)&t->scratch, sizeof(float) * t->scratch_floats);
   zalloc((void**)&t->zero_bias, sizeof(float) * wmax);
   for (int l = 0; l < s->L && e == cudaSuccess; ++l) {
     const int N = s->widths[l + 1], K = s->widths[l];
@@ -188,6 +191,7 @@ df_status ensure_batch(df_state* s, int64_t B) {
   const size_t eb = bf16 ? 2 : 4;
   const int64_t al = bf16 ? 16 : 8;
   const int64_t Bp = round_up(B, 64);
+  const int64_t ldT = Bp + 64;
   auto zalloc = [&](void** p, size_t bytes) {
     if (e != cudaSuccess) return;
     e = cudaMalloc(p, bytes ? bytes : 1);
@@ -213,8 +217,8 @@ df_status ensure_batch(df_state* s, int64_t B) {
   t->ldo = round_up(s->nout, 8);
   zalloc((void**)&t->O, sizeof(float) * B * t->ldo);
   zalloc((void**)&t->Oh, sizeof(float) * B * t->ldo);
-  zalloc(&t->ZT, eb * nmax * Bp);
-  zalloc(&t->HT, eb * kmax * Bp);
+  zalloc(&t->ZT, eb * nmax * ldT);
+  zalloc(&t->HT, eb * kmax * ldT);
   t->lddx = round_up(K0, 4);
   zalloc((void**)&t->dX, sizeof(float) * B * t->lddx);
   if (bf16) {
@@ -231,6 +235,7 @@ df_status ensure_batch(df_state* s, int64_t B) {
   }
   t->B = B;
   t->Bp = Bp;
+  t->ldT = ldT;
   if (bf16) {
     char emsg[256];
     bool ok = true;
@@ -282,7 +287,15 @@ df_status ensure_batch(df_state* s, int64_t B) {
       TcLayer Wg{};
       Wg.N = K;
       Wg.K = (int)Bp;
-      Wg.BN = K <= 32 ? 32 : 64;
+      // CTA pairs (256-row tiles, each CTA streaming half of the B tile) once dW has more
+      // than one 128-row tile and 128 columns; the narrow cases on single CTAs
+      Wg.pair = N > 128 && K >= 128;
+      if (Wg.pair) {
+        const int64_t c128 = (K + 127) / 128 * 192, c256 = (K + 255) / 256 * 256;
+        Wg.BN = c256 <= c128 ? 256 : 128;
+      } else {
+        Wg.BN = K <= 32 ? 32 : 64;
+      }
       Wg.bias = t->zero_bias;
       Wg.out = t->dWp;        // split-K partials, summed into dW afterwards
       Wg.ldo = t->ldw[l];
@@ -293,8 +306,8 @@ df_status ensure_batch(df_state* s, int64_t B) {
       Wg.mode = 0;
       Wg.ntan = 1;
       if (ok)
-        ok = encode(&Wg.tmA, t->ZT, Bp, N, Bp, 128, emsg, sizeof emsg) &&
-             encode(&Wg.tmB, t->HT, Bp, K, Bp, Wg.BN, emsg, sizeof emsg) &&
+        ok = encode(&Wg.tmA, t->ZT, Bp, N, ldT, 128, emsg, sizeof emsg) &&
+             encode(&Wg.tmB, t->HT, Bp, K, ldT, Wg.pair ? Wg.BN / 2 : Wg.BN, emsg, sizeof emsg) &&
              tc_encode_out(Wg, (uint64_t)kMaxSplit * round_up(N, 128), emsg, sizeof emsg);
       if (!ok) break;
       t->fwd.push_back(F);
@@ -355,16 +368,20 @@ cudaError_t backward(df_state* s, int64_t R, bool want_dx, cudaStream_t st) {
     const int N = s->widths[l + 1], K = s->widths[l];
     const void* Hin = l == 0 ? t->x : t->H[l - 1];
     const int64_t ldin = l == 0 ? t->ldx : t->ldh[l - 1];
-    e = launch_colsum(R, N, t->dZ[l], t->ldz[l], bf16, t->db[l], t->scratch, st);
-    if (e == cudaSuccess) e = launch_transpose(R, N, t->dZ[l], t->ldz[l], t->ZT, t->Bp, Rp, bf16, st);
-    if (e == cudaSuccess) e = launch_transpose(R, K, Hin, ldin, t->HT, t->Bp, Rp, bf16, st);
+    // dZ_l^T, with db_l = column sums of dZ_l from the same pass
+    e = launch_transpose(R, N, t->dZ[l], t->ldz[l], t->ZT, t->ldT, Rp, bf16, s->num_sms, st,
+                         t->db[l], t->scratch, t->scratch_floats);
+    if (e == cudaSuccess)
+      e = launch_transpose(R, K, Hin, ldin, t->HT, t->ldT, Rp, bf16, s->num_sms, st);
     const RowMap wrows{nullptr, nullptr, 0, N};
     if (e == cudaSuccess) {
       if (bf16) {
         TcLayer Wg = t->wgrad[l];
         Wg.K = (int)Rp;
-        const int64_t tiles = ((N + 127) / 128) * ((K + Wg.BN - 1) / Wg.BN);
-        Wg.ksplit = wgrad_splits(tiles, (int)(Rp / 64), s->num_sms);
+        // work items: 128-row tiles, or 256-row tiles on the GPU's CTA pairs
+        const int64_t rows_per = Wg.pair ? 256 : 128;
+        const int64_t tiles = ((N + rows_per - 1) / rows_per) * ((K + Wg.BN - 1) / Wg.BN);
+        Wg.ksplit = wgrad_splits(tiles, (int)(Rp / 64), Wg.pair ? s->num_sms / 2 : s->num_sms);
         // each split owns whole 128-row tiles (a tile's store covers all its rows)
         Wg.split_rows = round_up(N, 128);
         e = launch_tc_gemm(Wg, wrows, s->num_sms, s->d_err, st);
@@ -372,8 +389,8 @@ cudaError_t backward(df_state* s, int64_t R, bool want_dx, cudaStream_t st) {
           e = launch_sum_splits(Wg.ksplit, (int64_t)N * t->ldw[l], Wg.split_rows * t->ldw[l],
                                 t->dWp, t->dW[l], st);
       } else {
-        e = launch_sgemm_bias_act(wrows, K, (int)Rp, (const float*)t->ZT, t->Bp,
-                                  (const float*)t->HT, t->Bp, t->zero_bias, t->dW[l], t->ldw[l],
+        e = launch_sgemm_bias_act(wrows, K, (int)Rp, (const float*)t->ZT, t->ldT,
+                                  (const float*)t->HT, t->ldT, t->zero_bias, t->dW[l], t->ldw[l],
                                   false, s->num_sms, st);
       }
     }
