@@ -875,6 +875,22 @@ cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStrea
   constexpr int HID = FP8 ? kXFP8 : kXBF16;
   if (L.mode != kModePlain) {
     if (FP8 || L.out_kind != kXBF16) return cudaErrorInvalidValue;
+    if (L.pair) {
+      if (L.mode == kModeStoreG) {
+        switch (L.BN) {
+          case 160: return launch_bn<false, 160, kXBF16, kActTanh, kModeStoreG, true>(L, a, num_sms, st);
+          case 224: return launch_bn<false, 224, kXBF16, kActTanh, kModeStoreG, true>(L, a, num_sms, st);
+          case 256: return launch_bn<false, 256, kXBF16, kActTanh, kModeStoreG, true>(L, a, num_sms, st);
+          default: return cudaErrorInvalidValue;
+        }
+      }
+      switch (L.BN) {
+        case 160: return launch_bn<false, 160, kXBF16, kActNone, kModeRowG, true>(L, a, num_sms, st);
+        case 224: return launch_bn<false, 224, kXBF16, kActNone, kModeRowG, true>(L, a, num_sms, st);
+        case 256: return launch_bn<false, 256, kXBF16, kActNone, kModeRowG, true>(L, a, num_sms, st);
+        default: return cudaErrorInvalidValue;
+      }
+    }
     if (L.mode == kModeStoreG) {
       switch (L.BN) {
         case 64: return launch_bn<false, 64, kXBF16, kActTanh, kModeStoreG>(L, a, num_sms, st);

@@ -79,9 +79,6 @@ int pick_tile(int N, int K, bool hidden, int out_kind, bool allow_pair) {
   return best;
 }
 
-int pick_bn(int N, int K, bool hidden, int out_kind) {
-  return pick_tile(N, K, hidden, out_kind, false);
-}
 
 __global__ void cast_rows_kernel(int64_t rows, int K, const float* __restrict__ in,
                                  int64_t ldi, void* out, int64_t ldo, int kind, float scale) {
@@ -942,7 +939,9 @@ df_status build_jac(df_state* s) {
       TcLayer F{};
       F.N = s->widths[l + 1];
       F.K = s->widths[l];
-      F.BN = pick_bn(F.N, F.K, !last, last ? kXF32 : kXBF16);
+      const int tile = pick_tile(F.N, F.K, !last, last ? kXF32 : kXBF16, true);
+      F.BN = tile & ~DF_TILE_PAIR;
+      F.pair = (tile & DF_TILE_PAIR) != 0;
       F.bias = s->bias[l];
       F.out = last ? (void*)j->O : j->act[l & 1];
       F.ldo = last ? j->ldo : j->act_ld[l & 1];
@@ -959,7 +958,7 @@ df_status build_jac(df_state* s) {
       bool ok = tc_encode_2d(&F.tmA, Af, 2, (uint64_t)F.K, (uint64_t)B, (uint64_t)ldaf * 2, 64, 128,
                              emsg, sizeof emsg) &&
                 tc_encode_2d(&F.tmB, Wl, 2, (uint64_t)F.K, (uint64_t)F.N, (uint64_t)j->Kp[l] * 2, 64,
-                             (uint32_t)F.BN, emsg, sizeof emsg) &&
+                             (uint32_t)(F.pair ? F.BN / 2 : F.BN), emsg, sizeof emsg) &&
                 tc_encode_out(F, (uint64_t)B, emsg, sizeof emsg);
       // tangent pass of layers 1.. (layer 0's tangents come from jac_tangent0)
       TcLayer Tg = F;

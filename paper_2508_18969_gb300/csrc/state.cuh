@@ -136,7 +136,9 @@ void free_jac(Jac* j);
 void free_trn(Trn* t);
 // Refreshes the host weight copies from the training masters when training changed them.
 df_status sync_host_weights(df_state* s);
-int pick_bn(int N, int K, bool hidden, int out_kind);
+// Tile of a tensor-core layer of N outputs and K inputs: its width, | DF_TILE_PAIR when CTA
+// pairs are allowed and cheaper.
+int pick_tile(int N, int K, bool hidden, int out_kind, bool allow_pair);
 
 struct DeviceGuard {
   int prev = -1;

@@ -246,7 +246,9 @@ df_status ensure_batch(df_state* s, int64_t B) {
       TcLayer F{};
       F.N = N;
       F.K = K;
-      F.BN = pick_bn(N, K, !last, last ? kXF32 : kXBF16);
+      const int ftile = pick_tile(N, K, !last, last ? kXF32 : kXBF16, true);
+      F.BN = ftile & ~DF_TILE_PAIR;
+      F.pair = (ftile & DF_TILE_PAIR) != 0;
       F.bias = s->bias[l];
       F.out = last ? (void*)t->O : t->H[l];
       F.ldo = last ? t->ldo : t->ldh[l];
@@ -260,14 +262,16 @@ df_status ensure_batch(df_state* s, int64_t B) {
       F.ntan = 1;
       ok = encode(&F.tmA, l == 0 ? t->x : t->H[l - 1], K, B, l == 0 ? t->ldx : t->ldh[l - 1], 128,
                   emsg, sizeof emsg) &&
-           encode(&F.tmB, s->Wlp[l], K, N, s->Kp8[l], F.BN, emsg, sizeof emsg) &&
+           encode(&F.tmB, s->Wlp[l], K, N, s->Kp8[l], F.pair ? F.BN / 2 : F.BN, emsg, sizeof emsg) &&
            tc_encode_out(F, (uint64_t)B, emsg, sizeof emsg);
       // input gradient: dZ_l [B x N] times W_l, i.e. against W_l^T [K x N]; layer 0's result
       // is the FP32 gradient of the network input, the others are scaled by GELU'(Z_{l-1})
       TcLayer D{};
       D.N = K;
       D.K = N;
-      D.BN = pick_bn(K, N, l > 0, l > 0 ? kXBF16 : kXF32);
+      const int dtile = pick_tile(K, N, l > 0, l > 0 ? kXBF16 : kXF32, true);
+      D.BN = dtile & ~DF_TILE_PAIR;
+      D.pair = (dtile & DF_TILE_PAIR) != 0;
       D.bias = t->zero_bias;
       D.out = l > 0 ? t->dZ[l - 1] : (void*)t->dX;
       D.ldo = l > 0 ? t->ldz[l - 1] : t->lddx;
@@ -281,7 +285,7 @@ df_status ensure_batch(df_state* s, int64_t B) {
       D.ntan = 1;
       if (ok)
         ok = encode(&D.tmA, t->dZ[l], N, B, t->ldz[l], 128, emsg, sizeof emsg) &&
-             encode(&D.tmB, t->WT[l], N, K, t->ldt[l], D.BN, emsg, sizeof emsg) &&
+             encode(&D.tmB, t->WT[l], N, K, t->ldt[l], D.pair ? D.BN / 2 : D.BN, emsg, sizeof emsg) &&
              tc_encode_out(D, (uint64_t)B, emsg, sizeof emsg);
       // weight gradient: dZ_l^T [N x Bp] times (H_{l-1}^T [K x Bp])^T, FP32 out
       TcLayer Wg{};
