@@ -108,10 +108,11 @@ cudaError_t launch_jac_scale(const EosParams& P, int64_t ncell, const double* Y,
 cudaError_t launch_jac_tangent0(int64_t ncell, int ntan, int N1, const float* sc, const float* W1T,
                                 const void* G1, int64_t ldg, bool bf16, void* dH, int64_t ldh,
                                 cudaStream_t st);
+// scr: ncell x (5n + 2) doubles, cst: ncell int32 (per-cell results between the two kernels).
 cudaError_t launch_jac_post(const EosParams& P, int64_t ncell, int64_t cell0, const double* T,
                             const double* p, const double* Y, int64_t ldY, const float* O,
                             int64_t ldo, const float* dO, int64_t lddo, const double* h0, float* J,
-                            double* dTn, cudaStream_t st);
+                            double* dTn, double* scr, int32_t* cst, cudaStream_t st);
 
 // ---- launchers (train.cu) ----
 // Ohat [B x ldh] FP32 (zero pads) = (BC(Yt) - BC(Y) - out_mean) / out_std of cells 0..B-1.

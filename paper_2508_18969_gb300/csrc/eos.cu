@@ -639,16 +639,16 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) props_kernel(EosParams P
 //   da/dy_k = 2 W^2 sqrt(a_k) v_k - 2 W a,  da'/dy_k = -2 W a' - (W^2 / sqrt T)(r_k v_k + sqrt(a_k) w_k),
 //   db/dy_k = W (b_k - b),  dZ from the implicit cubic, h = sum y_k h_k(T) + sigma h_dep,
 //   dh/dY_k = (h_k(T) + h_dep + sigma dh_dep/dy_k) / W_k.
-__device__ void h_grad(const EosParams& P, int n, int stride, const double* ycol, double T, double p,
-                       double* ucol, double* rcol, double* vcol, double* wcol, double* out,
-                       int out_stride, int& st) {
+__device__ void h_grad(const EosParams& P, int n, int64_t ystride, const double* ycol, double T,
+                       double p, int stride, double* ucol, double* rcol, int vstride,
+                       double* vcol, double* wcol, double* out, int out_stride, int& st) {
   const double* spc = P.spc;
   const double* K = P.Kmat;
   const double t = sqrt(T);
   double sig = 0.0, bs = 0.0;
   for (int k = 0; k < n; ++k) {
     const double* q = spc + k * kSpcStride;
-    const double y = ycol[k * stride] * q[0];
+    const double y = ycol[k * ystride] * q[0];
     sig += y;
     bs += y * q[3];
     ucol[k * stride] = y * (q[1] - q[2] * t);
@@ -661,8 +661,8 @@ __device__ void h_grad(const EosParams& P, int n, int stride, const double* ycol
       v = fma(K[k * n + j], ucol[j * stride], v);
       w = fma(K[k * n + j], rcol[j * stride], w);
     }
-    vcol[k * stride] = v;
-    wcol[k * stride] = w;
+    vcol[k * vstride] = v;
+    wcol[k * vstride] = w;
     G = fma(ucol[k * stride], v, G);
     dGs = fma(rcol[k * stride], v, dGs);
   }
@@ -686,7 +686,7 @@ __device__ void h_grad(const EosParams& P, int n, int stride, const double* ycol
   for (int k = 0; k < n; ++k) {
     const double* q = spc + k * kSpcStride;
     const double sak = q[1] - q[2] * t;
-    const double vk = vcol[k * stride], wk = wcol[k * stride];
+    const double vk = vcol[k * vstride], wk = wcol[k * vstride];
     const double dak = 2.0 * W * W * sak * vk - 2.0 * W * a;
     const double ddak = -2.0 * W * da - W * W * (q[2] * vk + sak * wk) / t;
     const double dbk = W * (q[3] - b);
@@ -723,45 +723,92 @@ __global__ void jac_scale_kernel(EosParams P, int64_t ncell, const double* __res
 }
 
 // Layer-1 tangents: dH1[c ntan + t, j] = sc[c, t] * W1[j, col(t)] * G1[c, j], col(0) = 0 (T),
-// col(t) = t + 1 (Y_{t-1}); W1T is W1 transposed [K0 x N1].
+// col(t) = t + 1 (Y_{t-1}); W1T is W1 transposed [K0 x N1]. A block takes kTanCells cells at a
+// time; each thread holds eight G1 values of each of them, reads eight weights of a direction
+// once (two 16-byte loads when N1 is a multiple of four) and writes the scaled products into
+// the cells' tangent rows as 16-byte (BF16) or 32-byte (FP32) groups. Pitches ldg and ldh are
+// multiples of eight elements.
+constexpr int kTanCells = 4;
 template <typename OT, typename GT>
 __global__ void jac_tangent0_kernel(int64_t ncell, int ntan, int N1, const float* __restrict__ sc,
                                     const float* __restrict__ W1T, const GT* __restrict__ G1,
                                     int64_t ldg, OT* __restrict__ dH, int64_t ldh) {
-  const int64_t total = ncell * ntan * (int64_t)N1;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = e / N1;
-    const int j = (int)(e % N1);
-    const int64_t c = row / ntan;
-    const int t = (int)(row % ntan);
-    const int col = t == 0 ? 0 : t + 1;
-    const float v = sc[row] * W1T[(int64_t)col * N1 + j] * (float)G1[c * ldg + j];
-    dH[row * ldh + j] = (OT)v;
+  const int groups = (N1 + 7) / 8;
+  const bool vec_w = (N1 & 3) == 0;
+  for (int64_t c0 = (int64_t)blockIdx.x * kTanCells; c0 < ncell;
+       c0 += (int64_t)gridDim.x * kTanCells) {
+    const int nc = (int)(ncell - c0 < kTanCells ? ncell - c0 : kTanCells);
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+      const int j0 = 8 * g;
+      const int m = min(8, N1 - j0);
+      float gv[kTanCells][8];
+#pragma unroll
+      for (int q = 0; q < kTanCells; ++q) {
+        const GT* gp = G1 + (c0 + q) * ldg + j0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) gv[q][e] = (q < nc && e < m) ? (float)gp[e] : 0.0f;
+      }
+      for (int t = 0; t < ntan; ++t) {
+        const int col = t == 0 ? 0 : t + 1;
+        const float* wp = W1T + (int64_t)col * N1 + j0;
+        float w[8];
+        if (vec_w && m == 8) {
+          const float4 a = __ldg(reinterpret_cast<const float4*>(wp));
+          const float4 b = __ldg(reinterpret_cast<const float4*>(wp) + 1);
+          w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+          w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) w[e] = e < m ? __ldg(wp + e) : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < kTanCells; ++q) {
+          if (q >= nc) break;
+          const int64_t row = (c0 + q) * ntan + t;
+          const float s = sc[row];
+          OT o[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) o[e] = (OT)(s * w[e] * gv[q][e]);
+          OT* dst = dH + row * ldh + j0;
+          if (m == 8) {
+            // 8 elements at an offset that is a multiple of 8: 16 or 32 aligned bytes
+            if constexpr (sizeof(OT) == 2) {
+              *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(o);
+            } else {
+              reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(o)[0];
+              reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(o)[1];
+            }
+          } else {
+            for (int e = 0; e < m; ++e) dst[e] = o[e];
+          }
+        }
+      }
+    }
   }
 }
 
 // Jacobian of the step of every cell (treated as reacting): J[c][k][t] = d(Y'_k - Y_k)/dv_t and
 // dTn[c][t] = dT'/dv_t, v = (T, Y_1..Y_n), from the network output O, its tangents dO
 // ([c ntan + t][k] = dO_k/dv_t) and the implicit function h(T', p, Y') = h0(T, p, Y).
+// Two kernels: jac_post_kernel, a thread per cell, takes the cell's equation-of-state part
+// (Y', T' by Newton, dh/dY and c_p at both states) and leaves per cell in scr
+// [dZ_k/du_k (n), Y'_k (n), dh/dY'_k (n), 1/S, c_p(T', Y'), two O(n) work columns (2n)] and
+// its status in cst;
+// jac_assemble_kernel, a warp per cell and a lane per direction t, forms the columns.
 template <int NM>
 __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell, int64_t cell0,
     const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
-    int64_t ldY, const float* __restrict__ O, int64_t ldo, const float* __restrict__ dO,
-    int64_t lddo, const double* __restrict__ h0, float* __restrict__ J, double* __restrict__ dTn) {
+    int64_t ldY, const float* __restrict__ O, int64_t ldo, const double* __restrict__ h0,
+    double* __restrict__ dTn, double* __restrict__ scr, int32_t* __restrict__ cst) {
   extern __shared__ double sm[];
   const SharedConsts c = load_consts(P, sm);
   const int stride = blockDim.x;
+  // shared memory holds the per-thread columns read in O(n^2) loops (the double-float
+  // composition of the mixing sums, the two weighted columns of h_grad); the O(n) ones live
+  // in the cell's scratch row, which is also how they reach jac_assemble_kernel
   f2* ws = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
-  double* cols = sm + consts_words(P) + 2 * NM * stride + threadIdx.x;
-  double* Yc = cols;                       // Y
-  double* Ypc = cols + NM * stride;        // Y'
-  double* zlc = cols + 2 * NM * stride;    // dZ_k/du_k
-  double* hgc = cols + 3 * NM * stride;    // dh/dY' at (T', Y')
-  double* uc = cols + 4 * NM * stride;
-  double* rc = cols + 5 * NM * stride;
-  double* vc = cols + 6 * NM * stride;
-  double* wc = cols + 7 * NM * stride;
+  double* uc = sm + consts_words(P) + NM * stride + threadIdx.x;
+  double* rc = uc + NM * stride;
   const int n = P.n, K0 = P.K0, ntan = n + 1;
   const float* out_mean = c.normf + 2 * K0;
   const float* out_std = c.normf + 2 * K0 + n;
@@ -772,16 +819,21 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cell = cell0 + r;
     const double Tc = T[cell], pc = p[cell], h0c = h0[r];
+    // scratch row: dZ_k/du_k, Y'_k, dh/dY'_k, 1/S, c_p', then h_grad's v and w columns
+    double* q = scr + r * (int64_t)(5 * n + 2);
+    double* zlc = q;
+    double* Ypc = q + n;
+    double* hgc = q + 2 * n;
+    double* vc = q + 3 * n + 2;
+    double* wc = q + 4 * n + 2;
     double Yk[NM];
     bool finite = isfinite(Tc) && isfinite(pc) && pc > 0.0 && isfinite(h0c);
 #pragma unroll
     for (int k = 0; k < NM; ++k) {
       Yk[k] = (k < n) ? Y[k * ldY + cell] : 0.0;
       finite = finite && isfinite(Yk[k]);
-      if (k < n) Yc[k * stride] = Yk[k];
     }
     int st = finite ? 0 : kCellNonfinite;
-    float* Jc = J + cell * (int64_t)n * ntan;
     double* dTc = dTn ? dTn + cell * (int64_t)ntan : nullptr;
     double cp1 = 1.0;
     if (st == 0) {
@@ -792,7 +844,7 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
       const PRPoint q0 = pr_point<false>(m0, Tc, pc, true, c.lnt, st);
       if (dTc) {
         dTc[0] = cp_ig(m0, Tc) + q0.cp_dep * m0.inv;
-        h_grad(P, n, stride, Yc, Tc, pc, uc, rc, vc, wc, dTc + 1, 1, st);
+        h_grad(P, n, ldY, Y + cell, Tc, pc, stride, uc, rc, 1, vc, wc, dTc + 1, 1, st);
       }
       // Y' and dZ_k/du_k = Z_k^(1 - lambda) = Z_k / (Y_k^lambda + lambda du_k)
       double S = 0.0;
@@ -802,8 +854,8 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
         const float ldu = lamf * fmaf(out_std[k], Or[k], out_mean[k]);
         const double base = ((y > 0.0) ? pow(y, lam) : 0.0) + (double)ldu;
         const double z = (base > 0.0) ? ipow(base, mpow) : 0.0;
-        Ypc[k * stride] = z;
-        zlc[k * stride] = (base > 0.0) ? z / base : 0.0;
+        Ypc[k] = z;
+        zlc[k] = (base > 0.0) ? z / base : 0.0;
         S += z;
       }
       if (!(S > 0.0)) st |= kCellNonfinite;
@@ -812,8 +864,8 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
         double Yn[NM];
 #pragma unroll
         for (int k = 0; k < NM; ++k) {
-          Yn[k] = (k < n) ? Ypc[k * stride] * iS : 0.0;
-          if (k < n) Ypc[k * stride] = Yn[k];
+          Yn[k] = (k < n) ? Ypc[k] * iS : 0.0;
+          if (k < n) Ypc[k] = Yn[k];
         }
         Mixture m1;
         for (int k = 0; k < n; ++k) ws[k * stride] = f2_from(Yn[k]);
@@ -823,34 +875,70 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
         if (st == 0) {
           const PRPoint q1 = pr_point<false>(m1, Tn, pc, true, c.lnt, st);
           cp1 = cp_ig(m1, Tn) + q1.cp_dep * m1.inv;
-          if (dTc) h_grad(P, n, stride, Ypc, Tn, pc, uc, rc, vc, wc, hgc, stride, st);
+          if (dTc) h_grad(P, n, 1, Ypc, Tn, pc, stride, uc, rc, 1, vc, wc, hgc, 1, st);
         }
-        // columns t = 0 (T), 1 + j (Y_j)
-        for (int t = 0; t < ntan && st == 0; ++t) {
-          const float* dOr = dO + (r * ntan + t) * lddo;
-          double bcp = 0.0;
-          if (t > 0) bcp = pow(fmax(Yc[(t - 1) * stride], 1e-12), lam - 1.0);
-          double sumjz = 0.0;
-          for (int k = 0; k < n; ++k) {
-            const double ju = (double)out_std[k] * (double)dOr[k] + ((t == k + 1) ? bcp : 0.0);
-            sumjz += zlc[k * stride] * ju;
-          }
-          double acc = 0.0;
-          for (int k = 0; k < n; ++k) {
-            const double ju = (double)out_std[k] * (double)dOr[k] + ((t == k + 1) ? bcp : 0.0);
-            const double jy = (zlc[k * stride] * ju - Ypc[k * stride] * sumjz) * iS;
-            Jc[k * ntan + t] = (float)(jy - ((t == k + 1) ? 1.0 : 0.0));
-            if (dTc) acc = fma(hgc[k * stride], jy, acc);
-          }
-          if (dTc) dTc[t] = (dTc[t] - acc) / cp1;
+        if (st == 0) {
+          if (!dTc)
+            for (int k = 0; k < n; ++k) hgc[k] = 0.0;
+          q[3 * n] = iS;
+          q[3 * n + 1] = cp1;
         }
       }
     }
-    if (st != 0) {
+    cst[r] = st;
+  }
+}
+
+
+// Columns of the Jacobian from jac_post_kernel's per-cell results: a warp per cell, lane t takes
+// direction t (T, then Y_1..Y_n), in the arithmetic and order of the per-cell formulas:
+// ju_k = out_std_k dO_k/dv_t + [t = k + 1] BC'(Y_k), jy_k = (dZ_k/du_k ju_k - Y'_k sum_j dZ_j/du_j
+// ju_j) / S, J[k][t] = jy_k - [t = k + 1], dT'/dv_t = (dh/dv_t - sum_k dh/dY'_k jy_k) / c_p.
+// Cells whose status is not 0 get NaN.
+__global__ void __launch_bounds__(256) jac_assemble_kernel(EosParams P, int64_t ncell,
+    int64_t cell0, const double* __restrict__ Y, int64_t ldY, const float* __restrict__ dO,
+    int64_t lddo, const double* __restrict__ scr, const int32_t* __restrict__ cst,
+    float* __restrict__ J, double* __restrict__ dTn) {
+  const int n = P.n, K0 = P.K0, ntan = n + 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const double lam = P.lambda;
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < ncell;
+       r += warps) {
+    const int64_t cell = cell0 + r;
+    float* Jc = J + cell * (int64_t)n * ntan;
+    double* dTc = dTn ? dTn + cell * (int64_t)ntan : nullptr;
+    if (cst[r] != 0) {
       const float nanf = __int_as_float(0x7fc00000);
-      for (int e = 0; e < n * ntan; ++e) Jc[e] = nanf;
+      for (int e = lane; e < n * ntan; e += 32) Jc[e] = nanf;
       if (dTc)
-        for (int t = 0; t < ntan; ++t) dTc[t] = __longlong_as_double(0x7ff8000000000000LL);
+        for (int t = lane; t < ntan; t += 32) dTc[t] = __longlong_as_double(0x7ff8000000000000LL);
+      continue;
+    }
+    const double* q = scr + r * (int64_t)(5 * n + 2);
+    const double* zl = q;
+    const double* Yp = q + n;
+    const double* hg = q + 2 * n;
+    const double iS = q[3 * n], cp1 = q[3 * n + 1];
+    for (int t = lane; t < ntan; t += 32) {
+      const float* dOr = dO + (r * ntan + t) * lddo;
+      double bcp = 0.0;
+      if (t > 0) bcp = pow(fmax(Y[(int64_t)(t - 1) * ldY + cell], 1e-12), lam - 1.0);
+      double sumjz = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const float sd = (float)P.norm[2 * K0 + n + k];
+        const double ju = (double)sd * (double)dOr[k] + ((t == k + 1) ? bcp : 0.0);
+        sumjz += zl[k] * ju;
+      }
+      double acc = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const float sd = (float)P.norm[2 * K0 + n + k];
+        const double ju = (double)sd * (double)dOr[k] + ((t == k + 1) ? bcp : 0.0);
+        const double jy = (zl[k] * ju - Yp[k] * sumjz) * iS;
+        Jc[k * ntan + t] = (float)(jy - ((t == k + 1) ? 1.0 : 0.0));
+        if (dTc) acc = fma(hg[k], jy, acc);
+      }
+      if (dTc) dTc[t] = (dTc[t] - acc) / cp1;
     }
   }
 }
@@ -979,31 +1067,44 @@ cudaError_t launch_jac_tangent0(int64_t ncell, int ntan, int N1, const float* sc
                                 const void* G1, int64_t ldg, bool bf16, void* dH, int64_t ldh,
                                 cudaStream_t st) {
   if (ncell <= 0) return cudaSuccess;
-  const int g = grid_for(ncell * ntan * (int64_t)N1 / 4);
+  if ((ldg & 7) || (ldh & 7)) return cudaErrorInvalidValue;
+  // kTanCells cells per block at a time, a thread per group of eight columns
+  const int groups = (N1 + 7) / 8;
+  const int threads = std::min(256, (groups + 31) / 32 * 32);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int g = (int)std::min<int64_t>((ncell + kTanCells - 1) / kTanCells,
+                                       (int64_t)sms * (2048 / threads));
   if (bf16)
-    jac_tangent0_kernel<__nv_bfloat16, __nv_bfloat16><<<g, kThreads, 0, st>>>(
+    jac_tangent0_kernel<__nv_bfloat16, __nv_bfloat16><<<g, threads, 0, st>>>(
         ncell, ntan, N1, sc, W1T, (const __nv_bfloat16*)G1, ldg, (__nv_bfloat16*)dH, ldh);
   else
-    jac_tangent0_kernel<float, float><<<g, kThreads, 0, st>>>(ncell, ntan, N1, sc, W1T,
-                                                              (const float*)G1, ldg, (float*)dH, ldh);
+    jac_tangent0_kernel<float, float><<<g, threads, 0, st>>>(ncell, ntan, N1, sc, W1T,
+                                                             (const float*)G1, ldg, (float*)dH, ldh);
   return cudaGetLastError();
 }
 
 cudaError_t launch_jac_post(const EosParams& P, int64_t ncell, int64_t cell0, const double* T,
                             const double* p, const double* Y, int64_t ldY, const float* O,
                             int64_t ldo, const float* dO, int64_t lddo, const double* h0, float* J,
-                            double* dTn, cudaStream_t st) {
+                            double* dTn, double* scr, int32_t* cst, cudaStream_t st) {
   if (ncell <= 0) return cudaSuccess;
   constexpr int kJT = 64;
   const int64_t blocks = (ncell + kJT - 1) / kJT;
   const int g = (int)(blocks < 4096 ? blocks : 4096);
   if (P.n <= 16) {
-    const size_t smem = sizeof(double) * ((size_t)consts_words(P) + (size_t)(2 * 16 + 8 * 16) * kJT);
-    jac_post_kernel<16><<<g, kJT, smem, st>>>(P, ncell, cell0, T, p, Y, ldY, O, ldo, dO, lddo, h0, J, dTn);
+    const size_t smem = sizeof(double) * ((size_t)consts_words(P) + (size_t)(3 * 16) * kJT);
+    jac_post_kernel<16><<<g, kJT, smem, st>>>(P, ncell, cell0, T, p, Y, ldY, O, ldo, h0, dTn, scr, cst);
   } else {
-    const size_t smem = sizeof(double) * ((size_t)consts_words(P) + (size_t)(2 * 32 + 8 * 32) * kJT);
-    jac_post_kernel<32><<<g, kJT, smem, st>>>(P, ncell, cell0, T, p, Y, ldY, O, ldo, dO, lddo, h0, J, dTn);
+    const size_t smem = sizeof(double) * ((size_t)consts_words(P) + (size_t)(3 * 32) * kJT);
+    jac_post_kernel<32><<<g, kJT, smem, st>>>(P, ncell, cell0, T, p, Y, ldY, O, ldo, h0, dTn, scr, cst);
   }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t ablocks = (ncell + 7) / 8;   // eight cells (warps) per block
+  jac_assemble_kernel<<<(unsigned)std::min<int64_t>(ablocks, 1 << 20), 256, 0, st>>>(
+      P, ncell, cell0, Y, ldY, dO, lddo, scr, cst, J, dTn);
   return cudaGetLastError();
 }
 

@@ -116,7 +116,7 @@ void free_jac(Jac* j) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   f(j->x); f(j->act[0]); f(j->act[1]); f(j->tan[0]); f(j->tan[1]);
   for (auto p : j->G) f(p);
-  f(j->O); f(j->dO); f(j->h0); f(j->sc); f(j->W1T); f(j->zero_bias);
+  f(j->O); f(j->dO); f(j->h0); f(j->sc); f(j->jscr); f(j->jst); f(j->W1T); f(j->zero_bias);
   for (auto p : j->Wb) f(p);
   delete j;
 }
@@ -853,7 +853,7 @@ df_status build_jac(df_state* s) {
   const int L = s->L, n = s->n, ntan = n + 1;
   j->bf16 = s->precision != DF_FP32;
   j->eb = j->bf16 ? 2 : 4;
-  j->B = std::min<int64_t>(s->cap, 16384);
+  j->B = std::min<int64_t>(s->cap, 65536);
   const int64_t B = j->B, R = B * ntan;
   const int64_t al = j->bf16 ? 16 : 8;
   cudaError_t e = cudaSuccess;
@@ -887,6 +887,8 @@ df_status build_jac(df_state* s) {
   al_ok((void**)&j->dO, sizeof(float) * R * j->ldo, true);
   al_ok((void**)&j->h0, sizeof(double) * B, false);
   al_ok((void**)&j->sc, sizeof(float) * R, false);
+  al_ok((void**)&j->jscr, sizeof(double) * B * (5 * n + 2), false);
+  al_ok((void**)&j->jst, sizeof(int32_t) * B, false);
   int64_t zmax = 32;
   for (int l = 0; l < L; ++l) zmax = std::max<int64_t>(zmax, round_up(s->widths[l + 1], 32));
   al_ok((void**)&j->zero_bias, sizeof(float) * zmax, true);
@@ -1118,7 +1120,7 @@ df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const 
     }
     if (e == cudaSuccess)
       e = launch_jac_post(s->P, nb, c0, T, p, Y, ldY, j->O, j->ldo, j->dO, j->ldo, j->h0, J_dY,
-                          dTnew, st);
+                          dTnew, j->jscr, j->jst, st);
   }
   return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "Jacobian");
 }

@@ -29,6 +29,8 @@ struct Jac {
   float* dO = nullptr;
   double* h0 = nullptr;
   float* sc = nullptr;
+  double* jscr = nullptr;                // per-cell results between the two post kernels
+  int32_t* jst = nullptr;                // [B (5n + 2)] and [B]
   float* W1T = nullptr;
   float* zero_bias = nullptr;
   std::vector<void*> Wb;                 // BF16 weights owned here (FP8 states)
