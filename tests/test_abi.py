@@ -100,3 +100,27 @@ def test_static_compaction_rejects_oversize_before_device_use(lib):
     assert rc == _lib.DF_ERR_INVALID_ARG
     assert b"DF_COMPACT_STATIC_MAX_CELLS" in lib.df_get_last_error(None)
     assert lib.df_active_compact_static(10, 600.0, None, None, None, None) == _lib.DF_ERR_INVALID_ARG
+
+
+def _header_defines():
+    """Integer #define constants of include/*.h: name -> value."""
+    inc = os.path.join(ROOT, "include")
+    out = {}
+    for f in sorted(os.listdir(inc)):
+        if not f.endswith(".h"):
+            continue
+        for m in re.finditer(r"^#define\s+(DF_[A-Z0-9_]+)\s+\(?\s*(-?(?:0x[0-9A-Fa-f]+|\d+))\s*\)?",
+                             open(os.path.join(inc, f)).read(), flags=re.M):
+            out[m.group(1)] = int(m.group(2), 0)
+    return out
+
+
+def test_binding_constants_match_the_headers():
+    """Every DF_* integer constant the binding defines has the header's value."""
+    from paper_2508_18969_gb300 import _lib
+    hdr = _header_defines()
+    assert {"DF_OK", "DF_TILE_PAIR", "DF_HOST_DIRECT", "DF_SOLVER_FP64"} <= set(hdr)
+    shared = [k for k in hdr if hasattr(_lib, k)]
+    assert len(shared) >= 10, shared
+    for k in shared:
+        assert getattr(_lib, k) == hdr[k], (k, getattr(_lib, k), hdr[k])
