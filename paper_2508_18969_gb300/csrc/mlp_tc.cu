@@ -8,12 +8,14 @@
 // becomes a multi-stage TMA ring and two TMEM accumulators, so the epilogue of one tile
 // overlaps the MMAs of the next.
 //
-// Warp roles (320 threads, one CTA per SM):
+// Warp roles (64 + 32 * 4 * EPI_PER_QUARTER threads, 448 by default; one CTA per SM):
 //   warp 0      TMA producer (one lane)
 //   warp 1      TMEM allocator and MMA issuer (one lane)
-//   warps 2..9  epilogue; warp w reads TMEM lanes 32*(w%4) .. 32*(w%4)+31 and every other
-//               32-column chunk; results go through a shared-memory transpose so that each
-//               warp store writes whole 16-byte units of consecutive rows
+//   warps 2..   epilogue; warp w reads TMEM lanes 32*(w%4) .. 32*(w%4)+31 and every
+//               EPI_PER_QUARTER-th 32-column chunk; results go through swizzled shared-memory
+//               staging and leave by TMA tensor stores
+// A layer may instead run on CTA pairs (clusters of two, cta_group::2): 256-row tiles whose
+// MMAs the even CTA issues over both CTAs' operands (see "CTA pairs" below).
 // Every mbarrier wait is bounded by a clock budget; on expiry the CTA sets the error word,
 // drains its own copies and MMAs, frees its TMEM and returns.
 #include "dfgb_internal.cuh"
