@@ -177,8 +177,8 @@ def weak_scaling_value(world, cells_per_rank, ms_max):
 MEASURED_TRAFFIC = {
     ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "4b3c9714d132bb8d", 3158.0),
     ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "4b3c9714d132bb8d", 4756.0),
-    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 297.0),
-    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "3c008980bf56abdd", 549.0),
+    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "fd5072d2e2b27512", 296.1),
+    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "fd5072d2e2b27512", 543.3),
     # one block Gauss-Seidel sweep (gs_rhs_kernel + gs_sweep_kernel), per cell, FP64, 512 cells
     # per block row (profiles/solver_kernels_mesh-2m.md)
     ("gauss_seidel", "mesh-512"): ("paper_2508_18969_gb300/csrc/solver.cu", "05bcbf99e5a03a1e", 132.1),
