@@ -121,11 +121,14 @@ void df_state_destroy(df_state* s);
 
 /* One reaction step (a0-a10) of cells held in HOST memory: T [n_cells] and Y [n * ldY] are
  * updated in place, p is read, cell_status (HOST, [n_cells], may be NULL) receives the DF_CELL_*
- * bits. The cells go through the device in chunks of chunk_cells (0: a quarter of the cells, at
- * least 65,536, at most the state's batch) with two device buffers: the upload of one chunk and
- * the download of another overlap the step of a third (copies on two internal streams, the steps
- * on `stream`), the GPU form of the paper's double buffering of data movement against
- * computation (Sec. 3.3.3). Page-locked host memory lets the copies run asynchronously; with
+ * bits. The cells go through the device in chunks with two device buffers: the upload of one
+ * chunk and the download of another overlap the step of a third (copies on two internal
+ * streams, the steps on `stream`), the GPU form of the paper's double buffering of data
+ * movement against computation (Sec. 3.3.3). Chunks of chunk_cells cells (at most the state's
+ * batch), or with chunk_cells = 0 a short first and last chunk of 1/16 of the cells (at least
+ * 32,768) around as few middle chunks as the batch allows (at least two): only a short upload
+ * and a short download are left outside the steps, and the long chunks step at the long-batch
+ * rate. Page-locked host memory lets the copies run asynchronously; with
  * pageable memory CUDA stages them and they do not overlap.
  * Stream-ordered: the work starts behind the work already on `stream`, and `stream` reaches the
  * end of this call once every result is in host memory; synchronise it before reading T, Y or

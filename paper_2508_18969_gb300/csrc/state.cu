@@ -744,10 +744,30 @@ df_status df_chem_step_host(df_state* s, int64_t n_cells, double dt, double* T, 
                   "DF_HOST_DIRECT needs T, p, Y and cell_status in page-locked, mapped host memory");
     return run_step(s, n_cells, dt, dT, dp, dY, ldY, dst, nullptr, (cudaStream_t)stream, nullptr);
   }
-  // chunk: as asked, else a quarter of the cells (at least 65536, at most one batch)
-  int64_t chunk = chunk_cells > 0 ? chunk_cells
-                                   : std::max<int64_t>(65536, round_up((n_cells + 3) / 4, 128));
-  chunk = std::min(chunk, std::min(s->cap, n_cells));
+  // Chunk plan. As asked: equal chunks of chunk_cells. Automatic: a short first and last chunk
+  // (1/16 of the cells, at least 32768), so that only a small upload and a small download are
+  // not hidden behind a step, and the cells between them in as few chunks as the batch allows
+  // (at least two), whose steps run at the long-batch rate.
+  std::vector<int64_t> plan;
+  if (chunk_cells > 0) {
+    const int64_t c = std::min(chunk_cells, s->cap);
+    for (int64_t c0 = 0; c0 < n_cells; c0 += c) plan.push_back(std::min(c, n_cells - c0));
+  } else {
+    const int64_t edge = std::min(s->cap, std::max<int64_t>(32768, round_up((n_cells + 15) / 16, 128)));
+    if (n_cells <= 4 * edge) {
+      const int64_t c = std::min(s->cap, std::max<int64_t>(32768, round_up((n_cells + 3) / 4, 128)));
+      for (int64_t c0 = 0; c0 < n_cells; c0 += c) plan.push_back(std::min(c, n_cells - c0));
+    } else {
+      const int64_t mid = n_cells - 2 * edge;
+      const int64_t k = std::max<int64_t>(2, (mid + s->cap - 1) / s->cap);
+      const int64_t m = round_up((mid + k - 1) / k, 128);
+      plan.push_back(edge);
+      for (int64_t c0 = 0; c0 < mid; c0 += m) plan.push_back(std::min(m, mid - c0));
+      plan.push_back(edge);
+    }
+  }
+  int64_t chunk = 0;
+  for (int64_t c : plan) chunk = std::max(chunk, c);
   df_state::HostPipe& hp = s->hp;
   cudaError_t e = cudaSuccess;
   if (hp.chunk < chunk) {
@@ -784,9 +804,10 @@ df_status df_chem_step_host(df_state* s, int64_t n_cells, double dt, double* T, 
   e = cudaEventRecord(hp.ev_start, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.in, hp.ev_start, 0);
   int64_t nchunks = 0;
-  for (int64_t c0 = 0; c0 < n_cells && e == cudaSuccess; c0 += chunk, ++nchunks) {
+  for (int64_t c0 = 0; nchunks < (int64_t)plan.size() && e == cudaSuccess;
+       c0 += plan[nchunks], ++nchunks) {
     const int b = (int)(nchunks & 1);
-    const int64_t len = std::min(chunk, n_cells - c0);
+    const int64_t len = plan[nchunks];
     // upload into buffer b once its previous download has finished
     e = cudaStreamWaitEvent(hp.in, hp.ev_out[b], 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hp.T[b], T + c0, sizeof(double) * len, cudaMemcpyHostToDevice, hp.in);
