@@ -49,7 +49,7 @@ __global__ void targets_kernel(EosParams P, int64_t B, const double* __restrict_
 }
 
 // dO = 2 (O - Ohat) / B (columns >= n zero); part[block] = this block's share of
-// sum (O - Ohat)^2 / B (summed in a fixed order by sum_parts_kernel, so the loss is
+// sum (O - Ohat)^2 / B (summed in a fixed order by sum_parts_warp_kernel, so the loss is
 // reproducible run to run).
 template <typename GT>
 __global__ void loss_grad_kernel(int64_t B, int n, const float* __restrict__ O, int64_t ldo,
@@ -77,16 +77,6 @@ __global__ void loss_grad_kernel(int64_t B, int n, const float* __restrict__ O, 
     for (int w = 0; w < kThreads / 32; ++w) s += red[w];
     part[blockIdx.x] = s;
   }
-}
-
-// out[c] = sum_{j < parts} part[j * C + c], in order of j (one thread per c).
-__global__ void sum_parts_kernel(int parts, int C, const float* __restrict__ part,
-                                 float* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= C) return;
-  float s = 0.0f;
-  for (int j = 0; j < parts; ++j) s += part[(int64_t)j * C + c];
-  out[c] = s;
 }
 
 // Two adjacent elements of a row: the unit of every global access of transpose_kernel.
@@ -265,7 +255,7 @@ cudaError_t launch_loss_grad(int64_t B, int n, const float* O, int64_t ldo, cons
   else
     loss_grad_kernel<float><<<g, kThreads, 0, st>>>(B, n, O, ldo, Oh, ldh, (float*)dO, ldd, invB,
                                                     scratch);
-  sum_parts_kernel<<<1, 32, 0, st>>>(g, 1, scratch, loss);
+  sum_parts_warp_kernel<<<1, 32, 0, st>>>(g, 1, scratch, loss);
   return cudaGetLastError();
 }
 
