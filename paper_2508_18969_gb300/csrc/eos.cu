@@ -895,11 +895,17 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
 // ju_k = out_std_k dO_k/dv_t + [t = k + 1] BC'(Y_k), jy_k = (dZ_k/du_k ju_k - Y'_k sum_j dZ_j/du_j
 // ju_j) / S, J[k][t] = jy_k - [t = k + 1], dT'/dv_t = (dh/dv_t - sum_k dh/dY'_k jy_k) / c_p.
 // Cells whose status is not 0 get NaN.
+template <int NM>
 __global__ void __launch_bounds__(256) jac_assemble_kernel(EosParams P, int64_t ncell,
     int64_t cell0, const double* __restrict__ Y, int64_t ldY, const float* __restrict__ dO,
     int64_t lddo, const double* __restrict__ scr, const int32_t* __restrict__ cst,
     float* __restrict__ J, double* __restrict__ dTn) {
   const int n = P.n, K0 = P.K0, ntan = n + 1;
+  // the FP32 output spreads as FP64 (exact), once per block, and the FP32 -> FP64 conversions
+  // of dO on the integer pipes
+  __shared__ double sdd[NM];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) sdd[k] = f_to_d((float)P.norm[2 * K0 + n + k]);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const double lam = P.lambda;
@@ -925,15 +931,15 @@ __global__ void __launch_bounds__(256) jac_assemble_kernel(EosParams P, int64_t 
       double bcp = 0.0;
       if (t > 0) bcp = pow(fmax(Y[(int64_t)(t - 1) * ldY + cell], 1e-12), lam - 1.0);
       double sumjz = 0.0;
+#pragma unroll 4
       for (int k = 0; k < n; ++k) {
-        const float sd = (float)P.norm[2 * K0 + n + k];
-        const double ju = (double)sd * (double)dOr[k] + ((t == k + 1) ? bcp : 0.0);
+        const double ju = sdd[k] * f_to_d(dOr[k]) + ((t == k + 1) ? bcp : 0.0);
         sumjz += zl[k] * ju;
       }
       double acc = 0.0;
+#pragma unroll 4
       for (int k = 0; k < n; ++k) {
-        const float sd = (float)P.norm[2 * K0 + n + k];
-        const double ju = (double)sd * (double)dOr[k] + ((t == k + 1) ? bcp : 0.0);
+        const double ju = sdd[k] * f_to_d(dOr[k]) + ((t == k + 1) ? bcp : 0.0);
         const double jy = (zl[k] * ju - Yp[k] * sumjz) * iS;
         Jc[k * ntan + t] = (float)(jy - ((t == k + 1) ? 1.0 : 0.0));
         if (dTc) acc = fma(hg[k], jy, acc);
@@ -1103,8 +1109,11 @@ cudaError_t launch_jac_post(const EosParams& P, int64_t ncell, int64_t cell0, co
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t ablocks = (ncell + 7) / 8;   // eight cells (warps) per block
-  jac_assemble_kernel<<<(unsigned)std::min<int64_t>(ablocks, 1 << 20), 256, 0, st>>>(
-      P, ncell, cell0, Y, ldY, dO, lddo, scr, cst, J, dTn);
+  const unsigned ag = (unsigned)std::min<int64_t>(ablocks, 1 << 20);
+  if (P.n <= 16)
+    jac_assemble_kernel<16><<<ag, 256, 0, st>>>(P, ncell, cell0, Y, ldY, dO, lddo, scr, cst, J, dTn);
+  else
+    jac_assemble_kernel<32><<<ag, 256, 0, st>>>(P, ncell, cell0, Y, ldY, dO, lddo, scr, cst, J, dTn);
   return cudaGetLastError();
 }
 
