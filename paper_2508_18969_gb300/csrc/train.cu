@@ -14,37 +14,54 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = kTrainScratchFloats;   // element-wise grids, one loss partial each
 
-// Change of the Box-Cox coordinate, BC(yt) - BC(y) = (yt^l - y^l) / l. For positive y and yt
-// it is formed as y^l expm1(l ln(yt / y)) / l: the ratio in FP64, the rest in FP32, which keeps
-// ~1e-7 relative accuracy of the difference itself (no cancellation of two nearly equal BCs).
+// BC(yt) - BC(y) for the Box-Cox transform BC(x) = (x^l - 1) / l. When both are positive
+// it is formed as y^l expm1(l ln(yt / y)) / l: the difference yt - y in FP64 (no cancellation
+// of two nearly equal values), its ratio to y as a correctly rounded FP32 division, the rest in
+// FP32. That keeps the difference itself to ~2e-7 relative; GB300's FP64 division would cost
+// more than the rest of the kernel.
 __device__ __forceinline__ float dboxcox(double y, double yt, float lam) {
   if (y > 0.0 && yt > 0.0) {
-    const float q = (float)((yt - y) / y);
-    const float lr = (q > -0.5f && q < 1.0f) ? log1pf(q) : logf((float)(yt / y));
-    return powf((float)y, lam) * expm1f(lam * lr) / lam;
+    const float yf = (float)y;
+    const float q = __fdiv_rn((float)(yt - y), yf);
+    const float lr = (q > -0.5f && q < 1.0f) ? log1pf(q) : logf(__fdiv_rn((float)yt, yf));
+    return powf(yf, lam) * expm1f(lam * lr) / lam;
   }
   const float a = yt > 0.0 ? powf((float)yt, lam) : 0.0f;
   const float b = y > 0.0 ? powf((float)y, lam) : 0.0f;
   return (a - b) / lam;
 }
 
-// Ohat[b][k] = (BC(Yt) - BC(Y) - out_mean_k) / out_std_k, FP32 [B x ldh], zero pad.
+// Ohat[b][k] = (BC(Yt) - BC(Y) - out_mean_k) / out_std_k, FP32 [B x ldh], zero pad. A thread
+// per state: the FP64 reads of Y and Yt are coalesced across the batch, and each thread writes
+// its row in 16-byte groups (ldh a multiple of 4).
 __global__ void targets_kernel(EosParams P, int64_t B, const double* __restrict__ Y,
                                const double* __restrict__ Yt, int64_t ldY,
                                const double* __restrict__ norm, float* __restrict__ Oh,
                                int64_t ldh) {
   const int n = P.n, K0 = P.K0;
   const float lam = (float)P.lambda;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < B * ldh;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = e / ldh;
-    const int k = (int)(e % ldh);
-    float v = 0.0f;
-    if (k < n) {
-      const float du = dboxcox(Y[k * ldY + b], Yt[k * ldY + b], lam);
-      v = (du - (float)norm[2 * K0 + k]) / (float)norm[2 * K0 + n + k];
+  __shared__ float mean_f[64], std_f[64];
+  for (int k = threadIdx.x; k < n && k < 64; k += blockDim.x) {
+    mean_f[k] = (float)norm[2 * K0 + k];
+    std_f[k] = (float)norm[2 * K0 + n + k];
+  }
+  __syncthreads();
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < B;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    float* orow = Oh + b * ldh;
+    for (int k0 = 0; k0 < ldh; k0 += 4) {
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = k0 + j;
+        v[j] = 0.0f;
+        if (k < n) {
+          const float du = dboxcox(Y[k * ldY + b], Yt[k * ldY + b], lam);
+          v[j] = (du - mean_f[k]) / std_f[k];
+        }
+      }
+      *reinterpret_cast<float4*>(orow + k0) = make_float4(v[0], v[1], v[2], v[3]);
     }
-    Oh[e] = v;
   }
 }
 
@@ -239,7 +256,8 @@ int blocks_for(int64_t work) {
 cudaError_t launch_train_targets(const EosParams& P, int64_t B, const double* Y, const double* Yt,
                                  int64_t ldY, float* Oh, int64_t ldh, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
-  targets_kernel<<<blocks_for(B * ldh), kThreads, 0, st>>>(P, B, Y, Yt, ldY, P.norm, Oh, ldh);
+  if ((ldh & 3) || P.n > 64) return cudaErrorInvalidValue;
+  targets_kernel<<<blocks_for(B), kThreads, 0, st>>>(P, B, Y, Yt, ldY, P.norm, Oh, ldh);
   return cudaGetLastError();
 }
 
