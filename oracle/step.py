@@ -130,7 +130,30 @@ def chem_source(mech, net, T, p, Y, dt, T_react=600.0, newton_tol=1e-12, max_ite
     return omega, Tn, status
 
 
-__all__ = ["active_cells", "solve_T", "chem_step", "chem_source", "real_fluid_props",
+def chem_step_vjp(mech, net, T, p, Y, gT, gY, T_react=600.0, **fd):
+    """Reverse-mode product of the reaction step: given cotangents gT [N] and gY [n, N] of the
+    step's outputs (T', Y'), the cotangents of its inputs (T, Y) with p fixed,
+        g_v = gT dT'/dv + sum_k gY_k dY'_k/dv,   v = (T, Y_1..Y_n),
+    from chem_step_jacobian_fd (keyword arguments go to it) with Y'_k = Y_k + dY_k. Cells that
+    do not react (T <= T_react, or a non-finite T) are left as they were by the step, so their
+    cotangents pass through. Returns (g_T [N], g_Y [n, N]); entries whose Jacobian column is
+    NaN (species below the difference floor) are NaN."""
+    T = np.asarray(T, dtype=np.float64)
+    gT = np.asarray(gT, dtype=np.float64)
+    gY = np.asarray(gY, dtype=np.float64)
+    J, dTn = chem_step_jacobian_fd(mech, net, T, p, Y, **fd)
+    n, N = gY.shape
+    g = np.empty((N, n + 1))
+    for c in range(N):
+        dYp = J[c] + np.hstack([np.zeros((n, 1)), np.eye(n)])   # dY'_k/dv_t
+        g[c] = gT[c] * dTn[c] + gY[:, c] @ dYp
+    passive = ~(T > T_react)
+    g[passive, 0] = gT[passive]
+    g[passive, 1:] = gY[:, passive].T
+    return g[:, 0].copy(), g[:, 1:].T.copy()
+
+
+__all__ = ["active_cells", "solve_T", "chem_step", "chem_source", "real_fluid_props", "chem_step_vjp",
            "NOT_CONVERGED", "NONFINITE", "NO_ROOT"]
 
 

@@ -494,3 +494,54 @@ def test_tabulated_gelu_follows_its_definition_and_error_bound():
     np.testing.assert_allclose(nw.gelu_table(nodes), nw.gelu_tanh(nodes), atol=4e-7)
     # the jumps at the ends of the table are the paper's approximation: GELU(3) - 3, GELU(-3)
     assert abs(nw.gelu_tanh(3.0) - 3.0) > 1e-3 and abs(nw.gelu_tanh(-3.0)) > 1e-3
+
+
+def _vjp_case(n_cells, T_react):
+    mech, net, T, p, Y = synth.configs.build("small-fp32-4k", n_cells=n_cells)
+    # keep every temperature clear of the reaction threshold, so that no difference crosses it
+    T = np.where(np.abs(T - T_react) < 0.02 * T_react, T_react + 0.05 * T_react, T)
+    rng = np.random.default_rng(7)
+    gT = rng.uniform(-1e-3, 1e-3, n_cells)
+    gY = rng.uniform(-1.0, 1.0, Y.shape)
+    return mech, net, T, p, Y, gT, gY, rng
+
+
+def test_step_vjp_adjoint_identity_with_directional_differences():
+    """<g, S'(x) v> = <S'(x)^T g, v>: the directional difference of the whole step along a
+    random direction v (one perturbation of T and every Y_j at once) against the reverse-mode
+    product dotted with v, on reacting and non-reacting cells (which pass the cotangents)."""
+    T_react = 600.0
+    mech, net, T, p, Y, gT, gY, rng = _vjp_case(20, T_react)
+    assert np.any(T <= T_react) and np.any(T > T_react)
+    floor = 1e-4
+    vT = rng.uniform(-1.0, 1.0, T.shape) * T
+    vY = np.where(Y >= floor, rng.uniform(-1.0, 1.0, Y.shape) * Y, 0.0)
+    gvT, gvY = step.chem_step_vjp(mech, net, T, p, Y, gT, gY, T_react=T_react,
+                                  dY_rel=1e-4, dY_min=floor)
+    eps = 1e-4
+    Tp, Yp, sp = step.chem_step(mech, net, T + eps * vT, p, Y + eps * vY, net.dt, T_react)
+    Tm, Ym, sm = step.chem_step(mech, net, T - eps * vT, p, Y - eps * vY, net.dt, T_react)
+    assert np.all(sp == 0) and np.all(sm == 0)
+    lhs = gT * (Tp - Tm) / (2 * eps) + np.sum(gY * (Yp - Ym), axis=0) / (2 * eps)
+    rhs = gvT * vT + np.sum(np.where(vY != 0.0, gvY * vY, 0.0), axis=0)
+    scale = np.abs(gT * vT) + np.sum(np.abs(gY * vY), axis=0)
+    np.testing.assert_allclose(lhs, rhs, atol=1e-6 * scale.max())
+    off = ~(T > T_react)
+    np.testing.assert_array_equal(gvT[off], gT[off])
+    np.testing.assert_array_equal(gvY[:, off], gY[:, off])
+
+
+def test_step_vjp_zero_network_closed_form():
+    """With a zero read-out Y' = Y / sum(Y) (sum 1 here) and T' keeps h: dY'_k/dY_j =
+    [k = j] - Y_k, dY'/dT = 0, dT'/dT = 1 and dT'/dY_j = h / cp, so the product is
+    g_T = gT and g_Y_j = gT h / cp + gY_j - sum_k gY_k Y_k."""
+    mech, net, T, p, Y, gT, gY, _ = _vjp_case(12, 0.0)
+    net.W[-1] = np.zeros_like(net.W[-1])
+    net.b[-1] = np.zeros_like(net.b[-1])
+    gvT, gvY = step.chem_step_vjp(mech, net, T, p, Y, gT, gY, T_react=0.0, dY_min=1e-4)
+    s = pe.state(mech, T, p, Y)
+    want = gT[None, :] * (s["h"] / s["cp"])[None, :] + gY - np.sum(gY * Y, axis=0)[None, :]
+    fin = np.isfinite(gvY)
+    assert fin.sum() > 0.5 * fin.size
+    np.testing.assert_allclose(gvY[fin], want[fin], rtol=1e-5, atol=1e-3 * np.abs(gT).max() + 1e-7)
+    np.testing.assert_allclose(gvT, gT, rtol=1e-6)
