@@ -187,6 +187,27 @@ df_status df_chem_source(df_state* s, int64_t n_cells, double dt, const double* 
 df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const double* p,
                            const double* Y, int64_t ldY, float* J_dY, double* dTnew, void* stream);
 
+/* Reverse-mode product of the reaction step, the adjoint of df_chem_jacobian: it lets a model
+ * that contains the step (Sec. 2's network followed by the real-fluid T-from-h solve) be
+ * trained by back-propagation, e.g. through a torch.autograd.Function. Given cotangents of the
+ * step's outputs (T', Y'),
+ *   gT    (device [n_cells] FP64) and gY (device, [n][ldg] species-major FP64, ldg >= n_cells),
+ * it writes the cotangents of the inputs (T, Y) with p fixed and the Y_j independent:
+ *   out_gT[c]    = gT[c] dT'/dT   + sum_k gY[k][c] dY'_k/dT,
+ *   out_gY[j][c] = gT[c] dT'/dY_j + sum_k gY[k][c] dY'_k/dY_j     ([n][ldo], ldo >= n_cells),
+ * Y'_k = Y_k + (Y'_k - Y_k) with the Jacobian columns of df_chem_jacobian (same precision and
+ * Box-Cox floor). Cells that do not react (T <= T_react, or a non-finite T) are left as they
+ * were by the step, so their cotangents are copied through; reacting cells that the step would
+ * flag get NaN. The outputs must not overlap the inputs. Runs in batches of
+ * min(batch_cells, 65,536) cells: the Jacobian of a batch, then its contraction (a warp per
+ * cell, FP64 sums in a fixed order, so results repeat bit for bit). Allocates the Jacobian
+ * columns of one batch (batch x n x (n+1) FP32 and batch x (n+1) FP64) at its first call, on
+ * top of df_chem_jacobian's buffers, and shares that call's restrictions: DF_ERR_UNSUPPORTED
+ * for DF_GELU_TABLE, and no overlap with other calls on the same state. Asynchronous. */
+df_status df_chem_step_vjp(df_state* s, int64_t n_cells, const double* T, const double* p,
+                           const double* Y, int64_t ldY, const double* gT, const double* gY,
+                           int64_t ldg, double* out_gT, double* out_gY, int64_t ldo, void* stream);
+
 /* ---- training of the chemistry network ----
  * The paper trains its network offline and prints no loss; the library's reading: the network
  * is taught the change of the Box-Cox coordinates that a stiff integration of the cell

@@ -11,6 +11,6 @@ the thin Python binding of both.
 from ._lib import (DF_BF16, DF_FP8_E4M3, DF_FP32, DF_CELL_NO_ROOT, DF_CELL_NONFINITE,  # noqa: F401
                    DF_CELL_NOT_CONVERGED, DF_GELU_TABLE, DF_GELU_TANH, DF_SOLVER_DOUBLE_FLOAT,
                    DF_SOLVER_FP64, DF_TILE_PAIR, DF_HOST_DIRECT, LIB_PATH)
-from .api import DFError, MLPEOSFunction, State, version  # noqa: F401
+from .api import ChemStepFunction, DFError, MLPEOSFunction, State, version  # noqa: F401
 from .solver import Solver, mesh_decompose, mesh_renumber  # noqa: F401
 from .propnet import PropNet  # noqa: F401

@@ -88,6 +88,7 @@ SIGNATURES = {
     "df_chem_source": (_ST, [_VP, _I64, C.c_double, _VP, _VP, _VP, _I64, _VP, _I64, _VP, _VP, _VP,
                              _VP]),
     "df_chem_jacobian": (_ST, [_VP, _I64, _VP, _VP, _VP, _I64, _VP, _VP, _VP]),
+    "df_chem_step_vjp": (_ST, [_VP, _I64, _VP, _VP, _VP, _I64, _VP, _VP, _I64, _VP, _VP, _I64, _VP]),
     "df_get_step_summary": (_ST, [_VP, _VP, C.POINTER(StepStats)]),
     "df_active_compact": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP]),
     "df_eos_pre": (_ST, [_VP, _I64, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]),

@@ -130,6 +130,19 @@ class State:
                                                _ptr(J), _ptr(dTn), _stream(stream)))
         return J, dTn
 
+    def chem_step_vjp(self, T, p, Y, gT, gY, stream=None):
+        """(g_T [N], g_Y [n, N]) FP64: df_chem_step_vjp, the cotangents of (T, Y) from those
+        of the step's outputs (T', Y')."""
+        N = T.shape[0]
+        gT = gT.to(torch.float64).contiguous()
+        gY = gY.to(torch.float64).contiguous()
+        oT = torch.empty(N, dtype=torch.float64, device=T.device)
+        oY = torch.empty(self.n, N, dtype=torch.float64, device=T.device)
+        self._check(self._lib.df_chem_step_vjp(self.h, N, _ptr(T), _ptr(p), _ptr(Y), Y.stride(0),
+                                               _ptr(gT), _ptr(gY), max(N, 1), _ptr(oT), _ptr(oY),
+                                               max(N, 1), _stream(stream)))
+        return oT, oY
+
     def graph(self, T, p, Y, dt=None, status=None, n_active=None):
         """A Graph replaying df_chem_step on these exact buffers (see df_graph_create)."""
         return Graph(self, T, p, Y, dt, status, n_active)
@@ -287,6 +300,32 @@ class MLPEOSFunction(torch.autograd.Function):
     def backward(ctx, dO):
         dX = ctx.state.mlp_backward(dO.float(), want_dx=ctx.needs_input_grad[0])
         return dX, None
+
+
+class ChemStepFunction(torch.autograd.Function):
+    """The reaction step as a differentiable torch op, (T [N], Y [n, N]) -> (T', Y') at fixed p:
+    forward = df_chem_step on copies of T and Y, backward = df_chem_step_vjp (the network's
+    tangents and the equation-of-state chain, all in the library's kernels).
+    Usage: T1, Y1 = ChemStepFunction.apply(T, Y, p, state)."""
+
+    @staticmethod
+    def forward(ctx, T, Y, p, state):
+        T0, Y0 = T.detach().contiguous(), Y.detach().contiguous()
+        T1, Y1 = T0.clone(), Y0.clone()
+        state.chem_step(T1, p, Y1)
+        ctx.state = state
+        ctx.save_for_backward(T0, Y0, p)
+        return T1, Y1
+
+    @staticmethod
+    def backward(ctx, gT1, gY1):
+        T0, Y0, p = ctx.saved_tensors
+        if gT1 is None:
+            gT1 = torch.zeros_like(T0)
+        if gY1 is None:
+            gY1 = torch.zeros_like(Y0)
+        gT, gY = ctx.state.chem_step_vjp(T0, p, Y0, gT1, gY1)
+        return gT, gY, None, None
 
 
 class Graph:

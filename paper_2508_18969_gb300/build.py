@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdfgb.so")
 SOURCES = ["state.cu", "train_api.cu", "eos.cu", "compact.cu", "mlp_simt.cu", "mlp_tc.cu", "train.cu",
-           "solver.cu", "mesh.cpp", "propnet.cu"]
+           "solver.cu", "mesh.cpp", "propnet.cu", "step_vjp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-Xcompiler", "-pthread",

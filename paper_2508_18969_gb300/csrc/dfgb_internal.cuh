@@ -114,6 +114,14 @@ cudaError_t launch_jac_post(const EosParams& P, int64_t ncell, int64_t cell0, co
                             int64_t ldo, const float* dO, int64_t lddo, const double* h0, float* J,
                             double* dTn, double* scr, int32_t* cst, cudaStream_t st);
 
+// ---- launcher (step_vjp.cu) ----
+// Per cell of a batch: g_v = gT dT'/dv + sum_k gY_k dY'_k/dv from the batch's Jacobian J
+// [ncell][n][n+1] FP32 and dTn [ncell][n+1] FP64 (cell-local); non-reacting cells copy the
+// cotangents. gY / oY are species-major with leading dimensions ldg / ldo.
+cudaError_t launch_step_vjp(int n, int64_t ncell, double T_react, const double* T, const float* J,
+                            const double* dTn, const double* gT, const double* gY, int64_t ldg,
+                            double* oT, double* oY, int64_t ldo, cudaStream_t st);
+
 // ---- launchers (train.cu) ----
 // Ohat [B x ldh] FP32 (zero pads) = (BC(Yt) - BC(Y) - out_mean) / out_std of cells 0..B-1.
 cudaError_t launch_train_targets(const EosParams& P, int64_t B, const double* Y, const double* Yt,

@@ -133,7 +133,7 @@ void free_state(df_state* s) {
   for (auto p : s->Wlp) f(p);
   for (auto p : s->col_scale) f(p);
   f(s->x); f(s->act[0]); f(s->act[1]); f(s->O); f(s->h0); f(s->rho_row); f(s->rstat);
-  f(s->idx); f(s->cscr);
+  f(s->idx); f(s->cscr); f(s->vjpJ); f(s->vjpT);
   for (int b = 0; b < 2; ++b) {
     f(s->hp.T[b]); f(s->hp.p[b]); f(s->hp.Y[b]); f(s->hp.st[b]);
     if (s->hp.ev_in[b]) cudaEventDestroy(s->hp.ev_in[b]);
@@ -1144,6 +1144,50 @@ df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const 
                           dTnew, j->jscr, j->jst, st);
   }
   return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "Jacobian");
+}
+
+df_status df_chem_step_vjp(df_state* s, int64_t n_cells, const double* T, const double* p,
+                           const double* Y, int64_t ldY, const double* gT, const double* gY,
+                           int64_t ldg, double* out_gT, double* out_gY, int64_t ldo,
+                           void* stream) {
+  df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
+  if (rc != DF_OK || n_cells == 0) return rc;
+  if (!gT || !gY || !out_gT || !out_gY) return fail(s, DF_ERR_INVALID_ARG, "NULL cotangent pointer");
+  if (ldg < n_cells || ldo < n_cells)
+    return fail(s, DF_ERR_INVALID_ARG, "ldg (%lld) or ldo (%lld) < n_cells (%lld)", (long long)ldg,
+                (long long)ldo, (long long)n_cells);
+  DeviceGuard guard(s->device);
+  const int n = s->n, ntan = n + 1;
+  // batches of the Jacobian's own batch size, so that each Jacobian call below is one batch
+  const int64_t B = std::min<int64_t>(s->cap, 65536);
+  if (s->vjp_cap < B) {
+    cudaDeviceSynchronize();
+    if (s->vjpJ) cudaFree(s->vjpJ);
+    if (s->vjpT) cudaFree(s->vjpT);
+    s->vjpJ = nullptr;
+    s->vjpT = nullptr;
+    s->vjp_cap = 0;
+    cudaError_t e = cudaMalloc(&s->vjpJ, sizeof(float) * (size_t)B * n * ntan);
+    if (e == cudaSuccess) e = cudaMalloc(&s->vjpT, sizeof(double) * (size_t)B * ntan);
+    if (e != cudaSuccess) {
+      if (s->vjpJ) cudaFree(s->vjpJ);
+      s->vjpJ = nullptr;
+      s->vjpT = nullptr;
+      cudaGetLastError();
+      return fail(s, DF_ERR_OOM, "Jacobian columns of one batch (%lld cells)", (long long)B);
+    }
+    s->vjp_cap = B;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int64_t c0 = 0; c0 < n_cells; c0 += B) {
+    const int64_t nb = std::min<int64_t>(B, n_cells - c0);
+    rc = df_chem_jacobian(s, nb, T + c0, p + c0, Y + c0, ldY, s->vjpJ, s->vjpT, stream);
+    if (rc != DF_OK) return rc;
+    const cudaError_t e = launch_step_vjp(n, nb, s->T_react, T + c0, s->vjpJ, s->vjpT, gT + c0,
+                                          gY + c0, ldg, out_gT + c0, out_gY + c0, ldo, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "reverse-mode product of the step");
+  }
+  return DF_OK;
 }
 
 // ---- tile-width autotuning ----

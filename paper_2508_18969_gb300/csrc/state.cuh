@@ -102,6 +102,10 @@ struct df_state {
   std::vector<TcLayer> tcl;
   std::vector<std::vector<float>> Wh;    // host copies of the FP32 weights (Jacobian set-up)
   struct Jac* jac = nullptr;             // Jacobian context, built at the first Jacobian call
+  // one batch of Jacobian columns for df_chem_step_vjp, allocated at its first call
+  float* vjpJ = nullptr;                 // [vjp_cap][n][n+1]
+  double* vjpT = nullptr;                // [vjp_cap][n+1]
+  int64_t vjp_cap = 0;
   Trn* trn = nullptr;                    // training context, built at the first training call
   int64_t wver = 0;                      // bumped whenever training changes the weights
   std::string err;

@@ -90,6 +90,8 @@ def test_entry_points_reject_null_state(lib):
     assert lib.df_chem_step(None, 10, 1e-7, None, None, None, 10, None, None, None) == _lib.DF_ERR_INVALID_ARG
     assert lib.df_real_fluid_props(None, 10, None, None, None, 10, None, None, None, None, None) == _lib.DF_ERR_INVALID_ARG
     assert lib.df_active_compact(None, 10, None, None, None, None) == _lib.DF_ERR_INVALID_ARG
+    assert lib.df_chem_step_vjp(None, 10, None, None, None, 10, None, None, 10, None, None, 10,
+                                None) == _lib.DF_ERR_INVALID_ARG
     lib.df_state_destroy(None)
 
 
