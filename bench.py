@@ -687,6 +687,21 @@ def run_jacobian(args):
         e1.record(stream)
         torch.cuda.synchronize()
     ms = max_over_ranks(world, e0.elapsed_time(e1) / args.steps, local)
+    # the step's reverse-mode product (df_chem_step_vjp): each batch's Jacobian, then its
+    # contraction with the cotangents of (T', Y')
+    rng = np.random.default_rng(1 + rank)
+    gTd = torch.tensor(rng.uniform(-1e-3, 1e-3, N), device=dev)
+    gYd = torch.tensor(rng.uniform(-1.0, 1.0, Y.shape), device=dev)
+    for _ in range(args.warmup):
+        st.chem_step_vjp(Td, pd, Yd, gTd, gYd)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st.chem_step_vjp(Td, pd, Yd, gTd, gYd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    vjp_ms = max_over_ranks(world, e0.elapsed_time(e1) / args.steps, local)
     if rank != 0:
         return 0
     err = None
@@ -716,7 +731,10 @@ def run_jacobian(args):
                        "tangents_per_cell": ntan},
             "clocks": clk.summary(),
             "network_tflops": flops * N / (ms * 1e-3) / 1e12,
-            "error_vs_finite_differences": err}
+            "error_vs_finite_differences": err,
+            "reverse_mode_product": {"entry_point": "df_chem_step_vjp", "ms_per_step": vjp_ms,
+                                     "cells_per_s": weak_scaling_value(world, N, vjp_ms),
+                                     "over_jacobian": vjp_ms / ms}}
     print(json.dumps(line), flush=True)
     return 0
 
