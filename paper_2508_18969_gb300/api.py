@@ -24,6 +24,45 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _check_cells(n, T, p=None, Y=None, status=None, n_active=None, device_type="cuda"):
+    """Checks the cell arrays a device entry point dereferences, before any library call:
+    T and p 1-D float64 of N cells with unit stride, Y float64 [n, N] with unit stride along
+    the cells (its row stride is passed as ldY), status int32 and n_active int64 of at least
+    N and 1 elements, all on a CUDA device. Any other tensor would be read or written out of
+    bounds by the kernels. Returns N."""
+    def bad(name, what):
+        raise ValueError(f"{name} must be {what}")
+
+    def on_dev(name, t):
+        if t.device.type != device_type:
+            bad(name, f"on a {device_type} device (got {t.device})")
+
+    on_dev("T", T)
+    if T.dtype != torch.float64 or T.dim() != 1:
+        bad("T", "a 1-D float64 tensor")
+    N = T.shape[0]
+    if N > 1 and T.stride(0) != 1:
+        bad("T", "contiguous")
+    if p is not None:
+        on_dev("p", p)
+        if p.dtype != torch.float64 or p.dim() != 1 or p.shape[0] != N or (N > 1 and p.stride(0) != 1):
+            bad("p", f"a contiguous 1-D float64 tensor of {N} cells")
+    if Y is not None:
+        on_dev("Y", Y)
+        if Y.dtype != torch.float64 or Y.dim() != 2 or tuple(Y.shape) != (n, N) or \
+                (N > 1 and Y.stride(1) != 1):
+            bad("Y", f"a float64 tensor [{n}, {N}] with unit stride along the cells")
+    if status is not None:
+        on_dev("status", status)
+        if status.dtype != torch.int32 or not status.is_contiguous() or status.numel() < N:
+            bad("status", f"a contiguous int32 tensor of at least {N} elements")
+    if n_active is not None:
+        on_dev("n_active", n_active)
+        if n_active.dtype != torch.int64 or n_active.numel() < 1:
+            bad("n_active", "an int64 tensor of at least one element")
+    return N
+
+
 def _stream(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -91,7 +130,7 @@ class State:
 
     # ---- full step ----
     def chem_step(self, T, p, Y, dt=None, status=None, n_active=None, stream=None):
-        N = T.shape[0]
+        N = _check_cells(self.n, T, p, Y, status, n_active)
         self._check(self._lib.df_chem_step(self.h, N, self.dt if dt is None else float(dt),
                                            _ptr(T), _ptr(p), _ptr(Y), Y.stride(0), _ptr(status),
                                            _ptr(n_active), _stream(stream)))
@@ -112,7 +151,7 @@ class State:
 
     def chem_source(self, T, p, Y, dt=None, status=None, n_active=None, want_T=True, stream=None):
         """(omega [n, N] FP64 kg/(m^3 s), T' [N] or None): df_chem_source; T, Y unchanged."""
-        N = T.shape[0]
+        N = _check_cells(self.n, T, p, Y, status, n_active)
         om = torch.empty(self.n, N, dtype=torch.float64, device=T.device)
         Tn = torch.empty(N, dtype=torch.float64, device=T.device) if want_T else None
         self._check(self._lib.df_chem_source(self.h, N, self.dt if dt is None else float(dt),
@@ -123,7 +162,7 @@ class State:
 
     def chem_jacobian(self, T, p, Y, want_dT=True, stream=None):
         """(J [N, n, n+1] FP32, dTnew [N, n+1] FP64 or None): df_chem_jacobian."""
-        N = T.shape[0]
+        N = _check_cells(self.n, T, p, Y)
         J = torch.empty(N, self.n, self.n + 1, dtype=torch.float32, device=T.device)
         dTn = torch.empty(N, self.n + 1, dtype=torch.float64, device=T.device) if want_dT else None
         self._check(self._lib.df_chem_jacobian(self.h, N, _ptr(T), _ptr(p), _ptr(Y), Y.stride(0),
@@ -133,9 +172,11 @@ class State:
     def chem_step_vjp(self, T, p, Y, gT, gY, stream=None):
         """(g_T [N], g_Y [n, N]) FP64: df_chem_step_vjp, the cotangents of (T, Y) from those
         of the step's outputs (T', Y')."""
-        N = T.shape[0]
+        N = _check_cells(self.n, T, p, Y)
         gT = gT.to(torch.float64).contiguous()
         gY = gY.to(torch.float64).contiguous()
+        if _check_cells(self.n, gT, None, gY) != N:
+            raise ValueError(f"gT and gY must hold the {N} cells of T")
         oT = torch.empty(N, dtype=torch.float64, device=T.device)
         oY = torch.empty(self.n, N, dtype=torch.float64, device=T.device)
         self._check(self._lib.df_chem_step_vjp(self.h, N, _ptr(T), _ptr(p), _ptr(Y), Y.stride(0),
@@ -154,7 +195,7 @@ class State:
         return rc, s.n_active, s.n_flagged, s.newton_iterations
 
     def real_fluid_props(self, T, p, Y, stream=None):
-        N = T.shape[0]
+        N = _check_cells(self.n, T, p, Y)
         out = [torch.empty(N, dtype=torch.float64, device=T.device) for _ in range(4)]
         self._check(self._lib.df_real_fluid_props(self.h, N, _ptr(T), _ptr(p), _ptr(Y), Y.stride(0),
                                                   *[_ptr(o) for o in out], _stream(stream)))
@@ -254,7 +295,7 @@ class State:
 
     # ---- stages ----
     def active_compact(self, T, stream=None):
-        N = T.shape[0]
+        N = _check_cells(self.n, T)
         idx = torch.empty(max(N, 1), dtype=torch.int32, device=T.device)
         cnt = torch.zeros(1, dtype=torch.int64, device=T.device)
         self._check(self._lib.df_active_compact(self.h, N, _ptr(T), _ptr(idx), _ptr(cnt),
@@ -262,7 +303,7 @@ class State:
         return idx, cnt
 
     def eos_pre(self, T, p, Y, stream=None):
-        N = T.shape[0]
+        N = _check_cells(self.n, T, p, Y)
         h0 = torch.empty(N, dtype=torch.float64, device=T.device)
         Z = torch.empty(N, dtype=torch.float64, device=T.device)
         x = torch.empty(N, self.K0, dtype=torch.float32, device=T.device)

@@ -70,3 +70,40 @@ def test_chem_step_function_plumbing():
     (gY,) = torch.autograd.grad((wY * Y1).sum(), (Y,))
     assert torch.equal(st.calls[-1][0], torch.zeros(2, dtype=torch.float64))
     assert torch.equal(gY, 5.0 * wY)
+
+
+def test_cell_arrays_are_checked_before_the_library_is_called():
+    from paper_2508_18969_gb300.api import State, _check_cells
+    f64 = torch.float64
+    T, p, Y = torch.zeros(5, dtype=f64), torch.zeros(5, dtype=f64), torch.zeros(3, 5, dtype=f64)
+    ok = dict(device_type="cpu")
+    assert _check_cells(3, T, p, Y, torch.zeros(5, dtype=torch.int32),
+                        torch.zeros(1, dtype=torch.int64), **ok) == 5
+    assert _check_cells(3, T[:0], p[:0], Y[:, :0], **ok) == 0
+    Yw = torch.zeros(3, 8, dtype=f64)[:, :5]          # a row stride above N is allowed
+    assert _check_cells(3, T, p, Yw, **ok) == 5
+    bad = [
+        dict(T=T.float()),                             # FP32 temperatures
+        dict(T=torch.zeros(10, dtype=f64)[::2]),       # strided
+        dict(p=torch.zeros(4, dtype=f64)),             # wrong length
+        dict(Y=torch.zeros(4, 5, dtype=f64)),          # wrong species count
+        dict(Y=torch.zeros(5, 3, dtype=f64).t()),      # cells not contiguous
+        dict(Y=Y.float()),
+        dict(status=torch.zeros(5, dtype=torch.int64)),
+        dict(status=torch.zeros(4, dtype=torch.int32)),
+        dict(n_active=torch.zeros(1, dtype=torch.int32)),
+    ]
+    for b in bad:
+        a = dict(T=T, p=p, Y=Y)
+        a.update(b)
+        with pytest.raises(ValueError):
+            _check_cells(3, a["T"], a["p"], a["Y"], a.get("status"), a.get("n_active"), **ok)
+    # a state's entry points refuse host tensors without touching the library
+    st = object.__new__(State)
+    st.n, st.h, st._lib, st.dt = 3, None, None, 1e-7
+    for call in (lambda: st.chem_step(T, p, Y), lambda: st.chem_source(T, p, Y),
+                 lambda: st.chem_jacobian(T, p, Y), lambda: st.chem_step_vjp(T, p, Y, T, Y),
+                 lambda: st.real_fluid_props(T, p, Y), lambda: st.eos_pre(T, p, Y),
+                 lambda: st.active_compact(T)):
+        with pytest.raises(ValueError, match="cuda"):
+            call()
