@@ -319,9 +319,14 @@ class State:
         return O
 
     def eos_post(self, O, h0, T, p, Y, stream=None):
-        N = T.shape[0]
+        N = _check_cells(self.n, T, p, Y)
+        O = O.contiguous()
+        if _check_cells(self.n, h0) != N:
+            raise ValueError(f"h0 must hold the {N} cells of T")
+        if O.device.type != "cuda" or O.dtype != torch.float32 or tuple(O.shape) != (N, self.n):
+            raise ValueError(f"O must be a float32 CUDA tensor [{N}, {self.n}]")
         st = torch.empty(N, dtype=torch.int32, device=T.device)
-        self._check(self._lib.df_eos_post(self.h, N, _ptr(O.contiguous()), _ptr(h0), _ptr(T),
+        self._check(self._lib.df_eos_post(self.h, N, _ptr(O), _ptr(h0), _ptr(T),
                                           _ptr(p), _ptr(Y), Y.stride(0), _ptr(st), _stream(stream)))
         return st
 
@@ -373,6 +378,7 @@ class Graph:
     """One captured df_chem_step (df_graph_*); launch() replays it."""
 
     def __init__(self, state, T, p, Y, dt, status, n_active):
+        _check_cells(state.n, T, p, Y, status, n_active)
         self._lib = state._lib
         self._state = state
         self._bufs = (T, p, Y, status, n_active)  # keep the captured buffers alive
@@ -405,8 +411,8 @@ def active_compact_static(T, T_react: float, stream=None):
     """Allocation-free a0 (df_active_compact_static): no state, scratch in the library's
     static device array. Returns (idx, count) tensors; the caller allocates them here, the
     library does not."""
+    N = _check_cells(0, T)
     lib = L.load()
-    N = T.shape[0]
     idx = torch.empty(max(N, 1), dtype=torch.int32, device=T.device)
     cnt = torch.zeros(1, dtype=torch.int64, device=T.device)
     rc = lib.df_active_compact_static(N, float(T_react), _ptr(T), _ptr(idx), _ptr(cnt), _stream(stream))

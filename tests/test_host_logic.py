@@ -101,9 +101,13 @@ def test_cell_arrays_are_checked_before_the_library_is_called():
     # a state's entry points refuse host tensors without touching the library
     st = object.__new__(State)
     st.n, st.h, st._lib, st.dt = 3, None, None, 1e-7
+    from paper_2508_18969_gb300.api import Graph, active_compact_static
+    O = torch.zeros(5, 3)
     for call in (lambda: st.chem_step(T, p, Y), lambda: st.chem_source(T, p, Y),
                  lambda: st.chem_jacobian(T, p, Y), lambda: st.chem_step_vjp(T, p, Y, T, Y),
                  lambda: st.real_fluid_props(T, p, Y), lambda: st.eos_pre(T, p, Y),
-                 lambda: st.active_compact(T)):
+                 lambda: st.active_compact(T), lambda: st.eos_post(O, T, T, p, Y),
+                 lambda: Graph(st, T, p, Y, None, None, None),
+                 lambda: active_compact_static(T, 600.0)):
         with pytest.raises(ValueError, match="cuda"):
             call()
