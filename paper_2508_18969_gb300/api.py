@@ -24,7 +24,8 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
-def _check_cells(n, T, p=None, Y=None, status=None, n_active=None, device_type="cuda"):
+def _check_cells(n, T, p=None, Y=None, status=None, n_active=None, device_type="cuda",
+                 names=("T", "p", "Y")):
     """Checks the cell arrays a device entry point dereferences, before any library call:
     T and p 1-D float64 of N cells with unit stride, Y float64 [n, N] with unit stride along
     the cells (its row stride is passed as ldY), status int32 and n_active int64 of at least
@@ -37,21 +38,22 @@ def _check_cells(n, T, p=None, Y=None, status=None, n_active=None, device_type="
         if t.device.type != device_type:
             bad(name, f"on a {device_type} device (got {t.device})")
 
-    on_dev("T", T)
+    nT, np_, nY = names
+    on_dev(nT, T)
     if T.dtype != torch.float64 or T.dim() != 1:
-        bad("T", "a 1-D float64 tensor")
+        bad(nT, "a 1-D float64 tensor")
     N = T.shape[0]
     if N > 1 and T.stride(0) != 1:
-        bad("T", "contiguous")
+        bad(nT, "contiguous")
     if p is not None:
-        on_dev("p", p)
+        on_dev(np_, p)
         if p.dtype != torch.float64 or p.dim() != 1 or p.shape[0] != N or (N > 1 and p.stride(0) != 1):
-            bad("p", f"a contiguous 1-D float64 tensor of {N} cells")
+            bad(np_, f"a contiguous 1-D float64 tensor of {N} cells")
     if Y is not None:
-        on_dev("Y", Y)
+        on_dev(nY, Y)
         if Y.dtype != torch.float64 or Y.dim() != 2 or tuple(Y.shape) != (n, N) or \
                 (N > 1 and Y.stride(1) != 1):
-            bad("Y", f"a float64 tensor [{n}, {N}] with unit stride along the cells")
+            bad(nY, f"a float64 tensor [{n}, {N}] with unit stride along the cells")
     if status is not None:
         on_dev("status", status)
         if status.dtype != torch.int32 or not status.is_contiguous() or status.numel() < N:

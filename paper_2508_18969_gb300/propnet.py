@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from .api import DFError, State, _ptr, _stream
+from .api import DFError, State, _check_cells, _ptr, _stream
 
 
 class PropNet(State):
@@ -52,9 +52,10 @@ class PropNet(State):
 
     def infer(self, h, p, Y, out=None, stream=None):
         """Properties [m, N] (FP64) of the cells (df_propnet_infer)."""
-        N = h.shape[0]
+        N = _check_cells(self.n, h, p, Y, names=("h", "p", "Y"))
         if out is None:
             out = torch.empty(self.m, N, dtype=torch.float64, device=h.device)
+        _check_cells(self.m, h, None, out, names=("h", "p", "out"))
         self._check(self._lib.df_propnet_infer(self.h, N, _ptr(h), _ptr(p), _ptr(Y), Y.stride(0),
                                                _ptr(out), out.stride(0), _stream(stream)))
         return out
@@ -63,6 +64,8 @@ class PropNet(State):
                  stream=None):
         """One Adam step towards target properties [m, B] (df_propnet_train_step). Returns the
         device FP32 loss tensor (shape [1]) the step writes."""
+        _check_cells(self.n, h, p, Y, names=("h", "p", "Y"))
+        _check_cells(self.m, h, None, target, names=("h", "p", "target"))
         if loss is None:
             loss = torch.empty(1, dtype=torch.float32, device=h.device)
         hp = self._adam(lr, betas, eps)

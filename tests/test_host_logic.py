@@ -111,3 +111,16 @@ def test_cell_arrays_are_checked_before_the_library_is_called():
                  lambda: active_compact_static(T, 600.0)):
         with pytest.raises(ValueError, match="cuda"):
             call()
+    # the property network's entry points, with their own argument names
+    from paper_2508_18969_gb300.propnet import PropNet
+    pn = object.__new__(PropNet)
+    pn.n, pn.m, pn.h, pn._lib = 3, 1, None, None
+    with pytest.raises(ValueError, match="^h must be on a cuda"):
+        pn.infer(T, p, Y)
+    with pytest.raises(ValueError, match="^h must be on a cuda"):
+        pn.fit_step(T, p, Y, torch.zeros(1, 5, dtype=f64))
+    assert _check_cells(1, T, None, torch.zeros(1, 5, dtype=f64), device_type="cpu",
+                        names=("h", "p", "target")) == 5
+    with pytest.raises(ValueError, match="^target"):
+        _check_cells(1, T, None, torch.zeros(2, 5, dtype=f64), device_type="cpu",
+                     names=("h", "p", "target"))
