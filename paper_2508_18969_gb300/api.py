@@ -212,6 +212,8 @@ class State:
                    stream=None):
         """One Adam step on the states (T, p, Y) with targets Y_target (df_train_step).
         Returns the device FP32 loss tensor (shape [1]) the step writes."""
+        _check_cells(self.n, T, p, Y)
+        _check_cells(self.n, T, None, Y_target, names=("T", "p", "Y_target"))
         if Y_target.stride(0) != Y.stride(0):
             raise ValueError("Y and Y_target must share their row stride")
         if loss is None:

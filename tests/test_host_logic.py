@@ -107,7 +107,7 @@ def test_cell_arrays_are_checked_before_the_library_is_called():
                  lambda: st.chem_jacobian(T, p, Y), lambda: st.chem_step_vjp(T, p, Y, T, Y),
                  lambda: st.real_fluid_props(T, p, Y), lambda: st.eos_pre(T, p, Y),
                  lambda: st.active_compact(T), lambda: st.eos_post(O, T, T, p, Y),
-                 lambda: Graph(st, T, p, Y, None, None, None),
+                 lambda: Graph(st, T, p, Y, None, None, None), lambda: st.train_step(T, p, Y, Y),
                  lambda: active_compact_static(T, 600.0)):
         with pytest.raises(ValueError, match="cuda"):
             call()
