@@ -529,6 +529,11 @@ def test_step_vjp_adjoint_identity_with_directional_differences():
     off = ~(T > T_react)
     np.testing.assert_array_equal(gvT[off], gT[off])
     np.testing.assert_array_equal(gvY[:, off], gY[:, off])
+    # a non-finite temperature is left as it was by the step: its cotangents pass through too
+    Tn = T.copy()
+    Tn[0] = np.nan
+    gvT, gvY = step.chem_step_vjp(mech, net, Tn, p, Y, gT, gY, T_react=T_react, dY_min=floor)
+    assert gvT[0] == gT[0] and np.array_equal(gvY[:, 0], gY[:, 0])
 
 
 def test_step_vjp_zero_network_closed_form():
