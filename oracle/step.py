@@ -137,7 +137,9 @@ def chem_step_vjp(mech, net, T, p, Y, gT, gY, T_react=600.0, **fd):
     from chem_step_jacobian_fd (keyword arguments go to it) with Y'_k = Y_k + dY_k. Cells that
     do not react (T <= T_react, or a non-finite T) are left as they were by the step, so their
     cotangents pass through. Returns (g_T [N], g_Y [n, N]); entries whose Jacobian column is
-    NaN (species below the difference floor) are NaN."""
+    NaN (species below the difference floor) are NaN. The paper prints no derivative of the
+    step (its networks are trained offline); this is the transpose of the step's Jacobian,
+    applied to the cotangents, by definition of the chain rule."""
     T = np.asarray(T, dtype=np.float64)
     gT = np.asarray(gT, dtype=np.float64)
     gY = np.asarray(gY, dtype=np.float64)
