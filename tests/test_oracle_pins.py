@@ -257,6 +257,70 @@ def test_mlp_brute_force_2_3_1():
     assert out[1] == pytest.approx(0.5, rel=1e-15)
 
 
+def _net_2sp(lam=0.5):
+    """A two-species network holder with hand-picked normalisation constants (no layers)."""
+    return SimpleNamespace(lam=lam, in_mean=np.array([1000.0, 1.0e7, -1.0, 0.5]),
+                           in_std=np.array([500.0, 2.0e6, 2.0, 0.25]),
+                           out_mean=np.array([0.25, -0.5]), out_std=np.array([2.0, 0.5]))
+
+
+def test_normalise_inputs_by_hand():
+    """Sec. 2 fixes the input order (T, p, Y_1, Y_2) and Sec. 3.3.1 the Z-score
+    (v - mean) / std. With lambda = 1/2, BC(y) = 2 (sqrt(y) - 1) is exact on the chosen
+    mass fractions: BC(1/4) = -1, BC(1) = 0, BC(9/16) = -1/2, BC(0) = BC(-0.001) = -2.
+    Rows and columns written out by hand, one row per cell."""
+    net = _net_2sp()
+    T = np.array([1500.0, 750.0, 1000.0])
+    p = np.array([1.2e7, 8.0e6, 1.0e7])
+    Y = np.array([[0.25, 1.0, -0.001],      # species 1 of cells 0, 1, 2
+                  [0.5625, 0.0, 1.0]])      # species 2
+    x = nw.normalise_inputs(net, T, p, Y)
+    want = np.array([
+        # (T - 1000)/500, (p - 1e7)/2e6, (BC(Y1) + 1)/2, (BC(Y2) - 0.5)/0.25
+        [1.0, 1.0, 0.0, -4.0],              # BC = (-1, -1/2)
+        [-0.5, -1.0, 0.5, -10.0],           # BC = (0, -2)
+        [0.0, 0.0, -0.5, -2.0],             # BC = (-2, 0)
+    ])
+    assert x.shape == (3, 4)
+    np.testing.assert_allclose(x, want, rtol=0, atol=1e-15)
+
+
+def test_denormalise_by_hand():
+    """The read-out de-normalisation: du = out_std O + out_mean, u = BC(Y) + du,
+    Y' = max(lambda u + 1, 0)^(1/lambda), then Y' / sum Y'. With lambda = 1/2 every value is
+    exact: cell 0 has du = (2 * 0.5 + 0.25, 0.5 * 1 - 0.5) = (1.25, 0), u = (0.25, -0.5),
+    Y' = (1.125^2, 0.75^2) = (81/64, 36/64), renormalised (9/13, 4/13); cell 1 has
+    du = (-2.75, 0.5), u = (-2.75, -0.5), lambda u_1 + 1 < 0 clips species 1 to 0, so
+    Y' = (0, 1). A swapped mean and spread, a missing renormalisation or a forward instead of
+    an inverse transform all move these values."""
+    net = _net_2sp()
+    Y = np.array([[0.25, 1.0],
+                  [0.5625, 0.25]])
+    O = np.array([[0.5, 1.0],              # cell 0 (rows are cells)
+                  [-1.5, 2.0]])            # cell 1
+    Yn = nw.denormalise(net, Y, O)
+    want = np.array([[9.0 / 13.0, 0.0],
+                     [4.0 / 13.0, 1.0]])
+    np.testing.assert_allclose(Yn, want, rtol=1e-15, atol=1e-16)
+
+
+def test_mole_fractions_by_hand_and_sum():
+    """X_k = Y_k W_mix / W_k with W_mix = 1 / sum Y_k / W_k. Equal masses of species of
+    2 g/mol and 32 g/mol: 1 / W_mix = 250 + 15.625 = 265.625 mol/kg, X = (16/17, 1/17).
+    On a 30-species field: sum X = 1 and X_k W_k / W_mix gives back Y_k."""
+    X, Wm = pe.mole_fractions(np.array([0.002, 0.032]), np.array([[0.5], [0.5]]))
+    np.testing.assert_allclose(X[:, 0], [16.0 / 17.0, 1.0 / 17.0], rtol=1e-15)
+    assert Wm[0] == pytest.approx(1.0 / 265.625, rel=1e-15)
+    mech = synth.make_mechanism(30, 200, 20250820)
+    _, _, _, _, Y = synth.configs.build("layer1d-30sp-1m", n_cells=500)
+    X, Wm = pe.mole_fractions(mech.W, Y)
+    np.testing.assert_allclose(X.sum(axis=0), 1.0, rtol=1e-14)
+    np.testing.assert_allclose(X * mech.W[:, None] / Wm[None, :], Y, rtol=1e-14, atol=1e-300)
+    # heavier species have smaller mole fractions than mass fractions, and conversely
+    heavy = mech.W[:, None] > Wm[None, :]
+    assert np.all((X <= Y * (1 + 1e-14))[heavy]) and np.all((X >= Y * (1 - 1e-14))[~heavy])
+
+
 # ---------------------------------------------------------------- step level
 
 def test_newton_round_trip(mech30):
