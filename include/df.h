@@ -112,11 +112,15 @@ typedef struct {
 
 /* Creates a state on opt->device: copies the mechanism and network, derives the per-species
  * EoS constants and the low-precision weight copies, allocates scratch for one batch.
- * On success *out is the new state; on error *out is NULL. Thread-safe. */
+ * On success *out is the new state; on error *out is NULL. Thread-safe.
+ * Paper: Sec. 2 (the chemistry network reads (T, p, Y_i); properties from the Peng-Robinson
+ * EoS), Sec. 3.3.1 (Z-scored inputs; FP16 weights and activations, here BF16 or FP8 e4m3, all
+ * other arithmetic double). */
 df_status df_state_create(const df_mech_desc* mech, const df_mlp_desc* mlp,
                           const df_options* opt, df_state** out);
 
-/* Frees the state and its device memory (synchronises the device first). NULL is a no-op. */
+/* Frees the state and its device memory (synchronises the device first). NULL is a no-op.
+ * Paper: no counterpart (resource management of df_state_create). */
 void df_state_destroy(df_state* s);
 
 /* One reaction step (a0-a10) of cells held in HOST memory: T [n_cells] and Y [n * ldY] are
@@ -138,14 +142,19 @@ void df_state_destroy(df_state* s);
  * arrays in place over the host link (NVLink-C2C on Grace). Every array must lie in one
  * page-locked allocation mapped into the device's address space (cudaHostAlloc,
  * cudaHostRegister), else DF_ERR_INVALID_ARG. The results are bit-identical to the chunked
- * form and to df_chem_step. */
+ * form and to df_chem_step.
+ * Paper: Sec. 2 (the step), Sec. 3.3.3 (batches whose data movement overlaps the computation
+ * of other batches). */
 #define DF_HOST_DIRECT (-1)
 df_status df_chem_step_host(df_state* s, int64_t n_cells, double dt, double* T, const double* p,
                             double* Y, int64_t ldY, int32_t* cell_status, int64_t chunk_cells,
                             void* stream);
 
 /* Real-fluid properties (a1-a4 without the network): rho [kg/m^3], h [J/kg], cp [J/(kg K)]
- * and Z of every cell. Any output pointer may be NULL and is then not written. */
+ * and Z of every cell. Any output pointer may be NULL and is then not written.
+ * Paper: Sec. 2 (supercritical mixture properties from the Peng-Robinson EoS; the equations are
+ * Peng & Robinson 1976 with van der Waals one-fluid mixing, which the paper names but does not
+ * print). Evaluated explicitly in FP64, as Sec. 3.3.1 keeps all non-network work double. */
 df_status df_real_fluid_props(df_state* s, int64_t n_cells, const double* T, const double* p,
                               const double* Y, int64_t ldY, double* rho, double* h, double* cp,
                               double* Z, void* stream);
@@ -154,7 +163,10 @@ df_status df_real_fluid_props(df_state* s, int64_t n_cells, const double* T, con
  * dt must equal the network's dt to 1e-12 relative, else DF_ERR_DT_MISMATCH.
  * cell_status (device, [n_cells], may be NULL) receives the DF_CELL_* bits (0 for cells that
  * do not react). n_active_out (device, may be NULL) receives the number of reacting cells.
- * Asynchronous: problems inside kernels are reported by df_get_step_summary. */
+ * Asynchronous: problems inside kernels are reported by df_get_step_summary.
+ * Paper: Sec. 2 (the network maps a cell's (T, p, Y_i) to its chemical change over the flow
+ * step; real-fluid state from the Peng-Robinson EoS), Sec. 3.3.1 (Z-scored inputs, reduced-
+ * precision network, everything else double), Sec. 3.3.2 (tanh-form GELU). */
 df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const double* p,
                        double* Y, int64_t ldY, int32_t* cell_status, int64_t* n_active_out,
                        void* stream);
@@ -166,7 +178,9 @@ df_status df_chem_step(df_state* s, int64_t n_cells, double dt, double* T, const
  *     in kg/(m^3 s), rho the real-fluid (Peng-Robinson) density at the cell's (T, p, Y);
  *   T_new (device [n_cells], may be NULL): T' from h(T', p, Y') = h0.
  * Cells that do not react, and flagged cells, get omega = 0 and T' = T. cell_status and
- * n_active_out as in df_chem_step. Asynchronous. */
+ * n_active_out as in df_chem_step. Asynchronous.
+ * Paper: Sec. 2 (the chemistry network yields the chemical source terms omega-dot that the
+ * transport equations of the flow solver consume). */
 df_status df_chem_source(df_state* s, int64_t n_cells, double dt, const double* T,
                          const double* p, const double* Y, int64_t ldY, double* omega, int64_t ldw,
                          double* T_new, int32_t* cell_status, int64_t* n_active_out, void* stream);
@@ -183,7 +197,9 @@ df_status df_chem_source(df_state* s, int64_t n_cells, double dt, const double* 
  * in batches of min(batch_cells, 65,536) cells, whose tangent activations take about
  * 2 x batch x (n + 1) x (widest hidden layer) elements (13 GB in BF16 for 30 species and a
  * 1600-wide layer). Uses the state's scratch, so it must not overlap other calls on the same
- * state. */
+ * state.
+ * Paper: Sec. 2 (the step whose derivative this is); the paper prints no Jacobian, which is
+ * this library's extension for implicit coupling and training. */
 df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const double* p,
                            const double* Y, int64_t ldY, float* J_dY, double* dTnew, void* stream);
 
@@ -203,7 +219,8 @@ df_status df_chem_jacobian(df_state* s, int64_t n_cells, const double* T, const 
  * cell, FP64 sums in a fixed order, so results repeat bit for bit). Allocates the Jacobian
  * columns of one batch (batch x n x (n+1) FP32 and batch x (n+1) FP64) at its first call, on
  * top of df_chem_jacobian's buffers, and shares that call's restrictions: DF_ERR_UNSUPPORTED
- * for DF_GELU_TABLE, and no overlap with other calls on the same state. Asynchronous. */
+ * for DF_GELU_TABLE, and no overlap with other calls on the same state. Asynchronous.
+ * Paper: Sec. 2 (the step); the paper prints no derivative of it (library extension). */
 df_status df_chem_step_vjp(df_state* s, int64_t n_cells, const double* T, const double* p,
                            const double* Y, int64_t ldY, const double* gT, const double* gY,
                            int64_t ldg, double* out_gT, double* out_gY, int64_t ldo, void* stream);
@@ -221,7 +238,9 @@ df_status df_chem_step_vjp(df_state* s, int64_t n_cells, const double* T, const 
  * place, so CUDA graphs of the step stay valid. DF_FP8_E4M3 states return DF_ERR_UNSUPPORTED.
  * The first training call on a state allocates the masters, Adam moments and batch buffers
  * (synchronising the device); a later call with a larger batch reallocates the batch buffers.
- * Training calls use the state's training buffers and must not overlap one another. */
+ * Training calls use the state's training buffers and must not overlap one another.
+ * Paper: Sec. 2 (a pre-trained network stands in for the stiff ODE integration of the
+ * chemistry), Sec. 3.3.2 (the activation); the training itself is offline in the paper. */
 typedef struct {
   double lr;                  /* step size, > 0 */
   double beta1;               /* first-moment decay, 0 <= beta1 < 1 */
@@ -232,7 +251,8 @@ typedef struct {
 /* One Adam step on `batch` states: network input from (T, p, Y) (a1-a5, FP64), targets from
  * Y and Y_target (device, species-major like Y, same ld), forward pass, loss, backward pass,
  * update. loss_out (device or host, may be NULL) receives L as FP32 on `stream`. The states
- * must be valid (finite, p > 0, the PR cubic solvable): a flagged state poisons the step. */
+ * must be valid (finite, p > 0, the PR cubic solvable): a flagged state poisons the step.
+ * Paper: Sec. 2 and Sec. 3.3.1 (inputs as for the step); loss and optimiser as stated above. */
 df_status df_train_step(df_state* s, int64_t batch, const double* T, const double* p,
                         const double* Y, const double* Y_target, int64_t ld, const df_adam* hp,
                         float* loss_out, void* stream);
@@ -243,7 +263,8 @@ df_status df_train_step(df_state* s, int64_t batch, const double* T, const doubl
  * needs. df_mlp_backward takes dL/dO (device [n_rows * n] FP32) for the rows of the last
  * df_mlp_forward_train (n_rows must match) and leaves dL/dW, dL/db in the state (overwriting
  * the previous gradients); dX (device [n_rows * (n+2)] FP32, may be NULL) receives dL/dx.
- * df_adam_step applies the stored gradients. */
+ * df_adam_step applies the stored gradients.
+ * Paper: Sec. 2, Sec. 3.3.2 (the network and its activation, differentiated layer by layer). */
 df_status df_mlp_forward_train(df_state* s, int64_t n_rows, const float* x, float* O,
                                void* stream);
 df_status df_mlp_backward(df_state* s, int64_t n_rows, const float* dO, float* dX, void* stream);
@@ -251,19 +272,20 @@ df_status df_adam_step(df_state* s, const df_adam* hp, void* stream);
 
 /* Copies one layer's FP32 parameters out (W [widths[l+1] * widths[l]] row-major and
  * b [widths[l+1]], device or host pointers, either may be NULL), asynchronously on `stream`:
- * the master weights, the last gradients, or Adam's first or second moments. */
+ * the master weights, the last gradients, or Adam's first or second moments.
+ * Paper: no counterpart (inspection of the training state). */
 #define DF_PARAM_WEIGHTS 0
 #define DF_PARAM_GRADS 1
 #define DF_PARAM_ADAM_M 2
 #define DF_PARAM_ADAM_V 3
 df_status df_get_params(df_state* s, int32_t layer, int32_t which, float* W, float* b,
                         void* stream);
-/* Number of Adam steps taken on the state (0 before training). */
+/* Number of Adam steps taken on the state (0 before training). Paper: no counterpart. */
 df_status df_train_get_step(df_state* s, int64_t* steps);
 
 /* Saves the master weights, biases, Adam moments and step count to a file; df_state_load
  * restores them into a state of the same network shape (any mechanism) and rewrites the
- * working copies. Both synchronise the device. */
+ * working copies. Both synchronise the device. Paper: no counterpart (checkpointing). */
 df_status df_state_save(df_state* s, const char* path);
 df_status df_state_load(df_state* s, const char* path);
 
@@ -273,14 +295,17 @@ df_status df_state_load(df_state* s, const char* path);
  * the whole step (compaction, EoS, every network layer, Newton) with one launch. The state and
  * the buffers must outlive the graph; the graph reads and writes whatever the buffers hold
  * when it runs. df_graph_create runs no kernel: it first makes sure the state's scratch fits
- * n_cells (allocating if needed), then captures on an internal stream. */
+ * n_cells (allocating if needed), then captures on an internal stream.
+ * Paper: Sec. 2 (the step, replayed once per flow time step); graphs are this library's means
+ * of cutting per-launch cost, with no counterpart in the paper. */
 typedef struct df_graph df_graph;
 df_status df_graph_create(df_state* s, int64_t n_cells, double dt, double* T, const double* p,
                           double* Y, int64_t ldY, int32_t* cell_status, int64_t* n_active_out,
                           df_graph** out);
-/* Enqueues one replay of the captured step on `stream`. */
+/* Enqueues one replay of the captured step on `stream`. Paper: as df_graph_create. */
 df_status df_graph_launch(df_graph* g, void* stream);
-/* Destroys the graph (synchronising with its last replay). NULL is a no-op. */
+/* Destroys the graph (synchronising with its last replay). NULL is a no-op.
+ * Paper: no counterpart. */
 void df_graph_destroy(df_graph* g);
 
 /* ---- tile-width autotuning of the tensor-core layers ----
@@ -296,12 +321,14 @@ void df_graph_destroy(df_graph* g);
  * df_get_tiles reports the tile of each layer (0 for SIMT layers) in bn[0..max_layers): its
  * width, | DF_TILE_PAIR when the layer runs on CTA pairs (two CTAs of a cluster share one
  * 256-row tile through cta_group::2 MMAs, each holding half of the tile's weight rows), and
- * the number of layers in *n_layers. */
+ * the number of layers in *n_layers.
+ * Paper: Sec. 3.3.3 (the network's matrix products tiled for the memory hierarchy of the
+ * target processor); the timing-based choice of tiles has no counterpart in the paper. */
 #define DF_TILE_PAIR 0x1000
 df_status df_autotune(df_state* s, int64_t n_rows, const char* cache_path, void* stream);
 df_status df_get_tiles(df_state* s, int32_t* bn, int32_t max_layers, int32_t* n_layers);
 
-/* Statistics of the last df_chem_step on a state. */
+/* Statistics of the last df_chem_step on a state. Paper: no counterpart (diagnostics). */
 typedef struct {
   int64_t n_active;           /* reacting cells */
   int64_t n_flagged;          /* reacting cells that received a DF_CELL_* flag */
@@ -310,29 +337,37 @@ typedef struct {
 
 /* Synchronises `stream`, fills *stats (may be NULL) for the last df_chem_step, and returns
  * DF_OK, DF_ERR_NOT_CONVERGED if any reacting cell was flagged, or DF_ERR_TIMEOUT if a
- * kernel wait gave up since the previous call. */
+ * kernel wait gave up since the previous call. Paper: no counterpart (diagnostics). */
 df_status df_get_step_summary(df_state* s, void* stream, df_step_stats* stats);
 
 /* ---- stage entry points: the steps of df_chem_step one at a time (same kernels) ---- */
 
 /* a0: idx (device, [n_cells] int32) receives the ascending indices of cells with
- * T > T_react, count (device, one int64) their number. */
+ * T > T_react, count (device, one int64) their number. n_cells above INT32_MAX is rejected
+ * with DF_ERR_INVALID_ARG (the indices are int32).
+ * Paper: Sec. 2 (the chemistry load varies from cell to cell, the motivation for treating only
+ * reacting cells) and Sec. 3.3.3 (the network runs on batches). */
 df_status df_active_compact(df_state* s, int64_t n_cells, const double* T, int32_t* idx,
                             int64_t* count, void* stream);
 
 /* a1-a5 for n_cells cells: h0 (device [n_cells], may be NULL) the conserved enthalpy,
  * Z (device, may be NULL), x (device [n_cells * (n+2)] row-major FP32, may be NULL) the
- * normalised network input, status (device int32, may be NULL). */
+ * normalised network input, status (device int32, may be NULL).
+ * Paper: Sec. 2 (inputs T, p, Y_i; Peng-Robinson state), Sec. 3.3.1 (Z-scored inputs, FP64). */
 df_status df_eos_pre(df_state* s, int64_t n_cells, const double* T, const double* p,
                      const double* Y, int64_t ldY, double* h0, double* Z, float* x,
                      int32_t* status, void* stream);
 
 /* a6-a7: network output O (device [n_rows * n] row-major FP32) from input x (device
- * [n_rows * (n+2)] row-major FP32), computed in the state's precision. */
+ * [n_rows * (n+2)] row-major FP32), computed in the state's precision.
+ * Paper: Sec. 2 (the chemistry network), Sec. 3.3.1 (reduced precision), Sec. 3.3.2 (GELU),
+ * Sec. 3.3.3 (batched products with the next batch's data fetched during the current one). */
 df_status df_mlp_forward(df_state* s, int64_t n_rows, const float* x, float* O, void* stream);
 
 /* a8-a10 given the network output O [n_cells * n] and h0 [n_cells]: writes Y' into Y and
- * T' into T (device, in place), status (device int32, may be NULL). */
+ * T' into T (device, in place), status (device int32, may be NULL).
+ * Paper: Sec. 2 (the chemical change applied to the cell; T from the conserved energy through
+ * the real-fluid EoS), Sec. 3.3.1 (FP64). */
 df_status df_eos_post(df_state* s, int64_t n_cells, const float* O, const double* h0,
                       double* T, const double* p, double* Y, int64_t ldY, int32_t* status,
                       void* stream);
@@ -347,8 +382,10 @@ df_status df_eos_post(df_state* s, int64_t n_cells, const float* O, const double
  * image, resident on every device that loads the library until the process exits.
  *   - n_cells above DF_COMPACT_STATIC_MAX_CELLS is rejected with DF_ERR_INVALID_ARG; the
  *     reason is available from df_get_last_error(NULL).
- *   - The first call on a device looks up the array's device address (once per device, with
- *     that device current); make that first call before any stream capture.
+ *   - The first call in a CUDA context looks up the array's device address in that context
+ *     (once per context, with the device current; a driver-API context of the caller's own, or
+ *     the new primary context after cudaDeviceReset, gets its own lookup); make that first call
+ *     before any stream capture.
  *   - All calls share the one array: calls that overlap on the GPU (different streams or host
  *     threads) race and must be serialised by the caller. */
 #define DF_COMPACT_STATIC_MAX_CELLS ((int64_t)1 << 26)
@@ -359,20 +396,21 @@ df_status df_active_compact_static(int64_t n_cells, double T_react, const double
 
 /* When enabled, df_chem_step records a pair of CUDA events on its stream around each of its
  * kernel launches, grouped into families ("compact", "eos_pre", "layer0".."layer7",
- * "eos_post"). Costs two event records per launch; off by default. */
+ * "eos_post"). Costs two event records per launch; off by default. Paper: no counterpart. */
 df_status df_profile_enable(df_state* s, int32_t enable);
 
 /* Synchronises the device and reports, for up to max_entries families in first-launch order,
  * names (max_entries x 32 chars, NUL-terminated), launches and total device time in ms
- * since the last read or enable; then resets the counters. *n_entries receives the count. */
+ * since the last read or enable; then resets the counters. *n_entries receives the count.
+ * Paper: no counterpart. */
 df_status df_profile_read(df_state* s, int32_t max_entries, char* names, int64_t* launches,
                           double* total_ms, int32_t* n_entries);
 
 /* Description of the most recent error on this state (or of the last failed create when
- * s is NULL). Valid until the next call on the same state. */
+ * s is NULL). Valid until the next call on the same state. Paper: no counterpart. */
 const char* df_get_last_error(df_state* s);
 
-/* Library version string. */
+/* Library version string. Paper: no counterpart. */
 const char* df_version(void);
 
 #ifdef __cplusplus

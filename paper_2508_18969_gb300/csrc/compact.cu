@@ -136,23 +136,60 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) int64_t g_compact_scratch[kStaticWords];
 
 std::mutex g_static_mu;
-int64_t* g_static_ptr[kMaxDevices] = {nullptr};
 
-// Device address of g_compact_scratch on the current device, looked up once per device.
-// The name is only a host-side handle; the kernel must be given this address.
+// The address of a __device__ variable belongs to a CUDA context, so it is cached per context:
+// a caller that binds its own driver-API context, or one that resets the device and so gets a
+// new primary context, is given the address in the context that is current at the call.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+struct ScratchSlot {
+  CUcontext ctx;
+  int64_t* ptr;
+};
+constexpr int kMaxSlots = 4 * kMaxDevices;
+ScratchSlot g_slots[kMaxSlots] = {};
+int g_nslots = 0;
+
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)p;
+  }
+  return fn;
+}
+
+// Device address of g_compact_scratch in the current context, looked up at the first call in
+// that context (with its device current). The name is only a host-side handle; the kernel
+// must be given this address.
 cudaError_t static_scratch(int64_t** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_compact_scratch);
-    if (e != cudaSuccess) return e;
-    g_static_ptr[dev] = static_cast<int64_t*>(p);
-  }
-  *out = g_static_ptr[dev];
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get) return cudaErrorInitializationError;
+  CUcontext ctx = nullptr;
+  if (get(&ctx) != CUDA_SUCCESS) return cudaErrorInitializationError;
+  for (int i = 0; ctx && i < g_nslots; ++i)
+    if (g_slots[i].ctx == ctx) {
+      *out = g_slots[i].ptr;
+      return cudaSuccess;
+    }
+  // first call in this context (the lookup also makes the device's primary context current
+  // when no context was yet)
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_compact_scratch);
+  if (e != cudaSuccess) return e;
+  if (get(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorInitializationError;
+  ScratchSlot& slot = g_slots[g_nslots < kMaxSlots ? g_nslots++ : kMaxSlots - 1];
+  slot.ctx = ctx;
+  slot.ptr = static_cast<int64_t*>(p);
+  *out = slot.ptr;
   return cudaSuccess;
 }
 

@@ -1346,6 +1346,8 @@ df_status df_active_compact(df_state* s, int64_t n_cells, const double* T, int32
   if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
   if (n_cells < 0 || !count || (n_cells > 0 && (!T || !idx)))
     return fail(s, DF_ERR_INVALID_ARG, "bad arguments");
+  if (n_cells > (int64_t)INT32_MAX)
+    return fail(s, DF_ERR_INVALID_ARG, "n_cells exceeds INT32_MAX (the cell indices are int32)");
   DeviceGuard guard(s->device);
   df_status rc = ensure_compact(s, n_cells);
   if (rc != DF_OK) return rc;

@@ -2,7 +2,14 @@
 whole reaction step. Tolerances: integer work (the reacting-cell list, status bits) is
 bit-exact; EoS outputs (Z, rho, h, cp, h0) within 1e-10 relative; the FP32 network path
 within |dY| <= 1e-6 absolute of the FP64 network; recovered T within 1e-3 K of the oracle's
-Newton fed with the GPU's own Y'."""
+Newton fed with the GPU's own Y' (every precision).
+
+BF16 and FP8 networks have no fixed accuracy bar: their error against the FP64 oracle is a
+stated result. Their bounds here are regression bounds, about ten times the largest error
+measured on GB300 for the same case (the measured value is given beside each), so a loss of
+an order of magnitude in accuracy fails. The whole-step T error of a BF16/FP8 step against the
+FP64 oracle comes from the network's dY (T' follows Y' through h(T', p, Y') = h0), so it is
+bounded the same way and not by the 1e-3 K Newton bar."""
 import numpy as np
 import pytest
 
@@ -73,6 +80,23 @@ def test_compaction_bit_exact(df, N):
         assert int(host(cnt2)[0]) == expect
 
 
+def test_compaction_rejects_more_cells_than_int32_indices(df):
+    """The list holds int32 indices, so df_active_compact refuses more than INT32_MAX cells on
+    the host, before any launch (small buffers suffice: nothing is read)."""
+    import ctypes
+    mech, net, _, _, _ = synth.configs.build("small-fp32-4k", n_cells=8)
+    st = df.State(mech, net, T_react=600.0, batch_cells=256)
+    T = torch.zeros(8, dtype=torch.float64, device=DEV)
+    idx = torch.zeros(8, dtype=torch.int32, device=DEV)
+    cnt = torch.zeros(1, dtype=torch.int64, device=DEV)
+    lib = df._lib.load()
+    rc = lib.df_active_compact(st.h, (1 << 31), ctypes.c_void_p(T.data_ptr()),
+                               ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(cnt.data_ptr()), None)
+    assert rc == df._lib.DF_ERR_INVALID_ARG
+    assert b"INT32_MAX" in lib.df_get_last_error(st.h)
+    st.close()
+
+
 # ---------------------------------------------------------------- a1-a5 and properties
 
 @pytest.mark.parametrize("name,N", WORKLOADS)
@@ -85,8 +109,12 @@ def test_eos_pre_vs_oracle(df, name, N):
     assert np.array_equal(host(s), o["status"])
     np.testing.assert_allclose(host(Z), o["Z"], rtol=EOS_RTOL)
     scale = _h_scale(mech, T, p, Y)
-    assert np.max(np.abs(host(h0) - o["h"]) / scale) <= EOS_RTOL
+    eh = np.max(np.abs(host(h0) - o["h"]) / scale)
+    assert eh <= EOS_RTOL
     xo = onw.normalise_inputs(net, T, p, Y)
+    ex = np.abs(host(x) - xo).max()
+    print(f"ERR eos_pre {name}: Z rel {np.max(np.abs(host(Z) / o['Z'] - 1)):.3e} "
+          f"h0 rel {eh:.3e} x abs {ex:.3e}")
     np.testing.assert_allclose(host(x), xo, atol=2e-6, rtol=1e-6)
 
 
@@ -113,8 +141,9 @@ def test_mlp_fp32_vs_fp64(df, name, N):
     O = st.mlp_forward(dev(x.astype(np.float32)))
     torch.cuda.synchronize()
     Oo = onw.mlp_forward(net, x.astype(np.float32).astype(np.float64))
-    # |dY| <= out_std * |dO| <= 1e-3 * |dO|: 1e-4 on O keeps dY two decades inside 1e-6
-    np.testing.assert_allclose(host(O), Oo, atol=1e-4, rtol=0)
+    print(f"ERR mlp_fp32 {name}: max |dO| {np.abs(host(O) - Oo).max():.3e}")
+    # |dY| <= out_std * |dO| <= 1e-3 * |dO|; measured max |dO| 2.8e-7
+    np.testing.assert_allclose(host(O), Oo, atol=3e-6, rtol=0)
 
 
 @pytest.mark.parametrize("name,N,bn", [("small-fp32-4k", 1000, None), ("layer1d-30sp-1m", 3000, None),
@@ -133,11 +162,14 @@ def test_mlp_bf16_vs_rounded_oracle(df, name, N, bn, monkeypatch):
     torch.cuda.synchronize()
     Oq = onw.mlp_forward_rounded(net, x, onw.round_to_bf16)
     err = np.abs(O - Oq)
-    assert err.max() <= 2e-2, err.max()
-    assert err.mean() <= 1e-3, err.mean()
-    # and against the exact FP64 network: BF16 storage error only
     Oe = onw.mlp_forward(net, x)
-    assert np.abs(O - Oe).max() <= 5e-2
+    print(f"ERR mlp_bf16 {name} {N} {bn}: rounded max {err.max():.3e} mean {err.mean():.3e}; "
+          f"exact max {np.abs(O - Oe).max():.3e}")
+    # measured: max 5.4e-4, mean 1.35e-5 (rounded oracle); max 1.23e-3 (exact network)
+    assert err.max() <= 5e-3, err.max()
+    assert err.mean() <= 1.5e-4, err.mean()
+    # and against the exact FP64 network: BF16 storage error only
+    assert np.abs(O - Oe).max() <= 1.5e-2
 
 
 # ---------------------------------------------------------------- a8-a10
@@ -164,13 +196,15 @@ def test_eos_post_vs_oracle(df, name, N):
     du = O.astype(np.float64).T * net.out_std[:, None] + net.out_mean[:, None]
     raw = np.abs(onw.boxcox_inverse(onw.boxcox(Y, net.lam) + du, net.lam) - Y)
     tol = 1e-6 * (raw + raw.sum(axis=0, keepdims=True)) + 1e-13 * np.abs(Yn) + 1e-300
+    print(f"ERR eos_post {name}: max |dY| {np.abs(host(Yd) - Yn).max():.3e} "
+          f"max |dT| {np.abs(host(Td) - Tn).max():.3e}")
     assert np.all(np.abs(host(Yd) - Yn) <= tol)
     np.testing.assert_allclose(host(Td), Tn, rtol=0, atol=1e-3)
 
 
 # ---------------------------------------------------------------- whole step
 
-def _step_check(df, mech, net, T, p, Y, prec, T_react, batch, dY_tol):
+def _step_check(df, mech, net, T, p, Y, prec, T_react, batch, dY_tol, dT_tol=1e-3):
     st = df.State(mech, net, precision=prec, T_react=T_react, batch_cells=batch)
     Td, pd, Yd = dev(T), dev(p), dev(Y)
     status = torch.full((T.shape[0],), -1, dtype=torch.int32, device=DEV)
@@ -185,13 +219,18 @@ def _step_check(df, mech, net, T, p, Y, prec, T_react, batch, dY_tol):
     inact = np.setdiff1d(np.arange(T.shape[0]), act)
     assert np.array_equal(Tg[inact], T[inact]) and np.array_equal(Yg[:, inact], Y[:, inact])
     dY = np.abs(Yg - Yo).max()
-    assert dY <= dY_tol, dY
     # T recovery with the GPU's own Y' (network error kept out of the Newton check)
     ok = act[so[act] == 0]
     h0 = ope.state(mech, T[ok], p[ok], Y[:, ok])["h"]
     Tr, sr = ostep.solve_T(mech, p[ok], Yg[:, ok], h0, T[ok])
+    dTn = np.abs(Tg[ok] - Tr).max() if ok.size else 0.0
+    dT = np.abs(Tg - To).max()
+    print(f"ERR step prec={prec} n={mech.n} N={T.shape[0]}: max |dY| {dY:.3e} "
+          f"max |dT| step {dT:.3e} Newton {dTn:.3e}")
+    assert dY <= dY_tol, dY
+    assert dT <= dT_tol, dT
     assert np.all(sr == 0)
-    assert np.abs(Tg[ok] - Tr).max() <= 1e-3
+    assert dTn <= 1e-3
     return dY
 
 
@@ -209,7 +248,8 @@ def test_chem_step_fp32(df, name, N, T_react, batch):
                                                   ("react30-16m", 5000, 600.0, 700)])
 def test_chem_step_bf16(df, name, N, T_react, batch):
     mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
-    dY = _step_check(df, mech, net, T, p, Y, df.DF_BF16, T_react, batch, 1e-4)
+    # measured: max |dY| 3.3e-7 .. 3.6e-7, whole-step max |dT| 7.5e-4 .. 1.4e-3 K
+    dY = _step_check(df, mech, net, T, p, Y, df.DF_BF16, T_react, batch, 4e-6, 1.5e-2)
     print(f"BF16 {name}: max |dY| vs FP64 = {dY:.3e}")
 
 
@@ -228,9 +268,13 @@ def test_full_size_sampled(df, prec):
     To, Yo, so = ostep.chem_step(mech, net, T[sel], p[sel], Y[:, sel], net.dt, T_react=0.0)
     assert np.array_equal(host(status)[sel], so)
     dY = np.abs(host(Yd)[:, sel] - Yo).max()
-    assert dY <= (1e-6 if prec == "fp32" else 1e-4), dY
     h0 = ope.state(mech, T[sel], p[sel], Y[:, sel])["h"]
     Tr, _ = ostep.solve_T(mech, p[sel], host(Yd)[:, sel], h0, T[sel])
+    print(f"ERR full_size {prec}: max |dY| {dY:.3e} max |dT| step "
+          f"{np.abs(host(Td)[sel] - To).max():.3e} Newton {np.abs(host(Td)[sel] - Tr).max():.3e}")
+    # measured (BF16): max |dY| 3.0e-7, whole-step max |dT| 7.7e-4 K
+    assert dY <= (1e-6 if prec == "fp32" else 4e-6), dY
+    assert np.abs(host(Td)[sel] - To).max() <= (1e-3 if prec == "fp32" else 1e-2)
     assert np.abs(host(Td)[sel] - Tr).max() <= 1e-3
 
 
@@ -282,15 +326,17 @@ def test_mlp_fp8_vs_rounded_oracle(df, name, N, bn, monkeypatch):
     err = np.abs(O - Oq)
     print(f"FP8 {name}: max {err.max():.3e} mean {err.mean():.3e} vs rounded oracle; "
           f"max {np.abs(O - onw.mlp_forward(net, x)).max():.3e} vs exact")
-    assert err.max() <= 0.1, err.max()
-    assert err.mean() <= 5e-3, err.mean()
+    # measured: max 5.1e-3, mean 1.5e-5 (rounded oracle)
+    assert err.max() <= 5e-2, err.max()
+    assert err.mean() <= 1.5e-4, err.mean()
 
 
 @pytest.mark.parametrize("name,N,T_react,batch", [("layer1d-30sp-1m", 6000, 0.0, 2048),
                                                   ("react30-16m", 5000, 600.0, 700)])
 def test_chem_step_fp8(df, name, N, T_react, batch):
     mech, net, T, p, Y = synth.configs.build(name, n_cells=N)
-    dY = _step_check(df, mech, net, T, p, Y, df.DF_FP8_E4M3, T_react, batch, 1e-3)
+    # measured: max |dY| 3.6e-6 .. 4.1e-6, whole-step max |dT| 1.3e-2 .. 1.4e-2 K
+    dY = _step_check(df, mech, net, T, p, Y, df.DF_FP8_E4M3, T_react, batch, 4e-5, 0.15)
     print(f"FP8 {name}: max |dY| vs FP64 = {dY:.3e}")
 
 
@@ -373,7 +419,8 @@ def test_chem_source_matches_step_and_oracle(df, name, N, T_react, prec):
     # against the oracle's source terms: the step's dY bar scaled by rho / dt
     om_o, Tn_o, so = ostep.chem_source(mech, net, T, p, Y, net.dt, T_react=T_react)
     assert np.array_equal(sg, so)
-    dY_tol = 1e-6 if prec == "fp32" else 1e-4
+    dY_tol = 1e-6 if prec == "fp32" else 4e-6   # BF16 measured 3.1e-7
+    print(f"ERR source {name} {prec}: max |dw| dt/rho {np.max(np.abs(om - om_o) * net.dt / rho[None, :]):.3e}")
     assert np.all(np.abs(om - om_o) <= dY_tol * rho[None, :] / net.dt)
     assert np.all(np.abs(om.sum(axis=0)) <= 1e-11 * rho / net.dt)
 
@@ -434,7 +481,9 @@ def test_cta_pair_tiles_match_single_cta_tiles(df, prec, monkeypatch):
     Oq = (onw.mlp_forward_fp8(net, xr, 32.0) if prec == "fp8"
           else onw.mlp_forward_rounded(net, xr, onw.round_to_bf16))
     err = np.abs(O_pair - Oq)
-    assert err.max() <= (0.1 if prec == "fp8" else 2e-2), err.max()
+    print(f"ERR cta_pair {prec}: max {err.max():.3e} mean {err.mean():.3e}")
+    # measured: max 4.9e-3 (FP8), 3.8e-4 (BF16), 3.4e-4 (BF16, table)
+    assert err.max() <= (5e-2 if prec == "fp8" else 4e-3), err.max()
     st.close()
     st1.close()
 
@@ -457,7 +506,8 @@ def test_tabulated_gelu_mlp_fp32_vs_oracle(df, name, N):
     Oo = onw.mlp_forward(net, x, act=onw.gelu_table)
     # as the tanh-form FP32 path; the table is evaluated in FP32 (an interval index may fall
     # on the neighbouring node, which moves the value by at most the expansion remainder)
-    np.testing.assert_allclose(O, Oo, atol=1e-4, rtol=0)
+    print(f"ERR table_fp32 {name}: max {np.abs(O - Oo).max():.3e}")
+    np.testing.assert_allclose(O, Oo, atol=4e-6, rtol=0)   # measured max 3.8e-7
     # the tabulation is a different activation: against the tanh-form network the outputs move
     Ot = onw.mlp_forward(net, x)
     print(f"{name}: max |O_table - O_tanh| (FP64 oracle) = {np.abs(Oo - Ot).max():.3e}")
@@ -472,7 +522,9 @@ def test_tabulated_gelu_mlp_bf16_vs_rounded_oracle(df, name, N):
     torch.cuda.synchronize()
     Oq = onw.mlp_forward_rounded(net, x, onw.round_to_bf16, act=onw.gelu_table)
     err = np.abs(O - Oq)
-    assert err.max() <= 2e-2 and err.mean() <= 1e-3, (err.max(), err.mean())
+    print(f"ERR table_bf16 {name}: max {err.max():.3e} mean {err.mean():.3e}")
+    # measured: max 4.8e-4, mean 1.7e-5
+    assert err.max() <= 5e-3 and err.mean() <= 2e-4, (err.max(), err.mean())
 
 
 def test_tabulated_gelu_step_accuracy_and_unsupported_calls(df):
@@ -529,4 +581,5 @@ def test_species_count_extremes(df, n):
     assert np.all(np.abs(h - o["h"]) <= EOS_RTOL * (np.abs(o["h"]) + _h_scale(mech, T, p, Y)))
     np.testing.assert_allclose(rho, o["rho"], rtol=EOS_RTOL)
     _step_check(df, mech, net, T, p, Y, df.DF_FP32, 0.0, 1024, 1e-6)
-    _step_check(df, mech, net, T, p, Y, df.DF_BF16, 0.0, 1024, 1e-4)
+    # measured (BF16): max |dY| up to 1.2e-6 (n = 5), whole-step max |dT| up to 4.7e-3 K
+    _step_check(df, mech, net, T, p, Y, df.DF_BF16, 0.0, 1024, 1.5e-5, 5e-2)
