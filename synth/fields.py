@@ -78,18 +78,35 @@ def mixing_layer_1d(mech: Mechanism, N: int, seed: int, delta: float = 0.1, p: f
     return T, np.full(N, p), Y
 
 
-def reacting_mix(mech: Mechanism, N: int, seed: int, active_fraction: float = 0.3,
-                 p: float = 10.0e6):
-    """Cells of the 1D mixing layer's two populations, interleaved by a seeded Bernoulli mask:
-    reacting cells (probability active_fraction) take Zf ~ U[0.07, 0.33], whose burning
-    progress puts T above 727 K; the others are cold unburnt mixing (c = 0, T <= 150 K)."""
+def _reacting_chunk(mech: Mechanism, N: int, seed: int, active_fraction: float, p: float,
+                    j0: int, j1: int):
+    """(T, p, Y) of cells j0..j1-1 of the reacting-mix field of N cells. Every draw is indexed
+    by its position in the field's one stream (mask [0, N), reacting Zf [N, 2N), cold Zf
+    [2N, 3N), minor species k at [3N + k N, 3N + (k + 1) N)), so any chunking gives the values
+    of the serial draw."""
     s = Stream(seed, "reacting-mix")
-    act = s.uniform(N) < active_fraction
-    Zf = np.where(act, s.uniform(N, 0.07, 0.33), s.uniform(N))
+    j = np.arange(j0, j1, dtype=np.uint64)
+    N64 = np.uint64(N)
+    act = s.uniform_at(j) < active_fraction
+    Zf = np.where(act, s.uniform_at(N64 + j, 0.07, 0.33), s.uniform_at(2 * N64 + j))
     c = np.where(act, np.exp(-(((Zf - Z_ST) / 0.1) ** 2)), 0.0)
     T = _layer_T(Zf, c)
-    Y = mixing_burning_Y(mech, Zf, c, s, 1e-8, 1e-3)
-    return T, np.full(N, p), Y
+    nm = mech.n - 4
+    mu = None
+    if nm > 0:
+        k = np.arange(nm, dtype=np.uint64)[:, None]
+        mu = s.uniform_at(3 * N64 + k * N64 + j[None, :])
+    return T, np.full(j1 - j0, p), mixing_burning_Y(mech, Zf, c, s, 1e-8, 1e-3, minor_u=mu)
+
+
+def reacting_mix(mech: Mechanism, N: int, seed: int, active_fraction: float = 0.3,
+                 p: float = 10.0e6, chunk: int = 1 << 16, workers: int | None = None):
+    """Cells of the 1D mixing layer's two populations, interleaved by a seeded Bernoulli mask:
+    reacting cells (probability active_fraction) take Zf ~ U[0.07, 0.33], whose burning
+    progress puts T above 727 K; the others are cold unburnt mixing (c = 0, T <= 150 K),
+    minor species jittered in [1e-8, 1e-3]. Large fields are generated in chunks by a pool of
+    processes as the 3D layer is; the values do not depend on the chunking."""
+    return _generate(_reacting_chunk, (mech, N, seed, active_fraction, p), mech.n, N, chunk, workers)
 
 
 def training_states(mech: Mechanism, N: int, seed: int):
@@ -135,42 +152,34 @@ def _layer3d_chunk(mech: Mechanism, N: int, seed: int, side: int, delta: float, 
 _SHM = {}
 
 
-def _layer3d_worker_init(names, N, n):
+def _worker_init(names, N, n):
     from multiprocessing import shared_memory
     for key, shape in (("T", (N,)), ("p", (N,)), ("Y", (n, N))):
         shm = shared_memory.SharedMemory(name=names[key])
         _SHM[key] = (shm, np.ndarray(shape, dtype=np.float64, buffer=shm.buf))
 
 
-def _layer3d_worker(args):
-    mech, N, seed, side, delta, j0, j1 = args
-    T, p, Y = _layer3d_chunk(mech, N, seed, side, delta, j0, j1)
+def _worker(args):
+    fn, fargs, j0, j1 = args
+    T, p, Y = fn(*fargs, j0, j1)
     _SHM["T"][1][j0:j1] = T
     _SHM["p"][1][j0:j1] = p
     _SHM["Y"][1][:, j0:j1] = Y
     return j1 - j0
 
 
-def mixing_layer_3d(mech: Mechanism, N: int, seed: int, side: int = 400, delta: float = 0.1,
-                    chunk: int = 1 << 20, workers: int | None = None):
-    """3D supercritical mixing layer on a side^3 grid over [-1, 1] x [0, 1] x [0, 1], cells
-    numbered x fastest. The 1D layer's mixture fraction Zf(x) = (1 + tanh(x / delta)) / 2 is
-    displaced by improved gradient noise (two octaves, amplitude 0.15 in x), the burning zone
-    and T follow the 1D layer, p = 12.5 MPa + 7.5 MPa * clip(2.5 n_p, -1, 1) with a second,
-    single-octave noise field n_p (so p spans 5-20 MPa), minor species jittered in [1e-8, 1e-3].
-    N < side^3 takes the evenly strided grid cells floor(j side^3 / N) with the draws those
-    cells have in the full field (every draw is indexed by the global cell number); values
-    agree up to the last-bit rounding of numpy's vectorised transcendental functions. Large fields are generated by a pool of processes
-    (spawned, so it is safe after CUDA has been initialised) writing into shared memory."""
+def _generate(fn, fargs, n: int, N: int, chunk: int, workers: int | None):
+    """(T, p, Y) of N cells from fn(*fargs, j0, j1), which returns the cells j0..j1-1; chunks of
+    `chunk` cells, by a pool of processes writing into shared memory when the field is large
+    (spawned, so it is safe after CUDA has been initialised)."""
     import os
-    n = mech.n
     if workers is None:
         workers = min(len(os.sched_getaffinity(0)), 32) if N >= (1 << 23) else 1
     ranges = [(j0, min(N, j0 + chunk)) for j0 in range(0, N, chunk)]
     if workers <= 1 or len(ranges) <= 1:
         T, p, Y = np.empty(N), np.empty(N), np.empty((n, N))
         for j0, j1 in ranges:
-            T[j0:j1], p[j0:j1], Y[:, j0:j1] = _layer3d_chunk(mech, N, seed, side, delta, j0, j1)
+            T[j0:j1], p[j0:j1], Y[:, j0:j1] = fn(*fargs, j0, j1)
         return T, p, Y
     import multiprocessing as mp
     from multiprocessing import shared_memory
@@ -179,9 +188,8 @@ def mixing_layer_3d(mech: Mechanism, N: int, seed: int, side: int = 400, delta: 
     try:
         names = {k: b.name for k, b in blocks.items()}
         ctx = mp.get_context("spawn")
-        with ctx.Pool(workers, initializer=_layer3d_worker_init, initargs=(names, N, n)) as pool:
-            done = sum(pool.imap_unordered(
-                _layer3d_worker, [(mech, N, seed, side, delta, j0, j1) for j0, j1 in ranges]))
+        with ctx.Pool(workers, initializer=_worker_init, initargs=(names, N, n)) as pool:
+            done = sum(pool.imap_unordered(_worker, [(fn, fargs, j0, j1) for j0, j1 in ranges]))
         assert done == N
         T = np.ndarray((N,), np.float64, blocks["T"].buf).copy()
         p = np.ndarray((N,), np.float64, blocks["p"].buf).copy()
@@ -191,3 +199,17 @@ def mixing_layer_3d(mech: Mechanism, N: int, seed: int, side: int = 400, delta: 
         for b in blocks.values():
             b.close()
             b.unlink()
+
+
+def mixing_layer_3d(mech: Mechanism, N: int, seed: int, side: int = 400, delta: float = 0.1,
+                    chunk: int = 1 << 16, workers: int | None = None):
+    """3D supercritical mixing layer on a side^3 grid over [-1, 1] x [0, 1] x [0, 1], cells
+    numbered x fastest. The 1D layer's mixture fraction Zf(x) = (1 + tanh(x / delta)) / 2 is
+    displaced by improved gradient noise (two octaves, amplitude 0.15 in x), the burning zone
+    and T follow the 1D layer, p = 12.5 MPa + 7.5 MPa * clip(2.5 n_p, -1, 1) with a second,
+    single-octave noise field n_p (so p spans 5-20 MPa), minor species jittered in [1e-8, 1e-3].
+    N < side^3 takes the evenly strided grid cells floor(j side^3 / N) with the draws those
+    cells have in the full field (every draw is indexed by the global cell number); values
+    agree up to the last-bit rounding of numpy's vectorised transcendental functions. Large
+    fields are generated by a pool of processes."""
+    return _generate(_layer3d_chunk, (mech, N, seed, side, delta), mech.n, N, chunk, workers)

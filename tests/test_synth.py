@@ -61,3 +61,22 @@ def test_mixing_layer_3d_parallel_equals_serial():
     a = fields.mixing_layer_3d(mech, 60000, 4, side=50, chunk=7000, workers=1)
     b = fields.mixing_layer_3d(mech, 60000, 4, side=50, chunk=7000, workers=3)
     assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_reacting_mix_chunked_and_parallel_equal_the_sequential_draw():
+    """The reacting-mix field drawn in chunks (serially or by a pool) takes the values of one
+    sequential pass over its stream: mask, reacting Zf, cold Zf, then the minor species."""
+    from synth.rng import Stream
+    mech = synth.make_mechanism(30, 200, 20250820)
+    N, seed = 50000, 7
+    s = Stream(seed, "reacting-mix")
+    act = s.uniform(N) < 0.3
+    Zf = np.where(act, s.uniform(N, 0.07, 0.33), s.uniform(N))
+    c = np.where(act, np.exp(-(((Zf - fields.Z_ST) / 0.1) ** 2)), 0.0)
+    Y = fields.mixing_burning_Y(mech, Zf, c, s, 1e-8, 1e-3)
+    a = fields.reacting_mix(mech, N, seed, chunk=7000, workers=1)
+    b = fields.reacting_mix(mech, N, seed, chunk=6000, workers=3)
+    assert np.array_equal(a[2], Y) and np.array_equal(b[2], Y)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(a[0], fields._layer_T(Zf, c))
+    assert abs(np.mean(a[0] > 600.0) - 0.3) < 0.01
