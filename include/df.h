@@ -328,6 +328,19 @@ void df_graph_destroy(df_graph* g);
 df_status df_autotune(df_state* s, int64_t n_rows, const char* cache_path, void* stream);
 df_status df_get_tiles(df_state* s, int32_t* bn, int32_t max_layers, int32_t* n_layers);
 
+/* Clock budget of every pipeline wait (TMA stage, MMA completion, accumulator hand-over) in the
+ * tensor-core kernels of the state's reaction-step network layers: clocks > 0 sets it, clocks
+ * <= 0 restores the default (about one second of SM clocks). A wait that outlasts its budget
+ * makes the kernel give up: it sets the state's timeout flag, lets the copies and MMAs it has
+ * in flight finish (those drains always allow the full default), frees its tensor memory and
+ * returns; the step's later kernels still run on whatever the network left, and
+ * df_get_step_summary reports DF_ERR_TIMEOUT once. A budget of a few hundred clocks makes
+ * waits give up on purpose, which is how the timeout path is tested without a fault. Applies
+ * to launches made after the call (a captured graph keeps the budget it was captured with).
+ * DF_ERR_UNSUPPORTED for DF_FP32 states (no tensor-core layers). Paper: no counterpart
+ * (failure handling). */
+df_status df_set_wait_limit(df_state* s, int64_t clocks);
+
 /* Statistics of the last df_chem_step on a state. Paper: no counterpart (diagnostics). */
 typedef struct {
   int64_t n_active;           /* reacting cells */

@@ -109,6 +109,7 @@ SIGNATURES = {
     "df_graph_launch": (_ST, [_VP, _VP]),
     "df_graph_destroy": (None, [_VP]),
     "df_profile_enable": (_ST, [_VP, C.c_int32]),
+    "df_set_wait_limit": (_ST, [_VP, _I64]),
     "df_profile_read": (_ST, [_VP, C.c_int32, C.c_char_p, C.POINTER(_I64), C.POINTER(C.c_double),
                               C.POINTER(C.c_int32)]),
     "df_get_last_error": (C.c_char_p, [_VP]),

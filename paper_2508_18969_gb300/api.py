@@ -190,6 +190,11 @@ class State:
         """A Graph replaying df_chem_step on these exact buffers (see df_graph_create)."""
         return Graph(self, T, p, Y, dt, status, n_active)
 
+    def set_wait_limit(self, clocks: int = 0):
+        """Clock budget of the tensor-core kernels' pipeline waits (df_set_wait_limit); 0
+        restores the default (about one second)."""
+        self._check(self._lib.df_set_wait_limit(self.h, int(clocks)))
+
     def step_summary(self, stream=None):
         """(status code, reacting cells, flagged cells, Newton iterations) of the last step."""
         s = L.StepStats()

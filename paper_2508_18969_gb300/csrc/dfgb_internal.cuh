@@ -218,6 +218,8 @@ struct TcLayer {
   int ksplit = 1;        // split-K (plain mode): split s covers k-blocks [s kbs, (s+1) kbs) and
   int64_t split_rows = 0;  // stores its partial product at output rows + s * split_rows
   bool pair = false;     // computed by CTA pairs (cta_group::2): 256-row tiles, tmB box BN/2
+  long long wait_budget = 0;  // clocks a pipeline wait may take before the kernel gives up
+                              // (<= 0: the default, ~1 s)
 };
 bool tc_encode_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
                   uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,

@@ -17,7 +17,9 @@
 // A layer may instead run on CTA pairs (clusters of two, cta_group::2): 256-row tiles whose
 // MMAs the even CTA issues over both CTAs' operands (see "CTA pairs" below).
 // Every mbarrier wait is bounded by a clock budget; on expiry the CTA sets the error word,
-// drains its own copies and MMAs, frees its TMEM and returns.
+// drains its own copies and MMAs, frees its TMEM and returns. The budget of the pipeline waits
+// is a launch argument (default ~1 s); the drains on the way out always allow the full ~1 s,
+// so copies and MMAs in flight land before the CTA frees its tensor memory and exits.
 #include "dfgb_internal.cuh"
 
 #ifndef EPI_PER_QUARTER
@@ -60,6 +62,8 @@ struct TcArgs {
   const float4* gtab;  // tabulated GELU, or NULL for the tanh form
   int ksplit;      // split-K: partial products over ksplit ranges of k-blocks
   int64_t split_rows;  // output row offset between the partial products of two splits
+  long long budget;    // clock budget of each pipeline wait (kWaitBudget by default)
+  uint32_t suspend;    // try_wait suspend-time hint, ns (short when the budget is short)
 };
 
 // Epilogue modes: plain layer; layer that also stores GELU'(z) (forward pass of the Jacobian);
@@ -87,13 +91,14 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity,
+                                         uint32_t suspend = kSuspendNs) {
   uint32_t ok;
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(kSuspendNs)
+      : "r"(bar), "r"(parity), "r"(suspend)
       : "memory");
   return ok != 0;
 }
@@ -101,13 +106,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // Bounded wait: true when the phase of the given parity completed; false after the clock
 // budget or once another role of the CTA has given up (*abort set).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
-                                          int* err) {
-  if (mbar_try(bar, parity)) return true;
+                                          int* err, long long budget, uint32_t suspend) {
+  if (mbar_try(bar, parity, suspend)) return true;
   const long long t0 = clock64();
   while (true) {
-    if (mbar_try(bar, parity)) return true;
+    if (mbar_try(bar, parity, suspend)) return true;
     if (*abort) return false;
-    if (clock64() - t0 > kWaitBudget) {
+    if (clock64() - t0 > budget) {
       atomicOr(err, kErrTimeout);
       *abort = 1;
       return false;
@@ -194,26 +199,28 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity,
+                                                 uint32_t suspend = kSuspendNs) {
   uint32_t ok;
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(kSuspendNs)
+      : "r"(bar), "r"(parity), "r"(suspend)
       : "memory");
   return ok != 0;
 }
 
 // Bounded wait on a barrier that also receives arrivals from the peer CTA.
 __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
-                                                  volatile int* abort, int* err) {
-  if (mbar_try_cluster(bar, parity)) return true;
+                                                  volatile int* abort, int* err, long long budget,
+                                                  uint32_t suspend) {
+  if (mbar_try_cluster(bar, parity, suspend)) return true;
   const long long t0 = clock64();
   while (true) {
-    if (mbar_try_cluster(bar, parity)) return true;
+    if (mbar_try_cluster(bar, parity, suspend)) return true;
     if (*abort) return false;
-    if (clock64() - t0 > kWaitBudget) {
+    if (clock64() - t0 > budget) {
       atomicOr(err, kErrTimeout);
       *abort = 1;
       return false;
@@ -616,7 +623,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % C::kStages;
         const uint32_t ph = (it / C::kStages) & 1;
-        if (!mbar_wait(empty0 + 8 * s, ph ^ 1, abort, g.err)) { ok = false; break; }
+        if (!mbar_wait(empty0 + 8 * s, ph ^ 1, abort, g.err, g.budget, g.suspend)) {
+          ok = false;
+          break;
+        }
         const uint32_t dA = smem_u32(sA + s * BM * kRowBytes);
         const uint32_t dB = smem_u32(sB + s * C::kBRows * kRowBytes);
         if constexpr (PAIR) {
@@ -664,15 +674,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
       const int kb0 = (int)(t / tiles_mn) * kbs, kb1 = min(kblocks, kb0 + kbs);
       const int a = j & 1;
       const uint32_t aph = (j >> 1) & 1;
-      if (PAIR ? !mbar_wait_cluster(tempty0 + 8 * a, aph ^ 1, abort, g.err)
-               : !mbar_wait(tempty0 + 8 * a, aph ^ 1, abort, g.err))
+      if (PAIR ? !mbar_wait_cluster(tempty0 + 8 * a, aph ^ 1, abort, g.err, g.budget, g.suspend)
+               : !mbar_wait(tempty0 + 8 * a, aph ^ 1, abort, g.err, g.budget, g.suspend))
         break;
       tc_fence_after();
       const uint32_t dt = tmem + a * C::kAccStride;
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % C::kStages;
         const uint32_t ph = (it / C::kStages) & 1;
-        if (!mbar_wait(full0 + 8 * s, ph, abort, g.err)) { ok = false; break; }
+        if (!mbar_wait(full0 + 8 * s, ph, abort, g.err, g.budget, g.suspend)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
         const uint64_t da = desc_sw128(smem_u32(sA + s * BM * kRowBytes));
         const uint64_t db = desc_sw128(smem_u32(sB + s * C::kBRows * kRowBytes));
@@ -712,7 +725,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     for (int64_t t = t_first; t < ntiles; t += t_step, ++j) {
       const int a = j & 1;
       const uint32_t aph = (j >> 1) & 1;
-      if (!mbar_wait(tfull0 + 8 * a, aph, abort, g.err)) break;
+      if (!mbar_wait(tfull0 + 8 * a, aph, abort, g.err, g.budget, g.suspend)) break;
       tc_fence_after();
       const int64_t tt = t % tiles_mn;
       const int64_t mt = tile_m0(tt);
@@ -1090,6 +1103,9 @@ cudaError_t launch_tc_gemm(const TcLayer& L, const RowMap& rows, int num_sms, in
   a.gtab = L.gtab;
   a.ksplit = L.ksplit > 0 ? L.ksplit : 1;
   a.split_rows = L.split_rows;
+  a.budget = L.wait_budget > 0 ? L.wait_budget : kWaitBudget;
+  // a short budget needs a short suspend hint, or one try_wait could outlast it
+  a.suspend = a.budget < kWaitBudget ? 32u : kSuspendNs;
   return L.elem_bytes == 1 ? launch_fmt<true>(L, a, num_sms, st)
                            : launch_fmt<false>(L, a, num_sms, st);
 }

@@ -1316,6 +1316,13 @@ df_status df_get_tiles(df_state* s, int32_t* bn, int32_t max_layers, int32_t* n_
   return DF_OK;
 }
 
+df_status df_set_wait_limit(df_state* s, int64_t clocks) {
+  if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
+  if (s->tcl.empty()) return fail(s, DF_ERR_UNSUPPORTED, "the state has no tensor-core layers");
+  for (TcLayer& L : s->tcl) L.wait_budget = clocks > 0 ? (long long)clocks : 0;
+  return DF_OK;
+}
+
 df_status df_get_step_summary(df_state* s, void* stream, df_step_stats* stats) {
   if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
   DeviceGuard guard(s->device);
