@@ -159,6 +159,23 @@ df_status df_real_fluid_props(df_state* s, int64_t n_cells, const double* T, con
                               const double* Y, int64_t ldY, double* rho, double* h, double* cp,
                               double* Z, void* stream);
 
+/* Transport properties of every cell at its real-fluid state: dynamic viscosity mu [Pa s],
+ * thermal conductivity lam [W/(m K)] and thermal diffusivity alpha = lam / (rho c_p) [m^2/s]
+ * (device [n_cells] FP64 each, any may be NULL). The method of Chung, Ajlan, Lee & Starling
+ * (1988) for dense fluids and mixtures -- Chung's mixing rules over the mole fractions, critical
+ * volumes from the Peng-Robinson critical compressibility (Vc = 0.307401 R Tc / pc), nonpolar
+ * species -- evaluated at the Peng-Robinson molar density, with the ideal-gas Cv and the
+ * real-fluid c_p of the same state. The Peng-Robinson state and the outer mixing sums are FP64;
+ * the inner pair sums and the correlation itself (accurate to a few percent) are FP32, which
+ * leaves up to about 1e-5 relative against an FP64 evaluation.
+ * Cells whose state is not finite or has no PR root get NaN.
+ * Paper: Sec. 2 (PRNet yields density, temperature and transport properties such as viscosity
+ * and thermal diffusivity of the supercritical mixture, based on the Peng-Robinson EoS); the
+ * paper names no transport model, Chung's method is this library's reading. */
+df_status df_transport_props(df_state* s, int64_t n_cells, const double* T, const double* p,
+                             const double* Y, int64_t ldY, double* mu, double* lam, double* alpha,
+                             void* stream);
+
 /* One reaction step (a0-a10) of n_cells cells, in place on T and Y; p is read only.
  * dt must equal the network's dt to 1e-12 relative, else DF_ERR_DT_MISMATCH.
  * cell_status (device, [n_cells], may be NULL) receives the DF_CELL_* bits (0 for cells that

@@ -9,8 +9,10 @@
  * library evaluates the Peng-Robinson state explicitly and recovers T by Newton (df.h, a2-a9);
  * the calls below build, train and run the surrogate of that evaluation so that the two can be
  * compared on accuracy and cost. Inputs are the cell's conserved mass-specific enthalpy h (the
- * quantity the reaction step conserves), p and Y_1..Y_n; outputs are any m properties, here
- * density and temperature.
+ * quantity the reaction step conserves), p and Y_1..Y_n; outputs are any m properties, e.g.
+ * density alone, or temperature with the logarithms of viscosity, thermal conductivity and
+ * thermal diffusivity (the paper's 4-output temperature-and-transport network), trained on the
+ * explicit evaluation (df_real_fluid_props, df_transport_props of df.h).
  *
  * A property network lives in a network-only df_state (df_network_create). On it the generic
  * network calls of df.h work (df_mlp_forward, df_mlp_forward_train, df_mlp_backward,

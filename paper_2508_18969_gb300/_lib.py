@@ -83,6 +83,7 @@ SIGNATURES = {
                               C.POINTER(_VP)]),
     "df_state_destroy": (None, [_VP]),
     "df_real_fluid_props": (_ST, [_VP, _I64, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]),
+    "df_transport_props": (_ST, [_VP, _I64, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
     "df_chem_step": (_ST, [_VP, _I64, C.c_double, _VP, _VP, _VP, _I64, _VP, _VP, _VP]),
     "df_chem_step_host": (_ST, [_VP, _I64, C.c_double, _VP, _VP, _VP, _I64, _VP, _I64, _VP]),
     "df_chem_source": (_ST, [_VP, _I64, C.c_double, _VP, _VP, _VP, _I64, _VP, _I64, _VP, _VP, _VP,

@@ -208,6 +208,14 @@ class State:
                                                   *[_ptr(o) for o in out], _stream(stream)))
         return tuple(out)
 
+    def transport_props(self, T, p, Y, stream=None):
+        """(mu [Pa s], lambda [W/(m K)], alpha [m^2/s]) of every cell (df_transport_props)."""
+        N = _check_cells(self.n, T, p, Y)
+        out = [torch.empty(N, dtype=torch.float64, device=T.device) for _ in range(3)]
+        self._check(self._lib.df_transport_props(self.h, N, _ptr(T), _ptr(p), _ptr(Y), Y.stride(0),
+                                                 *[_ptr(o) for o in out], _stream(stream)))
+        return tuple(out)
+
     # ---- training ----
     @staticmethod
     def _adam(lr=1e-3, betas=(0.9, 0.999), eps=1e-8):

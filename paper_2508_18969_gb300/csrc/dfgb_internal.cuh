@@ -68,6 +68,11 @@ struct EosParams {
   const float* kfr;      // [n * n]
   // natural-log table: ln(c_j) for j < 128, then 1 / c_j, c_j = 1 + (j + 1/2) / 128
   const double* lntab;   // [256]
+  // Chung's mixing rules (transport properties): per species tsp[k] = (Tc, Vc [cm^3/mol],
+  // omega, M [g/mol]); per pair tpair[q][i][j], q = 0 sigma_ij^3, 1 eps_ij sigma_ij^3,
+  // 2 omega_ij sigma_ij^3, 3 eps_ij sigma_ij^2 M_ij^(1/2) (sigma in Angstrom, eps/k in K)
+  const double* tsp;     // [n * 4]
+  const float* tpair;    // [4 * n * n]
   int* err;              // device error word
   int64_t* flagged;      // device count of cells flagged by eos_post (may be NULL)
   int64_t* newton_iters; // device sum of Newton iterations (may be NULL)
@@ -96,6 +101,10 @@ cudaError_t launch_eos_post(const EosParams& P, const RowMap& rows, const float*
                             const double* h0, double* T, const double* p, double* Y,
                             int64_t ldY, const int32_t* pre_status, int32_t* cell_status,
                             cudaStream_t st, const Source* src = nullptr);
+// Transport properties (Chung et al. 1988 at the Peng-Robinson density); outputs may be NULL.
+cudaError_t launch_transport(const EosParams& P, int64_t n, const double* T, const double* p,
+                             const double* Y, int64_t ldY, double* mu, double* lam, double* alpha,
+                             cudaStream_t st);
 cudaError_t launch_props(const EosParams& P, int64_t n, const double* T, const double* p,
                          const double* Y, int64_t ldY, double* rho, double* h, double* cp,
                          double* Z, cudaStream_t st);

@@ -630,6 +630,136 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) props_kernel(EosParams P
 }
 
 
+// ---------------------------------------------------------------- transport properties
+// Chung, Ajlan, Lee & Starling (1988), the high-pressure viscosity and thermal conductivity of
+// a mixture from its pseudo-critical constants (Chung's mixing rules over the mole fractions)
+// and its molar density, here the Peng-Robinson density; the ideal-gas Cv and the real-fluid c_p
+// come from the same NASA-7 / Peng-Robinson state. The correlation is accurate to a few percent,
+// so it is evaluated in FP32 (the PR state and the outer mixing sums stay FP64).
+
+// Chung's coefficients E_i = a_i + b_i omega (viscosity) and B_i (conductivity), nonpolar,
+// non-associating species
+__constant__ float kChungE[10][2] = {
+    {6.324f, 50.412f}, {1.210e-3f, -1.154e-3f}, {5.283f, 254.209f}, {6.623f, 38.096f},
+    {19.745f, 7.630f}, {-1.900f, -12.537f}, {24.275f, 3.450f}, {0.7972f, 1.117f},
+    {-0.2382f, 0.06770f}, {0.06863f, 0.3479f}};
+__constant__ float kChungB[7][2] = {
+    {2.4166f, 0.74824f}, {-0.50924f, -1.5094f}, {6.6107f, 5.6207f}, {14.543f, -8.9139f},
+    {0.79274f, 0.82019f}, {-5.8634f, 12.801f}, {91.089f, 128.73f}};
+
+// Chung's G2 with coefficients C1..C5 at reduced density y (G1 the Carnahan-Starling contact
+// value); (1 - exp(-C4 y)) / y by expm1 so that dilute cells keep their digits
+__device__ __forceinline__ float chung_g2(const float (&C)[10], float y, float G1) {
+  const float t = y > 0.0f ? -expm1f(-C[3] * y) / y : C[3];
+  return (C[0] * t + C[1] * G1 * __expf(C[4] * y) + C[2] * G1) / (C[0] * C[3] + C[1] + C[2]);
+}
+
+// mu (Pa s) and lambda (W/(m K)) of a pseudo-pure fluid (Tc K, Vc cm^3/mol, omega, M g/mol) at
+// temperature T, molar density rho (mol/cm^3) and ideal-gas molar Cv (J/(mol K))
+__device__ void chung(float T, float rho, float Tc, float Vc, float om, float M, float cv,
+                      float& mu, float& lam) {
+  const float Ts = 1.2593f * T / Tc;
+  // collision integral of Neufeld, Janzen & Aziz (1972)
+  const float Om = 1.16145f * __powf(Ts, -0.14874f) + 0.52487f * __expf(-0.77320f * Ts) +
+                   2.16178f * __expf(-2.43787f * Ts);
+  const float y = rho * Vc * (1.0f / 6.0f);
+  const float omy = 1.0f - y;
+  const float G1 = (1.0f - 0.5f * y) / (omy * omy * omy);
+  float E[10], B[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) E[i] = kChungE[i][0] + kChungE[i][1] * om;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) B[i] = kChungB[i][0] + kChungB[i][1] * om;
+  const float G2 = chung_g2(E, y, G1);
+  const float Fc = 1.0f - 0.2756f * om;
+  const float c = cbrtf(Vc);
+  const float vc23 = c * c;
+  const float eta_k = sqrtf(Ts) / Om * Fc * (1.0f / G2 + E[5] * y);
+  const float eta_p = E[6] * y * y * G2 * __expf(E[7] + E[8] / Ts + E[9] / (Ts * Ts));
+  mu = (eta_k + eta_p) * 36.344f * sqrtf(M * Tc) / vc23 * 1e-7f;
+  // thermal conductivity: dilute viscosity (Pa s), Cv correction Psi, dense terms
+  const float Mk = M * 1e-3f;
+  const float eta0 = 40.785f * Fc * sqrtf(M * T) / (vc23 * Om) * 1e-7f;
+  const float a = cv * (float)kInvR - 1.5f;
+  const float b = 0.7862f - 0.7109f * om + 1.3168f * om * om;
+  const float Tr = T / Tc;
+  const float Zp = 2.0f + 10.5f * Tr * Tr;
+  const float psi = 1.0f + a * (0.215f + 0.28288f * a - 1.061f * b + 0.26665f * Zp) /
+                               (0.6366f + b * Zp + 1.061f * a * b);
+  const float H2 = chung_g2(B, y, G1);
+  const float q = 3.586e-3f * sqrtf(Tc / Mk) / vc23;
+  lam = 31.2f * eta0 * psi / Mk * (1.0f / H2 + B[5] * y) + q * B[6] * y * y * sqrtf(Tr) * H2;
+}
+
+template <int NM>
+__global__ void __launch_bounds__(kThreads, kPreBlocks) transport_kernel(EosParams P, int64_t ncell,
+    const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
+    int64_t ldY, double* mu, double* lam, double* alpha) {
+  extern __shared__ double sm[];
+  const SharedConsts c = load_consts(P, sm);
+  f2* ycol = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
+  const int n = P.n, nn = P.n * P.n;
+  const int stride = blockDim.x;
+  const float* __restrict__ tp = P.tpair;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncell;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double Tk = T[i], pk = p[i];
+    bool finite = d_finite(Tk) && d_finite(pk) && d_pos(pk) && d_pos(Tk);
+    for (int k = 0; k < n; ++k) {
+      const double yk = Y[k * ldY + i];
+      finite = finite && d_finite(yk);
+      ycol[k * stride] = f2_from(yk);
+    }
+    double m_out = __longlong_as_double(0x7ff8000000000000LL), l_out = m_out, a_out = m_out;
+    if (finite) {
+      Mixture m;
+      mixture(ycol, n, c, m);
+      int st = 0;
+      const PRPoint q = pr_point<false>(m, Tk, pk, true, c.lnt, st);
+      const double rho = pk / (m.inv * q.Z * kR * Tk);            // kg/m^3
+      const double cpm = cp_ig(m, Tk) + q.cp_dep * m.inv;           // J/(kg K)
+      const double Wm = 1.0 / m.inv;
+      // mole fractions x_k = (Y_k / W_k) W_mix, kept in the column's high words
+      const float Wmf = (float)Wm;
+      for (int k = 0; k < n; ++k) ycol[k * stride].h = ycol[k * stride].h * c.spcw[k * kSpcStride].h * Wmf;
+      // Chung's mixing sums, symmetric: sum_ij x_i x_j A_ij = sum_i x_i (A_ii x_i + 2 sum_{j>i} A_ij x_j)
+      double S[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 1
+      for (int a = 0; a < n; ++a) {
+        const float xa = ycol[a * stride].h;
+        float R4[4];
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) R4[qq] = 0.5f * __ldg(tp + qq * nn + a * n + a) * xa;
+        for (int b = a + 1; b < n; ++b) {
+          const float xb = ycol[b * stride].h;
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) R4[qq] = fmaf(__ldg(tp + qq * nn + a * n + b), xb, R4[qq]);
+        }
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) S[qq] = fma(2.0 * (double)xa, (double)R4[qq], S[qq]);
+      }
+      const double eps_m = S[1] / S[0];
+      const double sig2 = cbrt(S[0] * S[0]);                        // sigma_m^2
+      const double Mr = S[3] / (eps_m * sig2);
+      const float Tcm = (float)(1.2593 * eps_m);
+      const float Vcm = (float)(S[0] / (0.809 * 0.809 * 0.809));
+      const float omm = (float)(S[2] / S[0]);
+      const float cv = (float)(cp_ig(m, Tk) * Wm - kR);             // ideal-gas molar Cv
+      float muf, lamf;
+      chung((float)Tk, (float)(rho * m.inv * 1e-6), Tcm, Vcm, omm, (float)(Mr * Mr), cv, muf, lamf);
+      if (st == 0) {
+        m_out = (double)muf;
+        l_out = (double)lamf;
+        a_out = (double)lamf / (rho * cpm);
+      }
+    }
+    if (mu) mu[i] = m_out;
+    if (lam) lam[i] = l_out;
+    if (alpha) alpha[i] = a_out;
+  }
+}
+
+
 // ---------------------------------------------------------------- Jacobian of the step
 
 // dh/dY_k of the mass-specific real-fluid enthalpy at fixed T, p (FP64), for the composition in
@@ -1023,6 +1153,17 @@ cudaError_t post_nm(const EosParams& P, const RowMap& rows, const float* O, int6
 }
 
 template <int NM>
+cudaError_t transport_nm(const EosParams& P, int64_t n, const double* T, const double* p,
+                         const double* Y, int64_t ldY, double* mu, double* lam, double* alpha,
+                         cudaStream_t st) {
+  cudaError_t e = smem_optin<transport_kernel<NM>>();
+  if (e != cudaSuccess) return e;
+  transport_kernel<NM><<<grid_for(n), kThreads, eos_smem(P), st>>>(P, n, T, p, Y, ldY, mu, lam,
+                                                                   alpha);
+  return cudaGetLastError();
+}
+
+template <int NM>
 cudaError_t props_nm(const EosParams& P, int64_t n, const double* T, const double* p,
                      const double* Y, int64_t ldY, double* rho, double* h, double* cp, double* Z,
                      cudaStream_t st) {
@@ -1053,6 +1194,7 @@ cudaError_t prepare_nm(int xkind) {
   if (e == cudaSuccess) e = smem_optin<eos_pre_kernel<NM, float>>();  // stage entry point
   if (e == cudaSuccess) e = smem_optin<eos_post_kernel<NM>>();
   if (e == cudaSuccess) e = smem_optin<props_kernel<NM>>();
+  if (e == cudaSuccess) e = smem_optin<transport_kernel<NM>>();
   return e;
 }
 
@@ -1134,6 +1276,14 @@ cudaError_t launch_props(const EosParams& P, int64_t n, const double* T, const d
   if (n <= 0) return cudaSuccess;
   if (P.n <= 16) return props_nm<16>(P, n, T, p, Y, ldY, rho, h, cp, Z, st);
   return props_nm<32>(P, n, T, p, Y, ldY, rho, h, cp, Z, st);
+}
+
+cudaError_t launch_transport(const EosParams& P, int64_t n, const double* T, const double* p,
+                             const double* Y, int64_t ldY, double* mu, double* lam, double* alpha,
+                             cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (P.n <= 16) return transport_nm<16>(P, n, T, p, Y, ldY, mu, lam, alpha, st);
+  return transport_nm<32>(P, n, T, p, Y, ldY, mu, lam, alpha, st);
 }
 
 }  // namespace dfgb

@@ -127,7 +127,7 @@ void free_state(df_state* s) {
   s->jac = nullptr;
   free_trn(s->trn);
   s->trn = nullptr;
-  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_Kr2); f(s->d_kfs); f(s->d_kfr); f(s->d_lntab); f(s->d_gtab); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
+  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_Kr2); f(s->d_kfs); f(s->d_kfr); f(s->d_lntab); f(s->d_tsp); f(s->d_tpair); f(s->d_gtab); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
   for (auto p : s->W32) f(p);
   for (auto p : s->bias) f(p);
   for (auto p : s->Wlp) f(p);
@@ -412,6 +412,33 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
   }
   CK(dalloc(&s->d_lntab, lntab.size()), "constants");
   CK(cudaMemcpy(s->d_lntab, lntab.data(), sizeof(double) * 256, cudaMemcpyHostToDevice), "copy");
+  // Chung's mixing-rule tables (transport properties): sigma_i = 0.809 Vc_i^(1/3) Angstrom,
+  // eps_i / k = Tc_i / 1.2593, Vc_i = Zc R Tc_i / pc_i with the Peng-Robinson critical
+  // compressibility Zc = 0.307401, binary factors 1
+  std::vector<double> tsp((size_t)n * 4);
+  std::vector<float> tpair((size_t)4 * n * n);
+  for (int k = 0; !netonly && k < n; ++k) {
+    tsp[4 * k] = mech->Tc[k];
+    tsp[4 * k + 1] = 0.307401 * kR * mech->Tc[k] / mech->pc[k] * 1e6;
+    tsp[4 * k + 2] = mech->omega[k];
+    tsp[4 * k + 3] = mech->W[k] * 1e3;
+  }
+  for (int i = 0; !netonly && i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double si = 0.809 * std::cbrt(tsp[4 * i + 1]), sj = 0.809 * std::cbrt(tsp[4 * j + 1]);
+      const double eij = std::sqrt(tsp[4 * i] * tsp[4 * j]) / 1.2593;
+      const double s2 = si * sj, s3 = s2 * std::sqrt(s2);
+      const double Mi = tsp[4 * i + 3], Mj = tsp[4 * j + 3];
+      const size_t o = (size_t)i * n + j, nn = (size_t)n * n;
+      tpair[o] = (float)s3;
+      tpair[nn + o] = (float)(eij * s3);
+      tpair[2 * nn + o] = (float)(0.5 * (tsp[4 * i + 2] + tsp[4 * j + 2]) * s3);
+      tpair[3 * nn + o] = (float)(eij * s2 * std::sqrt(2.0 * Mi * Mj / (Mi + Mj)));
+    }
+  CK(dalloc(&s->d_tsp, tsp.size()), "constants");
+  CK(dalloc(&s->d_tpair, tpair.size()), "constants");
+  CK(cudaMemcpy(s->d_tsp, tsp.data(), sizeof(double) * tsp.size(), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(s->d_tpair, tpair.data(), sizeof(float) * tpair.size(), cudaMemcpyHostToDevice), "copy");
   CK(dalloc(&s->d_kfs, kfs.size()), "constants");
   CK(dalloc(&s->d_kfr, kfr.size()), "constants");
   CK(cudaMemcpy(s->d_kfs, kfs.data(), sizeof(float) * kfs.size(), cudaMemcpyHostToDevice), "copy");
@@ -447,6 +474,8 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
   P.kfs = s->d_kfs;
   P.kfr = s->d_kfr;
   P.lntab = s->d_lntab;
+  P.tsp = s->d_tsp;
+  P.tpair = s->d_tpair;
   P.err = s->d_err;
   P.flagged = s->d_flagged;
   P.newton_iters = s->d_iters;
@@ -619,6 +648,16 @@ df_status df_real_fluid_props(df_state* s, int64_t n_cells, const double* T, con
   DeviceGuard guard(s->device);
   cudaError_t e = launch_props(s->P, n_cells, T, p, Y, ldY, rho, h, cp, Z, (cudaStream_t)stream);
   return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "real-fluid properties");
+}
+
+df_status df_transport_props(df_state* s, int64_t n_cells, const double* T, const double* p,
+                             const double* Y, int64_t ldY, double* mu, double* lam, double* alpha,
+                             void* stream) {
+  df_status rc = check_fields(s, n_cells, T, p, Y, ldY);
+  if (rc != DF_OK || n_cells == 0) return rc;
+  DeviceGuard guard(s->device);
+  cudaError_t e = launch_transport(s->P, n_cells, T, p, Y, ldY, mu, lam, alpha, (cudaStream_t)stream);
+  return e == cudaSuccess ? DF_OK : cuda_fail(s, e, "transport properties");
 }
 
 }  // extern "C"

@@ -60,6 +60,8 @@ struct df_state {
   float* d_kfs = nullptr;                // FP32 k_ij tables (EosParams)
   float* d_kfr = nullptr;
   double* d_lntab = nullptr;             // log table (EosParams)
+  double* d_tsp = nullptr;               // transport species constants (EosParams)
+  float* d_tpair = nullptr;              // transport pair tables (EosParams)
   int gelu_mode = 0;                     // DF_GELU_TANH or DF_GELU_TABLE
   float4* d_gtab = nullptr;              // tabulated GELU (DF_GELU_TABLE)
   int* d_err = nullptr;                  // kernel error word

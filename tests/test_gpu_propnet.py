@@ -35,12 +35,12 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def _case(n_species, N, widths, seed=5):
-    """Mechanism, states, exact properties, and a property network whose normalisation
-    matches the states."""
+def _case(n_species, N, widths, seed=5, transport=False):
+    """Mechanism, states, exact properties (with transport: rho, T, ln mu, ln lambda,
+    ln alpha), and a property network whose normalisation matches the states."""
     mech = synth.make_mechanism(n_species, 12 if n_species < 20 else 200, 1)
     T, p, Y = synth.fields.uniform_states(mech, N, seed=seed)
-    h, props = opn.exact(mech, T, p, Y)
+    h, props = (opn.exact_with_transport if transport else opn.exact)(mech, T, p, Y)
     bc = onw.boxcox(Y, 0.1)
     v = np.concatenate([h[None, :], p[None, :], bc], axis=0)
     net = synth.make_propnet(widths, n_species, seed=seed + 1, lam=0.1,
@@ -81,13 +81,14 @@ def test_infer_bf16_vs_rounded_oracle(df):
 
 
 def test_paper_sizes_on_tensor_cores(df):
-    """Sec. 4.1's layer widths (hidden 1024-512-256 for density, 2048-1024-512 for
-    temperature) on 30 species, one output each, BF16 tcgen05 against the BF16-rounded
-    oracle on a strided sample."""
-    for widths in ([32, 1024, 512, 256, 1], [32, 2048, 1024, 512, 1]):
-        mech, net, h, p, Y, props = _case(30, 5000, widths, seed=11)
-        k = 0 if widths[1] == 1024 else 1
-        net.out_mean, net.out_std = net.out_mean[k:k + 1], net.out_std[k:k + 1]
+    """Sec. 4.1's layer widths (hidden 1024-512-256 for density, 2048-1024-512 for temperature
+    and transport) on 30 species: density alone, and T with the logarithms of viscosity, thermal
+    conductivity and thermal diffusivity (4 outputs, as the paper's second network); BF16
+    tcgen05 against the BF16-rounded oracle on a strided sample."""
+    for widths in ([32, 1024, 512, 256, 1], [32, 2048, 1024, 512, 4]):
+        mech, net, h, p, Y, props = _case(30, 5000, widths, seed=11, transport=True)
+        rows = [0] if widths[-1] == 1 else [1, 2, 3, 4]
+        net.out_mean, net.out_std = net.out_mean[rows], net.out_std[rows]
         pn = df.PropNet(net, precision=df.DF_BF16)
         got = host(pn.infer(dev(h), dev(p), dev(Y)))
         torch.cuda.synchronize()

@@ -55,6 +55,18 @@ def test_exact_properties_wrap_the_eos():
     assert np.array_equal(props[1], T)
 
 
+def test_exact_transport_properties_wrap_the_transport_oracle():
+    from oracle import transport
+    mech = synth.make_mechanism(9, 12, 1)
+    T, p, Y = synth.fields.uniform_states(mech, 50, seed=4)
+    h, props = opn.exact_with_transport(mech, T, p, Y)
+    s = transport.state(mech, T, p, Y)
+    assert np.array_equal(h, pr_eos.state(mech, T, p, Y)["h"])
+    assert np.array_equal(props[0], s["rho"]) and np.array_equal(props[1], T)
+    for r, k in ((2, "mu"), (3, "lam"), (4, "alpha")):
+        assert np.array_equal(props[r], np.log(s[k]))
+
+
 def test_regression_gradients_by_finite_differences():
     """loss_and_grads on a 6 -> 5 -> 2 network with two outputs, against central differences
     of the loss in every weight and bias."""
