@@ -181,9 +181,15 @@ def weak_scaling_value(world, cells_per_rank, ms_max):
 # kernel changes, the bench reports traffic as null until it is measured again. Where a file also
 # holds kernels that are not the measured ones, the hash leaves out their sections (each from a
 # start marker up to, not including, an end marker), so that editing them keeps the figure.
-_EOS_OTHER = (("// ---------------------------------------------------------------- Jacobian of the step",
+_EOS_OTHER = (("// ---------------------------------------------------------------- transport properties",
+               "// ---------------------------------------------------------------- Jacobian of the step"),
+              ("// ---------------------------------------------------------------- Jacobian of the step",
                "cudaError_t smem_optin()"),
-              ("cudaError_t launch_jac_scale(", "cudaError_t launch_eos_post("))
+              ("template <int NM>\ncudaError_t transport_nm(", "template <int NM>\ncudaError_t props_nm("),
+              ("  if (e == cudaSuccess) e = smem_optin<transport_kernel<NM>>();\n",
+               "  return e;\n}\n\ncudaError_t prepare_eos("),
+              ("cudaError_t launch_jac_scale(", "cudaError_t launch_eos_post("),
+              ("cudaError_t launch_transport(", "}  // namespace dfgb"))
 MEASURED_TRAFFIC = {
     ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "4b3c9714d132bb8d", 3158.0),
     ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "4b3c9714d132bb8d", 4756.0),
