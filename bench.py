@@ -191,8 +191,10 @@ _EOS_OTHER = (("// -------------------------------------------------------------
               ("cudaError_t launch_jac_scale(", "cudaError_t launch_eos_post("),
               ("cudaError_t launch_transport(", "}  // namespace dfgb"))
 MEASURED_TRAFFIC = {
-    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "4b3c9714d132bb8d", 3158.0),
-    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "4b3c9714d132bb8d", 4756.0),
+    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e83bc91ba940bed", 3152.0),
+    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e83bc91ba940bed", 4750.5),
+    ("layer2", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e83bc91ba940bed", 2340.2),
+    ("layer3", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e83bc91ba940bed", 1062.6),
     ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "eeab54a9bdb05447", 296.1,
                                         _EOS_OTHER),
     ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "eeab54a9bdb05447", 543.3,
@@ -637,14 +639,17 @@ def roofline_families(r, pk, pk_src, live, df, steps_timed_s):
     for fam, (launches, tot) in fams.items():
         avg_s = tot / r["steps"] * 1e-3
         if fam.startswith("layer") and prec != "fp32":
-            l = int(fam[5:])
+            ls = [int(v) for v in fam[5:].split("+")]   # "layer0+1": layers 0 and 1 fused
             if prec == "fp8" and live.get("fp8_tflops"):
                 peak, src = live["fp8_tflops"], "fp8 e4m3 GEMM measured live (torch._scaled_mm 8192^3)"
             else:
                 peak, src = bf16_peak, bf16_src
-            ach = fl[l] / avg_s / 1e12
+            ach = sum(fl[l] for l in ls) / avg_s / 1e12
             roofs[fam] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                          "frac": ach / peak, "kernel": f"tc_gemm {fam}", "peak_source": src}
+                          "frac": ach / peak, "peak_source": src,
+                          "kernel": f"tc_gemm {fam}" if len(ls) == 1 else
+                          f"fused01 (layers {ls[0]} and {ls[-1]}; algorithmic flops, the recomputed "
+                          "layer-0 blocks not counted)"}
         elif fam.startswith("layer"):
             l = int(fam[5:])
             peak = live.get("fp32_tflops") or 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e-6

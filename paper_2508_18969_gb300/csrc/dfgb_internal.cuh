@@ -230,6 +230,24 @@ struct TcLayer {
   long long wait_budget = 0;  // clocks a pipeline wait may take before the kernel gives up
                               // (<= 0: the default, ~1 s)
 };
+// Network layers 0 and 1 fused in one kernel (BF16, tanh GELU on both): x [rows x K0] ->
+// H1 [rows x N1], the layer-0 activations kept on chip (mlp_tc.cu: fused01_kernel).
+struct F01Layer {
+  CUtensorMap tmX;       // network input, as layer 0's tmA (box {64, 128})
+  CUtensorMap tmW0;      // W0 [N0 x K0], box {64, 64}
+  CUtensorMap tmW1a;     // W1 [N1 x N0], box {32, 224}, 64-byte swizzle
+  CUtensorMap tmW1b;     // W1, box {32, 192}, 64-byte swizzle
+  CUtensorMap tmO;       // H1 output, as layer 1's tmO
+  int N0, N1, K0;
+  const float* b0;
+  const float* b1;
+  long long wait_budget = 0;  // as TcLayer::wait_budget
+};
+bool f01_supported(int K0, int N0, int N1);
+bool f01_encode(F01Layer& F, const void* W0, int64_t ldw0, const void* W1, int64_t ldw1, char* err,
+                size_t errlen);
+cudaError_t prepare_f01();
+cudaError_t launch_f01(const F01Layer& F, const RowMap& rows, int num_sms, int* err, cudaStream_t st);
 bool tc_encode_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
                   uint64_t outer, uint64_t row_pitch_bytes, uint32_t box_inner,
                   uint32_t box_outer, char* err, size_t errlen);

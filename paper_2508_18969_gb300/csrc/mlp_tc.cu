@@ -460,8 +460,9 @@ __device__ __forceinline__ void store_chunk(const float (&v)[32], const CUtensor
 }
 
 // One 32-column chunk of the epilogue: per-channel scale, bias, GELU (or the row-group scale
-// of a tangent layer), then quantise and store; kModeStoreG also stores GELU'(z).
-template <int OUTK, int ACT, bool SCALE, int MODE>
+// of a tangent layer), then quantise and store; kModeStoreG also stores GELU'(z). With
+// SMEM_BIAS the bias pointer addresses shared memory (a plain load instead of ld.global.nc).
+template <int OUTK, int ACT, bool SCALE, int MODE, bool SMEM_BIAS = false>
 __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const TcArgs& g,
                                                const CUtensorMap* tmO, const CUtensorMap* tmG,
                                                int64_t M, int64_t m0, int col0, uint8_t* stg,
@@ -492,7 +493,7 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const Tc
   const float4* s4 = reinterpret_cast<const float4*>(g.col_scale + col0);
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
-    const float4 b = __ldg(b4 + u);
+    const float4 b = SMEM_BIAS ? b4[u] : __ldg(b4 + u);
     float2 z0 = make_float2(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]));
     float2 z1 = make_float2(__uint_as_float(r[4 * u + 2]), __uint_as_float(r[4 * u + 3]));
     if (SCALE) {
@@ -983,6 +984,328 @@ cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStrea
   }
 }
 
+
+// ---- layers 0 and 1 fused ----
+// H1 = GELU(GELU(x W0^T + b0) W1^T + b1) without the layer-0 activation leaving the SM. A CTA
+// owns 128 rows and 416 output columns of layer 1 (two MMAs per K step, N = 224 and N = 192,
+// into tensor-memory columns 0..415). Layer 1's K dimension (layer 0's outputs) is walked in
+// blocks of 64: for block kb the CTA first computes x W0[64 kb ..]^T (M = 128, N = 64, K <= 64)
+// into a 64-column tensor-memory buffer (columns 448..511), eight warps add the bias, apply the
+// tanh-form GELU, round to BF16 and write the 128 x 64 tile straight into a shared-memory stage
+// in the 128-byte-swizzled K-major layout the MMA reads; then layer 1's MMAs of block kb consume
+// that stage. The layer-0 block is recomputed for each of the row tile's two column tiles of
+// layer 1 (a tenth of layer 1's work); in return the 3.2 KB per row of layer-0 activations is
+// neither written to nor read back from HBM, and layer 1's A operand is not streamed from L2.
+// Layer 0's MMA of block kb + 1 is issued before layer 1's MMA of block kb, so the tensor pipe
+// works on the next block while the warps convert the current one. Single CTAs, not pairs: every
+// hand-over between the MMA issuer and the converting warps stays inside the CTA (a pair would
+// need a cluster-scope release per block, measured at 500-2000 clocks).
+//
+// Warp roles (448 threads): warp 0 TMA producer (x tiles, W0 slices, W1 stages); warp 1 tensor
+// memory and the MMAs; warps 2..9 layer-0 conversion (two per tensor-memory lane quarter, 32 of
+// the 64 columns each: the conversion of a block lies on the tensor pipe's critical path, so it
+// gets the most warps); warps 10..13 layer-1 epilogue (one per quarter; TMA tensor stores). Both
+// bias vectors are copied to shared memory first. All waits are bounded as in tc_gemm_kernel;
+// the drains on the way out allow the full default budget.
+constexpr int kF01Threads = 448;
+constexpr int kF01Cols = 416;            // layer-1 columns per tile
+constexpr int kF01N1a = 224, kF01N1b = 192;
+constexpr int kF01Acc0 = 448;            // tensor-memory column of the layer-0 block
+constexpr int kF01StX = 2, kF01StW0 = 2, kF01StA = 2, kF01StB = 2;
+constexpr int kF01XBytes = BM * kRowBytes;                      // 16 KB
+constexpr int kF01W0Bytes = 64 * kRowBytes;                     // the 64 W0 rows of a block
+constexpr int kF01ABytes = BM * kRowBytes;                      // 16 KB
+constexpr int kF01BBytes = kF01Cols * kRowBytes;                // 416 rows of W1 (52 KB)
+constexpr int kF01StageOut = 2 * 32 * 32 * 2;                   // per epilogue warp, BF16
+constexpr int kF01MaxN0 = 2048, kF01MaxN1 = 2 * kF01Cols;       // bias entries in shared memory
+constexpr int kF01Smem = kF01StX * kF01XBytes + kF01StW0 * kF01W0Bytes + kF01StA * kF01ABytes +
+                         kF01StB * kF01BBytes + 4 * kF01StageOut +
+                         4 * (kF01MaxN0 + kF01MaxN1) + 1024 + 1024;
+
+struct F01Args {
+  RowMap rows;
+  int N0, N1, K0;            // layer-0 outputs (= layer-1 inputs), layer-1 outputs, layer-0 inputs
+  const float* b0;           // [N0]
+  const float* b1;           // [N1] (zero padded to 32)
+  int* err;
+  long long budget;
+  uint32_t suspend;
+};
+
+__global__ void __launch_bounds__(kF01Threads, 1) fused01_kernel(
+    const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW0,
+    const __grid_constant__ CUtensorMap tmW1a, const __grid_constant__ CUtensorMap tmW1b,
+    const __grid_constant__ CUtensorMap tmO, F01Args g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sX = smem;
+  uint8_t* sW0 = sX + kF01StX * kF01XBytes;
+  uint8_t* sA = sW0 + kF01StW0 * kF01W0Bytes;
+  uint8_t* sB = sA + kF01StA * kF01ABytes;
+  uint8_t* sOut = sB + kF01StB * kF01BBytes;
+  float* sb0 = reinterpret_cast<float*>(sOut + 4 * kF01StageOut);
+  float* sb1 = sb0 + kF01MaxN0;
+  uint64_t* bars = (uint64_t*)(sb1 + kF01MaxN1);
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t b0a = smem_u32(bars);
+  // barriers: x full/empty, w0 full/empty, b full/empty, a full/empty, acc0 full/empty,
+  // acc1 full/empty, drain
+  const uint32_t xfull = b0a, xempty = xfull + 8 * kF01StX;
+  const uint32_t wfull = xempty + 8 * kF01StX, wempty = wfull + 8 * kF01StW0;
+  const uint32_t bfull = wempty + 8 * kF01StW0, bempty = bfull + 8 * kF01StB;
+  const uint32_t afull = bempty + 8 * kF01StB, aempty = afull + 8 * kF01StA;
+  const uint32_t c0full = aempty + 8 * kF01StA, c0empty = c0full + 8;
+  const uint32_t c1full = c0empty + 8, c1empty = c1full + 8, drain = c1empty + 8;
+
+  if (threadIdx.x == 0) {
+    abort_sh = 0;
+    for (int s = 0; s < kF01StX; ++s) { mbar_init(xfull + 8 * s, 1); mbar_init(xempty + 8 * s, 1); }
+    for (int s = 0; s < kF01StW0; ++s) { mbar_init(wfull + 8 * s, 1); mbar_init(wempty + 8 * s, 1); }
+    for (int s = 0; s < kF01StB; ++s) { mbar_init(bfull + 8 * s, 1); mbar_init(bempty + 8 * s, 1); }
+    for (int s = 0; s < kF01StA; ++s) { mbar_init(afull + 8 * s, 8); mbar_init(aempty + 8 * s, 1); }
+    mbar_init(c0full, 1);
+    mbar_init(c0empty, 8);
+    mbar_init(c1full, 1);
+    mbar_init(c1empty, 4);
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)), "r"(512u) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // biases (zero padded to whole 64- and 32-column blocks)
+  for (int i = threadIdx.x; i < kF01MaxN0; i += blockDim.x)
+    sb0[i] = i < ((g.N0 + 63) & ~63) ? g.b0[i] : 0.0f;
+  for (int i = threadIdx.x; i < kF01MaxN1; i += blockDim.x)
+    sb1[i] = i < ((g.N1 + 31) & ~31) ? g.b1[i] : 0.0f;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  volatile int* abort = &abort_sh;
+
+  const int64_t M = valid_rows(g.rows);
+  const int64_t tiles_m = (M + BM - 1) / BM;
+  const int tiles_n = (g.N1 + kF01Cols - 1) / kF01Cols;
+  const int64_t ntiles = tiles_m * tiles_n;
+  const int KB = (g.N0 + 63) / 64;              // layer-1 k-blocks = layer-0 column blocks
+  auto tile_m0 = [&](int64_t t) -> int64_t { return (t / tiles_n) * BM; };
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmX) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmW0) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmW1a) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmW1b) : "memory");
+    uint32_t ix = 0, iw = 0, ib = 0;   // loads issued: x tiles, W0 slices, W1 stages
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int m0 = (int)tile_m0(t);
+      const int n0 = (int)(t % tiles_n) * kF01Cols;
+      const int sx = ix % kF01StX;
+      if (!mbar_wait(xempty + 8 * sx, ((ix / kF01StX) & 1) ^ 1, abort, g.err, g.budget, g.suspend))
+        break;
+      mbar_arrive_expect_tx(xfull + 8 * sx, kF01XBytes);
+      tma_load_2d(smem_u32(sX + sx * kF01XBytes), &tmX, xfull + 8 * sx, 0, m0);
+      ++ix;
+      for (int kb = 0; kb < KB; ++kb) {
+        const int sw = iw % kF01StW0;
+        if (!mbar_wait(wempty + 8 * sw, ((iw / kF01StW0) & 1) ^ 1, abort, g.err, g.budget, g.suspend)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(wfull + 8 * sw, kF01W0Bytes);
+        tma_load_2d(smem_u32(sW0 + sw * kF01W0Bytes), &tmW0, wfull + 8 * sw, 0, 64 * kb);
+        ++iw;
+        const int sb = ib % kF01StB;
+        if (!mbar_wait(bempty + 8 * sb, ((ib / kF01StB) & 1) ^ 1, abort, g.err, g.budget, g.suspend)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(bfull + 8 * sb, kF01BBytes);
+        const uint32_t dB = smem_u32(sB + sb * kF01BBytes);
+        tma_load_2d(dB, &tmW1a, bfull + 8 * sb, 64 * kb, n0);
+        tma_load_2d(dB + kF01N1a * kRowBytes, &tmW1b, bfull + 8 * sb, 64 * kb, n0 + kF01N1a);
+        ++ib;
+      }
+    }
+    // Drain: every issued load lands before the CTA exits.
+    auto drain_ring = [&](uint32_t full, int stages, uint32_t issued) {
+      const uint32_t first = issued > (uint32_t)stages ? issued - stages : 0;
+      for (uint32_t j = first; j < issued; ++j) {
+        const long long t0 = clock64();
+        while (!mbar_try(full + 8 * (j % stages), (j / stages) & 1) && clock64() - t0 < kWaitBudget) {
+        }
+      }
+    };
+    drain_ring(xfull, kF01StX, ix);
+    drain_ring(wfull, kF01StW0, iw);
+    drain_ring(bfull, kF01StB, ib);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t id0 = idesc<false, 64, BM>();
+    constexpr uint32_t id1a = idesc<false, kF01N1a, BM>();
+    constexpr uint32_t id1b = idesc<false, kF01N1b, BM>();
+    const int kk0 = (g.K0 * 2 + 31) / 32;       // K = 16 steps of layer 0 (K0 <= 64)
+    uint32_t ix = 0, iw = 0, ia = 0, ib = 0, j0 = 0, jt = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++ix, ++jt) {
+      const int sx = ix % kF01StX;
+      if (!mbar_wait(xfull + 8 * sx, (ix / kF01StX) & 1, abort, g.err, g.budget, g.suspend)) break;
+      tc_fence_after();
+      const uint64_t dx = desc_sw128(smem_u32(sX + sx * kF01XBytes));
+      // one layer-0 block: acc0 = x W0[64 kb ..]^T
+      auto mma0 = [&](int kb) -> bool {
+        const int sw = iw % kF01StW0;
+        if (!mbar_wait(wfull + 8 * sw, (iw / kF01StW0) & 1, abort, g.err, g.budget, g.suspend))
+          return false;
+        if (!mbar_wait(c0empty, (j0 & 1) ^ 1, abort, g.err, g.budget, g.suspend)) return false;
+        tc_fence_after();
+        const uint64_t dw = desc_sw128(smem_u32(sW0 + sw * kF01W0Bytes));
+        for (int kk = 0; kk < kk0; ++kk)
+          mma_issue<false>(tmem + kF01Acc0, dx + 2 * kk, dw + 2 * kk, id0, kk ? 1u : 0u);
+        mma_commit(wempty + 8 * sw);
+        mma_commit(c0full);
+        if (kb == KB - 1) mma_commit(xempty + 8 * sx);
+        ++iw;
+        ++j0;
+        return true;
+      };
+      // one layer-1 block: acc1 += H0[:, 64 kb ..] W1[n0 .., 64 kb ..]^T
+      auto mma1 = [&](int kb) -> bool {
+        if (kb == 0 && !mbar_wait(c1empty, (jt & 1) ^ 1, abort, g.err, g.budget, g.suspend))
+          return false;
+        const int sa = ia % kF01StA;
+        if (!mbar_wait(afull + 8 * sa, (ia / kF01StA) & 1, abort, g.err, g.budget, g.suspend))
+          return false;
+        const int sb = ib % kF01StB;
+        if (!mbar_wait(bfull + 8 * sb, (ib / kF01StB) & 1, abort, g.err, g.budget, g.suspend))
+          return false;
+        tc_fence_after();
+        const uint64_t da = desc_sw128(smem_u32(sA + sa * kF01ABytes));
+        const uint64_t db = desc_sw128(smem_u32(sB + sb * kF01BBytes));
+        const uint64_t db2 = desc_sw128(smem_u32(sB + sb * kF01BBytes + kF01N1a * kRowBytes));
+#pragma unroll
+        for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+          const uint32_t acc = (kb != 0 || kk) ? 1u : 0u;
+          mma_issue<false>(tmem, da + 2 * kk, db + 2 * kk, id1a, acc);
+          mma_issue<false>(tmem + kF01N1a, da + 2 * kk, db2 + 2 * kk, id1b, acc);
+        }
+        mma_commit(aempty + 8 * sa);
+        mma_commit(bempty + 8 * sb);
+        ++ia;
+        ++ib;
+        return true;
+      };
+      if (!mma0(0)) break;
+      for (int kb = 1; kb < KB && ok; ++kb) ok = mma0(kb) && mma1(kb - 1);
+      if (ok) ok = mma1(KB - 1);
+      if (ok) mma_commit(c1full);
+    }
+    mma_commit(drain);
+    const long long t0 = clock64();
+    while (!mbar_try(drain, 0) && clock64() - t0 < kWaitBudget) {
+    }
+  } else if (warp >= 2 && warp < 10) {
+    // ---------------- layer-0 conversion: acc0 -> GELU -> BF16 A stage ----------------
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + kF01Acc0 + 32 * half;
+    const int row = q * 32 + lane;              // row of the CTA's 128-row tile
+    uint32_t j0 = 0, ia = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int kb = 0; kb < KB; ++kb, ++j0, ++ia) {
+        if (!mbar_wait(c0full, j0 & 1, abort, g.err, g.budget, g.suspend)) { ok = false; break; }
+        tc_fence_after();
+        uint32_t r[32];
+        tmem_ld32(tb, r);
+        tmem_wait(r);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(c0empty);
+        const float4* b4 = reinterpret_cast<const float4*>(sb0 + 64 * kb + 32 * half);
+        uint32_t w[16];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float4 b = b4[u];
+          const float2 z0 = gelu_fast2(__fadd2_rn(
+              make_float2(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1])), make_float2(b.x, b.y)));
+          const float2 z1 = gelu_fast2(__fadd2_rn(
+              make_float2(__uint_as_float(r[4 * u + 2]), __uint_as_float(r[4 * u + 3])), make_float2(b.z, b.w)));
+          const __nv_bfloat162 h0 = __floats2bfloat162_rn(z0.x, z0.y);
+          const __nv_bfloat162 h1 = __floats2bfloat162_rn(z1.x, z1.y);
+          memcpy(&w[2 * u], &h0, 4);
+          memcpy(&w[2 * u + 1], &h1, 4);
+        }
+        const int sa = ia % kF01StA;
+        if (!mbar_wait(aempty + 8 * sa, ((ia / kF01StA) & 1) ^ 1, abort, g.err, g.budget, g.suspend)) {
+          ok = false;
+          break;
+        }
+        // the 128-byte K-major row of the stage: 16-byte unit u sits at u ^ (row mod 8); this
+        // warp's 32 columns are units 4 half .. 4 half + 3
+        uint8_t* rowp = sA + sa * kF01ABytes + row * kRowBytes;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          *reinterpret_cast<uint4*>(rowp + (((4 * half + u) ^ (row & 7)) * 16)) =
+              make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(afull + 8 * sa);
+      }
+    }
+  } else if (warp >= 10) {
+    // ---------------- layer-1 epilogue: acc1 -> GELU -> BF16 -> TMA store ----------------
+    const int q = warp & 3;
+    uint8_t* stg = sOut + (warp - 10) * kF01StageOut;
+    int buf = 0;
+    if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmO) : "memory");
+    TcArgs ea{};
+    ea.bias = sb1;                                // indexed by the output column
+    ea.out_scale = 1.0f;
+    uint32_t jt = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++jt) {
+      if (!mbar_wait(c1full, jt & 1, abort, g.err, g.budget, g.suspend)) break;
+      tc_fence_after();
+      const int64_t m0 = tile_m0(t) + q * 32;
+      const int n0 = (int)(t % tiles_n) * kF01Cols;
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
+      uint32_t r0[32], r1[32];
+      int c = 0;
+      tmem_ld32(tbase + c, r0);
+      for (; c < kF01Cols; c += 64) {
+        tmem_wait(r0);
+        const int c1 = c + 32;
+        if (c1 < kF01Cols) tmem_ld32(tbase + c1, r1);
+        if (n0 + c < g.N1)
+          epilogue_chunk<kXBF16, kActTanh, false, kModePlain, true>(r0, ea, &tmO, &tmO, M, m0, n0 + c, stg, buf, lane);
+        if (c1 >= kF01Cols) break;
+        tmem_wait(r1);
+        if (c1 + 32 < kF01Cols) tmem_ld32(tbase + c1 + 32, r0);
+        if (n0 + c1 < g.N1)
+          epilogue_chunk<kXBF16, kActTanh, false, kModePlain, true>(r1, ea, &tmO, &tmO, M, m0, n0 + c1, stg, buf, lane);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(c1empty);
+    }
+    if (lane == 0) bulk_wait_all();
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+                 : "memory");
+}
+
 }  // namespace
 
 bool tc_encode_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t inner,
@@ -1108,6 +1431,63 @@ cudaError_t launch_tc_gemm(const TcLayer& L, const RowMap& rows, int num_sms, in
   a.suspend = a.budget < kWaitBudget ? 32u : kSuspendNs;
   return L.elem_bytes == 1 ? launch_fmt<true>(L, a, num_sms, st)
                            : launch_fmt<false>(L, a, num_sms, st);
+}
+
+// ---- fused layers 0 and 1 (host side) ----
+// Two 416-column tiles cover layer 1 with little padding only for 768..832 outputs; layer 0 must
+// fit one 64-element k-block and give whole 64-column blocks.
+bool f01_supported(int K0, int N0, int N1) {
+  return K0 >= 1 && K0 <= 64 && N0 >= 64 && N0 % 64 == 0 && N0 <= kF01MaxN0 && N1 >= 768 &&
+         N1 <= 2 * kF01Cols;
+}
+
+bool f01_encode(F01Layer& F, const void* W0, int64_t ldw0, const void* W1, int64_t ldw1, char* err,
+                size_t errlen) {
+  return tc_encode_2d(&F.tmW0, W0, 2, (uint64_t)F.K0, (uint64_t)F.N0, (uint64_t)ldw0 * 2, 64, 64,
+                      err, errlen) &&
+         tc_encode_2d(&F.tmW1a, W1, 2, (uint64_t)F.N0, (uint64_t)F.N1, (uint64_t)ldw1 * 2, 64,
+                      kF01N1a, err, errlen) &&
+         tc_encode_2d(&F.tmW1b, W1, 2, (uint64_t)F.N0, (uint64_t)F.N1, (uint64_t)ldw1 * 2, 64,
+                      kF01N1b, err, errlen);
+}
+
+namespace {
+// the kernel's dynamic shared memory, once per device
+cudaError_t f01_attr() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!done[dev]) {
+    e = cudaFuncSetAttribute(fused01_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kF01Smem);
+    if (e != cudaSuccess) return e;
+    done[dev] = true;
+  }
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t prepare_f01() { return f01_attr(); }
+
+cudaError_t launch_f01(const F01Layer& F, const RowMap& rows, int num_sms, int* err, cudaStream_t st) {
+  if (rows.nmax <= 0) return cudaSuccess;
+  cudaError_t e = f01_attr();
+  if (e != cudaSuccess) return e;
+  F01Args a;
+  a.rows = rows;
+  a.N0 = F.N0;
+  a.N1 = F.N1;
+  a.K0 = F.K0;
+  a.b0 = F.b0;
+  a.b1 = F.b1;
+  a.err = err;
+  a.budget = F.wait_budget > 0 ? F.wait_budget : kWaitBudget;
+  a.suspend = a.budget < kWaitBudget ? 32u : kSuspendNs;
+  const int64_t tiles = ((rows.nmax + BM - 1) / BM) * ((F.N1 + kF01Cols - 1) / kF01Cols);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, num_sms));
+  fused01_kernel<<<grid, kF01Threads, kF01Smem, st>>>(F.tmX, F.tmW0, F.tmW1a, F.tmW1b, F.tmO, a);
+  return cudaGetLastError();
 }
 
 }  // namespace dfgb

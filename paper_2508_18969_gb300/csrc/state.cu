@@ -171,7 +171,14 @@ df_status run_mlp(df_state* s, const RowMap& rm, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   static const char* kLayer[8] = {"layer0", "layer1", "layer2", "layer3",
                                   "layer4", "layer5", "layer6", "layer7"};
-  for (int l = 0; l < s->L; ++l) {
+  int l0 = 0;
+  if (s->fuse01) {
+    ProfScope ps(s, "layer0+1", st);
+    e = launch_f01(s->f01, rm, s->num_sms, s->d_err, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "fused layers 0 and 1");
+    l0 = 2;
+  }
+  for (int l = l0; l < s->L; ++l) {
     const bool last = l == s->L - 1;
     ProfScope ps(s, kLayer[l], st);
     if (s->precision == DF_FP32) {
@@ -605,10 +612,34 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
       }
       s->tcl.push_back(T);
     }
+    // Layers 0 and 1 of a BF16 tanh-GELU network as one kernel (the layer-0 activations never
+    // leave the SM), on request only (DFGB_FUSE01=1): on GB300 the fused kernel measured slower
+    // than the two layers apart (3.40 against 2.64 ms per 2^20 rows), because single-CTA MMAs
+    // run well below the CTA-pair rate and the layer-1 accumulator cannot be double-buffered
+    // beside the layer-0 block in tensor memory.
+    const char* fenv = getenv("DFGB_FUSE01");
+    if (s->precision == DF_BF16 && s->gelu_mode == DF_GELU_TANH && L >= 3 &&
+        f01_supported(s->widths[0], s->widths[1], s->widths[2]) && fenv && atoi(fenv) == 1) {
+      F01Layer& F = s->f01;
+      F.tmX = s->tcl[0].tmA;
+      F.tmO = s->tcl[1].tmO;
+      F.K0 = s->widths[0];
+      F.N0 = s->widths[1];
+      F.N1 = s->widths[2];
+      F.b0 = s->bias[0];
+      F.b1 = s->bias[1];
+      if (!f01_encode(F, s->Wlp[0], s->Kp8[0], s->Wlp[1], s->Kp8[1], emsg, sizeof emsg)) {
+        free_state(s);
+        delete s;
+        return fail(nullptr, DF_ERR_CUDA, "%s", emsg);
+      }
+      s->fuse01 = true;
+    }
   }
   // one-time per-device kernel attributes, so that no later call (or graph capture) sets any
   CK(prepare_eos(s->P, xk), "kernel attributes");
   for (const TcLayer& T : s->tcl) CK(prepare_tc(T), "kernel attributes");
+  if (s->fuse01) CK(prepare_f01(), "kernel attributes");
 #undef CK
   *out = s;
   return DF_OK;
@@ -1359,6 +1390,7 @@ df_status df_set_wait_limit(df_state* s, int64_t clocks) {
   if (!s) return fail(nullptr, DF_ERR_INVALID_ARG, "state is NULL");
   if (s->tcl.empty()) return fail(s, DF_ERR_UNSUPPORTED, "the state has no tensor-core layers");
   for (TcLayer& L : s->tcl) L.wait_budget = clocks > 0 ? (long long)clocks : 0;
+  s->f01.wait_budget = clocks > 0 ? (long long)clocks : 0;
   return DF_OK;
 }
 

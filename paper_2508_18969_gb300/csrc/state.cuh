@@ -102,6 +102,8 @@ struct df_state {
   int64_t* cscr = nullptr;
   int64_t cscr_words = 0;
   std::vector<TcLayer> tcl;
+  bool fuse01 = false;                   // layers 0 and 1 run as one fused kernel (f01)
+  F01Layer f01;
   std::vector<std::vector<float>> Wh;    // host copies of the FP32 weights (Jacobian set-up)
   struct Jac* jac = nullptr;             // Jacobian context, built at the first Jacobian call
   // one batch of Jacobian columns for df_chem_step_vjp, allocated at its first call

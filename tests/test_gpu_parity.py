@@ -488,6 +488,32 @@ def test_cta_pair_tiles_match_single_cta_tiles(df, prec, monkeypatch):
     st1.close()
 
 
+@pytest.mark.parametrize("N,batch", [(1, 256), (300, 512), (1300, 1408), (4097, 2048), (65613, 65536)])
+def test_fused_layers_match_separate_layers(df, N, batch, monkeypatch):
+    """Layers 0 and 1 of the 32-1600-800-400-30 network fused into one kernel (the layer-0
+    activations produced on chip, block by block, and consumed there by layer 1's MMAs; enabled
+    with DFGB_FUSE01=1) give the network outputs of the two layers run separately, bit for bit:
+    the same K=16 MMAs in the same order, the same bias, GELU and BF16 rounding. Row counts
+    cover a single row, a ragged row tile, several batches and a ragged last batch."""
+    mech, net, T, p, Y = synth.configs.build("layer1d-30sp-1m", n_cells=N)
+    x = onw.normalise_inputs(net, T, p, Y).astype(np.float32)
+    monkeypatch.setenv("DFGB_FUSE01", "1")
+    st = df.State(mech, net, precision=df.DF_BF16, batch_cells=batch)
+    st.profile_enable(True)
+    O_fused = host(st.mlp_forward(dev(x)))
+    fams = st.profile_read()
+    assert "layer0+1" in fams and "layer0" not in fams, fams
+    monkeypatch.setenv("DFGB_FUSE01", "0")
+    st1 = df.State(mech, net, precision=df.DF_BF16, batch_cells=batch)
+    st1.profile_enable(True)
+    O_sep = host(st1.mlp_forward(dev(x)))
+    assert "layer0" in st1.profile_read()
+    torch.cuda.synchronize()
+    assert np.array_equal(O_fused, O_sep), np.abs(O_fused - O_sep).max()
+    st.close()
+    st1.close()
+
+
 def test_autotune_is_a_no_op_for_fp32(df):
     mech, net, T, p, Y = synth.configs.build("small-fp32-4k", n_cells=64)
     st = df.State(mech, net, precision=df.DF_FP32)
