@@ -409,7 +409,17 @@ def measure_peaks_live(torch, dev):
 # Measured pipe utilisation of the EoS kernels (ncu sm__inst_executed_pipe_* / issue active, one
 # capture; summaries in profiles/), valid for the kernel source they were taken on (hash as for
 # MEASURED_TRAFFIC).
-MEASURED_PIPES = {}
+MEASURED_PIPES = {
+    # profiles/eos_kernels_layer1d-30sp-512k_bf16.md (full capture, 512K rows, first step)
+    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "eeab54a9bdb05447",
+                                        {"binding": "fma pipe and issue", "fma_pipe": 0.518,
+                                         "fp64_pipe": 0.312, "issue_active": 0.650,
+                                         "warps_per_sm": 15.1}, _EOS_OTHER),
+    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "eeab54a9bdb05447",
+                                         {"binding": "fp64 pipe", "fp64_pipe": 0.550,
+                                          "fma_pipe": 0.255, "issue_active": 0.453,
+                                          "warps_per_sm": 15.2}, _EOS_OTHER),
+}
 
 
 def measured_pipes(family, network):
