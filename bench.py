@@ -195,13 +195,13 @@ MEASURED_TRAFFIC = {
     ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e83bc91ba940bed", 4750.5),
     ("layer2", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e83bc91ba940bed", 2340.2),
     ("layer3", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e83bc91ba940bed", 1062.6),
-    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "eeab54a9bdb05447", 296.1,
+    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "c22dc9e5c97c9062", 297.6,
                                         _EOS_OTHER),
-    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "eeab54a9bdb05447", 543.3,
+    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "c22dc9e5c97c9062", 550.5,
                                          _EOS_OTHER),
     # one block Gauss-Seidel sweep (gs_rhs_kernel + gs_sweep_kernel), per cell, FP64, 512 cells
     # per block row (profiles/solver_kernels_mesh-2m.md)
-    ("gauss_seidel", "mesh-512"): ("paper_2508_18969_gb300/csrc/solver.cu", "05bcbf99e5a03a1e", 132.1),
+    ("gauss_seidel", "mesh-512"): ("paper_2508_18969_gb300/csrc/solver.cu", "bdf796170bcbf319", 128.1),
 }
 
 
@@ -411,14 +411,14 @@ def measure_peaks_live(torch, dev):
 # MEASURED_TRAFFIC).
 MEASURED_PIPES = {
     # profiles/eos_kernels_layer1d-30sp-512k_bf16.md (full capture, 512K rows, first step)
-    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "eeab54a9bdb05447",
-                                        {"binding": "fma pipe and issue", "fma_pipe": 0.518,
-                                         "fp64_pipe": 0.312, "issue_active": 0.650,
-                                         "warps_per_sm": 15.1}, _EOS_OTHER),
-    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "eeab54a9bdb05447",
-                                         {"binding": "fp64 pipe", "fp64_pipe": 0.550,
-                                          "fma_pipe": 0.255, "issue_active": 0.453,
-                                          "warps_per_sm": 15.2}, _EOS_OTHER),
+    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "c22dc9e5c97c9062",
+                                        {"binding": "issue (FP32 double-float arithmetic)",
+                                         "fma_pipe": 0.406, "alu_pipe": 0.262, "fp64_pipe": 0.071,
+                                         "issue_active": 0.626, "warps_per_sm": 15.4}, _EOS_OTHER),
+    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "c22dc9e5c97c9062",
+                                         {"binding": "issue (FP32 double-float arithmetic)",
+                                          "fma_pipe": 0.262, "alu_pipe": 0.358, "fp64_pipe": 0.012,
+                                          "issue_active": 0.629, "warps_per_sm": 18.3}, _EOS_OTHER),
 }
 
 
@@ -679,7 +679,8 @@ def roofline_families(r, pk, pk_src, live, df, steps_timed_s):
             e["fp64_equivalent"] = {
                 "flop_per_cell": per_f, "achieved_tflops": per_f * rows / avg_s / 1e12,
                 "fp64_peak_tflops": f64, "frac": (per_f * rows / avg_s / 1e12 / f64) if f64 else None,
-                "note": "the O(n^2) sums run in double-float on the FP32 pipes, so this can exceed 1"}
+                "note": "the state is evaluated in double-float on the FP32 pipes (no FP64 "
+                        "arithmetic in the hot loops), so this can exceed 1"}
             e["ncu_pipes"] = measured_pipes(fam, net_str)
             roofs[fam] = e
         else:

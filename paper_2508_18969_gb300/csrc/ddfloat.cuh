@@ -173,4 +173,72 @@ __device__ __forceinline__ void acc_fma(f2& s, f2 a, f2 b) {
 
 __device__ __forceinline__ f2 f2_fin(f2 s) { return f2_norm(s.h, s.l); }
 
+// Double-float constant from an FP64 value (hi = fl32(x), lo = fl32(x - hi)).
+__host__ __device__ constexpr f2 f2_const(double x) {
+  return f2{(float)x, (float)(x - (double)(float)x)};
+}
+
+__device__ __forceinline__ f2 f2_neg(f2 a) { return f2{-a.h, -a.l}; }
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) { return f2_add(a, f2_neg(b)); }
+__device__ __forceinline__ f2 f2_addf(f2 a, float b) {
+  float s, e;
+  two_sum(a.h, b, s, e);
+  return f2_norm(s, __fadd_rn(e, a.l));
+}
+
+// a * b + c in one pass: the product's error term and both low parts join the TwoSum error.
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  float p, e, s, t;
+  f2_prod(a, b, p, e);
+  two_sum(p, c.h, s, t);
+  return f2_norm(s, __fadd_rn(t, __fadd_rn(e, c.l)));
+}
+
+// Order of normalised pairs (|lo| <= ulp(hi) / 2): compare the high parts, then the low parts.
+__device__ __forceinline__ bool f2_gt(f2 a, f2 b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
+__device__ __forceinline__ bool f2_lt(f2 a, f2 b) { return f2_gt(b, a); }
+
+// sqrt(a) for a positive normal a: t0 = a.h r with r = rsqrt_32(a.h), then one Newton step
+// t = t0 + (a - t0^2) r / 2, the residual formed exactly (t0^2 by a product error, a.h - t0^2
+// by Sterbenz) and rounded once (relative error ~2^-46).
+__device__ __forceinline__ f2 f2_sqrt_pos(f2 a) {
+  const float r = rsqrtf(a.h);
+  const float t0 = __fmul_rn(a.h, r);
+  const float p = __fmul_rn(t0, t0);
+  const float pe = __fmaf_rn(t0, t0, -p);
+  const float res = __fadd_rn(__fsub_rn(a.h, p), __fsub_rn(a.l, pe));
+  return f2_norm(t0, __fmul_rn(res, __fmul_rn(0.5f, r)));
+}
+
+// s += a * b into an accumulator offset by a power of two sigma: h starts at sigma, and every
+// partial sum and every product are bounded by B <= sigma (terms of one sign: h stays in
+// [sigma, 2 sigma]) or by B <= sigma / 4 (terms of both signs: h stays within sigma / 4 of
+// sigma). Then s = fl(a.h b.h + h) and h lie within a factor of two of each other, so h - s
+// is exact (Sterbenz) and fma(a.h, b.h, h - s) is the rounding error of the first FMA, itself
+// rounded once (below ulp(sigma) 2^-25). l collects it with the cross terms a.h b.l + a.l b.h;
+// the sum is (h - sigma) + l, where h - sigma is exact too. Six FP32 operations per term
+// against twelve for a product error plus TwoSum.
+__device__ __forceinline__ void acc_off_fma(float& h, float& l, f2 a, f2 b) {
+  const float s = __fmaf_rn(a.h, b.h, h);
+  const float r = __fmaf_rn(a.h, b.h, __fsub_rn(h, s));
+  l = __fadd_rn(l, r);
+  l = __fmaf_rn(a.h, b.l, l);
+  l = __fmaf_rn(a.l, b.h, l);
+  h = s;
+}
+
+// Moves the part of l on h's grid into h (both steps exact: t - h by Sterbenz, the remainder
+// because it is l less its rounding onto that grid), so that l stays small and its own FP32
+// rounding stays far below ulp(h). The value (h - sigma) + l is unchanged.
+__device__ __forceinline__ void acc_renorm(float& h, float& l) {
+  const float t = __fadd_rn(h, l);
+  l = __fsub_rn(l, __fsub_rn(t, h));
+  h = t;
+}
+
+// Smallest power of two >= x for a finite x >= 0 (the smallest normal for subnormal x).
+__device__ __forceinline__ float pow2_up(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x007FFFFFu) & 0xFF800000u);
+}
+
 }  // namespace dfgb

@@ -49,6 +49,9 @@ struct EosParams {
   int n;                 // species
   int K0;                // n + 2 network inputs
   int inv_lambda;        // Box-Cox 1/lambda (integer)
+  // binomial coefficients C(m, k), k = 0..m, of m = inv_lambda when m <= 16 (exact in FP32),
+  // for (1 + eps)^m - 1 by its expansion; binom[0] = 0 marks m > 16
+  float binom[17];
   double lambda;
   double T_react;
   double newton_tol;
@@ -58,16 +61,19 @@ struct EosParams {
   const double* norm;
   // Double-float (hi, lo) tables of the mixing sums, with 1/W folded in:
   //   spcw2[k][j]: j = 0 1/W_k, 1 s_k/W_k, 2 r_k/W_k, 3 b_k/W_k, 4..9 hc_j/W_k;
-  //   Ks2[i][j] = (1 - k_ij) s_j / W_j,  Kr2[i][j] = (1 - k_ij) r_j / W_j.
+  //   K4[i][j] = (Ks hi, Ks lo, Kr hi, Kr lo) with Ks_ij = (1 - k_ij) s_j / W_j,
+  //   Kr_ij = (1 - k_ij) r_j / W_j; kcol[j] = max_i |Ks_ij|, kcol[n + j] = max_i |Kr_ij|
+  //   (rounded up by 2^-10: bounds for the pair sums' accumulator offsets).
   const float* spcw2;    // [n * kSpcStride * 2]
-  const float* Ks2;      // [n * n * 2]
-  const float* Kr2;      // [n * n * 2]
+  const float* K4;       // [n * n * 4]
+  const float* kcol;     // [2 * n]
   // FP32 pair corrections of the T-from-h solve: kfs[i][j] = k_ij s_j / W_j,
   // kfr[i][j] = k_ij r_j / W_j (k_ii = 0)
   const float* kfs;      // [n * n]
   const float* kfr;      // [n * n]
   // natural-log table: ln(c_j) for j < 128, then 1 / c_j, c_j = 1 + (j + 1/2) / 128
   const double* lntab;   // [256]
+  const float* lntab2;   // [512] the same table as double-float (hi, lo) pairs
   // Chung's mixing rules (transport properties): per species tsp[k] = (Tc, Vc [cm^3/mol],
   // omega, M [g/mol]); per pair tpair[q][i][j], q = 0 sigma_ij^3, 1 eps_ij sigma_ij^3,
   // 2 omega_ij sigma_ij^3, 3 eps_ij sigma_ij^2 M_ij^(1/2) (sigma in Angstrom, eps/k in K)
@@ -235,8 +241,8 @@ struct TcLayer {
 struct F01Layer {
   CUtensorMap tmX;       // network input, as layer 0's tmA (box {64, 128})
   CUtensorMap tmW0;      // W0 [N0 x K0], box {64, 64}
-  CUtensorMap tmW1a;     // W1 [N1 x N0], box {32, 224}, 64-byte swizzle
-  CUtensorMap tmW1b;     // W1, box {32, 192}, 64-byte swizzle
+  CUtensorMap tmW1a;     // W1 [N1 x N0], box {64, 224}
+  CUtensorMap tmW1b;     // W1, box {64, 192}
   CUtensorMap tmO;       // H1 output, as layer 1's tmO
   int N0, N1, K0;
   const float* b0;

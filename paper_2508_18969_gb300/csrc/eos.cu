@@ -33,7 +33,7 @@ constexpr double kSQ2 = 1.41421356237309504880;
 constexpr double kInvR = 1.0 / kR;
 constexpr int kThreads = 128;
 constexpr int kPreBlocks = 4;    // resident blocks per SM the register budget is sized for
-constexpr int kPostBlocks = 4;
+constexpr int kPostBlocks = 5;
 constexpr int kCellNotConverged = 1;
 constexpr int kCellNoRoot = 2;
 constexpr int kCellNonfinite = 4;
@@ -47,13 +47,28 @@ struct Mixture {
   double kb;         // 1 / (2 sqrt2 b_m)
 };
 
+// The same coefficients in double-float, for the kernels that evaluate the state in double-float.
+struct MixDF {
+  f2 inv;
+  f2 e[6];
+  f2 A0, A1, A2;
+  f2 bm;
+  f2 kb;
+};
+
+// The raw double-float sums of one composition (before the 1/W_mix scalings).
+struct MixSums {
+  f2 inv, bs, e[6], F0, F1, F2;
+};
+
 struct SharedConsts {
   const f2* spcw;      // [n * kSpcStride] double-float species constants over W
-  const f2* Ks;        // [n * n] (1 - k_ij) s_j / W_j
-  const f2* Kr;        // [n * n] (1 - k_ij) r_j / W_j
+  const float4* K4;    // [n * n] (Ks, Kr) double-float: (1 - k_ij) s_j / W_j, (1 - k_ij) r_j / W_j
+  const float* kcol;   // [2 n] max_i |Ks_ij|, then max_i |Kr_ij| (rounded up)
   const float* kfs;    // [n * n] k_ij s_j / W_j (FP32; the T-from-h layout only)
   const float* kfr;    // [n * n] k_ij r_j / W_j
-  const double* lnt;   // [256] log table (ln c_j, then 1 / c_j)
+  const double* lnt;   // [256] log table (ln c_j, then 1 / c_j); FP64 kernels only
+  const f2* lt2;       // the same table in double-float, in the same words; DF kernels only
   const double* norm;  // [2 K0 + 2 n]
   const float* normf;  // the same in FP32 (for the FP32 feature and increment arithmetic)
 };
@@ -61,35 +76,47 @@ struct SharedConsts {
 // 8-byte words of shared memory the constants take: FP64 normalisation, then the
 // double-float tables (one f2 per word), then the FP32 normalisation.
 __host__ __device__ inline int consts_words(const EosParams& P) {
-  return 256 + 2 * P.K0 + 2 * P.n + P.n * kSpcStride + 2 * P.n * P.n + (P.K0 + P.n + 1);
+  return 256 + 2 * P.K0 + 2 * P.n + P.n * kSpcStride + 2 * P.n * P.n + P.n + (P.K0 + P.n + 1);
 }
 
+// DF: the first 256 words hold the double-float log table (the kernels that evaluate the state
+// in double-float) instead of the FP64 one.
+template <bool DF = false>
 __device__ SharedConsts load_consts(const EosParams& P, double* sm0) {
   const int nspc = P.n * kSpcStride, nk = P.n * P.n, nn = 2 * P.K0 + 2 * P.n;
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) sm0[i] = P.lntab[i];
+  if (DF) {
+    float* t = reinterpret_cast<float*>(sm0);
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) t[i] = P.lntab2[i];
+  } else {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) sm0[i] = P.lntab[i];
+  }
   double* sm = sm0 + 256;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) sm[i] = P.norm[i];
+  // fs is 16-byte aligned (256 + nn doubles; nn is even) and so is the pair table after
+  // the 8 n kSpcStride bytes of the species table
   float* fs = reinterpret_cast<float*>(sm + nn);
   for (int i = threadIdx.x; i < 2 * nspc; i += blockDim.x) fs[i] = P.spcw2[i];
-  for (int i = threadIdx.x; i < 2 * nk; i += blockDim.x) fs[2 * nspc + i] = P.Ks2[i];
-  for (int i = threadIdx.x; i < 2 * nk; i += blockDim.x) fs[2 * nspc + 2 * nk + i] = P.Kr2[i];
-  float* nf = fs + 2 * nspc + 4 * nk;
+  for (int i = threadIdx.x; i < 4 * nk; i += blockDim.x) fs[2 * nspc + i] = P.K4[i];
+  for (int i = threadIdx.x; i < 2 * P.n; i += blockDim.x) fs[2 * nspc + 4 * nk + i] = P.kcol[i];
+  float* nf = fs + 2 * nspc + 4 * nk + 2 * P.n;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) nf[i] = (float)P.norm[i];
   __syncthreads();
-  return SharedConsts{reinterpret_cast<const f2*>(fs), reinterpret_cast<const f2*>(fs + 2 * nspc),
-                      reinterpret_cast<const f2*>(fs + 2 * nspc + 2 * nk), nullptr, nullptr, sm0,
-                      sm, nf};
+  return SharedConsts{reinterpret_cast<const f2*>(fs),
+                      reinterpret_cast<const float4*>(fs + 2 * nspc), fs + 2 * nspc + 4 * nk,
+                      nullptr, nullptr, DF ? nullptr : sm0,
+                      DF ? reinterpret_cast<const f2*>(sm0) : nullptr, sm, nf};
 }
 
-// The layout of the T-from-h kernel: FP64 normalisation, double-float species table, the two
-// FP32 k_ij tables, FP32 normalisation (no double-float pair tables).
+// The layout of the T-from-h kernel: double-float log table, FP64 normalisation, double-float
+// species table, the two FP32 k_ij tables, FP32 normalisation (no double-float pair tables).
 __host__ __device__ inline int consts_words_post(const EosParams& P) {
   return 256 + 2 * P.K0 + 2 * P.n + P.n * kSpcStride + P.n * P.n + (P.K0 + P.n + 1);
 }
 
 __device__ SharedConsts load_consts_post(const EosParams& P, double* sm0) {
   const int nspc = P.n * kSpcStride, nk = P.n * P.n, nn = 2 * P.K0 + 2 * P.n;
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) sm0[i] = P.lntab[i];
+  float* t = reinterpret_cast<float*>(sm0);
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) t[i] = P.lntab2[i];
   double* sm = sm0 + 256;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) sm[i] = P.norm[i];
   float* fs = reinterpret_cast<float*>(sm + nn);
@@ -100,7 +127,8 @@ __device__ SharedConsts load_consts_post(const EosParams& P, double* sm0) {
   float* nf = ks + 2 * nk;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) nf[i] = (float)P.norm[i];
   __syncthreads();
-  return SharedConsts{reinterpret_cast<const f2*>(fs), nullptr, nullptr, ks, ks + nk, sm0, sm, nf};
+  return SharedConsts{reinterpret_cast<const f2*>(fs), nullptr, nullptr, ks, ks + nk, nullptr,
+                      reinterpret_cast<const f2*>(sm0), sm, nf};
 }
 
 // FP64 reciprocal: FP32 seed, two FP64 Newton steps (relative error ~1 ulp).
@@ -118,51 +146,156 @@ __device__ __forceinline__ double drcp(double x) {
 //   F0 = sum_ij K_ij ys_i ys_j = sum_i ys_i (ys_i + 2 P_i),  P_i = sum_{j>i} Ks_ij Y_j,
 //   F1 = sum_ij K_ij ys_i yr_j = sum_i ys_i (yr_i + Q_i) + yr_i P_i,  Q_i = sum_{j>i} Kr_ij Y_j,
 //   F2 = sum_ij K_ij yr_i yr_j = sum_i yr_i (yr_i + 2 Q_i).
-__device__ void mixture(const f2* ycol, int n, const SharedConsts& c, Mixture& m) {
+// The O(n^2) sums P_i and Q_i use offset accumulators (acc_off_fma): B_i = sum_{j>i} |Y_j|
+// max_l |Ks_lj| bounds every partial sum of P_i (likewise for Q_i), and the offset of row i is
+// the power of two above B_i, or above 4 B_i when some Y_j is negative. B_i is the total (summed
+// rounding up) less the leading terms (rounded down, each subtraction rounded up), so it never
+// falls below the exact suffix bound.
+__device__ void mixture_sums(const f2* ycol, int n, const SharedConsts& c, MixSums& ms) {
   const int stride = blockDim.x;
-  f2 inv = {0.f, 0.f}, bs = {0.f, 0.f};
-  f2 e0 = {0.f, 0.f}, e1 = e0, e2 = e0, e3 = e0, e4 = e0, e5 = e0;
-  f2 F0 = {0.f, 0.f}, F1 = F0, F2 = F0;
+  // The O(n) sums (1/W, b/W and the six enthalpy coefficients, species-table columns 0 and 3..9)
+  // take offset accumulators too, with bounds Bq = sum_j |Y_j| |q_j| from the same pass.
+  float Bs = 0.f, Br = 0.f, Bq[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) Bq[k] = 0.f;
+  unsigned neg = 0u;
+#pragma unroll 2
+  for (int j = 0; j < n; ++j) {
+    const float yh = ycol[j * stride].h, y = fabsf(yh);
+    neg |= __float_as_uint(yh);
+    const float4* q4 = reinterpret_cast<const float4*>(c.spcw + j * kSpcStride);
+    const float4 a = q4[0], b = q4[1], d = q4[2], e = q4[3], g = q4[4];
+    Bs = __fmaf_ru(y, c.kcol[j], Bs);
+    Br = __fmaf_ru(y, c.kcol[n + j], Br);
+    Bq[0] = __fmaf_ru(y, fabsf(a.x), Bq[0]);
+    Bq[1] = __fmaf_ru(y, fabsf(b.z), Bq[1]);
+    Bq[2] = __fmaf_ru(y, fabsf(d.x), Bq[2]);
+    Bq[3] = __fmaf_ru(y, fabsf(d.z), Bq[3]);
+    Bq[4] = __fmaf_ru(y, fabsf(e.x), Bq[4]);
+    Bq[5] = __fmaf_ru(y, fabsf(e.z), Bq[5]);
+    Bq[6] = __fmaf_ru(y, fabsf(g.x), Bq[6]);
+    Bq[7] = __fmaf_ru(y, fabsf(g.z), Bq[7]);
+  }
+  // the bounds are rounded up throughout; |Y_j| <= |hi| (1 + 2^-23) is inside kcol's margin,
+  // and the 2^-10 margin of the O(n) offsets covers the low parts of Y and of the table. The
+  // terms are non-negative for Y >= 0 except in the enthalpy columns, whose coefficients have
+  // either sign: those take the offset for terms of both signs.
+  const float sgf = (neg >> 31) ? 4.0f : 1.0f;
+  float sq[8], hq[8], lq[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    sq[k] = pow2_up(__fmul_ru((k < 2 ? sgf : 4.0f) * Bq[k], 1.0009765625f));
+    hq[k] = sq[k];
+    lq[k] = 0.f;
+  }
+  // The forms themselves: F0 += ys_i ys_i + ys_i (2 P_i), F1 += ys_i yr_i + ys_i Q_i + yr_i P_i,
+  // F2 += yr_i yr_i + yr_i (2 Q_i), each into an offset accumulator. The absolute values of the
+  // terms of F0 sum to sum_ij |K_ij| |ys_i| |ys_j| <= S_s Bs <= Bs^2, since S_s = sum_i |ys_i|
+  // <= Bs (K_jj = 1) and sum_j |K_ij| |ys_j| <= Bs for every i; likewise Bs Br bounds F1 and
+  // Br^2 bounds F2.
+  const float sF0 = pow2_up(__fmul_ru(sgf, __fmul_ru(Bs, Bs)));
+  const float sF1 = pow2_up(__fmul_ru(sgf, __fmul_ru(Bs, Br)));
+  const float sF2 = pow2_up(__fmul_ru(sgf, __fmul_ru(Br, Br)));
+  float F0h = sF0, F0l = 0.f, F1h = sF1, F1l = 0.f, F2h = sF2, F2l = 0.f;
 #pragma unroll 1
   for (int i = 0; i < n; ++i) {
-    const f2* q = c.spcw + i * kSpcStride;
+    const float4* q4 = reinterpret_cast<const float4*>(c.spcw + i * kSpcStride);
+    const float4 a = q4[0], b = q4[1], d = q4[2], e = q4[3], g = q4[4];
     const f2 y = ycol[i * stride];
-    acc_fma(inv, y, q[0]);
-    acc_fma(bs, y, q[3]);
-    acc_fma(e0, y, q[4]);
-    acc_fma(e1, y, q[5]);
-    acc_fma(e2, y, q[6]);
-    acc_fma(e3, y, q[7]);
-    acc_fma(e4, y, q[8]);
-    acc_fma(e5, y, q[9]);
-    f2 Pi = {0.f, 0.f}, Qi = {0.f, 0.f};
-    const f2* Ksr = c.Ks + i * n;
-    const f2* Krr = c.Kr + i * n;
+    acc_off_fma(hq[0], lq[0], y, f2{a.x, a.y});
+    acc_off_fma(hq[1], lq[1], y, f2{b.z, b.w});
+    acc_off_fma(hq[2], lq[2], y, f2{d.x, d.y});
+    acc_off_fma(hq[3], lq[3], y, f2{d.z, d.w});
+    acc_off_fma(hq[4], lq[4], y, f2{e.x, e.y});
+    acc_off_fma(hq[5], lq[5], y, f2{e.z, e.w});
+    acc_off_fma(hq[6], lq[6], y, f2{g.x, g.y});
+    acc_off_fma(hq[7], lq[7], y, f2{g.z, g.w});
+    Bs = __fsub_ru(Bs, __fmul_rd(fabsf(y.h), c.kcol[i]));
+    Br = __fsub_ru(Br, __fmul_rd(fabsf(y.h), c.kcol[n + i]));
+    const float sgs = pow2_up(sgf * Bs), sgr = pow2_up(sgf * Br);
+    float ph = sgs, pl = 0.f, qh = sgr, ql = 0.f;
+    const float4* Kr4 = c.K4 + i * n;
 #pragma unroll 4
     for (int j = i + 1; j < n; ++j) {
       const f2 yj = ycol[j * stride];
-      acc_fma(Pi, Ksr[j], yj);
-      acc_fma(Qi, Krr[j], yj);
+      const float4 k = Kr4[j];
+      acc_off_fma(ph, pl, f2{k.x, k.y}, yj);
+      acc_off_fma(qh, ql, f2{k.z, k.w}, yj);
     }
-    Pi = f2_fin(Pi);
-    Qi = f2_fin(Qi);
-    const f2 ysi = f2_mul(y, q[1]), yri = f2_mul(y, q[2]);
-    acc_fma(F0, ysi, f2_add(ysi, f2_scale2(Pi)));
-    acc_fma(F1, ysi, f2_add(yri, Qi));
-    acc_fma(F1, yri, Pi);
-    acc_fma(F2, yri, f2_add(yri, f2_scale2(Qi)));
+    const f2 Pi = f2_norm(__fsub_rn(ph, sgs), pl);
+    const f2 Qi = f2_norm(__fsub_rn(qh, sgr), ql);
+    const f2 ysi = f2_mul(y, f2{a.z, a.w}), yri = f2_mul(y, f2{b.x, b.y});
+    acc_off_fma(F0h, F0l, ysi, ysi);
+    acc_off_fma(F0h, F0l, ysi, f2_scale2(Pi));
+    acc_off_fma(F1h, F1l, ysi, yri);
+    acc_off_fma(F1h, F1l, ysi, Qi);
+    acc_off_fma(F1h, F1l, yri, Pi);
+    acc_off_fma(F2h, F2l, yri, yri);
+    acc_off_fma(F2h, F2l, yri, f2_scale2(Qi));
+    if ((i & 3) == 3) {  // every fourth species: keep the low parts small
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc_renorm(hq[k], lq[k]);
+      acc_renorm(F0h, F0l);
+      acc_renorm(F1h, F1l);
+      acc_renorm(F2h, F2l);
+    }
   }
-  const double invd = f2_to(f2_fin(inv));
+  const f2 F0 = f2_norm(__fsub_rn(F0h, sF0), F0l);
+  const f2 F1 = f2_norm(__fsub_rn(F1h, sF1), F1l);
+  const f2 F2 = f2_norm(__fsub_rn(F2h, sF2), F2l);
+  ms.inv = f2_norm(__fsub_rn(hq[0], sq[0]), lq[0]);
+  ms.bs = f2_norm(__fsub_rn(hq[1], sq[1]), lq[1]);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) ms.e[k] = f2_norm(__fsub_rn(hq[k + 2], sq[k + 2]), lq[k + 2]);
+  ms.F0 = F0;
+  ms.F1 = F1;
+  ms.F2 = F2;
+}
+
+__device__ void mixture(const f2* ycol, int n, const SharedConsts& c, Mixture& m) {
+  MixSums s;
+  mixture_sums(ycol, n, c, s);
+  const double invd = f2_to(s.inv);
   const double Wm = drcp(invd);
   const double W2 = Wm * Wm;
   m.inv = invd;
-  m.e[0] = f2_to(f2_fin(e0)); m.e[1] = f2_to(f2_fin(e1)); m.e[2] = f2_to(f2_fin(e2));
-  m.e[3] = f2_to(f2_fin(e3)); m.e[4] = f2_to(f2_fin(e4)); m.e[5] = f2_to(f2_fin(e5));
-  m.A0 = W2 * f2_to(f2_fin(F0));
-  m.A1 = W2 * f2_to(f2_fin(F1));
-  m.A2 = W2 * f2_to(f2_fin(F2));
-  m.bm = Wm * f2_to(f2_fin(bs));
+#pragma unroll
+  for (int k = 0; k < 6; ++k) m.e[k] = f2_to(s.e[k]);
+  m.A0 = W2 * f2_to(s.F0);
+  m.A1 = W2 * f2_to(s.F1);
+  m.A2 = W2 * f2_to(s.F2);
+  m.bm = Wm * f2_to(s.bs);
   m.kb = drcp(2.0 * kSQ2 * m.bm);
+}
+
+// Double-float constants (hi, lo) of the state evaluation.
+constexpr float kRh = (float)kR, kRl = (float)(kR - (double)(float)kR);
+constexpr float kIRh = (float)(1.0 / kR), kIRl = (float)(1.0 / kR - (double)(float)(1.0 / kR));
+constexpr float kS2h = (float)(2.0 * kSQ2), kS2l = (float)(2.0 * kSQ2 - (double)(float)(2.0 * kSQ2));
+constexpr float kSPh = (float)(1.0 + kSQ2), kSPl = (float)(1.0 + kSQ2 - (double)(float)(1.0 + kSQ2));
+constexpr float kSMh = (float)(1.0 - kSQ2), kSMl = (float)(1.0 - kSQ2 - (double)(float)(1.0 - kSQ2));
+constexpr float k3h = (float)(1.0 / 3.0), k3l = (float)(1.0 / 3.0 - (double)(float)(1.0 / 3.0));
+constexpr float kL2h = (float)0.69314718055994530942,
+                kL2l = (float)(0.69314718055994530942 - (double)(float)0.69314718055994530942);
+
+// W_mix scalings of the sums, in double-float.
+__device__ __forceinline__ void mix_df_final(const MixSums& s, MixDF& m) {
+  const f2 Wm = f2_rcp(s.inv);
+  const f2 W2 = f2_mul(Wm, Wm);
+  m.inv = s.inv;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) m.e[k] = s.e[k];
+  m.A0 = f2_mul(W2, s.F0);
+  m.A1 = f2_mul(W2, s.F1);
+  m.A2 = f2_mul(W2, s.F2);
+  m.bm = f2_mul(Wm, s.bs);
+  m.kb = f2_rcp(f2_mul(m.bm, f2{kS2h, kS2l}));
+}
+
+__device__ void mixture_df(const f2* ycol, int n, const SharedConsts& c, MixDF& m) {
+  MixSums s;
+  mixture_sums(ycol, n, c, s);
+  mix_df_final(s, m);
 }
 
 // ln(x) for a positive normal x from the shared table: x = 2^e m, m in [1, 2); with c the
@@ -201,25 +334,48 @@ __device__ __forceinline__ double dsqrt_pos(double x) {
 // corrections (k <= 0.1 of the squares) summed in FP32,
 //   F0 = S_s^2 - 2 sum_i ys_i Pk_i,  F1 = S_s S_r - sum_i (ys_i Qk_i + yr_i Pk_i),
 //   F2 = S_r^2 - 2 sum_i yr_i Qk_i,  Pk_i = sum_{j>i} k_ij ys_j,  Qk_i = sum_{j>i} k_ij yr_j.
-__device__ void mixture_post(const f2* ycol, int n, const SharedConsts& c, Mixture& m) {
+__device__ void mixture_post(const f2* ycol, int n, const SharedConsts& c, MixDF& m) {
   const int stride = blockDim.x;
-  f2 inv = {0.f, 0.f}, bs = {0.f, 0.f}, Ss = {0.f, 0.f}, Sr = {0.f, 0.f};
-  f2 e0 = {0.f, 0.f}, e1 = e0, e2 = e0, e3 = e0, e4 = e0, e5 = e0;
+  // the ten O(n) sums over the species table take offset accumulators, as in mixture()
+  float Bq[kSpcStride];
+#pragma unroll
+  for (int k = 0; k < kSpcStride; ++k) Bq[k] = 0.f;
+  unsigned neg = 0u;
+#pragma unroll 2
+  for (int j = 0; j < n; ++j) {
+    const float yh = ycol[j * stride].h, y = fabsf(yh);
+    neg |= __float_as_uint(yh);
+    const float4* q4 = reinterpret_cast<const float4*>(c.spcw + j * kSpcStride);
+#pragma unroll
+    for (int k = 0; k < kSpcStride / 2; ++k) {
+      const float4 a = q4[k];
+      Bq[2 * k] = __fmaf_ru(y, fabsf(a.x), Bq[2 * k]);
+      Bq[2 * k + 1] = __fmaf_ru(y, fabsf(a.z), Bq[2 * k + 1]);
+    }
+  }
+  // columns 0..3 (1/W, s/W, r/W, b/W) are non-negative; the enthalpy columns have either sign
+  const float sgf = (neg >> 31) ? 4.0f : 1.0f;
+  float sq[kSpcStride], hq[kSpcStride], lq[kSpcStride];
+#pragma unroll
+  for (int k = 0; k < kSpcStride; ++k) {
+    sq[k] = pow2_up(__fmul_ru((k < 4 ? sgf : 4.0f) * Bq[k], 1.0009765625f));
+    hq[k] = sq[k];
+    lq[k] = 0.f;
+  }
   float C0 = 0.f, C1 = 0.f, C2 = 0.f;
 #pragma unroll 1
   for (int i = 0; i < n; ++i) {
-    const f2* q = c.spcw + i * kSpcStride;
+    const float4* q4 = reinterpret_cast<const float4*>(c.spcw + i * kSpcStride);
     const f2 y = ycol[i * stride];
-    acc_fma(inv, y, q[0]);
-    acc_fma(Ss, y, q[1]);
-    acc_fma(Sr, y, q[2]);
-    acc_fma(bs, y, q[3]);
-    acc_fma(e0, y, q[4]);
-    acc_fma(e1, y, q[5]);
-    acc_fma(e2, y, q[6]);
-    acc_fma(e3, y, q[7]);
-    acc_fma(e4, y, q[8]);
-    acc_fma(e5, y, q[9]);
+    float q1h = 0.f, q2h = 0.f;
+#pragma unroll
+    for (int k = 0; k < kSpcStride / 2; ++k) {
+      const float4 a = q4[k];
+      acc_off_fma(hq[2 * k], lq[2 * k], y, f2{a.x, a.y});
+      acc_off_fma(hq[2 * k + 1], lq[2 * k + 1], y, f2{a.z, a.w});
+      if (k == 0) q1h = a.z;
+      if (k == 1) q2h = a.x;
+    }
     float Pk = 0.f, Qk = 0.f;
     const float* ksr = c.kfs + i * n;
     const float* krr = c.kfr + i * n;
@@ -229,24 +385,29 @@ __device__ void mixture_post(const f2* ycol, int n, const SharedConsts& c, Mixtu
       Pk = fmaf(ksr[j], yj, Pk);
       Qk = fmaf(krr[j], yj, Qk);
     }
-    const float ysi = y.h * q[1].h, yri = y.h * q[2].h;
+    if ((i & 3) == 3) {  // every fourth species: keep the low parts small
+#pragma unroll
+      for (int k = 0; k < kSpcStride; ++k) acc_renorm(hq[k], lq[k]);
+    }
+    const float ysi = y.h * q1h, yri = y.h * q2h;
     C0 = fmaf(ysi, Pk, C0);
     C1 = fmaf(ysi, Qk, fmaf(yri, Pk, C1));
     C2 = fmaf(yri, Qk, C2);
   }
-  Ss = f2_fin(Ss);
-  Sr = f2_fin(Sr);
-  const double invd = f2_to(f2_fin(inv));
-  const double Wm = drcp(invd);
-  const double W2 = Wm * Wm;
-  m.inv = invd;
-  m.e[0] = f2_to(f2_fin(e0)); m.e[1] = f2_to(f2_fin(e1)); m.e[2] = f2_to(f2_fin(e2));
-  m.e[3] = f2_to(f2_fin(e3)); m.e[4] = f2_to(f2_fin(e4)); m.e[5] = f2_to(f2_fin(e5));
-  m.A0 = W2 * f2_to(f2_add(f2_mul(Ss, Ss), f2{-2.0f * C0, 0.f}));
-  m.A1 = W2 * f2_to(f2_add(f2_mul(Ss, Sr), f2{-C1, 0.f}));
-  m.A2 = W2 * f2_to(f2_add(f2_mul(Sr, Sr), f2{-2.0f * C2, 0.f}));
-  m.bm = Wm * f2_to(f2_fin(bs));
-  m.kb = drcp(2.0 * kSQ2 * m.bm);
+  f2 r[kSpcStride];
+#pragma unroll
+  for (int k = 0; k < kSpcStride; ++k) r[k] = f2_norm(__fsub_rn(hq[k], sq[k]), lq[k]);
+  const f2 inv = r[0], Ss = r[1], Sr = r[2], bs = r[3];
+  const f2 Wm = f2_rcp(inv);
+  const f2 W2 = f2_mul(Wm, Wm);
+  m.inv = inv;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) m.e[k] = r[4 + k];
+  m.A0 = f2_mul(W2, f2_addf(f2_mul(Ss, Ss), -2.0f * C0));
+  m.A1 = f2_mul(W2, f2_addf(f2_mul(Ss, Sr), -C1));
+  m.A2 = f2_mul(W2, f2_addf(f2_mul(Sr, Sr), -2.0f * C2));
+  m.bm = f2_mul(Wm, bs);
+  m.kb = f2_rcp(f2_mul(m.bm, f2{kS2h, kS2l}));
 }
 
 __device__ __forceinline__ double h_ig(const Mixture& m, double T) {
@@ -282,6 +443,12 @@ __device__ __forceinline__ double g_dep(double Z, double A, double B, const doub
 // Seeds come from the FP32 closed form (Cardano for one real root, the trigonometric form
 // for three), each polished by FP64 Newton steps on the cubic: two, or with FAST one, plus a
 // second where the first moved the seed by more than 1e-6 relative (a poor seed).
+// The three-real-root case of select_Z: seeds from the trigonometric form, each polished, the
+// root above B with least departure Gibbs energy kept. Out of line: it is the rarer branch,
+// and keeping it out of the Newton loop's body keeps that loop's code small.
+__device__ __noinline__ double select_Z3(double A, double B, double c2, double c1, double c0,
+                                         double P, double Q, const double* lnt, int& status);
+
 template <bool FAST>
 __device__ double select_Z(double A, double B, const double* lnt, int& status) {
   const double c2 = B - 1.0;
@@ -302,6 +469,11 @@ __device__ double select_Z(double A, double B, const double* lnt, int& status) {
     if (!(Z > B)) status |= kCellNoRoot;
     return Z;
   }
+  return select_Z3(A, B, c2, c1, c0, P, Q, lnt, status);
+}
+
+__device__ __noinline__ double select_Z3(double A, double B, double c2, double c1, double c0,
+                                         double P, double Q, const double* lnt, int& status) {
   const float pf = d_to_f_trunc(P);
   const float m = (pf < 0.0f) ? 2.0f * sqrtf(-pf / 3.0f) : 0.0f;
   float cphi = (pf < 0.0f) ? (3.0f * d_to_f_trunc(Q) / (2.0f * pf)) * sqrtf(-3.0f / pf) : 0.0f;
@@ -434,6 +606,213 @@ __device__ double solve_T(const Mixture& m, double pc, double h0c, double Told, 
   return Tn;
 }
 
+// ---------------------------------------------------------------- double-float state
+// The real-fluid point of eos_pre and every Newton iteration of eos_post in double-float on
+// the FP32 pipes (~2^-46 relative per operation). On this GPU one FP64 instruction costs the
+// issue time of ~30 FP32 instructions (measured in the T-from-h kernel), and a double-float
+// operation takes 4 to 15. The steps are those of pr_point / solve_T above.
+
+// ln x for a positive normal double-float x from the double-float table lt (ln c_j, then
+// 1 / c_j): x = 2^e m, m in [1, 2); r = m / c_j - 1 (|r| < 2^-8) formed exactly to first order;
+// ln(1 + r) = r - r^2/2 in double-float plus r^3 (1/3 - r/4 + r^2/5) in FP32 (below 2^-25).
+__device__ __noinline__ f2 f2_log_slow(f2 x) { return f2_from(log(f2_to(x))); }
+
+__device__ __forceinline__ f2 f2_log_tab(f2 x, const f2* lt) {
+  const unsigned u = __float_as_uint(x.h);
+  const int be = (int)((u >> 23) & 0xFFu);
+  if ((int)u <= 0 || be == 0 || be >= 254) return f2_log_slow(x);
+  const int j = (int)((u >> 16) & 127u);
+  const float sc = __uint_as_float((unsigned)(254 - be) << 23);   // 2^-(be - 127), exact
+  const float mh = __fmul_rn(x.h, sc), ml = __fmul_rn(x.l, sc);
+  const f2 ic = lt[128 + j];
+  const float p = __fmul_rn(mh, ic.h);
+  const float pe = __fmaf_rn(mh, ic.h, -p);
+  const f2 r = f2_norm(__fsub_rn(p, 1.0f), __fmaf_rn(mh, ic.l, __fmaf_rn(ml, ic.h, pe)));
+  const float r2 = __fmul_rn(r.h, r.h);
+  const float r2e = __fmaf_rn(2.0f * r.h, r.l, __fmaf_rn(r.h, r.h, -r2));
+  const float tail =
+      __fmul_rn(__fmul_rn(r2, r.h), __fmaf_rn(r.h, __fmaf_rn(r.h, 0.2f, -0.25f), 0.33333334f));
+  const f2 l1p = f2_addf(f2_add(r, f2{-0.5f * r2, -0.5f * r2e}), tail);
+  const float E = (float)(be - 127);
+  const float q = __fmul_rn(E, kL2h);
+  const f2 el2 = f2_norm(q, __fmaf_rn(E, kL2l, __fmaf_rn(E, kL2h, -q)));
+  return f2_add(f2_add(el2, lt[j]), l1p);
+}
+
+// One Newton step on the cubic, f(Z) and f'(Z) in double-float, the step with an FP32
+// reciprocal of f'(Z) (it scales the correction by 1 + O(1e-7)).
+__device__ __forceinline__ f2 cubic_step_df(f2 Z, f2 c2, f2 c1, f2 c0) {
+  const f2 f = f2_fma(f2_fma(f2_add(Z, c2), Z, c1), Z, c0);
+  const f2 fp = f2_fma(f2_add(f2_mulf(Z, 3.0f), f2_scale2(c2)), Z, c1);
+  return fp.h != 0.0f ? f2_add(Z, f2_mulf(f, -__frcp_rn(fp.h))) : Z;
+}
+
+__device__ __forceinline__ f2 g_dep_df(f2 Z, f2 A, f2 B, const f2* lt) {
+  const f2 Zp = f2_fma(B, f2{kSPh, kSPl}, Z), Zm = f2_fma(B, f2{kSMh, kSMl}, Z);
+  const f2 L = f2_log_tab(f2_mul(Zp, f2_rcp(Zm)), lt);
+  const f2 a = f2_mul(A, f2_rcp(f2_mul(B, f2{kS2h, kS2l})));
+  return f2_sub(f2_sub(f2_addf(Z, -1.0f), f2_log_tab(f2_sub(Z, B), lt)), f2_mul(a, L));
+}
+
+// Three real roots (select_Z3 in double-float). Out of line, as there.
+__device__ __noinline__ f2 select_Z3_df(f2 A, f2 B, f2 c2, f2 c1, f2 c0, f2 c23, float Pf,
+                                        float Qf, const f2* lt, int& status) {
+  const float m = (Pf < 0.0f) ? 2.0f * sqrtf(-Pf / 3.0f) : 0.0f;
+  float cphi = (Pf < 0.0f) ? (3.0f * Qf / (2.0f * Pf)) * sqrtf(-3.0f / Pf) : 0.0f;
+  cphi = fminf(fmaxf(cphi, -1.0f), 1.0f);
+  const float phi = acosf(cphi) * (1.0f / 3.0f);
+  f2 best = f2{__int_as_float(0x7fc00000), 0.0f};
+  f2 gbest = f2{__int_as_float(0x7f800000), 0.0f};
+  bool have = false;
+#pragma unroll 1
+  for (int k = 0; k < 3; ++k) {  // k = 0, 1, 2 give descending seeds
+    const float tk = m * cosf(phi - 2.0943951023931955f * (float)k);
+    f2 Z = f2_sub(f2{tk, 0.0f}, c23);
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) Z = cubic_step_df(Z, c2, c1, c0);
+    if (f2_gt(Z, B)) {
+      const f2 g = g_dep_df(Z, A, B, lt);
+      if (!have || f2_lt(g, f2_addf(gbest, -1e-12f))) {
+        gbest = g;
+        best = Z;
+        have = true;
+      }
+    }
+  }
+  if (!have) status |= kCellNoRoot;
+  return best;
+}
+
+// select_Z in double-float: the coefficients, P, Q and the discriminant in double-float, the
+// seeds in FP32, one or two double-float Newton polishes as in select_Z.
+template <bool FAST>
+__device__ __forceinline__ f2 select_Z_df(f2 A, f2 B, const f2* lt, int& status) {
+  const f2 c2 = f2_addf(B, -1.0f);
+  const f2 c1 = f2_sub(A, f2_mul(B, f2_addf(f2_mulf(B, 3.0f), 2.0f)));  // A - 3B^2 - 2B
+  const f2 c0 = f2_mul(B, f2_sub(f2_fma(B, B, B), A));                 // B^2 + B^3 - AB
+  const f2 c23 = f2_mul(c2, f2{k3h, k3l});                              // c2 / 3
+  const f2 P = f2_sub(c1, f2_mul(c2, c23));                             // c1 - c2^2 / 3
+  // Q = 2 c2^3 / 27 - c2 c1 / 3 + c0 = 2 (c2/3)^3 - (c2/3) c1 + c0
+  const f2 Q = f2_add(f2_sub(f2_scale2(f2_mul(c23, f2_mul(c23, c23))), f2_mul(c23, c1)), c0);
+  const f2 P3 = f2_mul(P, f2{k3h, k3l});
+  const f2 Qh = f2{0.5f * Q.h, 0.5f * Q.l};
+  const f2 disc = f2_fma(Qh, Qh, f2_mul(P3, f2_mul(P3, P3)));          // Q^2/4 + P^3/27
+  if (disc.h > 0.0f) {
+    const float qf = Q.h, pf = P.h;
+    const float sq = sqrtf(disc.h);
+    const float u = cbrtf(-0.5f * qf - copysignf(sq, qf));
+    const float t = (u != 0.0f) ? u - pf / (3.0f * u) : 0.0f;
+    const f2 Z0 = f2_sub(f2{t, 0.0f}, c23);
+    f2 Z = cubic_step_df(Z0, c2, c1, c0);
+    if (!FAST || fabsf(Z.h - Z0.h) > 1e-6f * fabsf(Z.h)) Z = cubic_step_df(Z, c2, c1, c0);
+    if (!f2_gt(Z, B)) status |= kCellNoRoot;
+    return Z;
+  }
+  return select_Z3_df(A, B, c2, c1, c0, c23, P.h, Q.h, lt, status);
+}
+
+struct PRPointDF {
+  f2 Z, h_dep;    // compressibility, molar departure enthalpy
+  float cp_dep;   // its T-derivative in FP32 (FAST with want_cp only)
+};
+
+// pr_point in double-float; with FAST the departure cp (the chord slope of the T-from-h
+// solve) in FP32 as there.
+template <bool FAST>
+__device__ PRPointDF pr_point_df(const MixDF& m, f2 T, f2 p, bool want_cp, const f2* lt,
+                                 int& status) {
+  const f2 iT = f2_rcp(T);
+  const f2 t = f2_sqrt_pos(T);
+  const f2 it = f2_mul(t, iT);                                   // 1 / sqrt(T)
+  const f2 am = f2_fma(m.A1, f2{-2.0f * t.h, -2.0f * t.l}, f2_fma(m.A2, T, m.A0));
+  const f2 dam = f2_fma(f2_neg(m.A1), it, m.A2);
+  const f2 RT = f2_mul(T, f2{kRh, kRl});
+  const f2 iRT = f2_mul(iT, f2{kIRh, kIRl});
+  const f2 piRT = f2_mul(p, iRT);
+  const f2 A = f2_mul(f2_mul(am, piRT), iRT);
+  const f2 B = f2_mul(m.bm, piRT);
+  PRPointDF r;
+  r.Z = select_Z_df<FAST>(A, B, lt, status);
+  const f2 Zp = f2_fma(B, f2{kSPh, kSPl}, r.Z), Zm = f2_fma(B, f2{kSMh, kSMl}, r.Z);
+  const f2 L = f2_log_tab(f2_mul(Zp, f2_rcp(Zm)), lt);
+  const f2 tdam_am = f2_fma(T, dam, f2_neg(am));
+  r.h_dep = f2_fma(RT, f2_addf(r.Z, -1.0f), f2_mul(f2_mul(tdam_am, m.kb), L));
+  r.cp_dep = 0.0f;
+  if (FAST && want_cp) {
+    // FP32: dA/dT = p (dam - 2 am / T) / (RT)^2 needs no division by am
+    const float Tf = T.h, iTf = __frcp_rn(Tf), itf = rsqrtf(Tf);
+    const float Z = r.Z.h, Af = A.h, Bf = B.h;
+    const float pf = p.h, iRTf = iTf * (float)kInvR;
+    const float d2am = 0.5f * m.A1.h * itf * iTf;
+    const float dB = -Bf * iTf;
+    const float dA = pf * iRTf * iRTf * (dam.h - 2.0f * am.h * iTf);
+    const float FZ = fmaf(3.0f * Z, Z, -2.0f * (1.0f - Bf) * Z) + (Af - 3.0f * Bf * Bf - 2.0f * Bf);
+    const float FA = Z - Bf;
+    const float FB = Z * Z - (6.0f * Bf + 2.0f) * Z - (Af - 2.0f * Bf - 3.0f * Bf * Bf);
+    const float dZ = -(FA * dA + FB * dB) / FZ;
+    const float s2 = (float)kSQ2;
+    const float dL = (dZ + (1.0f + s2) * dB) / Zp.h - (dZ + (1.0f - s2) * dB) / Zm.h;
+    r.cp_dep = (float)kR * (Z - 1.0f) + (float)kR * Tf * dZ +
+               m.kb.h * (Tf * d2am * L.h + tdam_am.h * dL);
+  }
+  return r;
+}
+
+__device__ __forceinline__ f2 h_ig_df(const MixDF& m, f2 T) {
+  f2 a = m.e[5];
+#pragma unroll
+  for (int k = 4; k >= 0; --k) a = f2_fma(a, T, m.e[k]);
+  return a;
+}
+
+__device__ __forceinline__ float cp_ig_f(const MixDF& m, float T) {
+  return fmaf(fmaf(fmaf(fmaf(5.0f * m.e[5].h, T, 4.0f * m.e[4].h), T, 3.0f * m.e[3].h), T,
+                   2.0f * m.e[2].h), T, m.e[1].h);
+}
+
+// solve_T in double-float (a9): the same safeguarded chord-Newton iteration inside the bracket
+// [50, 5000] K, the residual h(T) - h0 and the iterates in double-float.
+__device__ f2 solve_T_df(const MixDF& m, f2 p, f2 h0, double Told, const EosParams& P,
+                         const f2* lt, int& iters, int& st) {
+  f2 lo = f2{(float)kTLo, 0.0f}, hi = f2{(float)kTHi, 0.0f};
+  f2 Tn = f2_from(Told);
+  if (f2_lt(Tn, lo)) Tn = lo;
+  if (f2_gt(Tn, hi)) Tn = hi;
+  bool conv = false, need_cp = true;
+  float icp = 0.0f;
+  const float tolf = (float)P.newton_tol;
+  for (int it = 0; it < P.newton_max_iter; ++it) {
+    ++iters;
+    int s2 = 0;
+    const PRPointDF q = pr_point_df<true>(m, Tn, p, need_cp, lt, s2);
+    if (s2) {
+      st |= s2;
+      break;
+    }
+    const f2 f = f2_sub(f2_fma(q.h_dep, m.inv, h_ig_df(m, Tn)), h0);
+    // chord steps with an FP32 reciprocal slope, as in solve_T
+    if (need_cp) icp = __frcp_rn(fmaf(q.cp_dep, m.inv.h, cp_ig_f(m, Tn.h)));
+    if (__float_as_int(f.h) >= 0) hi = Tn; else lo = Tn;
+    const f2 step = f2_mulf(f, -icp);
+    f2 Tx = f2_add(Tn, step);
+    const bool done = fabsf(step.h) <= tolf * Tn.h;
+    need_cp = false;
+    if (!done && !(f2_gt(Tx, lo) && f2_lt(Tx, hi))) {
+      const f2 mid = f2_add(lo, hi);
+      Tx = f2{0.5f * mid.h, 0.5f * mid.l};
+      need_cp = true;
+    }
+    Tn = Tx;
+    if (done) {
+      conv = true;
+      break;
+    }
+  }
+  if (!conv && st == 0) st |= kCellNotConverged;
+  if (!isfinite(Tn.h)) st |= kCellNonfinite;
+  return Tn;
+}
+
 template <typename XT>
 __device__ __forceinline__ XT to_x(float v, float scale);
 template <>
@@ -453,8 +832,8 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams
     const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
     int64_t ldY, double* __restrict__ h0, double* __restrict__ Zout, XT* __restrict__ x,
     int64_t ldx, float x_scale, int32_t* __restrict__ status, double* __restrict__ rho) {
-  extern __shared__ double sm[];
-  const SharedConsts c = load_consts(P, sm);
+  extern __shared__ __align__(16) double sm[];
+  const SharedConsts c = load_consts<true>(P, sm);
   f2* ycol = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
   const int64_t nrow = valid_rows(rows);
   const int n = P.n, K0 = P.K0;
@@ -489,13 +868,16 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams
     int st = 0;
     double h = __longlong_as_double(0x7ff8000000000000LL), Z = h;
     if (finite) {
-      Mixture m;
-      mixture(ycol, n, c, m);
-      const PRPoint q = pr_point<false>(m, Tc, pc, false, c.lnt, st);
-      Z = q.Z;
-      h = h_ig(m, Tc) + q.h_dep * m.inv;
-      if (!d_finite(h)) st |= kCellNonfinite;
-      if (rho) rho[r] = pc * drcp(m.inv * Z * kR * Tc);
+      MixDF m;
+      mixture_df(ycol, n, c, m);
+      const f2 Td = f2_from(Tc), pd = f2_from(pc);
+      const PRPointDF q = pr_point_df<false>(m, Td, pd, false, c.lt2, st);
+      Z = f2_to_int(q.Z);
+      const f2 hd = f2_fma(q.h_dep, m.inv, h_ig_df(m, Td));
+      h = f2_to_int(hd);
+      if (!isfinite(hd.h)) st |= kCellNonfinite;
+      // rho = p W_mix / (Z R T)
+      if (rho) rho[r] = f2_to_int(f2_mul(pd, f2_rcp(f2_mul(f2_mul(m.inv, q.Z), f2_mul(Td, f2{kRh, kRl})))));
     } else {
       st = kCellNonfinite;
     }
@@ -515,6 +897,26 @@ __device__ __forceinline__ double ipow(double b, int m) {
   return r;
 }
 
+// Y' = Y (1 + eps)^m for a growth (1 + eps)^m beyond e^80, in FP64. Out of line (rare).
+__device__ __noinline__ f2 yprime_large(double y, float eps, int mpow) {
+  return f2_from(y * ipow(1.0 + f_to_d(eps), mpow));
+}
+
+// Y' for Y below 1e-30 (or not positive): the closed form (Y^lambda + lambda du)^(1/lambda).
+// Y^lambda (< 1e-30^lambda) in FP32, lambda du is FP32 already, the power in double-float: an
+// absolute error of ~1e-7 Y^lambda in the base moves Y' by less than m 1e-7 Y^lambda base^(m-1).
+__device__ __forceinline__ f2 yprime_small(double y, float lamf, float ldu, int mpow) {
+  const float yf = d_to_f_trunc(y);
+  const float base = ((yf > 0.0f) ? exp2f(lamf * log2f(yf)) : 0.0f) + ldu;
+  if (!(base > 0.0f)) return f2{0.f, 0.f};
+  f2 r = f2{1.0f, 0.0f}, b = f2{base, 0.0f};
+  for (int m = mpow; m; m >>= 1) {
+    if (m & 1) r = f2_mul(r, b);
+    b = f2_mul(b, b);
+  }
+  return r;
+}
+
 // a8-a10 for the valid rows of a batch. Y' lives in this thread's shared-memory column (double-
 // float) from the increment to the write-back, which happens only once the Newton solve for T
 // has succeeded.
@@ -523,7 +925,7 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
     const float* __restrict__ O, int64_t ldo, const double* __restrict__ h0,
     double* __restrict__ T, const double* __restrict__ p, double* __restrict__ Y, int64_t ldY,
     const int32_t* __restrict__ pre_status, int32_t* __restrict__ cell_status, Source src) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   const SharedConsts c = load_consts_post(P, sm);
   f2* ycol = reinterpret_cast<f2*>(sm + consts_words_post(P)) + threadIdx.x;
   const int stride = blockDim.x;
@@ -531,10 +933,10 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
   const int n = P.n, K0 = P.K0;
   const float* out_mean = c.normf + 2 * K0;
   const float* out_std = c.normf + 2 * K0 + n;
-  const double lam = P.lambda;
   const float lamf = (float)P.lambda;
   const int mpow = P.inv_lambda;
   const float mf = (float)P.inv_lambda;
+  const bool binom = P.binom[0] != 0.0f;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrow;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cell = row_cell(rows, r);
@@ -554,18 +956,19 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
         // the increment delta = (1 + eps)^m - 1 only scales Y' - Y, so FP32 suffices.
         const f2 yf = f2_from(y);
         const float eps = ldu * exp2f(-lamf * log2f(yf.h));
-        if (eps > -1.0f) {
+        if (binom && fabsf(eps) <= 0.0625f) {
+          // delta = sum_{k=1..m} C(m, k) eps^k by Horner; for |eps| <= 1/16 the terms fall
+          // off at least like (m eps)^k / k!, so the FP32 sum is good to a few ulp
+          float b = 1.0f;
+#pragma unroll 4
+          for (int k = mpow - 1; k >= 1; --k) b = fmaf(b, eps, P.binom[k]);
+          yn = f2_add(yf, f2_mulf(yf, b * eps));
+        } else if (eps > -1.0f) {
           const float lg = mf * log1pf(eps);
-          if (lg < 80.0f) {
-            yn = f2_add(yf, f2_mulf(yf, expm1f(lg)));
-          } else {
-            yn = f2_from(y * ipow(1.0 + f_to_d(eps), mpow));
-          }
+          yn = (lg < 80.0f) ? f2_add(yf, f2_mulf(yf, expm1f(lg))) : yprime_large(y, eps, mpow);
         }
       } else if (d_finite(y)) {
-        // Y below 1e-30 (or not positive): the closed form in FP64
-        const double base = ((y > 0.0) ? pow(y, lam) : 0.0) + f_to_d(ldu);
-        if (base > 0.0) yn = f2_from(ipow(base, mpow));
+        yn = yprime_small(y, lamf, ldu, mpow);
       }
       ycol[k * stride] = yn;
       acc_add(S, yn);
@@ -577,9 +980,9 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
     if (st == 0) {
       const f2 iS = f2_rcp(S);
       for (int k = 0; k < n; ++k) ycol[k * stride] = f2_mul(ycol[k * stride], iS);
-      Mixture m;
+      MixDF m;
       mixture_post(ycol, n, c, m);
-      Tn = solve_T<true>(m, pc, h0c, Told, P, c.lnt, iters, st);
+      Tn = f2_to_int(solve_T_df(m, f2_from(pc), f2_from(h0c), Told, P, c.lt2, iters, st));
     }
     if (st == 0 && src.omega) {
       // source terms rho (Y' - Y) / dt; Y' - Y in double-float
@@ -610,7 +1013,7 @@ template <int NM>
 __global__ void __launch_bounds__(kThreads, kPreBlocks) props_kernel(EosParams P, int64_t ncell,
     const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
     int64_t ldY, double* rho, double* h, double* cp, double* Zo) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   const SharedConsts c = load_consts(P, sm);
   f2* ycol = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
   const int n = P.n;
@@ -695,7 +1098,7 @@ template <int NM>
 __global__ void __launch_bounds__(kThreads, kPreBlocks) transport_kernel(EosParams P, int64_t ncell,
     const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
     int64_t ldY, double* mu, double* lam, double* alpha) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   const SharedConsts c = load_consts(P, sm);
   f2* ycol = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
   const int n = P.n, nn = P.n * P.n;
@@ -930,7 +1333,7 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
     const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
     int64_t ldY, const float* __restrict__ O, int64_t ldo, const double* __restrict__ h0,
     double* __restrict__ dTn, double* __restrict__ scr, int32_t* __restrict__ cst) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   const SharedConsts c = load_consts(P, sm);
   const int stride = blockDim.x;
   // shared memory holds the per-thread columns read in O(n^2) loops (the double-float
@@ -1099,10 +1502,37 @@ cudaError_t smem_optin() {
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!done[dev]) {
     e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    // these kernels are bound by their shared-memory columns: ask for the largest carveout
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(Kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     done[dev] = true;
   }
   return cudaSuccess;
+}
+
+// Grid of a grid-stride kernel: one wave of the blocks that fit on the device at once (the
+// occupancy of Kern at kThreads threads and smem bytes), fewer when there is less work.
+template <auto Kern>
+int grid_resident(int64_t nmax, size_t smem) {
+  static int per_sm[64] = {0};
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int nb = (dev >= 0 && dev < 64) ? per_sm[dev] : 0;
+  if (nb <= 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, Kern, kThreads, smem) != cudaSuccess ||
+        nb <= 0) {
+      cudaGetLastError();
+      nb = 4;
+    }
+    if (dev >= 0 && dev < 64) per_sm[dev] = nb;
+  }
+  int64_t need = (nmax + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)sms * nb;
+  if (need < 1) need = 1;
+  return (int)(need < cap ? need : cap);
 }
 
 int grid_for(int64_t nmax) {
@@ -1121,7 +1551,8 @@ cudaError_t pre_launch(const EosParams& P, const RowMap& rows, const double* T, 
                        float xs, int32_t* status, cudaStream_t st, double* rho) {
   cudaError_t e = smem_optin<eos_pre_kernel<NM, XT>>();
   if (e != cudaSuccess) return e;
-  eos_pre_kernel<NM, XT><<<grid_for(rows.nmax), kThreads, eos_smem(P), st>>>(
+  eos_pre_kernel<NM, XT><<<grid_resident<eos_pre_kernel<NM, XT>>(rows.nmax, eos_smem(P)), kThreads,
+                           eos_smem(P), st>>>(
       P, rows, T, p, Y, ldY, h0, Z, x, ldx, xs, status, rho);
   return cudaGetLastError();
 }
@@ -1147,7 +1578,8 @@ cudaError_t post_nm(const EosParams& P, const RowMap& rows, const float* O, int6
                     const Source& src) {
   cudaError_t e = smem_optin<eos_post_kernel<NM>>();
   if (e != cudaSuccess) return e;
-  eos_post_kernel<NM><<<grid_for(rows.nmax), kThreads, eos_smem_post(P), st>>>(
+  eos_post_kernel<NM><<<grid_resident<eos_post_kernel<NM>>(rows.nmax, eos_smem_post(P)), kThreads,
+                        eos_smem_post(P), st>>>(
       P, rows, O, ldo, h0, T, p, Y, ldY, pre_status, cell_status, src);
   return cudaGetLastError();
 }

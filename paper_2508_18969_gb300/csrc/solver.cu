@@ -80,7 +80,6 @@ __device__ __forceinline__ f2 ld2(const float2* p) {
   return f2{v.x, v.y};
 }
 __device__ __forceinline__ void st2(float2* p, f2 a) { *p = make_float2(a.h, a.l); }
-__device__ __forceinline__ f2 f2_neg(f2 a) { return f2{-a.h, -a.l}; }
 
 // ---------------------------------------------------------------------------------------
 // Sec. 3.2.2: values of the block matrix from the LDU arrays through the position maps.

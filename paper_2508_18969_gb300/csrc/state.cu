@@ -127,7 +127,7 @@ void free_state(df_state* s) {
   s->jac = nullptr;
   free_trn(s->trn);
   s->trn = nullptr;
-  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K2); f(s->d_Kr2); f(s->d_kfs); f(s->d_kfr); f(s->d_lntab); f(s->d_tsp); f(s->d_tpair); f(s->d_gtab); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
+  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K4); f(s->d_kcol); f(s->d_kfs); f(s->d_kfr); f(s->d_lntab); f(s->d_lntab2); f(s->d_tsp); f(s->d_tpair); f(s->d_gtab); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
   for (auto p : s->W32) f(p);
   for (auto p : s->bias) f(p);
   for (auto p : s->Wlp) f(p);
@@ -387,6 +387,30 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
       Kr[(size_t)i * n + j] = K[(size_t)i * n + j] * q[2] * q[0];
     }
   const std::vector<float> spcw2 = split(spcw), Ks2 = split(Ks), Kr2 = split(Kr);
+  // the pair tables interleaved per (i, j): (Ks hi, Ks lo, Kr hi, Kr lo), one 16-byte load;
+  // then the column maxima max_i |Ks_ij| and max_i |Kr_ij|, rounded up, for the accumulator
+  // offsets of the pair sums
+  std::vector<float> K4((size_t)4 * n * n), kcol((size_t)2 * n, 0.0f);
+  for (size_t o = 0; o < (size_t)n * n; ++o) {
+    K4[4 * o] = Ks2[2 * o];
+    K4[4 * o + 1] = Ks2[2 * o + 1];
+    K4[4 * o + 2] = Kr2[2 * o];
+    K4[4 * o + 3] = Kr2[2 * o + 1];
+  }
+  // (a negative entry, k_ij > 1, makes terms of both signs even for Y >= 0: the maxima are
+  // scaled by four, which is what the offset needs for terms of both signs)
+  bool kneg = false;
+  for (size_t o = 0; o < (size_t)n * n; ++o) kneg = kneg || Ks[o] < 0.0 || Kr[o] < 0.0;
+  for (int j = 0; j < n; ++j) {
+    double ms = 0.0, mr = 0.0;
+    for (int i = 0; i < n; ++i) {
+      ms = std::max(ms, std::fabs(Ks[(size_t)i * n + j]));
+      mr = std::max(mr, std::fabs(Kr[(size_t)i * n + j]));
+    }
+    const double f = (kneg ? 4.0 : 1.0) * (1.0 + 1.0 / 1024.0);
+    kcol[j] = (float)(ms * f);
+    kcol[n + j] = (float)(mr * f);
+  }
   std::vector<float> kfs((size_t)n * n), kfr((size_t)n * n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
@@ -419,6 +443,11 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
   }
   CK(dalloc(&s->d_lntab, lntab.size()), "constants");
   CK(cudaMemcpy(s->d_lntab, lntab.data(), sizeof(double) * 256, cudaMemcpyHostToDevice), "copy");
+  // the same table in double-float pairs (hi, lo) for the double-float state evaluation
+  const std::vector<float> lntab2 = split(lntab);
+  CK(dalloc(&s->d_lntab2, lntab2.size()), "constants");
+  CK(cudaMemcpy(s->d_lntab2, lntab2.data(), sizeof(float) * lntab2.size(), cudaMemcpyHostToDevice),
+     "copy");
   // Chung's mixing-rule tables (transport properties): sigma_i = 0.809 Vc_i^(1/3) Angstrom,
   // eps_i / k = Tc_i / 1.2593, Vc_i = Zc R Tc_i / pc_i with the Peng-Robinson critical
   // compressibility Zc = 0.307401, binary factors 1
@@ -451,11 +480,11 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
   CK(cudaMemcpy(s->d_kfs, kfs.data(), sizeof(float) * kfs.size(), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(s->d_kfr, kfr.data(), sizeof(float) * kfr.size(), cudaMemcpyHostToDevice), "copy");
   CK(dalloc(&s->d_spc2, spcw2.size()), "constants");
-  CK(dalloc(&s->d_K2, Ks2.size()), "constants");
-  CK(dalloc(&s->d_Kr2, Kr2.size()), "constants");
+  CK(dalloc(&s->d_K4, K4.size()), "constants");
+  CK(dalloc(&s->d_kcol, kcol.size()), "constants");
   CK(cudaMemcpy(s->d_spc2, spcw2.data(), sizeof(float) * spcw2.size(), cudaMemcpyHostToDevice), "copy");
-  CK(cudaMemcpy(s->d_K2, Ks2.data(), sizeof(float) * Ks2.size(), cudaMemcpyHostToDevice), "copy");
-  CK(cudaMemcpy(s->d_Kr2, Kr2.data(), sizeof(float) * Kr2.size(), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(s->d_K4, K4.data(), sizeof(float) * K4.size(), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(s->d_kcol, kcol.data(), sizeof(float) * kcol.size(), cudaMemcpyHostToDevice), "copy");
   CK(dalloc(&s->d_err, 1), "error word");
   CK(cudaMemset(s->d_err, 0, sizeof(int)), "memset");
   CK(dalloc(&s->d_count, 1), "counters");
@@ -468,6 +497,14 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
   P.n = n;
   P.K0 = s->K0;
   P.inv_lambda = m;
+  for (int k = 0; k <= 16; ++k) P.binom[k] = 0.0f;
+  if (m >= 1 && m <= 16) {
+    double c = 1.0;
+    for (int k = 0; k <= m; ++k) {
+      P.binom[k] = (float)c;
+      c = c * (m - k) / (k + 1);
+    }
+  }
   P.lambda = mlp->lambda;
   P.T_react = opt->T_react;
   P.newton_tol = opt->newton_tol > 0 ? opt->newton_tol : 1e-8;
@@ -476,11 +513,12 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
   P.Kmat = s->d_K;
   P.norm = s->d_norm;
   P.spcw2 = s->d_spc2;
-  P.Ks2 = s->d_K2;
-  P.Kr2 = s->d_Kr2;
+  P.K4 = s->d_K4;
+  P.kcol = s->d_kcol;
   P.kfs = s->d_kfs;
   P.kfr = s->d_kfr;
   P.lntab = s->d_lntab;
+  P.lntab2 = s->d_lntab2;
   P.tsp = s->d_tsp;
   P.tpair = s->d_tpair;
   P.err = s->d_err;

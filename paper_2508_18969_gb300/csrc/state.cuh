@@ -55,11 +55,12 @@ struct df_state {
   double* d_K = nullptr;
   double* d_norm = nullptr;
   float* d_spc2 = nullptr;               // double-float mixing-sum tables (EosParams)
-  float* d_K2 = nullptr;
-  float* d_Kr2 = nullptr;
+  float* d_K4 = nullptr;
+  float* d_kcol = nullptr;
   float* d_kfs = nullptr;                // FP32 k_ij tables (EosParams)
   float* d_kfr = nullptr;
   double* d_lntab = nullptr;             // log table (EosParams)
+  float* d_lntab2 = nullptr;             // the log table in double-float pairs
   double* d_tsp = nullptr;               // transport species constants (EosParams)
   float* d_tpair = nullptr;              // transport pair tables (EosParams)
   int gelu_mode = 0;                     // DF_GELU_TANH or DF_GELU_TABLE
