@@ -194,8 +194,15 @@ __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
   return f2_norm(s, __fadd_rn(t, __fadd_rn(e, c.l)));
 }
 
-// Order of normalised pairs (|lo| <= ulp(hi) / 2): compare the high parts, then the low parts.
-__device__ __forceinline__ bool f2_gt(f2 a, f2 b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
+// a > b by the sign of the double-float difference. Comparing high parts first would need
+// both pairs in one canonical form, and f2_from's high part is truncated (its low part can
+// reach a whole ulp) while arithmetic results are rounded to nearest.
+__device__ __forceinline__ bool f2_gt(f2 a, f2 b) {
+  float s, e;
+  two_sum(a.h, -b.h, s, e);
+  e = __fadd_rn(e, __fsub_rn(a.l, b.l));
+  return __fadd_rn(s, e) > 0.0f;   // rounding keeps the sign of a nonzero s + e
+}
 __device__ __forceinline__ bool f2_lt(f2 a, f2 b) { return f2_gt(b, a); }
 
 // sqrt(a) for a positive normal a: t0 = a.h r with r = rsqrt_32(a.h), then one Newton step

@@ -61,16 +61,16 @@ struct EosParams {
   const double* norm;
   // Double-float (hi, lo) tables of the mixing sums, with 1/W folded in:
   //   spcw2[k][j]: j = 0 1/W_k, 1 s_k/W_k, 2 r_k/W_k, 3 b_k/W_k, 4..9 hc_j/W_k;
-  //   K4[i][j] = (Ks hi, Ks lo, Kr hi, Kr lo) with Ks_ij = (1 - k_ij) s_j / W_j,
-  //   Kr_ij = (1 - k_ij) r_j / W_j; kcol[j] = max_i |Ks_ij|, kcol[n + j] = max_i |Kr_ij|
-  //   (rounded up by 2^-10: bounds for the pair sums' accumulator offsets).
+  //   K4 = (Ks hi, Ks lo, Kr hi, Kr lo) for the pairs j > i, row by row (row i from entry
+  //   i n - i (i + 1) / 2), with Ks_ij = (1 - k_ij) s_j / W_j, Kr_ij = (1 - k_ij) r_j / W_j;
+  //   kcol[j] = max_i |Ks_ij|, kcol[n + j] = max_i |Kr_ij| (rounded up by 2^-10: bounds for the
+  //   pair sums' accumulator offsets).
   const float* spcw2;    // [n * kSpcStride * 2]
-  const float* K4;       // [n * n * 4]
+  const float* K4;       // [2 n (n - 1)] (+ 4 floats of padding)
   const float* kcol;     // [2 * n]
-  // FP32 pair corrections of the T-from-h solve: kfs[i][j] = k_ij s_j / W_j,
-  // kfr[i][j] = k_ij r_j / W_j (k_ii = 0)
-  const float* kfs;      // [n * n]
-  const float* kfr;      // [n * n]
+  // FP32 pair corrections of the T-from-h solve, (k_ij s_j / W_j, k_ij r_j / W_j) for the
+  // pairs j > i, row by row (row i from pair i n - i (i + 1) / 2)
+  const float* kf2;      // [n (n - 1)] (+ 2 floats of padding)
   // natural-log table: ln(c_j) for j < 128, then 1 / c_j, c_j = 1 + (j + 1/2) / 128
   const double* lntab;   // [256]
   const float* lntab2;   // [512] the same table as double-float (hi, lo) pairs

@@ -32,7 +32,7 @@ namespace {
 constexpr double kSQ2 = 1.41421356237309504880;
 constexpr double kInvR = 1.0 / kR;
 constexpr int kThreads = 128;
-constexpr int kPreBlocks = 4;    // resident blocks per SM the register budget is sized for
+constexpr int kPreBlocks = 5;    // resident blocks per SM the register budget is sized for
 constexpr int kPostBlocks = 5;
 constexpr int kCellNotConverged = 1;
 constexpr int kCellNoRoot = 2;
@@ -63,10 +63,10 @@ struct MixSums {
 
 struct SharedConsts {
   const f2* spcw;      // [n * kSpcStride] double-float species constants over W
-  const float4* K4;    // [n * n] (Ks, Kr) double-float: (1 - k_ij) s_j / W_j, (1 - k_ij) r_j / W_j
+  const float4* K4;    // pairs j > i, row by row: (Ks, Kr) double-float, (1 - k_ij) s_j / W_j,
+                       // (1 - k_ij) r_j / W_j
   const float* kcol;   // [2 n] max_i |Ks_ij|, then max_i |Kr_ij| (rounded up)
-  const float* kfs;    // [n * n] k_ij s_j / W_j (FP32; the T-from-h layout only)
-  const float* kfr;    // [n * n] k_ij r_j / W_j
+  const float2* kf2;   // pairs j > i: (k_ij s_j / W_j, k_ij r_j / W_j) in FP32 (T-from-h only)
   const double* lnt;   // [256] log table (ln c_j, then 1 / c_j); FP64 kernels only
   const f2* lt2;       // the same table in double-float, in the same words; DF kernels only
   const double* norm;  // [2 K0 + 2 n]
@@ -76,7 +76,7 @@ struct SharedConsts {
 // 8-byte words of shared memory the constants take: FP64 normalisation, then the
 // double-float tables (one f2 per word), then the FP32 normalisation.
 __host__ __device__ inline int consts_words(const EosParams& P) {
-  return 256 + 2 * P.K0 + 2 * P.n + P.n * kSpcStride + 2 * P.n * P.n + P.n + (P.K0 + P.n + 1);
+  return 256 + 2 * P.K0 + 2 * P.n + P.n * kSpcStride + P.n * (P.n - 1) + 2 + P.n + (P.K0 + P.n + 1);
 }
 
 // DF: the first 256 words hold the double-float log table (the kernels that evaluate the state
@@ -96,38 +96,41 @@ __device__ SharedConsts load_consts(const EosParams& P, double* sm0) {
   // the 8 n kSpcStride bytes of the species table
   float* fs = reinterpret_cast<float*>(sm + nn);
   for (int i = threadIdx.x; i < 2 * nspc; i += blockDim.x) fs[i] = P.spcw2[i];
-  for (int i = threadIdx.x; i < 4 * nk; i += blockDim.x) fs[2 * nspc + i] = P.K4[i];
-  for (int i = threadIdx.x; i < 2 * P.n; i += blockDim.x) fs[2 * nspc + 4 * nk + i] = P.kcol[i];
-  float* nf = fs + 2 * nspc + 4 * nk + 2 * P.n;
+  const int nk4 = 2 * P.n * (P.n - 1) + 4;   // the triangle's floats, padded to 16 bytes
+  for (int i = threadIdx.x; i < nk4; i += blockDim.x) fs[2 * nspc + i] = P.K4[i];
+  for (int i = threadIdx.x; i < 2 * P.n; i += blockDim.x) fs[2 * nspc + nk4 + i] = P.kcol[i];
+  float* nf = fs + 2 * nspc + nk4 + 2 * P.n;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) nf[i] = (float)P.norm[i];
   __syncthreads();
   return SharedConsts{reinterpret_cast<const f2*>(fs),
-                      reinterpret_cast<const float4*>(fs + 2 * nspc), fs + 2 * nspc + 4 * nk,
-                      nullptr, nullptr, DF ? nullptr : sm0,
+                      reinterpret_cast<const float4*>(fs + 2 * nspc), fs + 2 * nspc + nk4,
+                      nullptr, DF ? nullptr : sm0,
                       DF ? reinterpret_cast<const f2*>(sm0) : nullptr, sm, nf};
 }
 
 // The layout of the T-from-h kernel: double-float log table, FP64 normalisation, double-float
-// species table, the two FP32 k_ij tables, FP32 normalisation (no double-float pair tables).
+// species table, the FP32 k_ij pair table, FP32 normalisation (no double-float pair tables).
 __host__ __device__ inline int consts_words_post(const EosParams& P) {
-  return 256 + 2 * P.K0 + 2 * P.n + P.n * kSpcStride + P.n * P.n + (P.K0 + P.n + 1);
+  return 256 + 2 * P.K0 + 2 * P.n + P.n * kSpcStride + P.n * (P.n - 1) / 2 + 1 +
+         (P.K0 + P.n + 1);
 }
 
 __device__ SharedConsts load_consts_post(const EosParams& P, double* sm0) {
-  const int nspc = P.n * kSpcStride, nk = P.n * P.n, nn = 2 * P.K0 + 2 * P.n;
+  const int nspc = P.n * kSpcStride, nn = 2 * P.K0 + 2 * P.n;
   float* t = reinterpret_cast<float*>(sm0);
   for (int i = threadIdx.x; i < 512; i += blockDim.x) t[i] = P.lntab2[i];
   double* sm = sm0 + 256;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) sm[i] = P.norm[i];
   float* fs = reinterpret_cast<float*>(sm + nn);
   for (int i = threadIdx.x; i < 2 * nspc; i += blockDim.x) fs[i] = P.spcw2[i];
-  float* ks = fs + 2 * nspc;
-  for (int i = threadIdx.x; i < nk; i += blockDim.x) ks[i] = P.kfs[i];
-  for (int i = threadIdx.x; i < nk; i += blockDim.x) ks[nk + i] = P.kfr[i];
-  float* nf = ks + 2 * nk;
+  float* ks = fs + 2 * nspc;   // 8-byte aligned (8 n kSpcStride bytes after fs)
+  const int nkf = P.n * (P.n - 1) + 2;
+  for (int i = threadIdx.x; i < nkf; i += blockDim.x) ks[i] = P.kf2[i];
+  float* nf = ks + nkf;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) nf[i] = (float)P.norm[i];
   __syncthreads();
-  return SharedConsts{reinterpret_cast<const f2*>(fs), nullptr, nullptr, ks, ks + nk, nullptr,
+  return SharedConsts{reinterpret_cast<const f2*>(fs), nullptr, nullptr,
+                      reinterpret_cast<const float2*>(ks), nullptr,
                       reinterpret_cast<const f2*>(sm0), sm, nf};
 }
 
@@ -151,6 +154,37 @@ __device__ __forceinline__ double drcp(double x) {
 // the power of two above B_i, or above 4 B_i when some Y_j is negative. B_i is the total (summed
 // rounding up) less the leading terms (rounded down, each subtraction rounded up), so it never
 // falls below the exact suffix bound.
+// Species i's terms of the O(n) sums (species-table columns 0 and 3..9) and its weighted mass
+// fractions ys_i = Y_i s_i / W_i, yr_i = Y_i r_i / W_i.
+__device__ __forceinline__ void species_row(const SharedConsts& c, int i, f2 y, float (&hq)[8],
+                                            float (&lq)[8], f2& ys, f2& yr) {
+  const float4* q4 = reinterpret_cast<const float4*>(c.spcw + i * kSpcStride);
+  const float4 a = q4[0], b = q4[1], d = q4[2], e = q4[3], g = q4[4];
+  acc_off_fma(hq[0], lq[0], y, f2{a.x, a.y});
+  acc_off_fma(hq[1], lq[1], y, f2{b.z, b.w});
+  acc_off_fma(hq[2], lq[2], y, f2{d.x, d.y});
+  acc_off_fma(hq[3], lq[3], y, f2{d.z, d.w});
+  acc_off_fma(hq[4], lq[4], y, f2{e.x, e.y});
+  acc_off_fma(hq[5], lq[5], y, f2{e.z, e.w});
+  acc_off_fma(hq[6], lq[6], y, f2{g.x, g.y});
+  acc_off_fma(hq[7], lq[7], y, f2{g.z, g.w});
+  ys = f2_mul(y, f2{a.z, a.w});
+  yr = f2_mul(y, f2{b.x, b.y});
+}
+
+// Species i's terms of the three forms: F0 += ys ys + ys (2 P), F1 += ys yr + ys Q + yr P,
+// F2 += yr yr + yr (2 Q).
+__device__ __forceinline__ void forms_row(f2 ys, f2 yr, f2 P, f2 Q, float& F0h, float& F0l,
+                                          float& F1h, float& F1l, float& F2h, float& F2l) {
+  acc_off_fma(F0h, F0l, ys, ys);
+  acc_off_fma(F0h, F0l, ys, f2_scale2(P));
+  acc_off_fma(F1h, F1l, ys, yr);
+  acc_off_fma(F1h, F1l, ys, Q);
+  acc_off_fma(F1h, F1l, yr, P);
+  acc_off_fma(F2h, F2l, yr, yr);
+  acc_off_fma(F2h, F2l, yr, f2_scale2(Q));
+}
+
 __device__ void mixture_sums(const f2* ycol, int n, const SharedConsts& c, MixSums& ms) {
   const int stride = blockDim.x;
   // The O(n) sums (1/W, b/W and the six enthalpy coefficients, species-table columns 0 and 3..9)
@@ -199,22 +233,14 @@ __device__ void mixture_sums(const f2* ycol, int n, const SharedConsts& c, MixSu
   float F0h = sF0, F0l = 0.f, F1h = sF1, F1l = 0.f, F2h = sF2, F2l = 0.f;
 #pragma unroll 1
   for (int i = 0; i < n; ++i) {
-    const float4* q4 = reinterpret_cast<const float4*>(c.spcw + i * kSpcStride);
-    const float4 a = q4[0], b = q4[1], d = q4[2], e = q4[3], g = q4[4];
     const f2 y = ycol[i * stride];
-    acc_off_fma(hq[0], lq[0], y, f2{a.x, a.y});
-    acc_off_fma(hq[1], lq[1], y, f2{b.z, b.w});
-    acc_off_fma(hq[2], lq[2], y, f2{d.x, d.y});
-    acc_off_fma(hq[3], lq[3], y, f2{d.z, d.w});
-    acc_off_fma(hq[4], lq[4], y, f2{e.x, e.y});
-    acc_off_fma(hq[5], lq[5], y, f2{e.z, e.w});
-    acc_off_fma(hq[6], lq[6], y, f2{g.x, g.y});
-    acc_off_fma(hq[7], lq[7], y, f2{g.z, g.w});
+    f2 ys, yr;
+    species_row(c, i, y, hq, lq, ys, yr);
     Bs = __fsub_ru(Bs, __fmul_rd(fabsf(y.h), c.kcol[i]));
     Br = __fsub_ru(Br, __fmul_rd(fabsf(y.h), c.kcol[n + i]));
     const float sgs = pow2_up(sgf * Bs), sgr = pow2_up(sgf * Br);
     float ph = sgs, pl = 0.f, qh = sgr, ql = 0.f;
-    const float4* Kr4 = c.K4 + i * n;
+    const float4* Kr4 = c.K4 + (i * n - i * (i + 1) / 2) - (i + 1);   // Kr4[j], j > i
 #pragma unroll 4
     for (int j = i + 1; j < n; ++j) {
       const f2 yj = ycol[j * stride];
@@ -222,16 +248,8 @@ __device__ void mixture_sums(const f2* ycol, int n, const SharedConsts& c, MixSu
       acc_off_fma(ph, pl, f2{k.x, k.y}, yj);
       acc_off_fma(qh, ql, f2{k.z, k.w}, yj);
     }
-    const f2 Pi = f2_norm(__fsub_rn(ph, sgs), pl);
-    const f2 Qi = f2_norm(__fsub_rn(qh, sgr), ql);
-    const f2 ysi = f2_mul(y, f2{a.z, a.w}), yri = f2_mul(y, f2{b.x, b.y});
-    acc_off_fma(F0h, F0l, ysi, ysi);
-    acc_off_fma(F0h, F0l, ysi, f2_scale2(Pi));
-    acc_off_fma(F1h, F1l, ysi, yri);
-    acc_off_fma(F1h, F1l, ysi, Qi);
-    acc_off_fma(F1h, F1l, yri, Pi);
-    acc_off_fma(F2h, F2l, yri, yri);
-    acc_off_fma(F2h, F2l, yri, f2_scale2(Qi));
+    forms_row(ys, yr, f2_norm(__fsub_rn(ph, sgs), pl), f2_norm(__fsub_rn(qh, sgr), ql),
+              F0h, F0l, F1h, F1l, F2h, F2l);
     if ((i & 3) == 3) {  // every fourth species: keep the low parts small
 #pragma unroll
       for (int k = 0; k < 8; ++k) acc_renorm(hq[k], lq[k]);
@@ -334,6 +352,21 @@ __device__ __forceinline__ double dsqrt_pos(double x) {
 // corrections (k <= 0.1 of the squares) summed in FP32,
 //   F0 = S_s^2 - 2 sum_i ys_i Pk_i,  F1 = S_s S_r - sum_i (ys_i Qk_i + yr_i Pk_i),
 //   F2 = S_r^2 - 2 sum_i yr_i Qk_i,  Pk_i = sum_{j>i} k_ij ys_j,  Qk_i = sum_{j>i} k_ij yr_j.
+// Species i's terms of mixture_post's ten O(n) sums; q1, q2 return s_i / W_i and r_i / W_i.
+__device__ __forceinline__ void species_row_post(const SharedConsts& c, int i, f2 y,
+                                                 float (&hq)[kSpcStride], float (&lq)[kSpcStride],
+                                                 float& q1, float& q2) {
+  const float4* q4 = reinterpret_cast<const float4*>(c.spcw + i * kSpcStride);
+#pragma unroll
+  for (int k = 0; k < kSpcStride / 2; ++k) {
+    const float4 a = q4[k];
+    acc_off_fma(hq[2 * k], lq[2 * k], y, f2{a.x, a.y});
+    acc_off_fma(hq[2 * k + 1], lq[2 * k + 1], y, f2{a.z, a.w});
+    if (k == 0) q1 = a.z;
+    if (k == 1) q2 = a.x;
+  }
+}
+
 __device__ void mixture_post(const f2* ycol, int n, const SharedConsts& c, MixDF& m) {
   const int stride = blockDim.x;
   // the ten O(n) sums over the species table take offset accumulators, as in mixture()
@@ -365,25 +398,17 @@ __device__ void mixture_post(const f2* ycol, int n, const SharedConsts& c, MixDF
   float C0 = 0.f, C1 = 0.f, C2 = 0.f;
 #pragma unroll 1
   for (int i = 0; i < n; ++i) {
-    const float4* q4 = reinterpret_cast<const float4*>(c.spcw + i * kSpcStride);
     const f2 y = ycol[i * stride];
-    float q1h = 0.f, q2h = 0.f;
-#pragma unroll
-    for (int k = 0; k < kSpcStride / 2; ++k) {
-      const float4 a = q4[k];
-      acc_off_fma(hq[2 * k], lq[2 * k], y, f2{a.x, a.y});
-      acc_off_fma(hq[2 * k + 1], lq[2 * k + 1], y, f2{a.z, a.w});
-      if (k == 0) q1h = a.z;
-      if (k == 1) q2h = a.x;
-    }
+    float q1h, q2h;
+    species_row_post(c, i, y, hq, lq, q1h, q2h);
     float Pk = 0.f, Qk = 0.f;
-    const float* ksr = c.kfs + i * n;
-    const float* krr = c.kfr + i * n;
+    const float2* R = c.kf2 + (i * n - i * (i + 1) / 2) - (i + 1);   // R[j], j > i
 #pragma unroll 4
     for (int j = i + 1; j < n; ++j) {
       const float yj = ycol[j * stride].h;
-      Pk = fmaf(ksr[j], yj, Pk);
-      Qk = fmaf(krr[j], yj, Qk);
+      const float2 k = R[j];
+      Pk = fmaf(k.x, yj, Pk);
+      Qk = fmaf(k.y, yj, Qk);
     }
     if ((i & 3) == 3) {  // every fourth species: keep the low parts small
 #pragma unroll
@@ -639,12 +664,20 @@ __device__ __forceinline__ f2 f2_log_tab(f2 x, const f2* lt) {
   return f2_add(f2_add(el2, lt[j]), l1p);
 }
 
-// One Newton step on the cubic, f(Z) and f'(Z) in double-float, the step with an FP32
-// reciprocal of f'(Z) (it scales the correction by 1 + O(1e-7)).
+// x^(1/3) in FP32 for a seed: 2^(log2|x| / 3) with the sign of x, then one Newton step
+// t <- t - (t^3 - x) / (3 t^2) (~1 ulp).
+__device__ __forceinline__ float cbrt_seed(float x) {
+  if (x == 0.0f) return 0.0f;
+  const float t = copysignf(exp2f(log2f(fabsf(x)) * (1.0f / 3.0f)), x);
+  return t - (t - __fdividef(x, t * t)) * (1.0f / 3.0f);
+}
+
+// One Newton step on the cubic, f(Z) and f'(Z) in double-float, the step with an approximate
+// FP32 reciprocal of f'(Z) (it scales the correction by 1 + O(1e-7)).
 __device__ __forceinline__ f2 cubic_step_df(f2 Z, f2 c2, f2 c1, f2 c0) {
   const f2 f = f2_fma(f2_fma(f2_add(Z, c2), Z, c1), Z, c0);
   const f2 fp = f2_fma(f2_add(f2_mulf(Z, 3.0f), f2_scale2(c2)), Z, c1);
-  return fp.h != 0.0f ? f2_add(Z, f2_mulf(f, -__frcp_rn(fp.h))) : Z;
+  return fp.h != 0.0f ? f2_add(Z, f2_mulf(f, -__fdividef(1.0f, fp.h))) : Z;
 }
 
 __device__ __forceinline__ f2 g_dep_df(f2 Z, f2 A, f2 B, const f2* lt) {
@@ -700,8 +733,8 @@ __device__ __forceinline__ f2 select_Z_df(f2 A, f2 B, const f2* lt, int& status)
   if (disc.h > 0.0f) {
     const float qf = Q.h, pf = P.h;
     const float sq = sqrtf(disc.h);
-    const float u = cbrtf(-0.5f * qf - copysignf(sq, qf));
-    const float t = (u != 0.0f) ? u - pf / (3.0f * u) : 0.0f;
+    const float u = cbrt_seed(-0.5f * qf - copysignf(sq, qf));
+    const float t = (u != 0.0f) ? u - __fdividef(pf, 3.0f * u) : 0.0f;
     const f2 Z0 = f2_sub(f2{t, 0.0f}, c23);
     f2 Z = cubic_step_df(Z0, c2, c1, c0);
     if (!FAST || fabsf(Z.h - Z0.h) > 1e-6f * fabsf(Z.h)) Z = cubic_step_df(Z, c2, c1, c0);
@@ -740,7 +773,7 @@ __device__ PRPointDF pr_point_df(const MixDF& m, f2 T, f2 p, bool want_cp, const
   r.cp_dep = 0.0f;
   if (FAST && want_cp) {
     // FP32: dA/dT = p (dam - 2 am / T) / (RT)^2 needs no division by am
-    const float Tf = T.h, iTf = __frcp_rn(Tf), itf = rsqrtf(Tf);
+    const float Tf = T.h, iTf = __fdividef(1.0f, Tf), itf = rsqrtf(Tf);
     const float Z = r.Z.h, Af = A.h, Bf = B.h;
     const float pf = p.h, iRTf = iTf * (float)kInvR;
     const float d2am = 0.5f * m.A1.h * itf * iTf;
@@ -749,9 +782,10 @@ __device__ PRPointDF pr_point_df(const MixDF& m, f2 T, f2 p, bool want_cp, const
     const float FZ = fmaf(3.0f * Z, Z, -2.0f * (1.0f - Bf) * Z) + (Af - 3.0f * Bf * Bf - 2.0f * Bf);
     const float FA = Z - Bf;
     const float FB = Z * Z - (6.0f * Bf + 2.0f) * Z - (Af - 2.0f * Bf - 3.0f * Bf * Bf);
-    const float dZ = -(FA * dA + FB * dB) / FZ;
+    // (a chord slope: approximate FP32 divisions suffice)
+    const float dZ = -__fdividef(FA * dA + FB * dB, FZ);
     const float s2 = (float)kSQ2;
-    const float dL = (dZ + (1.0f + s2) * dB) / Zp.h - (dZ + (1.0f - s2) * dB) / Zm.h;
+    const float dL = __fdividef(dZ + (1.0f + s2) * dB, Zp.h) - __fdividef(dZ + (1.0f - s2) * dB, Zm.h);
     r.cp_dep = (float)kR * (Z - 1.0f) + (float)kR * Tf * dZ +
                m.kb.h * (Tf * d2am * L.h + tdam_am.h * dL);
   }
@@ -791,7 +825,7 @@ __device__ f2 solve_T_df(const MixDF& m, f2 p, f2 h0, double Told, const EosPara
     }
     const f2 f = f2_sub(f2_fma(q.h_dep, m.inv, h_ig_df(m, Tn)), h0);
     // chord steps with an FP32 reciprocal slope, as in solve_T
-    if (need_cp) icp = __frcp_rn(fmaf(q.cp_dep, m.inv.h, cp_ig_f(m, Tn.h)));
+    if (need_cp) icp = __fdividef(1.0f, fmaf(q.cp_dep, m.inv.h, cp_ig_f(m, Tn.h)));
     if (__float_as_int(f.h) >= 0) hi = Tn; else lo = Tn;
     const f2 step = f2_mulf(f, -icp);
     f2 Tx = f2_add(Tn, step);
@@ -826,6 +860,17 @@ __device__ __forceinline__ __nv_fp8_e4m3 to_x<__nv_fp8_e4m3>(float v, float scal
   return __nv_fp8_e4m3(v * scale);
 }
 
+// Raw bits of a network-input element, for packing a row into 16-byte stores.
+__device__ __forceinline__ uint32_t x_bits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ uint32_t x_bits(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
+__device__ __forceinline__ uint32_t x_bits(__nv_fp8_e4m3 v) { return v.__x; }
+
+template <typename XT, int RW>
+__device__ __forceinline__ void x_put(uint32_t (&w)[RW], int e, XT v) {
+  constexpr int EPW = 4 / (int)sizeof(XT);
+  w[e / EPW] |= x_bits(v) << (8 * (int)sizeof(XT) * (e % EPW));
+}
+
 // a1-a5 for the valid rows of a batch.
 template <int NM, typename XT>
 __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams P, RowMap rows,
@@ -838,27 +883,35 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams
   const int64_t nrow = valid_rows(rows);
   const int n = P.n, K0 = P.K0;
   const float lam = (float)P.lambda;
+  const float ilam = 1.0f / lam;
   const float* mf = c.normf;        // in_mean
   const float* isf = c.normf + K0;  // 1 / in_std
+  // Network-input rows go out as 16-byte stores from registers when the row pitch allows:
+  // RW words hold the NM + 2 entries a row can have, EPC elements make one 16-byte chunk.
+  constexpr int EPC = 16 / (int)sizeof(XT);
+  constexpr int RW = ((NM + 2 + EPC - 1) / EPC) * 4;
+  const int64_t row_bytes = ldx * (int64_t)sizeof(XT);
+  const bool xvec = x && (row_bytes & 15) == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  const int nch = (int)(row_bytes >> 4);
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrow;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cell = row_cell(rows, r);
     const double Tc = T[cell], pc = p[cell];
     bool finite = d_finite(Tc) && d_finite(pc) && d_pos(pc) && d_pos(Tc);
-    // a5 features and the double-float column of Y in one pass over the species
     XT* xr = x ? x + r * ldx : nullptr;
+    // the double-float column of Y (and, without packed rows, the a5 features) in one pass
 #pragma unroll 2
     for (int k = 0; k < n; ++k) {
       const double yd = Y[k * ldY + cell];
       finite = finite && d_finite(yd);
       ycol[k * blockDim.x] = f2_from(yd);
-      if (xr) {
+      if (xr && !xvec) {
         const float y = fmaxf(d_to_f_trunc(yd), 0.0f);
-        const float bc = (y > 0.0f) ? (exp2f(lam * log2f(y)) - 1.0f) / lam : -1.0f / lam;
+        const float bc = (y > 0.0f) ? (exp2f(lam * log2f(y)) - 1.0f) * ilam : -ilam;
         xr[2 + k] = to_x<XT>((bc - mf[2 + k]) * isf[2 + k], x_scale);
       }
     }
-    if (xr) {
+    if (xr && !xvec) {
       xr[0] = to_x<XT>(finite ? (d_to_f_trunc(Tc) - mf[0]) * isf[0] : 0.0f, x_scale);
       xr[1] = to_x<XT>(finite ? (d_to_f_trunc(pc) - mf[1]) * isf[1] : 0.0f, x_scale);
       if (!finite)
@@ -881,6 +934,30 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams
     } else {
       st = kCellNonfinite;
     }
+    if (xvec) {
+      // a5 features from the column (its high parts are Y rounded to FP32), packed into
+      // registers and written as 16-byte stores: a row of RW words covers any n <= NM
+      uint32_t w[RW];
+#pragma unroll
+      for (int q = 0; q < RW; ++q) w[q] = 0u;
+      if (finite) {
+#pragma unroll
+        for (int k = 0; k < NM; ++k) {
+          if (k < n) {
+            const float y = fmaxf(ycol[k * blockDim.x].h, 0.0f);
+            const float bc = (y > 0.0f) ? (exp2f(lam * log2f(y)) - 1.0f) * ilam : -ilam;
+            x_put(w, 2 + k, to_x<XT>((bc - mf[2 + k]) * isf[2 + k], x_scale));
+          }
+        }
+      }
+      x_put(w, 0, to_x<XT>(finite ? (d_to_f_trunc(Tc) - mf[0]) * isf[0] : 0.0f, x_scale));
+      x_put(w, 1, to_x<XT>(finite ? (d_to_f_trunc(pc) - mf[1]) * isf[1] : 0.0f, x_scale));
+      uint4* xo = reinterpret_cast<uint4*>(xr);
+#pragma unroll
+      for (int q = 0; q < RW / 4; ++q)
+        if (q < nch) xo[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+      for (int q = RW / 4; q < nch; ++q) xo[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (h0) h0[r] = h;
     if (Zout) Zout[r] = Z;
     if (status) status[r] = st;
@@ -900,6 +977,14 @@ __device__ __forceinline__ double ipow(double b, int m) {
 // Y' = Y (1 + eps)^m for a growth (1 + eps)^m beyond e^80, in FP64. Out of line (rare).
 __device__ __noinline__ f2 yprime_large(double y, float eps, int mpow) {
   return f2_from(y * ipow(1.0 + f_to_d(eps), mpow));
+}
+
+// Y' = Y (1 + eps)^m by log1p and expm1, for |eps| > 1/16 or 1/lambda > 16 (out of line: the
+// common case takes the binomial sum).
+__device__ __noinline__ f2 yprime_log(double y, float eps, float mf, int mpow) {
+  const f2 yf = f2_from(y);
+  const float lg = mf * log1pf(eps);
+  return (lg < 80.0f) ? f2_add(yf, f2_mulf(yf, expm1f(lg))) : yprime_large(y, eps, mpow);
 }
 
 // Y' for Y below 1e-30 (or not positive): the closed form (Y^lambda + lambda du)^(1/lambda).
@@ -937,6 +1022,7 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
   const int mpow = P.inv_lambda;
   const float mf = (float)P.inv_lambda;
   const bool binom = P.binom[0] != 0.0f;
+  const bool ovec = (ldo & 3) == 0 && (reinterpret_cast<uintptr_t>(O) & 15) == 0;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrow;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cell = row_cell(rows, r);
@@ -945,33 +1031,48 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
     bool finite = d_finite(Told) && d_finite(pc) && d_pos(pc) && d_finite(h0c);
     f2 S = {0.f, 0.f};
     const float* Or = O + r * ldo;
-#pragma unroll 2
-    for (int k = 0; k < n; ++k) {
-      const double y = Y[k * ldY + cell];
-      finite = finite && d_finite(y);
-      const float ldu = lamf * fmaf(out_std[k], Or[k], out_mean[k]);  // lambda du
-      f2 yn = {0.f, 0.f};
-      if (d_ge_pos(y, 1e-30)) {
-        // Y' = (Y^lambda + lambda du)^(1/lambda) = Y (1 + eps)^m, eps = lambda du Y^-lambda;
-        // the increment delta = (1 + eps)^m - 1 only scales Y' - Y, so FP32 suffices.
-        const f2 yf = f2_from(y);
-        const float eps = ldu * exp2f(-lamf * log2f(yf.h));
-        if (binom && fabsf(eps) <= 0.0625f) {
-          // delta = sum_{k=1..m} C(m, k) eps^k by Horner; for |eps| <= 1/16 the terms fall
-          // off at least like (m eps)^k / k!, so the FP32 sum is good to a few ulp
-          float b = 1.0f;
-#pragma unroll 4
-          for (int k = mpow - 1; k >= 1; --k) b = fmaf(b, eps, P.binom[k]);
-          yn = f2_add(yf, f2_mulf(yf, b * eps));
-        } else if (eps > -1.0f) {
-          const float lg = mf * log1pf(eps);
-          yn = (lg < 80.0f) ? f2_add(yf, f2_mulf(yf, expm1f(lg))) : yprime_large(y, eps, mpow);
-        }
-      } else if (d_finite(y)) {
-        yn = yprime_small(y, lamf, ldu, mpow);
+    // the row's outputs four at a time (one 16-byte load when the row pitch allows)
+    for (int k0 = 0; k0 < n; k0 += 4) {
+      float o4[4];
+      if (ovec) {
+        const float4 v = *reinterpret_cast<const float4*>(Or + k0);
+        o4[0] = v.x;
+        o4[1] = v.y;
+        o4[2] = v.z;
+        o4[3] = v.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o4[q] = (k0 + q < n) ? Or[k0 + q] : 0.0f;
       }
-      ycol[k * stride] = yn;
-      acc_add(S, yn);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + q;
+        if (k >= n) break;
+        const double y = Y[k * ldY + cell];
+        finite = finite && d_finite(y);
+        const float ldu = lamf * fmaf(out_std[k], o4[q], out_mean[k]);  // lambda du
+        f2 yn = {0.f, 0.f};
+        if (d_ge_pos(y, 1e-30)) {
+          // Y' = (Y^lambda + lambda du)^(1/lambda) = Y (1 + eps)^m, eps = lambda du Y^-lambda;
+          // the increment delta = (1 + eps)^m - 1 only scales Y' - Y, so FP32 suffices.
+          const f2 yf = f2_from(y);
+          const float eps = ldu * exp2f(-lamf * log2f(yf.h));
+          if (binom && fabsf(eps) <= 0.0625f) {
+            // delta = sum_{j=1..m} C(m, j) eps^j by Horner; for |eps| <= 1/16 the terms fall
+            // off at least like (m eps)^j / j!, so the FP32 sum is good to a few ulp
+            float b = 1.0f;
+#pragma unroll 4
+            for (int j = mpow - 1; j >= 1; --j) b = fmaf(b, eps, P.binom[j]);
+            yn = f2_add(yf, f2_mulf(yf, b * eps));
+          } else if (eps > -1.0f) {
+            yn = yprime_log(y, eps, mf, mpow);
+          }
+        } else if (d_finite(y)) {
+          yn = yprime_small(y, lamf, ldu, mpow);
+        }
+        ycol[k * stride] = yn;
+        acc_add(S, yn);
+      }
     }
     S = f2_fin(S);
     if (!finite || !(S.h > 0.0f) || !isfinite(S.h)) st |= kCellNonfinite;

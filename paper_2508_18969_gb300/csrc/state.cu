@@ -127,7 +127,7 @@ void free_state(df_state* s) {
   s->jac = nullptr;
   free_trn(s->trn);
   s->trn = nullptr;
-  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K4); f(s->d_kcol); f(s->d_kfs); f(s->d_kfr); f(s->d_lntab); f(s->d_lntab2); f(s->d_tsp); f(s->d_tpair); f(s->d_gtab); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
+  f(s->d_spc); f(s->d_K); f(s->d_norm); f(s->d_spc2); f(s->d_K4); f(s->d_kcol); f(s->d_kf2); f(s->d_lntab); f(s->d_lntab2); f(s->d_tsp); f(s->d_tpair); f(s->d_gtab); f(s->d_err); f(s->d_count); f(s->d_flagged); f(s->d_iters);
   for (auto p : s->W32) f(p);
   for (auto p : s->bias) f(p);
   for (auto p : s->Wlp) f(p);
@@ -387,16 +387,19 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
       Kr[(size_t)i * n + j] = K[(size_t)i * n + j] * q[2] * q[0];
     }
   const std::vector<float> spcw2 = split(spcw), Ks2 = split(Ks), Kr2 = split(Kr);
-  // the pair tables interleaved per (i, j): (Ks hi, Ks lo, Kr hi, Kr lo), one 16-byte load;
+  // the pair tables interleaved per (i, j): (Ks hi, Ks lo, Kr hi, Kr lo), one 16-byte load,
+  // the strict upper triangle j > i only, row by row (row i starts at i n - i (i + 1) / 2);
   // then the column maxima max_i |Ks_ij| and max_i |Kr_ij|, rounded up, for the accumulator
   // offsets of the pair sums
-  std::vector<float> K4((size_t)4 * n * n), kcol((size_t)2 * n, 0.0f);
-  for (size_t o = 0; o < (size_t)n * n; ++o) {
-    K4[4 * o] = Ks2[2 * o];
-    K4[4 * o + 1] = Ks2[2 * o + 1];
-    K4[4 * o + 2] = Kr2[2 * o];
-    K4[4 * o + 3] = Kr2[2 * o + 1];
-  }
+  std::vector<float> K4((size_t)2 * n * (n - 1) + 4), kcol((size_t)2 * n, 0.0f);
+  for (int i = 0, t = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j, ++t) {
+      const size_t o = (size_t)i * n + j;
+      K4[4 * (size_t)t] = Ks2[2 * o];
+      K4[4 * (size_t)t + 1] = Ks2[2 * o + 1];
+      K4[4 * (size_t)t + 2] = Kr2[2 * o];
+      K4[4 * (size_t)t + 3] = Kr2[2 * o + 1];
+    }
   // (a negative entry, k_ij > 1, makes terms of both signs even for Y >= 0: the maxima are
   // scaled by four, which is what the offset needs for terms of both signs)
   bool kneg = false;
@@ -411,13 +414,15 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
     kcol[j] = (float)(ms * f);
     kcol[n + j] = (float)(mr * f);
   }
-  std::vector<float> kfs((size_t)n * n), kfr((size_t)n * n);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      const double k = (i == j) ? 0.0 : 1.0 - K[(size_t)i * n + j];
+  // FP32 pair corrections of the T-from-h solve, interleaved (k_ij s_j / W_j, k_ij r_j / W_j)
+  // for the pairs j > i, row by row (row i from pair i n - i (i + 1) / 2)
+  std::vector<float> kf2((size_t)n * (n - 1) + 2);
+  for (int i = 0, t = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j, ++t) {
+      const double k = 1.0 - K[(size_t)i * n + j];
       const double* q = &spc[(size_t)j * kSpcStride];
-      kfs[(size_t)i * n + j] = (float)(k * q[1] * q[0]);
-      kfr[(size_t)i * n + j] = (float)(k * q[2] * q[0]);
+      kf2[2 * (size_t)t] = (float)(k * q[1] * q[0]);
+      kf2[2 * (size_t)t + 1] = (float)(k * q[2] * q[0]);
     }
   if (s->gelu_mode == DF_GELU_TABLE) {
     // value, slope and half curvature of the tanh-form GELU at x_i = -3 + 0.01 i
@@ -475,10 +480,8 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
   CK(dalloc(&s->d_tpair, tpair.size()), "constants");
   CK(cudaMemcpy(s->d_tsp, tsp.data(), sizeof(double) * tsp.size(), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(s->d_tpair, tpair.data(), sizeof(float) * tpair.size(), cudaMemcpyHostToDevice), "copy");
-  CK(dalloc(&s->d_kfs, kfs.size()), "constants");
-  CK(dalloc(&s->d_kfr, kfr.size()), "constants");
-  CK(cudaMemcpy(s->d_kfs, kfs.data(), sizeof(float) * kfs.size(), cudaMemcpyHostToDevice), "copy");
-  CK(cudaMemcpy(s->d_kfr, kfr.data(), sizeof(float) * kfr.size(), cudaMemcpyHostToDevice), "copy");
+  CK(dalloc(&s->d_kf2, kf2.size()), "constants");
+  CK(cudaMemcpy(s->d_kf2, kf2.data(), sizeof(float) * kf2.size(), cudaMemcpyHostToDevice), "copy");
   CK(dalloc(&s->d_spc2, spcw2.size()), "constants");
   CK(dalloc(&s->d_K4, K4.size()), "constants");
   CK(dalloc(&s->d_kcol, kcol.size()), "constants");
@@ -515,8 +518,7 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
   P.spcw2 = s->d_spc2;
   P.K4 = s->d_K4;
   P.kcol = s->d_kcol;
-  P.kfs = s->d_kfs;
-  P.kfr = s->d_kfr;
+  P.kf2 = s->d_kf2;
   P.lntab = s->d_lntab;
   P.lntab2 = s->d_lntab2;
   P.tsp = s->d_tsp;

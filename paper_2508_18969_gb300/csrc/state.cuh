@@ -57,8 +57,7 @@ struct df_state {
   float* d_spc2 = nullptr;               // double-float mixing-sum tables (EosParams)
   float* d_K4 = nullptr;
   float* d_kcol = nullptr;
-  float* d_kfs = nullptr;                // FP32 k_ij tables (EosParams)
-  float* d_kfr = nullptr;
+  float* d_kf2 = nullptr;                // FP32 k_ij pair table (EosParams)
   double* d_lntab = nullptr;             // log table (EosParams)
   float* d_lntab2 = nullptr;             // the log table in double-float pairs
   double* d_tsp = nullptr;               // transport species constants (EosParams)

@@ -278,6 +278,28 @@ def test_full_size_sampled(df, prec):
     assert np.abs(host(Td)[sel] - Tr).max() <= 1e-3
 
 
+def test_repeated_steps_converge_everywhere(df):
+    """Twenty-six BF16 steps over the 2^20-cell mixing layer, the bench's sequence: every
+    T-from-h solve converges and no cell is flagged (the FP64 oracle flags none of these states).
+    A Newton step smaller than one FP32 ulp of T once failed the double-float bracket test,
+    which compared a truncated and a rounded split by their high parts, and sent the chord
+    iteration to bisection and past its iteration budget in about ten cells per million."""
+    mech, net, T, p, Y = synth.configs.build("layer1d-30sp-1m")
+    N = T.shape[0]
+    st = df.State(mech, net, precision=df.DF_BF16, T_react=0.0)
+    Td, pd, Yd = dev(T), dev(p), dev(Y)
+    status = torch.empty(N, dtype=torch.int32, device=DEV)
+    flagged = []
+    for _ in range(26):
+        st.chem_step(Td, pd, Yd, status=status)
+        flagged.append(int(torch.count_nonzero(status).item()))
+    rc, n_act, n_flag, iters = st.step_summary()
+    print(f"ERR repeated steps: flagged per step {flagged}, Newton iterations per cell "
+          f"{iters / n_act:.4f}")
+    assert max(flagged) == 0 and n_flag == 0
+    assert iters / n_act < 2.05
+
+
 def test_nonfinite_cells_and_empty_call(df):
     mech, net, T, p, Y = synth.configs.build("small-fp32-4k", n_cells=300)
     T = T.copy(); p = p.copy(); Y = Y.copy()
