@@ -687,13 +687,51 @@ __device__ __forceinline__ f2 g_dep_df(f2 Z, f2 A, f2 B, const f2* lt) {
   return f2_sub(f2_sub(f2_addf(Z, -1.0f), f2_log_tab(f2_sub(Z, B), lt)), f2_mul(a, L));
 }
 
-// Three real roots (select_Z3 in double-float). Out of line, as there.
+// Departure Gibbs energy in FP32 (for choosing among the three roots when the choice is clear).
+__device__ __forceinline__ float g_dep_f(float Z, float A, float B) {
+  const float s2 = 1.41421356f;
+  return Z - 1.0f - __logf(Z - B) -
+         __fdividef(A, 2.0f * s2 * B) * __logf(__fdividef(Z + (1.0f + s2) * B, Z + (1.0f - s2) * B));
+}
+
+// Three real roots (select_Z3 in double-float). Out of line, as there. The roots above B are
+// first ranked by their FP32 seeds and FP32 departure Gibbs energies; when one root is lower
+// by more than 1e-4 (FP32 errors are ~1e-6 there) and no seed lies within 1e-5 of B, only
+// that root is polished. Otherwise every root is polished and compared in double-float.
 __device__ __noinline__ f2 select_Z3_df(f2 A, f2 B, f2 c2, f2 c1, f2 c0, f2 c23, float Pf,
                                         float Qf, const f2* lt, int& status) {
   const float m = (Pf < 0.0f) ? 2.0f * sqrtf(-Pf / 3.0f) : 0.0f;
   float cphi = (Pf < 0.0f) ? (3.0f * Qf / (2.0f * Pf)) * sqrtf(-3.0f / Pf) : 0.0f;
   cphi = fminf(fmaxf(cphi, -1.0f), 1.0f);
   const float phi = acosf(cphi) * (1.0f / 3.0f);
+  {
+    float tbest = 0.0f, g1 = __int_as_float(0x7f800000), g2 = g1;
+    bool clear = true;
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+      const float tk = m * cosf(phi - 2.0943951023931955f * (float)k);
+      const float zk = tk - c23.h;
+      if (fabsf(zk - B.h) <= 1e-5f * fabsf(B.h)) clear = false;
+      if (zk > B.h) {
+        const float g = g_dep_f(zk, A.h, B.h);
+        if (!(g == g)) clear = false;
+        if (g < g1) {
+          g2 = g1;
+          g1 = g;
+          tbest = tk;
+        } else if (g < g2) {
+          g2 = g;
+        }
+      }
+    }
+    if (clear && g1 < g2 - 1e-4f) {
+      f2 Z = f2_sub(f2{tbest, 0.0f}, c23);
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) Z = cubic_step_df(Z, c2, c1, c0);
+      if (!f2_gt(Z, B)) status |= kCellNoRoot;
+      return Z;
+    }
+  }
   f2 best = f2{__int_as_float(0x7fc00000), 0.0f};
   f2 gbest = f2{__int_as_float(0x7f800000), 0.0f};
   bool have = false;
