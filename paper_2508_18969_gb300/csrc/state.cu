@@ -855,24 +855,29 @@ df_status df_chem_step_host(df_state* s, int64_t n_cells, double dt, double* T, 
     return run_step(s, n_cells, dt, dT, dp, dY, ldY, dst, nullptr, (cudaStream_t)stream, nullptr);
   }
   // Chunk plan. As asked: equal chunks of chunk_cells. Automatic: a short first and last chunk
-  // (1/16 of the cells, at least 32768), so that only a small upload and a small download are
-  // not hidden behind a step, and the cells between them in as few chunks as the batch allows
-  // (at least two), whose steps run at the long-batch rate.
+  // (1/32 of the cells, at least 32768), so that only a small upload and a small download are
+  // not hidden behind a step; then ramp chunks of 3/16 of the cells, whose steps are long
+  // enough to hide the upload of the chunk after them (and, at the end, the download of the
+  // chunk before them), the copies running at about a quarter of the step's cells/s; and the
+  // cells between them in as few chunks as the batch allows, at the long-batch rate.
   std::vector<int64_t> plan;
   if (chunk_cells > 0) {
     const int64_t c = std::min(chunk_cells, s->cap);
     for (int64_t c0 = 0; c0 < n_cells; c0 += c) plan.push_back(std::min(c, n_cells - c0));
   } else {
-    const int64_t edge = std::min(s->cap, std::max<int64_t>(32768, round_up((n_cells + 15) / 16, 128)));
-    if (n_cells <= 4 * edge) {
+    const int64_t edge = std::min(s->cap, std::max<int64_t>(32768, round_up((n_cells + 31) / 32, 128)));
+    const int64_t ramp = std::min(s->cap, std::max<int64_t>(32768, round_up((3 * n_cells + 15) / 16, 128)));
+    if (n_cells <= 2 * edge + 3 * ramp) {
       const int64_t c = std::min(s->cap, std::max<int64_t>(32768, round_up((n_cells + 3) / 4, 128)));
       for (int64_t c0 = 0; c0 < n_cells; c0 += c) plan.push_back(std::min(c, n_cells - c0));
     } else {
-      const int64_t mid = n_cells - 2 * edge;
-      const int64_t k = std::max<int64_t>(2, (mid + s->cap - 1) / s->cap);
+      const int64_t mid = n_cells - 2 * edge - 2 * ramp;
+      const int64_t k = (mid + s->cap - 1) / s->cap;
       const int64_t m = round_up((mid + k - 1) / k, 128);
       plan.push_back(edge);
+      plan.push_back(ramp);
       for (int64_t c0 = 0; c0 < mid; c0 += m) plan.push_back(std::min(m, mid - c0));
+      plan.push_back(ramp);
       plan.push_back(edge);
     }
   }
