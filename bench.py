@@ -195,9 +195,9 @@ MEASURED_TRAFFIC = {
     ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e83bc91ba940bed", 4750.5),
     ("layer2", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e83bc91ba940bed", 2340.2),
     ("layer3", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "3e83bc91ba940bed", 1062.6),
-    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "2641219730b58010", 293.1,
+    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "2480938820fdffc9", 294.6,
                                         _EOS_OTHER),
-    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "2641219730b58010", 548.3,
+    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "2480938820fdffc9", 548.0,
                                          _EOS_OTHER),
     # one block Gauss-Seidel sweep (gs_rhs_kernel + gs_sweep_kernel), per cell, FP64, 512 cells
     # per block row (profiles/solver_kernels_mesh-2m.md)
@@ -411,14 +411,14 @@ def measure_peaks_live(torch, dev):
 # MEASURED_TRAFFIC).
 MEASURED_PIPES = {
     # profiles/eos_kernels_layer1d-30sp-512k_bf16.md (full capture, 512K rows, first step)
-    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "2641219730b58010",
+    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "2480938820fdffc9",
                                         {"binding": "issue (FP32 double-float arithmetic)",
-                                         "fma_pipe": 0.437, "alu_pipe": 0.243, "fp64_pipe": 0.006,
-                                         "issue_active": 0.688, "warps_per_sm": 18.8}, _EOS_OTHER),
-    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "2641219730b58010",
+                                         "fma_pipe": 0.446, "alu_pipe": 0.224, "fp64_pipe": 0.006,
+                                         "issue_active": 0.679, "warps_per_sm": 18.8}, _EOS_OTHER),
+    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "2480938820fdffc9",
                                          {"binding": "issue (FP32 double-float arithmetic)",
-                                          "fma_pipe": 0.290, "alu_pipe": 0.420, "fp64_pipe": 0.014,
-                                          "issue_active": 0.677, "warps_per_sm": 19.1}, _EOS_OTHER),
+                                          "fma_pipe": 0.297, "alu_pipe": 0.367, "fp64_pipe": 0.014,
+                                          "issue_active": 0.656, "warps_per_sm": 18.9}, _EOS_OTHER),
 }
 
 

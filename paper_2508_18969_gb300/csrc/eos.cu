@@ -32,6 +32,7 @@ namespace {
 constexpr double kSQ2 = 1.41421356237309504880;
 constexpr double kInvR = 1.0 / kR;
 constexpr int kThreads = 128;
+constexpr int kJacThreads = 64;  // the Jacobian's EoS kernel
 constexpr int kPreBlocks = 5;    // resident blocks per SM the register budget is sized for
 constexpr int kPostBlocks = 5;
 constexpr int kCellNotConverged = 1;
@@ -144,7 +145,8 @@ __device__ __forceinline__ double drcp(double x) {
 }
 
 // Mixture coefficients of one composition (a1, a2 and the ideal-gas part of a4), all sums in
-// double-float. ycol is this thread's column of mass fractions (entry k at ycol[k * blockDim.x]).
+// double-float. ycol is this thread's column of mass fractions (entry k at ycol[k * STRIDE], STRIDE
+// the block's threads).
 // Symmetric quadratic forms with K_ii = 1, ys_i = Y_i s_i / W_i, yr_i = Y_i r_i / W_i:
 //   F0 = sum_ij K_ij ys_i ys_j = sum_i ys_i (ys_i + 2 P_i),  P_i = sum_{j>i} Ks_ij Y_j,
 //   F1 = sum_ij K_ij ys_i yr_j = sum_i ys_i (yr_i + Q_i) + yr_i P_i,  Q_i = sum_{j>i} Kr_ij Y_j,
@@ -185,8 +187,9 @@ __device__ __forceinline__ void forms_row(f2 ys, f2 yr, f2 P, f2 Q, float& F0h, 
   acc_off_fma(F2h, F2l, yr, f2_scale2(Q));
 }
 
+template <int STRIDE>
 __device__ void mixture_sums(const f2* ycol, int n, const SharedConsts& c, MixSums& ms) {
-  const int stride = blockDim.x;
+  constexpr int stride = STRIDE;   // threads per block: the column's entries are that far apart
   // The O(n) sums (1/W, b/W and the six enthalpy coefficients, species-table columns 0 and 3..9)
   // take offset accumulators too, with bounds Bq = sum_j |Y_j| |q_j| from the same pass.
   float Bs = 0.f, Br = 0.f, Bq[8];
@@ -270,9 +273,10 @@ __device__ void mixture_sums(const f2* ycol, int n, const SharedConsts& c, MixSu
   ms.F2 = F2;
 }
 
+template <int STRIDE>
 __device__ void mixture(const f2* ycol, int n, const SharedConsts& c, Mixture& m) {
   MixSums s;
-  mixture_sums(ycol, n, c, s);
+  mixture_sums<STRIDE>(ycol, n, c, s);
   const double invd = f2_to(s.inv);
   const double Wm = drcp(invd);
   const double W2 = Wm * Wm;
@@ -310,9 +314,10 @@ __device__ __forceinline__ void mix_df_final(const MixSums& s, MixDF& m) {
   m.kb = f2_rcp(f2_mul(m.bm, f2{kS2h, kS2l}));
 }
 
+template <int STRIDE>
 __device__ void mixture_df(const f2* ycol, int n, const SharedConsts& c, MixDF& m) {
   MixSums s;
-  mixture_sums(ycol, n, c, s);
+  mixture_sums<STRIDE>(ycol, n, c, s);
   mix_df_final(s, m);
 }
 
@@ -367,8 +372,9 @@ __device__ __forceinline__ void species_row_post(const SharedConsts& c, int i, f
   }
 }
 
+template <int STRIDE>
 __device__ void mixture_post(const f2* ycol, int n, const SharedConsts& c, MixDF& m) {
-  const int stride = blockDim.x;
+  constexpr int stride = STRIDE;
   // the ten O(n) sums over the species table take offset accumulators, as in mixture()
   float Bq[kSpcStride];
 #pragma unroll
@@ -942,7 +948,7 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams
     for (int k = 0; k < n; ++k) {
       const double yd = Y[k * ldY + cell];
       finite = finite && d_finite(yd);
-      ycol[k * blockDim.x] = f2_from(yd);
+      ycol[k * kThreads] = f2_from(yd);
       if (xr && !xvec) {
         const float y = fmaxf(d_to_f_trunc(yd), 0.0f);
         const float bc = (y > 0.0f) ? (exp2f(lam * log2f(y)) - 1.0f) * ilam : -ilam;
@@ -960,7 +966,7 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams
     double h = __longlong_as_double(0x7ff8000000000000LL), Z = h;
     if (finite) {
       MixDF m;
-      mixture_df(ycol, n, c, m);
+      mixture_df<kThreads>(ycol, n, c, m);
       const f2 Td = f2_from(Tc), pd = f2_from(pc);
       const PRPointDF q = pr_point_df<false>(m, Td, pd, false, c.lt2, st);
       Z = f2_to_int(q.Z);
@@ -982,7 +988,7 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams
 #pragma unroll
         for (int k = 0; k < NM; ++k) {
           if (k < n) {
-            const float y = fmaxf(ycol[k * blockDim.x].h, 0.0f);
+            const float y = fmaxf(ycol[k * kThreads].h, 0.0f);
             const float bc = (y > 0.0f) ? (exp2f(lam * log2f(y)) - 1.0f) * ilam : -ilam;
             x_put(w, 2 + k, to_x<XT>((bc - mf[2 + k]) * isf[2 + k], x_scale));
           }
@@ -1051,7 +1057,7 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
   extern __shared__ __align__(16) double sm[];
   const SharedConsts c = load_consts_post(P, sm);
   f2* ycol = reinterpret_cast<f2*>(sm + consts_words_post(P)) + threadIdx.x;
-  const int stride = blockDim.x;
+  constexpr int stride = kThreads;
   const int64_t nrow = valid_rows(rows);
   const int n = P.n, K0 = P.K0;
   const float* out_mean = c.normf + 2 * K0;
@@ -1120,7 +1126,7 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
       const f2 iS = f2_rcp(S);
       for (int k = 0; k < n; ++k) ycol[k * stride] = f2_mul(ycol[k * stride], iS);
       MixDF m;
-      mixture_post(ycol, n, c, m);
+      mixture_post<kThreads>(ycol, n, c, m);
       Tn = f2_to_int(solve_T_df(m, f2_from(pc), f2_from(h0c), Told, P, c.lt2, iters, st));
     }
     if (st == 0 && src.omega) {
@@ -1159,9 +1165,9 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) props_kernel(EosParams P
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncell;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double Tc = T[i], pc = p[i];
-    for (int k = 0; k < n; ++k) ycol[k * blockDim.x] = f2_from(Y[k * ldY + i]);
+    for (int k = 0; k < n; ++k) ycol[k * kThreads] = f2_from(Y[k * ldY + i]);
     Mixture m;
-    mixture(ycol, n, c, m);
+    mixture<kThreads>(ycol, n, c, m);
     int st = 0;
     const PRPoint q = pr_point<false>(m, Tc, pc, cp != nullptr, c.lnt, st);
     if (rho) rho[i] = pc / (m.inv * q.Z * kR * Tc);
@@ -1241,7 +1247,7 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) transport_kernel(EosPara
   const SharedConsts c = load_consts(P, sm);
   f2* ycol = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
   const int n = P.n, nn = P.n * P.n;
-  const int stride = blockDim.x;
+  constexpr int stride = kThreads;
   const float* __restrict__ tp = P.tpair;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncell;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1255,7 +1261,7 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) transport_kernel(EosPara
     double m_out = __longlong_as_double(0x7ff8000000000000LL), l_out = m_out, a_out = m_out;
     if (finite) {
       Mixture m;
-      mixture(ycol, n, c, m);
+      mixture<kThreads>(ycol, n, c, m);
       int st = 0;
       const PRPoint q = pr_point<false>(m, Tk, pk, true, c.lnt, st);
       const double rho = pk / (m.inv * q.Z * kR * Tk);            // kg/m^3
@@ -1468,13 +1474,13 @@ __global__ void jac_tangent0_kernel(int64_t ncell, int ntan, int N1, const float
 // its status in cst;
 // jac_assemble_kernel, a warp per cell and a lane per direction t, forms the columns.
 template <int NM>
-__global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell, int64_t cell0,
+__global__ void __launch_bounds__(kJacThreads) jac_post_kernel(EosParams P, int64_t ncell, int64_t cell0,
     const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
     int64_t ldY, const float* __restrict__ O, int64_t ldo, const double* __restrict__ h0,
     double* __restrict__ dTn, double* __restrict__ scr, int32_t* __restrict__ cst) {
   extern __shared__ __align__(16) double sm[];
   const SharedConsts c = load_consts(P, sm);
-  const int stride = blockDim.x;
+  constexpr int stride = kJacThreads;
   // shared memory holds the per-thread columns read in O(n^2) loops (the double-float
   // composition of the mixing sums, the two weighted columns of h_grad); the O(n) ones live
   // in the cell's scratch row, which is also how they reach jac_assemble_kernel
@@ -1512,7 +1518,7 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
       // (T, Y): cp and dh/dY, parked in dTn (its entries are final after the column loop)
       Mixture m0;
       for (int k = 0; k < n; ++k) ws[k * stride] = f2_from(Yk[k]);
-      mixture(ws, n, c, m0);
+      mixture<kJacThreads>(ws, n, c, m0);
       const PRPoint q0 = pr_point<false>(m0, Tc, pc, true, c.lnt, st);
       if (dTc) {
         dTc[0] = cp_ig(m0, Tc) + q0.cp_dep * m0.inv;
@@ -1541,7 +1547,7 @@ __global__ void __launch_bounds__(64) jac_post_kernel(EosParams P, int64_t ncell
         }
         Mixture m1;
         for (int k = 0; k < n; ++k) ws[k * stride] = f2_from(Yn[k]);
-        mixture(ws, n, c, m1);
+        mixture<kJacThreads>(ws, n, c, m1);
         int iters = 0;
         const double Tn = solve_T<false>(m1, pc, h0c, Tc, P, c.lnt, iters, st);
         if (st == 0) {
@@ -1809,7 +1815,7 @@ cudaError_t launch_jac_post(const EosParams& P, int64_t ncell, int64_t cell0, co
                             int64_t ldo, const float* dO, int64_t lddo, const double* h0, float* J,
                             double* dTn, double* scr, int32_t* cst, cudaStream_t st) {
   if (ncell <= 0) return cudaSuccess;
-  constexpr int kJT = 64;
+  constexpr int kJT = kJacThreads;
   const int64_t blocks = (ncell + kJT - 1) / kJT;
   const int g = (int)(blocks < 4096 ? blocks : 4096);
   if (P.n <= 16) {
