@@ -137,7 +137,7 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 }
 
 // Instruction descriptor: FP32 accumulator, K-major A and B, M = 128 (256 for a CTA pair),
-// N = BN.
+// N = BN (N / 8 in bits 17..22; BN = 0 leaves the field for a width chosen at run time).
 template <bool FP8, int BN, int MROWS = BM>
 __device__ constexpr uint32_t idesc() {
   return (1u << 4) | (FP8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(BN >> 3) << 17) |
@@ -342,9 +342,12 @@ constexpr int out_bytes(int outk) { return outk == kXF32 ? 4 : (outk == kXBF16 ?
 
 template <int BN, int OUTK, bool PAIR = false>
 struct Cfg {
-  // per warp: two staging buffers of 32 rows x 32 columns (the GELU' of kModeStoreG is BF16,
-  // no wider than the output)
-  static constexpr int kStageOut = 2 * 32 * 32 * out_bytes(OUTK);
+  // Per warp: staging buffers of 32 rows x 32 columns (the GELU' of kModeStoreG is BF16, no
+  // wider than the output). Two let a warp fill one while the other's store still reads it.
+  // A pair tile streams several k-blocks per accumulator, so its epilogue has time to spare,
+  // and the operand ring is what sets its pace: with one buffer per warp the ring gains a stage.
+  static constexpr int kStgBufs = PAIR ? 1 : 2;
+  static constexpr int kStageOut = kStgBufs * 32 * 32 * out_bytes(OUTK);
   static constexpr int kBRows = PAIR ? BN / 2 : BN;   // rows of W this CTA holds per stage
   static constexpr int kStageBytes = (BM + kBRows) * kRowBytes;
   static constexpr int kStages0 = (kSmemLimit - 2048 - kEpiWarps * kStageOut) / kStageBytes;
@@ -398,15 +401,19 @@ __device__ __forceinline__ void bulk_commit() {
 __device__ __forceinline__ void bulk_wait_read1() {
   asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
 }
+// Waits until no bulk store group of this thread is still reading shared memory.
+__device__ __forceinline__ void bulk_wait_read0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
 __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
-// Quantises 32 values of row `lane` to OUTK, writes them into one of the warp's two staging
+// Quantises 32 values of row `lane` to OUTK, writes them into one of the warp's NBUF staging
 // buffers (32 rows x 32 columns, swizzled) and has lane 0 issue a TMA tensor store of the box
 // at (col0, m0); the tensor map clips rows and columns outside the output. A buffer is reused
-// only after the store issued from it two calls earlier has finished reading it.
-template <int OUTK>
+// only after the store issued from it NBUF calls earlier has finished reading it.
+template <int OUTK, int NBUF = 2>
 __device__ __forceinline__ void store_chunk(const float (&v)[32], const CUtensorMap* map,
                                             float out_scale, int64_t m0, int col0, uint8_t* stg2,
                                             int& buf, int lane) {
@@ -444,7 +451,10 @@ __device__ __forceinline__ void store_chunk(const float (&v)[32], const CUtensor
     }
   }
   uint8_t* stg = stg2 + buf * (32 * RB);
-  if (lane == 0) bulk_wait_read1();
+  if (lane == 0) {
+    if constexpr (NBUF == 1) bulk_wait_read0();
+    else bulk_wait_read1();
+  }
   __syncwarp();
   const int sw = swz<RB>(lane);
 #pragma unroll
@@ -456,13 +466,13 @@ __device__ __forceinline__ void store_chunk(const float (&v)[32], const CUtensor
     tma_store_2d(map, smem_u32(stg), col0, (int)m0);
     bulk_commit();
   }
-  buf ^= 1;
+  if constexpr (NBUF == 2) buf ^= 1;
 }
 
 // One 32-column chunk of the epilogue: per-channel scale, bias, GELU (or the row-group scale
 // of a tangent layer), then quantise and store; kModeStoreG also stores GELU'(z). With
 // SMEM_BIAS the bias pointer addresses shared memory (a plain load instead of ld.global.nc).
-template <int OUTK, int ACT, bool SCALE, int MODE, bool SMEM_BIAS = false>
+template <int OUTK, int ACT, bool SCALE, int MODE, bool SMEM_BIAS = false, int NBUF = 2>
 __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const TcArgs& g,
                                                const CUtensorMap* tmO, const CUtensorMap* tmG,
                                                int64_t M, int64_t m0, int col0, uint8_t* stg,
@@ -486,7 +496,7 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const Tc
         v[8 * u + 2 * e + 1] = __uint_as_float(r[8 * u + 2 * e + 1]) * f.y;
       }
     }
-    store_chunk<OUTK>(v, tmO, g.out_scale, m0, col0, stg, buf, lane);
+    store_chunk<OUTK, NBUF>(v, tmO, g.out_scale, m0, col0, stg, buf, lane);
     return;
   }
   const float4* b4 = reinterpret_cast<const float4*>(g.bias + col0);  // zero padded to 32
@@ -513,7 +523,7 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const Tc
     }
     v[4 * u] = z0.x; v[4 * u + 1] = z0.y; v[4 * u + 2] = z1.x; v[4 * u + 3] = z1.y;
   }
-  store_chunk<OUTK>(v, tmO, g.out_scale, m0, col0, stg, buf, lane);
+  store_chunk<OUTK, NBUF>(v, tmO, g.out_scale, m0, col0, stg, buf, lane);
   if (MODE == kModeStoreG) {
     // second pass over the same accumulators: GELU'(z), so only one 32-value array is live
 #pragma unroll
@@ -525,9 +535,62 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&r)[32], const Tc
           make_float2(__uint_as_float(r[4 * u + 2]), __uint_as_float(r[4 * u + 3])), make_float2(b.z, b.w)));
       v[4 * u] = g0.x; v[4 * u + 1] = g0.y; v[4 * u + 2] = g1.x; v[4 * u + 3] = g1.y;
     }
-    store_chunk<kXBF16>(v, tmG, 1.0f, m0, col0, stg, buf, lane);
+    store_chunk<kXBF16, NBUF>(v, tmG, 1.0f, m0, col0, stg, buf, lane);
   }
 }
+
+// The grid stride of the work items in whole m units (q), n positions (r) and q mod tiles_n
+// (rot). One copy per CTA, in shared memory: the epilogue warps have no registers to spare.
+struct WalkStep {
+  uint32_t q;
+  int r, rot;
+};
+
+// Walks the work items t = first, first + step, ... of one CTA (or CTA pair). Item t lies in
+// split t / (units_m tiles_n), m unit mu = (t mod units_m tiles_n) / tiles_n and n position
+// r = t mod tiles_n; its n tile is r rotated by the m unit, (r + mu) mod tiles_n, so that the
+// items one CTA visits a grid stride apart cycle through the n tiles (whose MMA widths differ
+// when the last one is narrowed). The position advances by additions and compares: divisions
+// per item cost the layers with short k loops a few per cent. Item counts fit in 32 bits (the
+// launch checks).
+struct ItemWalk {
+  uint32_t mu;          // m unit within the split
+  int split, r, rot;    // split, n position in the m unit, mu mod tiles_n
+  __device__ __forceinline__ ItemWalk(uint32_t first, uint32_t units_m, int tiles_n) {
+    if (units_m == 0) {
+      mu = 0;
+      split = 0x7FFFFFFF;   // no items
+      r = rot = 0;
+    } else {
+      const uint32_t tiles_mn = units_m * (uint32_t)tiles_n;
+      split = (int)(first / tiles_mn);
+      const uint32_t rem = first - (uint32_t)split * tiles_mn;
+      mu = rem / (uint32_t)tiles_n;
+      r = (int)(rem - mu * (uint32_t)tiles_n);
+      rot = (int)(mu % (uint32_t)tiles_n);
+    }
+  }
+  __device__ __forceinline__ int nt(int tiles_n) const {
+    const int x = r + rot;
+    return x < tiles_n ? x : x - tiles_n;
+  }
+  __device__ __forceinline__ void next(const WalkStep& st, uint32_t units_m, int tiles_n) {
+    mu += st.q;
+    r += st.r;
+    rot += st.rot;
+    if (rot >= tiles_n) rot -= tiles_n;
+    if (r >= tiles_n) {
+      r -= tiles_n;
+      ++mu;
+      if (++rot == tiles_n) rot = 0;
+    }
+    if (mu >= units_m) {   // into a later split
+      split += (int)(mu / units_m);
+      mu %= units_m;
+      rot = (int)(mu % (uint32_t)tiles_n);
+    }
+  }
+};
 
 template <bool FP8, int BN, int OUTK, int ACT, bool SCALE, int MODE, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
@@ -547,6 +610,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
   // bars: full[S], empty[S], tfull[2], tempty[2], drain
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
+  __shared__ WalkStep walk_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * C::kStages;
@@ -559,6 +623,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
 
   if (threadIdx.x == 0) {
     abort_sh = 0;
+    const uint32_t step = PAIR ? (gridDim.x >> 1) : gridDim.x, tn = (uint32_t)((g.N + BN - 1) / BN);
+    walk_sh.q = step / tn;
+    walk_sh.r = (int)(step - walk_sh.q * tn);
+    walk_sh.rot = (int)(walk_sh.q % tn);
     for (int s = 0; s < C::kStages; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
@@ -598,17 +666,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
   // work items: (split, m tile, n tile), or for a pair (split, pair of m tiles, n tile)
   const int64_t units_m = PAIR ? (tiles_m + 1) / 2 : tiles_m;
   const int tiles_n = (g.N + BN - 1) / BN;
-  const int64_t tiles_mn = units_m * tiles_n;
-  const int64_t ntiles = tiles_mn * g.ksplit;
+  const uint32_t units_m32 = (uint32_t)units_m;
   const int kblocks = (g.K * (FP8 ? 1 : 2) + kRowBytes - 1) / kRowBytes;
   const int kelems = kRowBytes / (FP8 ? 1 : 2);
   const int kbs = (kblocks + g.ksplit - 1) / g.ksplit;   // k-blocks per split (host: none empty)
-  const int64_t t_first = PAIR ? (blockIdx.x >> 1) : blockIdx.x;
-  const int64_t t_step = PAIR ? (gridDim.x >> 1) : gridDim.x;
-  // first row of this CTA's part of work item tt
-  auto tile_m0 = [&](int64_t tt) -> int64_t {
-    return PAIR ? ((tt / tiles_n) * 2 + rank) * BM : (tt / tiles_n) * BM;
-  };
+  const uint32_t t_first = PAIR ? (blockIdx.x >> 1) : blockIdx.x;
+  // first row of this CTA's part of a work item in m unit mu
+  auto tile_m0 = [&](int64_t mu) -> int64_t { return PAIR ? (mu * 2 + rank) * BM : mu * BM; };
+  // MMA width of n tile nt: the last tile covers only the columns left, rounded up to 16 (the N
+  // granule at M = 128 and M = 256); its columns past N are clipped by the output tensor map
+  auto tile_w = [&](int nt) -> int { return min(BN, (g.N - nt * BN + 15) & ~15); };
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
@@ -616,11 +683,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
     uint32_t it = 0;
     bool ok = true;
-    for (int64_t t = t_first; t < ntiles && ok; t += t_step) {
-      const int64_t tt = t % tiles_mn;
-      const int kb0 = (int)(t / tiles_mn) * kbs, kb1 = min(kblocks, kb0 + kbs);
-      const int m0 = (int)tile_m0(tt);
-      const int n0 = (int)(tt % tiles_n) * BN + (int)rank * C::kBRows;
+    for (ItemWalk w(t_first, units_m32, tiles_n); w.split < g.ksplit && ok;
+         w.next(walk_sh, units_m32, tiles_n)) {
+      const int kb0 = w.split * kbs, kb1 = min(kblocks, kb0 + kbs);
+      const int m0 = (int)tile_m0(w.mu);
+      // a pair splits the tile's MMA width between its CTAs: each holds half of the W rows
+      const int nt = w.nt(tiles_n);
+      const int n0 = nt * BN + (PAIR ? (int)rank * (tile_w(nt) >> 1) : 0);
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % C::kStages;
         const uint32_t ph = (it / C::kStages) & 1;
@@ -668,11 +737,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     }
   } else if (warp == 1 && lane == 0 && rank == 0) {
     // ---------------- MMA issuer ----------------
-    constexpr uint32_t id = idesc<FP8, BN, PAIR ? 2 * BM : BM>();
+    constexpr uint32_t id0 = idesc<FP8, 0, PAIR ? 2 * BM : BM>();
     uint32_t it = 0, j = 0;
     bool ok = true;
-    for (int64_t t = t_first; t < ntiles && ok; t += t_step, ++j) {
-      const int kb0 = (int)(t / tiles_mn) * kbs, kb1 = min(kblocks, kb0 + kbs);
+    for (ItemWalk w(t_first, units_m32, tiles_n); w.split < g.ksplit && ok;
+         w.next(walk_sh, units_m32, tiles_n), ++j) {
+      const int kb0 = w.split * kbs, kb1 = min(kblocks, kb0 + kbs);
+      const uint32_t id = id0 | ((uint32_t)(tile_w(w.nt(tiles_n)) >> 3) << 17);
       const int a = j & 1;
       const uint32_t aph = (j >> 1) & 1;
       if (PAIR ? !mbar_wait_cluster(tempty0 + 8 * a, aph ^ 1, abort, g.err, g.budget, g.suspend)
@@ -723,16 +794,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmO) : "memory");
     }
     uint32_t j = 0;
-    for (int64_t t = t_first; t < ntiles; t += t_step, ++j) {
+    for (ItemWalk w(t_first, units_m32, tiles_n); w.split < g.ksplit;
+         w.next(walk_sh, units_m32, tiles_n), ++j) {
       const int a = j & 1;
       const uint32_t aph = (j >> 1) & 1;
       if (!mbar_wait(tfull0 + 8 * a, aph, abort, g.err, g.budget, g.suspend)) break;
       tc_fence_after();
-      const int64_t tt = t % tiles_mn;
-      const int64_t mt = tile_m0(tt);
+      const int64_t mt = tile_m0(w.mu);
       // row of the output: the tile's rows, shifted to this split's partial product
-      const int64_t m0 = mt + q * 32 + (t / tiles_mn) * g.split_rows;
-      const int n0 = (int)(tt % tiles_n) * BN;
+      const int64_t m0 = mt + q * 32 + w.split * g.split_rows;
+      const int n0 = w.nt(tiles_n) * BN;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + a * C::kAccStride;
       // chunks c = 32 slot + kChunkStride i; TMEM loads run one chunk ahead of the math,
       // except in kModeStoreG, whose two stores per chunk leave no registers for a second
@@ -744,7 +815,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
           tmem_ld32(tbase + c0, r0);
           tmem_wait(r0);
           if (n0 + c0 < g.N)
-            epilogue_chunk<OUTK, ACT, SCALE, MODE>(r0, g, &tmO, &tmG, M, m0, n0 + c0, stg, buf, lane);
+            epilogue_chunk<OUTK, ACT, SCALE, MODE, false, C::kStgBufs>(r0, g, &tmO, &tmG, M, m0,
+                                                                       n0 + c0, stg, buf, lane);
         }
         c0 = BN;
       }
@@ -754,12 +826,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
         const int c1 = c0 + kChunkStride;
         if (c1 < BN) tmem_ld32(tbase + c1, r1);
         if (n0 + c0 < g.N)
-          epilogue_chunk<OUTK, ACT, SCALE, MODE>(r0, g, &tmO, &tmG, M, m0, n0 + c0, stg, buf, lane);
+          epilogue_chunk<OUTK, ACT, SCALE, MODE, false, C::kStgBufs>(r0, g, &tmO, &tmG, M, m0,
+                                                                     n0 + c0, stg, buf, lane);
         if (c1 >= BN) break;
         tmem_wait(r1);
         if (c1 + kChunkStride < BN) tmem_ld32(tbase + c1 + kChunkStride, r0);
         if (n0 + c1 < g.N)
-          epilogue_chunk<OUTK, ACT, SCALE, MODE>(r1, g, &tmO, &tmG, M, m0, n0 + c1, stg, buf, lane);
+          epilogue_chunk<OUTK, ACT, SCALE, MODE, false, C::kStgBufs>(r1, g, &tmO, &tmG, M, m0,
+                                                                     n0 + c1, stg, buf, lane);
       }
       tc_fence_before();
       __syncwarp();
@@ -858,8 +932,12 @@ cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream
   if (num_sms <= 0) return cudaSuccess;  // attribute set-up only
   const CUtensorMap& tmG = L.mode == kModeStoreG ? L.tmG : L.tmO;
   const int64_t tiles_n = (L.N + BN - 1) / BN;
+  // the kernel walks its work items with 32-bit counts
+  const int64_t items = (PAIR ? (a.rows.nmax + 2 * BM - 1) / (2 * BM) : (a.rows.nmax + BM - 1) / BM) *
+                        tiles_n * a.ksplit;
+  if (items > 0x7FFFFFFF) return cudaErrorInvalidValue;
   if constexpr (PAIR) {
-    const int64_t units = ((a.rows.nmax + 2 * BM - 1) / (2 * BM)) * tiles_n * a.ksplit;
+    const int64_t units = items;
     const int64_t cap = std::min<int64_t>(max_clusters, num_sms / 2);
     const int64_t nc = std::max<int64_t>(1, std::min<int64_t>(units, cap));
     cudaLaunchAttribute at[1];
@@ -876,7 +954,7 @@ cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, L.tmA, L.tmB, L.tmO, tmG, a);
   } else {
-    const int64_t tiles = ((a.rows.nmax + BM - 1) / BM) * tiles_n * a.ksplit;
+    const int64_t tiles = items;
     const unsigned grid = (unsigned)(tiles < num_sms ? (tiles > 0 ? tiles : 1) : num_sms);
     kern<<<grid, kThreads, C::kSmemBytes, st>>>(L.tmA, L.tmB, L.tmO, tmG, a);
     return cudaGetLastError();
