@@ -191,10 +191,10 @@ _EOS_OTHER = (("// -------------------------------------------------------------
               ("cudaError_t launch_jac_scale(", "cudaError_t launch_eos_post("),
               ("cudaError_t launch_transport(", "}  // namespace dfgb"))
 MEASURED_TRAFFIC = {
-    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "fbdf61e2f31d3e59", 3158.0),
-    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "fbdf61e2f31d3e59", 4757.4),
-    ("layer2", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "fbdf61e2f31d3e59", 2346.5),
-    ("layer3", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "fbdf61e2f31d3e59", 1068.1),
+    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "5f2260ea2ce1b739", 3157.3),
+    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "5f2260ea2ce1b739", 4752.1),
+    ("layer2", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "5f2260ea2ce1b739", 2340.2),
+    ("layer3", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "5f2260ea2ce1b739", 1061.8),
     ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "2480938820fdffc9", 294.6,
                                         _EOS_OTHER),
     ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "2480938820fdffc9", 548.0,

@@ -326,7 +326,7 @@ df_status df_graph_launch(df_graph* g, void* stream);
 void df_graph_destroy(df_graph* g);
 
 /* ---- tile-width autotuning of the tensor-core layers ----
- * df_autotune times every compiled tile (64, 128, 160, 224, 256 output columns per CTA for
+ * df_autotune times every compiled tile (64, 128, 160, 192, 224, 256 output columns per CTA for
  * hidden layers, and 160, 224, 256 on CTA pairs for hidden layers of more than one k-block of
  * 64 BF16 / 128 FP8 inputs; 32 and 64 for the read-out) of each network layer on n_rows rows of the
  * state's own buffers (<= 0 or above the batch capacity: the capacity), keeps the fastest and

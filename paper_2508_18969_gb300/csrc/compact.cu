@@ -1,7 +1,8 @@
 // a0: stable compaction of the reacting cells (T > T_react) into an ascending index list.
 // Three launches, no inter-block waiting: per-chunk counts (warp ballot + popc), one-block
 // exclusive scan of the chunk counts, then a scatter that ranks each reacting cell inside
-// its chunk with ballot/popc prefix sums. Cells are visited in the same order by the
+// its chunk with ballot/popc prefix sums. Both chunk passes load all of a thread's cells
+// before testing any, so a chunk costs one memory latency. Cells are visited in the same order by the
 // count and the scatter pass, so the list is in ascending cell order.
 #include "dfgb_internal.cuh"
 
@@ -21,16 +22,19 @@ __global__ void __launch_bounds__(kThreads) count_kernel(int64_t n, double thr,
   __shared__ int warp_tot[kWarps];
   const int64_t base = (int64_t)blockIdx.x * kChunk;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int mine = 0;
-#pragma unroll 4
+  // all of the thread's cells are loaded before any is tested: one memory latency per chunk
+  double t[kItems];
+#pragma unroll
   for (int j = 0; j < kItems; ++j) {
     const int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
-    bool a = false;
-    if (i < n) {
-      const double t = T[i];
-      a = reacts(t, thr);
-      if (status) status[i] = isfinite(t) ? 0 : kCellNonfinite;
-    }
+    t[j] = i < n ? T[i] : 0.0;
+  }
+  int mine = 0;
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
+    const bool a = i < n && reacts(t[j], thr);
+    if (status && i < n) status[i] = isfinite(t[j]) ? 0 : kCellNonfinite;
     mine += __popc(__ballot_sync(0xffffffffu, a)) * (lane == 0);
   }
   if (lane == 0) warp_tot[warp] = mine;
@@ -70,26 +74,39 @@ __global__ void __launch_bounds__(1024) scan_kernel(int64_t nb, const int64_t* _
 
 __global__ void __launch_bounds__(kThreads) scatter_kernel(int64_t n, double thr,
     const double* __restrict__ T, const int64_t* __restrict__ offsets, int32_t* __restrict__ idx) {
-  __shared__ int warp_tot[kWarps];
+  // reacting cells per (pass j, warp w) of the chunk; the chunk's cells are visited pass by
+  // pass, warp by warp, lane by lane, the order of the count pass
+  __shared__ int warp_tot[kItems][kWarps];
   const int64_t base = (int64_t)blockIdx.x * kChunk;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t run = offsets[blockIdx.x];
+  double t[kItems];
+#pragma unroll
   for (int j = 0; j < kItems; ++j) {
     const int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
-    const bool a = (i < n) && reacts(T[i], thr);
-    const unsigned m = __ballot_sync(0xffffffffu, a);
-    if (lane == 0) warp_tot[warp] = __popc(m);
-    __syncthreads();
+    t[j] = i < n ? T[i] : 0.0;
+  }
+  unsigned m[kItems];
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
+    m[j] = __ballot_sync(0xffffffffu, i < n && reacts(t[j], thr));
+    if (lane == 0) warp_tot[j][warp] = __popc(m[j]);
+  }
+  __syncthreads();
+  int64_t run = offsets[blockIdx.x];
+  const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
     int before = 0, total = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
-      const int c = warp_tot[w];
+      const int c = warp_tot[j][w];
       before += (w < warp) ? c : 0;
       total += c;
     }
-    if (a) idx[run + before + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
+    if ((m[j] >> lane) & 1u)
+      idx[run + before + __popc(m[j] & below)] = (int32_t)(base + (int64_t)j * kThreads + threadIdx.x);
     run += total;
-    __syncthreads();
   }
 }
 

@@ -990,6 +990,7 @@ cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStrea
         case 64: return launch_bn<false, 64, kXBF16, kActTanh, kModeStoreG>(L, a, num_sms, st);
         case 128: return launch_bn<false, 128, kXBF16, kActTanh, kModeStoreG>(L, a, num_sms, st);
         case 160: return launch_bn<false, 160, kXBF16, kActTanh, kModeStoreG>(L, a, num_sms, st);
+        case 192: return launch_bn<false, 192, kXBF16, kActTanh, kModeStoreG>(L, a, num_sms, st);
         case 224: return launch_bn<false, 224, kXBF16, kActTanh, kModeStoreG>(L, a, num_sms, st);
         case 256: return launch_bn<false, 256, kXBF16, kActTanh, kModeStoreG>(L, a, num_sms, st);
         default: return cudaErrorInvalidValue;
@@ -999,6 +1000,7 @@ cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStrea
       case 64: return launch_bn<false, 64, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
       case 128: return launch_bn<false, 128, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
       case 160: return launch_bn<false, 160, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
+      case 192: return launch_bn<false, 192, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
       case 224: return launch_bn<false, 224, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
       case 256: return launch_bn<false, 256, kXBF16, kActNone, kModeRowG>(L, a, num_sms, st);
       default: return cudaErrorInvalidValue;
@@ -1038,6 +1040,7 @@ cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStrea
       case 64: return launch_bn<false, 64, kXBF16, kActTable>(L, a, num_sms, st);
       case 128: return launch_bn<false, 128, kXBF16, kActTable>(L, a, num_sms, st);
       case 160: return launch_bn<false, 160, kXBF16, kActTable>(L, a, num_sms, st);
+      case 192: return launch_bn<false, 192, kXBF16, kActTable>(L, a, num_sms, st);
       case 224: return launch_bn<false, 224, kXBF16, kActTable>(L, a, num_sms, st);
       case 256: return launch_bn<false, 256, kXBF16, kActTable>(L, a, num_sms, st);
       default: return cudaErrorInvalidValue;
@@ -1049,6 +1052,7 @@ cudaError_t launch_fmt(const TcLayer& L, const TcArgs& a, int num_sms, cudaStrea
       case 64: return launch_bn<FP8, 64, HID, kActTanh>(L, a, num_sms, st);
       case 128: return launch_bn<FP8, 128, HID, kActTanh>(L, a, num_sms, st);
       case 160: return launch_bn<FP8, 160, HID, kActTanh>(L, a, num_sms, st);
+      case 192: return launch_bn<FP8, 192, HID, kActTanh>(L, a, num_sms, st);
       case 224: return launch_bn<FP8, 224, HID, kActTanh>(L, a, num_sms, st);
       case 256: return launch_bn<FP8, 256, HID, kActTanh>(L, a, num_sms, st);
       default: return cudaErrorInvalidValue;
@@ -1470,6 +1474,7 @@ int tc_stages(int BN, int out_kind, bool pair) {
     case 64: return pick(std::integral_constant<int, 64>{});
     case 128: return pick(std::integral_constant<int, 128>{});
     case 160: return pick(std::integral_constant<int, 160>{});
+    case 192: return pick(std::integral_constant<int, 192>{});
     case 224: return pick(std::integral_constant<int, 224>{});
     case 256: return pick(std::integral_constant<int, 256>{});
     default: return 0;

@@ -36,23 +36,24 @@ df_status cuda_fail(df_state* s, cudaError_t e, const char* where) {
               cudaGetErrorString(e));
 }
 
-// Tile of a tensor-core layer: BN output columns per CTA from {64, 128, 160, 224, 256} for
+// Tile of a tensor-core layer: BN output columns per CTA from {64, 128, 160, 192, 224, 256} for
 // hidden layers and {32, 64} for the read-out; hidden layers of more than one k-block may also
 // run on CTA pairs (BN from {160, 224, 256} | DF_TILE_PAIR: 256-row tiles, each CTA holding
 // half of the tile's weight rows). Cost per layer, fitted to measured tcgen05 times on this GPU:
 //   * one k-block (K <= 64 BF16, 128 FP8): the epilogue is the work; each tile costs the
-//     32-column chunks its busiest epilogue warp handles, plus half a chunk of fixed cost;
+//     32-column chunks its busiest epilogue warp handles, plus half a chunk of fixed cost (the
+//     last tile only the chunks of the columns left);
 //   * longer K: a tile costs the larger of its MMA work (0.97 BN) and the operand rows an SM
 //     streams per k-block (128 + BN/2 on a pair; 0.8 (128 + BN) on a single CTA, whose loads
 //     stream faster per row), x1.25 when the tile leaves the TMA ring fewer than four stages.
 //     On the 1600 -> 800 layer of 2^20 rows this orders the measured times of single 160, 224
 //     and pair 160, 224, 256 tiles (2.15, 1.91, 1.82, 1.73, 1.75 ms) within 7 %.
 int pick_tile(int N, int K, bool hidden, int out_kind, bool allow_pair) {
-  static const int hid[] = {256, 224, 160, 128, 64};
+  static const int hid[] = {256, 224, 192, 160, 128, 64};
   static const int last[] = {64, 32};
   static const int paired[] = {256, 224, 160};
   const int* cand = hidden ? hid : last;
-  const int nc = hidden ? 5 : 2;
+  const int nc = hidden ? 6 : 2;
   const bool one_kblock = K * (out_kind == kXFP8 ? 1 : 2) <= 128;
   const int epq = tc_epi_warps_per_quarter();
   int best = cand[nc - 1];
@@ -61,8 +62,9 @@ int pick_tile(int N, int K, bool hidden, int out_kind, bool allow_pair) {
     const double tiles = (double)((N + bn - 1) / bn);
     double cost;
     if (one_kblock) {
-      const int chunks = (bn + 31) / 32;
-      cost = tiles * ((chunks + epq - 1) / epq + 0.5);
+      auto busiest = [&](int cols) { return (double)(((cols + 31) / 32 + epq - 1) / epq) + 0.5; };
+      const int full = N / bn, rest = N - full * bn;
+      cost = full * busiest(bn) + (rest > 0 ? busiest(rest) : 0.0);
     } else {
       const double rows = pair ? 128.0 + bn / 2 : 0.8 * (128.0 + bn);
       cost = tiles * std::max<double>(0.97 * bn, rows) *
@@ -623,7 +625,7 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
       T.pair = (tile & DF_TILE_PAIR) != 0;
       if (const char* env = getenv("DFGB_BN")) {  // hidden-layer tile-width override (sweeps)
         const int v = atoi(env);
-        if (!last && (v == 64 || v == 128 || v == 160 || v == 224 || v == 256)) {
+        if (!last && (v == 64 || v == 128 || v == 160 || v == 192 || v == 224 || v == 256)) {
           T.BN = v;
           T.pair = false;
         }
@@ -1381,12 +1383,12 @@ df_status df_autotune(df_state* s, int64_t n_rows, const char* cache_path, void*
     int chosen = 0;
     for (auto& kv : cache)
       if (kv.first == key) chosen = kv.second;
-    static const int hid[] = {64, 128, 160, 224, 256, 160 | DF_TILE_PAIR, 224 | DF_TILE_PAIR,
-                              256 | DF_TILE_PAIR};
+    static const int hid[] = {64, 128, 160, 192, 224, 256, 160 | DF_TILE_PAIR,
+                              224 | DF_TILE_PAIR, 256 | DF_TILE_PAIR};
     static const int rd[] = {32, 64};
     const bool one_kblock = s->tcl[l].K * (int)elem_of(s->precision) <= 128;
     const int* cand = last ? rd : hid;
-    const int nc = last ? 2 : (one_kblock ? 5 : 8);
+    const int nc = last ? 2 : (one_kblock ? 6 : 9);
     bool known = false;
     for (int i = 0; i < nc; ++i) known = known || cand[i] == chosen;
     if (!known) {

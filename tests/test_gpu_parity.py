@@ -148,7 +148,7 @@ def test_mlp_fp32_vs_fp64(df, name, N):
 
 @pytest.mark.parametrize("name,N,bn", [("small-fp32-4k", 1000, None), ("layer1d-30sp-1m", 3000, None),
                                         ("layer1d-30sp-1m", 777, "160"), ("layer1d-30sp-1m", 777, "256"),
-                                        ("layer1d-30sp-1m", 777, "128")])
+                                        ("layer1d-30sp-1m", 777, "128"), ("layer1d-30sp-1m", 777, "192")])
 def test_mlp_bf16_vs_rounded_oracle(df, name, N, bn, monkeypatch):
     """tcgen05 BF16 path against the FP64 network with BF16 rounding at the same points
     (input, weights, hidden activations); differences come only from FP32 accumulation
@@ -331,7 +331,7 @@ def test_dt_mismatch_is_rejected(df):
 # ---------------------------------------------------------------- FP8 e4m3
 
 @pytest.mark.parametrize("name,N,bn", [("small-fp32-4k", 1000, None), ("layer1d-30sp-1m", 3000, None),
-                                        ("layer1d-30sp-1m", 777, "256")])
+                                        ("layer1d-30sp-1m", 777, "256"), ("layer1d-30sp-1m", 777, "192")])
 def test_mlp_fp8_vs_rounded_oracle(df, name, N, bn, monkeypatch):
     """tcgen05 FP8 path against the FP64 network with e4m3 rounding at the same points
     (input and hidden activations x32, per-output-channel weight scales). A hidden
@@ -463,7 +463,7 @@ def test_autotune_keeps_results_and_caches(df, prec, tmp_path):
     paired = [b & ~df.DF_TILE_PAIR for b in after[:-1] if b & df.DF_TILE_PAIR]
     single = [b for b in after[:-1] if not b & df.DF_TILE_PAIR]
     assert all(b in (160, 224, 256) for b in paired) and after[-1] in (32, 64)
-    assert all(b in (64, 128, 160, 224, 256) for b in single)
+    assert all(b in (64, 128, 160, 192, 224, 256) for b in single)
     T2, Y2 = dev(T), dev(Y)
     st.chem_step(T2, dev(p), Y2)
     torch.cuda.synchronize()
@@ -475,6 +475,28 @@ def test_autotune_keeps_results_and_caches(df, prec, tmp_path):
     assert st2.autotune(n_rows=4096, cache_path=cache) == after
     assert cache.read_text().strip().splitlines() == lines
     print(f"{prec}: tiles {before} -> {after}")
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_every_tile_width_gives_the_same_outputs(df, prec, monkeypatch):
+    """Every single-CTA tile width gives the network outputs of the cost model's tiles bit for
+    bit. With widths 1600, 800 and 400 the last n tile of a layer is narrowed to the columns
+    left (rounded up to 16): 64 columns at 192 and 256, 32 at 224, 16 for the 400-wide layer at
+    192, none at 160 and 64; 1100 rows leave a ragged last row tile."""
+    mech, net, T, p, Y = synth.configs.build("layer1d-30sp-1m", n_cells=1100)
+    P = df.DF_FP8_E4M3 if prec == "fp8" else df.DF_BF16
+    x = dev(onw.normalise_inputs(net, T, p, Y).astype(np.float32))
+    st = df.State(mech, net, precision=P, batch_cells=1100)
+    O_ref = host(st.mlp_forward(x))
+    st.close()
+    for bn in ("64", "128", "160", "192", "224", "256"):
+        monkeypatch.setenv("DFGB_BN", bn)
+        st = df.State(mech, net, precision=P, batch_cells=1100)
+        assert all(t & ~df.DF_TILE_PAIR == int(bn) for t in st.tiles()[:-1]), st.tiles()
+        O = host(st.mlp_forward(x))
+        torch.cuda.synchronize()
+        assert np.array_equal(O, O_ref), (bn, np.abs(O - O_ref).max())
+        st.close()
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8", "bf16-table"])
