@@ -915,6 +915,9 @@ __device__ __forceinline__ void x_put(uint32_t (&w)[RW], int e, XT v) {
   w[e / EPW] |= x_bits(v) << (8 * (int)sizeof(XT) * (e % EPW));
 }
 
+// Species whose mass fractions a thread loads before using any (NM is a multiple of it).
+constexpr int kLoadBatch = 16;
+
 // a1-a5 for the valid rows of a batch.
 template <int NM, typename XT>
 __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams P, RowMap rows,
@@ -943,16 +946,26 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) eos_pre_kernel(EosParams
     const double Tc = T[cell], pc = p[cell];
     bool finite = d_finite(Tc) && d_finite(pc) && d_pos(pc) && d_pos(Tc);
     XT* xr = x ? x + r * ldx : nullptr;
-    // the double-float column of Y (and, without packed rows, the a5 features) in one pass
-#pragma unroll 2
-    for (int k = 0; k < n; ++k) {
-      const double yd = Y[k * ldY + cell];
-      finite = finite && d_finite(yd);
-      ycol[k * kThreads] = f2_from(yd);
-      if (xr && !xvec) {
-        const float y = fmaxf(d_to_f_trunc(yd), 0.0f);
-        const float bc = (y > 0.0f) ? (exp2f(lam * log2f(y)) - 1.0f) * ilam : -ilam;
-        xr[2 + k] = to_x<XT>((bc - mf[2 + k]) * isf[2 + k], x_scale);
+    // the double-float column of Y (and, without packed rows, the a5 features), sixteen
+    // species at a time with all their loads issued first: one memory latency per batch
+#pragma unroll
+    for (int k0 = 0; k0 < NM; k0 += kLoadBatch) {
+      double yv[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) yv[u] = k0 + u < n ? Y[(k0 + u) * ldY + cell] : 0.0;
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int k = k0 + u;
+        if (k < n) {
+          const double yd = yv[u];
+          finite = finite && d_finite(yd);
+          ycol[k * kThreads] = f2_from(yd);
+          if (xr && !xvec) {
+            const float y = fmaxf(d_to_f_trunc(yd), 0.0f);
+            const float bc = (y > 0.0f) ? (exp2f(lam * log2f(y)) - 1.0f) * ilam : -ilam;
+            xr[2 + k] = to_x<XT>((bc - mf[2 + k]) * isf[2 + k], x_scale);
+          }
+        }
       }
     }
     if (xr && !xvec) {
@@ -1075,11 +1088,27 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
     bool finite = d_finite(Told) && d_finite(pc) && d_pos(pc) && d_finite(h0c);
     f2 S = {0.f, 0.f};
     const float* Or = O + r * ldo;
-    // the row's outputs four at a time (one 16-byte load when the row pitch allows)
+    // Y's column into this thread's column slots as FP64 bit patterns, sixteen loads in flight
+    // at a time; each slot is overwritten by Y'_k below
+#pragma unroll
+    for (int k0 = 0; k0 < NM; k0 += kLoadBatch) {
+      double yv[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) yv[u] = k0 + u < n ? Y[(k0 + u) * ldY + cell] : 0.0;
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u)
+        if (k0 + u < n)
+          ycol[(k0 + u) * stride] = f2{__int_as_float(__double2loint(yv[u])),
+                                       __int_as_float(__double2hiint(yv[u]))};
+    }
+    // the row's outputs four at a time (one 16-byte load when the row pitch allows, the next
+    // group's load issued before this group's arithmetic)
+    float4 onext = ovec ? *reinterpret_cast<const float4*>(Or) : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int k0 = 0; k0 < n; k0 += 4) {
       float o4[4];
       if (ovec) {
-        const float4 v = *reinterpret_cast<const float4*>(Or + k0);
+        const float4 v = onext;
+        if (k0 + 4 < n) onext = *reinterpret_cast<const float4*>(Or + k0 + 4);
         o4[0] = v.x;
         o4[1] = v.y;
         o4[2] = v.z;
@@ -1092,7 +1121,8 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
       for (int q = 0; q < 4; ++q) {
         const int k = k0 + q;
         if (k >= n) break;
-        const double y = Y[k * ldY + cell];
+        const f2 yraw = ycol[k * stride];
+        const double y = __hiloint2double(__float_as_int(yraw.l), __float_as_int(yraw.h));
         finite = finite && d_finite(y);
         const float ldu = lamf * fmaf(out_std[k], o4[q], out_mean[k]);  // lambda du
         f2 yn = {0.f, 0.f};

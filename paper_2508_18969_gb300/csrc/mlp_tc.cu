@@ -8,12 +8,13 @@
 // becomes a multi-stage TMA ring and two TMEM accumulators, so the epilogue of one tile
 // overlaps the MMAs of the next.
 //
-// Warp roles (64 + 32 * 4 * EPI_PER_QUARTER threads, 448 by default; one CTA per SM):
+// Warp roles (64 + 128 E threads for E epilogue warps per TMEM lane quarter: 576 with E = 4 on
+// single-CTA layers with an activation, 448 with E = 3 otherwise; one CTA per SM):
 //   warp 0      TMA producer (one lane)
 //   warp 1      TMEM allocator and MMA issuer (one lane)
-//   warps 2..   epilogue; warp w reads TMEM lanes 32*(w%4) .. 32*(w%4)+31 and every
-//               EPI_PER_QUARTER-th 32-column chunk; results go through swizzled shared-memory
-//               staging and leave by TMA tensor stores
+//   warps 2..   epilogue; warp w reads TMEM lanes 32*(w%4) .. 32*(w%4)+31 and every E-th
+//               32-column chunk; results go through swizzled shared-memory staging and leave
+//               by TMA tensor stores
 // A layer may instead run on CTA pairs (clusters of two, cta_group::2): 256-row tiles whose
 // MMAs the even CTA issues over both CTAs' operands (see "CTA pairs" below).
 // Every mbarrier wait is bounded by a clock budget; on expiry the CTA sets the error word,
@@ -21,10 +22,6 @@
 // is a launch argument (default ~1 s); the drains on the way out always allow the full ~1 s,
 // so copies and MMAs in flight land before the CTA frees its tensor memory and exits.
 #include "dfgb_internal.cuh"
-
-#ifndef EPI_PER_QUARTER
-#define EPI_PER_QUARTER 3
-#endif
 
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -38,9 +35,7 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int kRowBytes = 128;                 // K bytes per stage row (one swizzle span)
-constexpr int kEpiPerQuarter = EPI_PER_QUARTER;  // epilogue warps per TMEM lane quarter
-constexpr int kEpiWarps = 4 * kEpiPerQuarter;
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+__host__ __device__ constexpr int threads_for(int epq) { return 64 + 128 * epq; }
 constexpr long long kWaitBudget = 2000000000LL;  // ~1 s of SM clocks per wait
 constexpr int kSmemLimit = 232448;             // opt-in dynamic shared memory per block
 constexpr uint32_t kSuspendNs = 200000;        // try_wait may park the thread this long
@@ -73,6 +68,17 @@ constexpr int kModePlain = 0, kModeStoreG = 1, kModeRowG = 2;
 // Epilogue activation: none (read-out, tangent and gradient GEMMs), the tanh form with the
 // hardware tanh, or the paper's table (compiled for BF16 hidden layers only).
 constexpr int kActNone = 0, kActTanh = 1, kActTable = 2;
+
+// Epilogue warps per TMEM lane quarter. Single-CTA layers with an activation (the
+// epilogue-bound layers of one k-block among them) take four, each loading one 32-column chunk
+// from tensor memory at a time; pair tiles, the read-out and the layers that also store GELU'
+// (whose second store per chunk needs the registers that four warps would not leave) take
+// three, each loading the next chunk while it stores the current one. Measured on the
+// 32 -> 1600 layer of 2^20 rows: 0.83 ms with three per quarter (192-wide tiles), 0.61 ms with
+// four (256-wide); on the CTA-pair 1600 -> 800 layer four were 2 % slower.
+__host__ __device__ constexpr int epi_per_quarter(bool pair, int act, int mode = 0) {
+  return !pair && act != kActNone && mode != kModeStoreG ? 4 : 3;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -340,8 +346,11 @@ __device__ __forceinline__ float2 gelu_fast2(float2 x) {
 
 constexpr int out_bytes(int outk) { return outk == kXF32 ? 4 : (outk == kXBF16 ? 2 : 1); }
 
-template <int BN, int OUTK, bool PAIR = false>
+template <int BN, int OUTK, bool PAIR = false, int EPQ = 3>
 struct Cfg {
+  static constexpr int kEpq = EPQ;               // epilogue warps per TMEM lane quarter
+  static constexpr int kEpiWarps = 4 * EPQ;
+  static constexpr int kThreads = threads_for(EPQ);
   // Per warp: staging buffers of 32 rows x 32 columns (the GELU' of kModeStoreG is BF16, no
   // wider than the output). Two let a warp fill one while the other's store still reads it.
   // A pair tile streams several k-blocks per accumulator, so its epilogue has time to spare,
@@ -593,10 +602,11 @@ struct ItemWalk {
 };
 
 template <bool FP8, int BN, int OUTK, int ACT, bool SCALE, int MODE, bool PAIR>
-__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
+__global__ void __launch_bounds__(threads_for(epi_per_quarter(PAIR, ACT, MODE)), 1) tc_gemm_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
     const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmG, TcArgs g) {
-  using C = Cfg<BN, OUTK, PAIR>;
+  using C = Cfg<BN, OUTK, PAIR, epi_per_quarter(PAIR, ACT, MODE)>;
+  constexpr int kEpiWarps = C::kEpiWarps;
   // a 32-column epilogue chunk is stored as one TMA box, so chunks must not straddle tiles
   static_assert(BN % 32 == 0, "tile width must be a multiple of 32");
   // each CTA of a pair holds whole 8-row swizzle atoms of W
@@ -787,7 +797,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
     // ---------------- epilogue ----------------
     const int q = warp & 3;                   // TMEM lane quarter this warp may access
     const int slot = (warp - 2) >> 2;         // which of the quarter's interleaved chunks
-    constexpr int kChunkStride = 32 * kEpiPerQuarter;
+    constexpr int kChunkStride = 32 * C::kEpq;
     uint8_t* stg = sOut + (warp - 2) * C::kStageOut;
     int buf = 0;
     if (lane == 0) {
@@ -805,12 +815,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(
       const int64_t m0 = mt + q * 32 + w.split * g.split_rows;
       const int n0 = w.nt(tiles_n) * BN;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + a * C::kAccStride;
-      // chunks c = 32 slot + kChunkStride i; TMEM loads run one chunk ahead of the math,
-      // except in kModeStoreG, whose two stores per chunk leave no registers for a second
-      // chunk in flight. The odd CTA of a pair whose m tile lies past the rows stores nothing.
+      // chunks c = 32 slot + kChunkStride i; with three warps per quarter TMEM loads run one
+      // chunk ahead of the math, except in kModeStoreG, whose two stores per chunk leave no
+      // registers for a second chunk in flight; with four, the quarter's other warps cover the
+      // load. The odd CTA of a pair whose m tile lies past the rows stores nothing.
       uint32_t r0[32], r1[32];
       int c0 = (PAIR && mt >= M) ? BN : 32 * slot;
-      if constexpr (MODE == kModeStoreG) {
+      if constexpr (MODE == kModeStoreG || C::kEpq == 4) {
         for (; c0 < BN; c0 += kChunkStride) {
           tmem_ld32(tbase + c0, r0);
           tmem_wait(r0);
@@ -891,7 +902,7 @@ cudaError_t tc_attr(int* max_clusters) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_done[dev]) {
-    using C = Cfg<BN, OUTK, PAIR>;
+    using C = Cfg<BN, OUTK, PAIR, epi_per_quarter(PAIR, ACT, MODE)>;
     auto kern = tc_gemm_kernel<FP8, BN, OUTK, ACT, FP8, MODE, PAIR>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
@@ -905,7 +916,7 @@ cudaError_t tc_attr(int* max_clusters) {
       at[0].val.clusterDim.z = 1;
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(2, 1, 1);
-      cfg.blockDim = dim3(kThreads, 1, 1);
+      cfg.blockDim = dim3(C::kThreads, 1, 1);
       cfg.dynamicSmemBytes = C::kSmemBytes;
       cfg.attrs = at;
       cfg.numAttrs = 1;
@@ -923,7 +934,7 @@ cudaError_t tc_attr(int* max_clusters) {
 
 template <bool FP8, int BN, int OUTK, int ACT, int MODE = kModePlain, bool PAIR = false>
 cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream_t st) {
-  using C = Cfg<BN, OUTK, PAIR>;
+  using C = Cfg<BN, OUTK, PAIR, epi_per_quarter(PAIR, ACT, MODE)>;
   constexpr bool SCALE = FP8;
   auto kern = tc_gemm_kernel<FP8, BN, OUTK, ACT, SCALE, MODE, PAIR>;
   int max_clusters = 0;
@@ -947,7 +958,7 @@ cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream
     at[0].val.clusterDim.z = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * nc), 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.blockDim = dim3(C::kThreads, 1, 1);
     cfg.dynamicSmemBytes = C::kSmemBytes;
     cfg.stream = st;
     cfg.attrs = at;
@@ -956,7 +967,7 @@ cudaError_t launch_bn(const TcLayer& L, const TcArgs& a, int num_sms, cudaStream
   } else {
     const int64_t tiles = items;
     const unsigned grid = (unsigned)(tiles < num_sms ? (tiles > 0 ? tiles : 1) : num_sms);
-    kern<<<grid, kThreads, C::kSmemBytes, st>>>(L.tmA, L.tmB, L.tmO, tmG, a);
+    kern<<<grid, C::kThreads, C::kSmemBytes, st>>>(L.tmA, L.tmB, L.tmO, tmG, a);
     return cudaGetLastError();
   }
 }
@@ -1466,8 +1477,10 @@ int tc_stages(int BN, int out_kind, bool pair) {
     if (pair)
       return out_kind == kXF32 ? Cfg<B, kXF32, true>::kStages
              : out_kind == kXBF16 ? Cfg<B, kXBF16, true>::kStages : Cfg<B, kXFP8, true>::kStages;
+    // single CTAs: FP32 out is the read-out (no activation), the others hidden layers
     return out_kind == kXF32 ? Cfg<B, kXF32>::kStages
-           : out_kind == kXBF16 ? Cfg<B, kXBF16>::kStages : Cfg<B, kXFP8>::kStages;
+           : out_kind == kXBF16 ? Cfg<B, kXBF16, false, epi_per_quarter(false, kActTanh)>::kStages
+                                : Cfg<B, kXFP8, false, epi_per_quarter(false, kActTanh)>::kStages;
   };
   switch (BN) {
     case 32: return pick(std::integral_constant<int, 32>{});
@@ -1481,7 +1494,7 @@ int tc_stages(int BN, int out_kind, bool pair) {
   }
 }
 
-int tc_epi_warps_per_quarter() { return kEpiPerQuarter; }
+int tc_epi_warps_per_quarter() { return epi_per_quarter(false, kActTanh); }
 
 cudaError_t prepare_tc(const TcLayer& L) {
   TcArgs a{};
