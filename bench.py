@@ -195,9 +195,9 @@ MEASURED_TRAFFIC = {
     ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "0ae124804481960c", 4752.6),
     ("layer2", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "0ae124804481960c", 2342.7),
     ("layer3", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "0ae124804481960c", 1061.7),
-    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "0c299570daf9c556", 292.9,
+    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "fa5f9366994d47f9", 291.4,
                                         _EOS_OTHER),
-    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "0c299570daf9c556", 548.2,
+    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "fa5f9366994d47f9", 578.2,
                                          _EOS_OTHER),
     # one block Gauss-Seidel sweep (gs_rhs_kernel + gs_sweep_kernel), per cell, FP64, 512 cells
     # per block row (profiles/solver_kernels_mesh-2m.md)
@@ -411,14 +411,14 @@ def measure_peaks_live(torch, dev):
 # MEASURED_TRAFFIC).
 MEASURED_PIPES = {
     # profiles/eos_kernels_layer1d-30sp-512k_bf16.md (full capture, 512K rows, first step)
-    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "0c299570daf9c556",
+    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "fa5f9366994d47f9",
                                         {"binding": "issue (FP32 double-float arithmetic)",
-                                         "fma_pipe": 0.481, "alu_pipe": 0.262, "fp64_pipe": 0.009,
-                                         "issue_active": 0.706, "warps_per_sm": 18.0}, _EOS_OTHER),
-    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "0c299570daf9c556",
+                                         "fma_pipe": 0.486, "alu_pipe": 0.237, "fp64_pipe": 0.011,
+                                         "issue_active": 0.758, "warps_per_sm": 21.0}, _EOS_OTHER),
+    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "fa5f9366994d47f9",
                                          {"binding": "issue (FP32 double-float arithmetic)",
-                                          "fma_pipe": 0.314, "alu_pipe": 0.483, "fp64_pipe": 0.014,
-                                          "issue_active": 0.694, "warps_per_sm": 18.7}, _EOS_OTHER),
+                                          "fma_pipe": 0.327, "alu_pipe": 0.516, "fp64_pipe": 0.036,
+                                          "issue_active": 0.729, "warps_per_sm": 22.2}, _EOS_OTHER),
 }
 
 

@@ -31,10 +31,16 @@ namespace {
 
 constexpr double kSQ2 = 1.41421356237309504880;
 constexpr double kInvR = 1.0 / kR;
-constexpr int kThreads = 128;
+// The step's EoS kernels run blocks of 256 threads, three per SM (80 registers): the constant
+// tables in shared memory are then shared by more threads than with five blocks of 128, and the
+// SM holds 24 warps instead of 20 (eos_pre 0.71 -> 0.66 ms, eos_post 0.69 -> 0.66 ms on the
+// 2^20-cell step).
+constexpr int kThreads = 256;
 constexpr int kJacThreads = 64;  // the Jacobian's EoS kernel
-constexpr int kPreBlocks = 5;    // resident blocks per SM the register budget is sized for
-constexpr int kPostBlocks = 5;
+constexpr int kPreBlocks = 3;    // resident blocks per SM the register budget is sized for
+constexpr int kPostBlocks = 3;
+constexpr int kPropThreads = 128;  // the property and transport kernels
+constexpr int kPropBlocks = 5;
 constexpr int kCellNotConverged = 1;
 constexpr int kCellNoRoot = 2;
 constexpr int kCellNonfinite = 4;
@@ -1185,7 +1191,7 @@ __global__ void __launch_bounds__(kThreads, kPostBlocks) eos_post_kernel(EosPara
 }
 
 template <int NM>
-__global__ void __launch_bounds__(kThreads, kPreBlocks) props_kernel(EosParams P, int64_t ncell,
+__global__ void __launch_bounds__(kPropThreads, kPropBlocks) props_kernel(EosParams P, int64_t ncell,
     const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
     int64_t ldY, double* rho, double* h, double* cp, double* Zo) {
   extern __shared__ __align__(16) double sm[];
@@ -1195,9 +1201,9 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) props_kernel(EosParams P
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncell;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double Tc = T[i], pc = p[i];
-    for (int k = 0; k < n; ++k) ycol[k * kThreads] = f2_from(Y[k * ldY + i]);
+    for (int k = 0; k < n; ++k) ycol[k * kPropThreads] = f2_from(Y[k * ldY + i]);
     Mixture m;
-    mixture<kThreads>(ycol, n, c, m);
+    mixture<kPropThreads>(ycol, n, c, m);
     int st = 0;
     const PRPoint q = pr_point<false>(m, Tc, pc, cp != nullptr, c.lnt, st);
     if (rho) rho[i] = pc / (m.inv * q.Z * kR * Tc);
@@ -1270,14 +1276,14 @@ __device__ void chung(float T, float rho, float Tc, float Vc, float om, float M,
 }
 
 template <int NM>
-__global__ void __launch_bounds__(kThreads, kPreBlocks) transport_kernel(EosParams P, int64_t ncell,
+__global__ void __launch_bounds__(kPropThreads, kPropBlocks) transport_kernel(EosParams P, int64_t ncell,
     const double* __restrict__ T, const double* __restrict__ p, const double* __restrict__ Y,
     int64_t ldY, double* mu, double* lam, double* alpha) {
   extern __shared__ __align__(16) double sm[];
   const SharedConsts c = load_consts(P, sm);
   f2* ycol = reinterpret_cast<f2*>(sm + consts_words(P)) + threadIdx.x;
   const int n = P.n, nn = P.n * P.n;
-  constexpr int stride = kThreads;
+  constexpr int stride = kPropThreads;
   const float* __restrict__ tp = P.tpair;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncell;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1291,7 +1297,7 @@ __global__ void __launch_bounds__(kThreads, kPreBlocks) transport_kernel(EosPara
     double m_out = __longlong_as_double(0x7ff8000000000000LL), l_out = m_out, a_out = m_out;
     if (finite) {
       Mixture m;
-      mixture<kThreads>(ycol, n, c, m);
+      mixture<kPropThreads>(ycol, n, c, m);
       int st = 0;
       const PRPoint q = pr_point<false>(m, Tk, pk, true, c.lnt, st);
       const double rho = pk / (m.inv * q.Z * kR * Tk);            // kg/m^3
@@ -1657,10 +1663,10 @@ __global__ void __launch_bounds__(256) jac_assemble_kernel(EosParams P, int64_t 
   }
 }
 
-// Dynamic shared memory of an EoS block: constants and the per-thread double-float column
-// of mass fractions (n words per thread).
-size_t eos_smem(const EosParams& P) {
-  return sizeof(double) * ((size_t)consts_words(P) + (size_t)P.n * kThreads);
+// Dynamic shared memory of an EoS block of `threads` threads: constants and the per-thread
+// double-float column of mass fractions (n words per thread).
+size_t eos_smem(const EosParams& P, int threads = kThreads) {
+  return sizeof(double) * ((size_t)consts_words(P) + (size_t)P.n * threads);
 }
 
 size_t eos_smem_post(const EosParams& P) {
@@ -1710,11 +1716,11 @@ int grid_resident(int64_t nmax, size_t smem) {
   return (int)(need < cap ? need : cap);
 }
 
-int grid_for(int64_t nmax) {
+int grid_for(int64_t nmax, int threads = kThreads) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t need = (nmax + kThreads - 1) / kThreads;
+  int64_t need = (nmax + threads - 1) / threads;
   int64_t cap = (int64_t)sms * 8;
   if (need < 1) need = 1;
   return (int)(need < cap ? need : cap);
@@ -1765,8 +1771,8 @@ cudaError_t transport_nm(const EosParams& P, int64_t n, const double* T, const d
                          cudaStream_t st) {
   cudaError_t e = smem_optin<transport_kernel<NM>>();
   if (e != cudaSuccess) return e;
-  transport_kernel<NM><<<grid_for(n), kThreads, eos_smem(P), st>>>(P, n, T, p, Y, ldY, mu, lam,
-                                                                   alpha);
+  transport_kernel<NM><<<grid_for(n, kPropThreads), kPropThreads, eos_smem(P, kPropThreads), st>>>(
+      P, n, T, p, Y, ldY, mu, lam, alpha);
   return cudaGetLastError();
 }
 
@@ -1776,8 +1782,8 @@ cudaError_t props_nm(const EosParams& P, int64_t n, const double* T, const doubl
                      cudaStream_t st) {
   cudaError_t e = smem_optin<props_kernel<NM>>();
   if (e != cudaSuccess) return e;
-  props_kernel<NM><<<grid_for(n), kThreads, eos_smem(P), st>>>(P, n, T, p, Y, ldY,
-                                                                           rho, h, cp, Z);
+  props_kernel<NM><<<grid_for(n, kPropThreads), kPropThreads, eos_smem(P, kPropThreads), st>>>(
+      P, n, T, p, Y, ldY, rho, h, cp, Z);
   return cudaGetLastError();
 }
 
