@@ -2,8 +2,8 @@
 // Three launches, no inter-block waiting: per-chunk counts (warp ballot + popc), one-block
 // exclusive scan of the chunk counts, then a scatter that ranks each reacting cell inside
 // its chunk with ballot/popc prefix sums. Both chunk passes load all of a thread's cells
-// before testing any, so a chunk costs one memory latency. Cells are visited in the same order by the
-// count and the scatter pass, so the list is in ascending cell order.
+// before testing any, so a chunk costs one memory latency. Cells are visited in the same
+// order by the count and the scatter pass, so the list is in ascending cell order.
 #include "dfgb_internal.cuh"
 
 namespace dfgb {
