@@ -191,10 +191,10 @@ _EOS_OTHER = (("// -------------------------------------------------------------
               ("cudaError_t launch_jac_scale(", "cudaError_t launch_eos_post("),
               ("cudaError_t launch_transport(", "}  // namespace dfgb"))
 MEASURED_TRAFFIC = {
-    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "0ae124804481960c", 3157.1),
-    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "0ae124804481960c", 4752.6),
-    ("layer2", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "0ae124804481960c", 2342.7),
-    ("layer3", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "0ae124804481960c", 1061.7),
+    ("layer0", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "c22bd239ff26b709", 3157.2),
+    ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "c22bd239ff26b709", 4751.2),
+    ("layer2", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "c22bd239ff26b709", 2340.1),
+    ("layer3", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "c22bd239ff26b709", 1062.8),
     ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "fa5f9366994d47f9", 291.4,
                                         _EOS_OTHER),
     ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "fa5f9366994d47f9", 578.2,

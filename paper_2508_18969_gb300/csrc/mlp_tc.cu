@@ -8,7 +8,7 @@
 // becomes a multi-stage TMA ring and two TMEM accumulators, so the epilogue of one tile
 // overlaps the MMAs of the next.
 //
-// Warp roles (64 + 128 E threads for E epilogue warps per TMEM lane quarter: 576 with E = 4 on
+// Warp roles (64 + 128 E threads for E epilogue warps per TMEM lane quarter: 704 with E = 5 on
 // single-CTA layers with an activation, 448 with E = 3 otherwise; one CTA per SM):
 //   warp 0      TMA producer (one lane)
 //   warp 1      TMEM allocator and MMA issuer (one lane)
@@ -70,14 +70,15 @@ constexpr int kModePlain = 0, kModeStoreG = 1, kModeRowG = 2;
 constexpr int kActNone = 0, kActTanh = 1, kActTable = 2;
 
 // Epilogue warps per TMEM lane quarter. Single-CTA layers with an activation (the
-// epilogue-bound layers of one k-block among them) take four, each loading one 32-column chunk
+// epilogue-bound layers of one k-block among them) take five, each loading one 32-column chunk
 // from tensor memory at a time; pair tiles, the read-out and the layers that also store GELU'
-// (whose second store per chunk needs the registers that four warps would not leave) take
-// three, each loading the next chunk while it stores the current one. Measured on the
-// 32 -> 1600 layer of 2^20 rows: 0.83 ms with three per quarter (192-wide tiles), 0.61 ms with
-// four (256-wide); on the CTA-pair 1600 -> 800 layer four were 2 % slower.
+// (whose second store per chunk needs the registers that more warps would not leave) take
+// three, each loading the next chunk while it stores the current one. Measured on 2^20 rows of
+// the 32 -> 1600 layer: 0.83 ms with three per quarter (192-wide tiles), 0.61 ms with four
+// (256-wide), 0.60 ms with five (160-wide, one chunk per warp); on the CTA-pair 1600 -> 800
+// layer four were 2 % slower than three.
 __host__ __device__ constexpr int epi_per_quarter(bool pair, int act, int mode = 0) {
-  return !pair && act != kActNone && mode != kModeStoreG ? 4 : 3;
+  return !pair && act != kActNone && mode != kModeStoreG ? 5 : 3;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -817,11 +818,11 @@ __global__ void __launch_bounds__(threads_for(epi_per_quarter(PAIR, ACT, MODE)),
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + a * C::kAccStride;
       // chunks c = 32 slot + kChunkStride i; with three warps per quarter TMEM loads run one
       // chunk ahead of the math, except in kModeStoreG, whose two stores per chunk leave no
-      // registers for a second chunk in flight; with four, the quarter's other warps cover the
+      // registers for a second chunk in flight; with five, the quarter's other warps cover the
       // load. The odd CTA of a pair whose m tile lies past the rows stores nothing.
       uint32_t r0[32], r1[32];
       int c0 = (PAIR && mt >= M) ? BN : 32 * slot;
-      if constexpr (MODE == kModeStoreG || C::kEpq == 4) {
+      if constexpr (MODE == kModeStoreG || C::kEpq >= 4) {
         for (; c0 < BN; c0 += kChunkStride) {
           tmem_ld32(tbase + c0, r0);
           tmem_wait(r0);
