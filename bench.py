@@ -195,9 +195,9 @@ MEASURED_TRAFFIC = {
     ("layer1", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "c22bd239ff26b709", 4751.2),
     ("layer2", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "c22bd239ff26b709", 2340.1),
     ("layer3", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/mlp_tc.cu", "c22bd239ff26b709", 1062.8),
-    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "db0a60314ba3e670", 292.8,
+    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "c12e4383ce9da4a2", 292.1,
                                         _EOS_OTHER),
-    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "db0a60314ba3e670", 578.2,
+    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "c12e4383ce9da4a2", 578.5,
                                          _EOS_OTHER),
     # one block Gauss-Seidel sweep (gs_rhs_kernel + gs_sweep_kernel), per cell, FP64, 512 cells
     # per block row (profiles/solver_kernels_mesh-2m.md)
@@ -411,14 +411,14 @@ def measure_peaks_live(torch, dev):
 # MEASURED_TRAFFIC).
 MEASURED_PIPES = {
     # profiles/eos_kernels_layer1d-30sp-512k_bf16.md (full capture, 512K rows, first step)
-    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "db0a60314ba3e670",
+    ("eos_pre", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "c12e4383ce9da4a2",
                                         {"binding": "issue (FP32 double-float arithmetic)",
                                          "fma_pipe": 0.484, "alu_pipe": 0.197, "fp64_pipe": 0.012,
                                          "issue_active": 0.740, "warps_per_sm": 20.9}, _EOS_OTHER),
-    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "db0a60314ba3e670",
+    ("eos_post", "32-1600-800-400-30"): ("paper_2508_18969_gb300/csrc/eos.cu", "c12e4383ce9da4a2",
                                          {"binding": "issue (FP32 double-float arithmetic)",
-                                          "fma_pipe": 0.327, "alu_pipe": 0.516, "fp64_pipe": 0.036,
-                                          "issue_active": 0.729, "warps_per_sm": 22.2}, _EOS_OTHER),
+                                          "fma_pipe": 0.323, "alu_pipe": 0.527, "fp64_pipe": 0.037,
+                                          "issue_active": 0.722, "warps_per_sm": 22.3}, _EOS_OTHER),
 }
 
 

@@ -71,6 +71,9 @@ struct EosParams {
   // FP32 pair corrections of the T-from-h solve, (k_ij s_j / W_j, k_ij r_j / W_j) for the
   // pairs j > i, row by row (row i from pair i n - i (i + 1) / 2)
   const float* kf2;      // [n (n - 1)] (+ 2 floats of padding)
+  // max_k |column j of the species table over W| (the hi parts of spcw2, rounded up): with the
+  // sum of |Y| they bound the T-from-h solve's species sums
+  float spcmax[kSpcStride];
   // natural-log table: ln(c_j) for j < 128, then 1 / c_j, c_j = 1 + (j + 1/2) / 128
   const double* lntab;   // [256]
   const float* lntab2;   // [512] the same table as double-float (hi, lo) pairs

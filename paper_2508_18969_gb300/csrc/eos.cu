@@ -78,6 +78,7 @@ struct SharedConsts {
   const f2* lt2;       // the same table in double-float, in the same words; DF kernels only
   const double* norm;  // [2 K0 + 2 n]
   const float* normf;  // the same in FP32 (for the FP32 feature and increment arithmetic)
+  const float* smax;   // [kSpcStride] EosParams::spcmax (T-from-h kernel only)
 };
 
 // 8-byte words of shared memory the constants take: FP64 normalisation, then the
@@ -119,7 +120,7 @@ __device__ SharedConsts load_consts(const EosParams& P, double* sm0) {
 // species table, the FP32 k_ij pair table, FP32 normalisation (no double-float pair tables).
 __host__ __device__ inline int consts_words_post(const EosParams& P) {
   return 256 + 2 * P.K0 + 2 * P.n + P.n * kSpcStride + P.n * (P.n - 1) / 2 + 1 +
-         (P.K0 + P.n + 1);
+         (P.K0 + P.n + 1) + kSpcStride / 2;
 }
 
 __device__ SharedConsts load_consts_post(const EosParams& P, double* sm0) {
@@ -135,10 +136,12 @@ __device__ SharedConsts load_consts_post(const EosParams& P, double* sm0) {
   for (int i = threadIdx.x; i < nkf; i += blockDim.x) ks[i] = P.kf2[i];
   float* nf = ks + nkf;
   for (int i = threadIdx.x; i < nn; i += blockDim.x) nf[i] = (float)P.norm[i];
+  float* mx = nf + nn + 2;   // the FP32 normalisation takes K0 + n + 1 words
+  for (int i = threadIdx.x; i < kSpcStride; i += blockDim.x) mx[i] = P.spcmax[i];
   __syncthreads();
   return SharedConsts{reinterpret_cast<const f2*>(fs), nullptr, nullptr,
                       reinterpret_cast<const float2*>(ks), nullptr,
-                      reinterpret_cast<const f2*>(sm0), sm, nf};
+                      reinterpret_cast<const f2*>(sm0), sm, nf, mx};
 }
 
 // FP64 reciprocal: FP32 seed, two FP64 Newton steps (relative error ~1 ulp).
@@ -380,23 +383,20 @@ __device__ __forceinline__ void species_row_post(const SharedConsts& c, int i, f
 template <int STRIDE>
 __device__ void mixture_post(const f2* ycol, int n, const SharedConsts& c, MixDF& m) {
   constexpr int stride = STRIDE;
-  // the ten O(n) sums over the species table take offset accumulators, as in mixture()
-  float Bq[kSpcStride];
-#pragma unroll
-  for (int k = 0; k < kSpcStride; ++k) Bq[k] = 0.f;
+  // the ten O(n) sums over the species table take offset accumulators, as in mixture(), here
+  // with the looser bounds (sum_j |Y_j|) max_j |q_j|: h(T) is needed to ~1e-8 only, and the
+  // bounds then cost one addition per species instead of ten
+  float S = 0.f;
   unsigned neg = 0u;
 #pragma unroll 2
   for (int j = 0; j < n; ++j) {
-    const float yh = ycol[j * stride].h, y = fabsf(yh);
+    const float yh = ycol[j * stride].h;
     neg |= __float_as_uint(yh);
-    const float4* q4 = reinterpret_cast<const float4*>(c.spcw + j * kSpcStride);
-#pragma unroll
-    for (int k = 0; k < kSpcStride / 2; ++k) {
-      const float4 a = q4[k];
-      Bq[2 * k] = __fmaf_ru(y, fabsf(a.x), Bq[2 * k]);
-      Bq[2 * k + 1] = __fmaf_ru(y, fabsf(a.z), Bq[2 * k + 1]);
-    }
+    S = __fadd_ru(S, fabsf(yh));
   }
+  float Bq[kSpcStride];
+#pragma unroll
+  for (int k = 0; k < kSpcStride; ++k) Bq[k] = __fmul_ru(S, c.smax[k]);
   // columns 0..3 (1/W, s/W, r/W, b/W) are non-negative; the enthalpy columns have either sign
   const float sgf = (neg >> 31) ? 4.0f : 1.0f;
   float sq[kSpcStride], hq[kSpcStride], lq[kSpcStride];

@@ -521,6 +521,12 @@ static df_status create_state(const df_mech_desc* mech, const df_mlp_desc* mlp,
   P.K4 = s->d_K4;
   P.kcol = s->d_kcol;
   P.kf2 = s->d_kf2;
+  for (int j = 0; j < kSpcStride; ++j) {
+    float mx = 0.0f;
+    for (int k = 0; k < n; ++k)
+      mx = std::max(mx, std::fabs(spcw2[2 * ((size_t)k * kSpcStride + j)]));
+    P.spcmax[j] = std::nextafter(mx, INFINITY);
+  }
   P.lntab = s->d_lntab;
   P.lntab2 = s->d_lntab2;
   P.tsp = s->d_tsp;
