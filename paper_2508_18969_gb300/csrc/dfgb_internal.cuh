@@ -92,6 +92,7 @@ enum XKind { kXF32 = 0, kXBF16 = 1, kXFP8 = 2 };
 // ---- launchers (eos.cu) ----
 // status (row-indexed, may be NULL) receives the per-row flags.
 // rho (row-indexed, may be NULL) receives the real-fluid density.
+int64_t eos_wave_cells(const EosParams& P, int xkind);
 cudaError_t launch_eos_pre(const EosParams& P, const RowMap& rows, const double* T,
                            const double* p, const double* Y, int64_t ldY, double* h0,
                            double* Z, void* x, int xkind, int64_t ldx, float x_scale,

@@ -1907,4 +1907,25 @@ cudaError_t launch_transport(const EosParams& P, int64_t n, const double* T, con
   return transport_nm<32>(P, n, T, p, Y, ldY, mu, lam, alpha, st);
 }
 
+// Cells the step's eos_pre launch covers in one pass of its resident blocks (SMs x blocks per
+// SM x threads); 0 if the occupancy query fails.
+int64_t eos_wave_cells(const EosParams& P, int xkind) {
+  const size_t smem = eos_smem(P);
+  auto wave = [&](auto kern) -> int64_t {
+    int nb = 0, dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return (int64_t)sms * nb * kThreads;
+  };
+  if (P.n <= 16)
+    return xkind == kXBF16 ? wave(eos_pre_kernel<16, __nv_bfloat16>)
+           : xkind == kXFP8 ? wave(eos_pre_kernel<16, __nv_fp8_e4m3>) : wave(eos_pre_kernel<16, float>);
+  return xkind == kXBF16 ? wave(eos_pre_kernel<32, __nv_bfloat16>)
+         : xkind == kXFP8 ? wave(eos_pre_kernel<32, __nv_fp8_e4m3>) : wave(eos_pre_kernel<32, float>);
+}
+
 }  // namespace dfgb

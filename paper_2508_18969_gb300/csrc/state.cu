@@ -864,7 +864,7 @@ df_status df_chem_step_host(df_state* s, int64_t n_cells, double dt, double* T, 
   }
   // Chunk plan. As asked: equal chunks of chunk_cells. Automatic: a short first and last chunk
   // (1/32 of the cells, at least 32768), so that only a small upload and a small download are
-  // not hidden behind a step; then ramp chunks of 3/16 of the cells, whose steps are long
+  // not hidden behind a step; then ramp chunks of about 3/16 of the cells, whose steps are long
   // enough to hide the upload of the chunk after them (and, at the end, the download of the
   // chunk before them), the copies running at about a quarter of the step's cells/s; and the
   // cells between them in as few chunks as the batch allows, at the long-batch rate.
@@ -879,13 +879,26 @@ df_status df_chem_step_host(df_state* s, int64_t n_cells, double dt, double* T, 
       const int64_t c = std::min(s->cap, std::max<int64_t>(32768, round_up((n_cells + 3) / 4, 128)));
       for (int64_t c0 = 0; c0 < n_cells; c0 += c) plan.push_back(std::min(c, n_cells - c0));
     } else {
-      const int64_t mid = n_cells - 2 * edge - 2 * ramp;
+      int64_t mid = n_cells - 2 * edge - 2 * ramp;
       const int64_t k = (mid + s->cap - 1) / s->cap;
+      int64_t ramp1 = ramp, ramp2 = ramp;
+      // A single middle chunk is cut to whole passes of the EoS kernels' resident blocks, the
+      // rest going to the ramps: otherwise its last, partial pass runs a few blocks alone,
+      // latency-bound, in each EoS kernel.
+      const int64_t wave = k == 1 ? eos_wave_cells(s->P, xkind_of(s->precision)) : 0;
+      if (wave > 0 && mid > wave) {
+        const int64_t extra = mid - mid / wave * wave;
+        if (ramp + extra <= s->cap) {
+          ramp1 += extra / 2;
+          ramp2 += extra - extra / 2;
+          mid -= extra;
+        }
+      }
       const int64_t m = round_up((mid + k - 1) / k, 128);
       plan.push_back(edge);
-      plan.push_back(ramp);
+      plan.push_back(ramp1);
       for (int64_t c0 = 0; c0 < mid; c0 += m) plan.push_back(std::min(m, mid - c0));
-      plan.push_back(ramp);
+      plan.push_back(ramp2);
       plan.push_back(edge);
     }
   }
